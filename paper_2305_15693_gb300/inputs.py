@@ -1,0 +1,238 @@
+"""Seeded synthetic inputs: point sets, wavevector masks, targets S0 and weights w.
+
+This module is shared by the GPU tests, the bench and the oracle checks. It holds none
+of the method's arithmetic (no Fourier sums, no loss, no gradient): only the problem
+definitions the paper's workloads are made of.
+
+* Points: i.i.d. uniform in the periodic box (the Poisson starts of the SI benchmark,
+  "Benchmark of FReSCo"), or perfect square / cubic lattices (the Bragg-peak examples
+  of SI "Saturating peaks" and the square lattice of SI "Born approximation").
+* Masks: the integer wavevectors n != 0 with |n| <= K (k = 2 pi n / L), the constrained
+  region of Eq. 2. K follows from the constraint ratio chi = N_K / (2 d N) of Methods
+  "Algorithm parameters", with N_K counted over the full ball (both n and -n).
+* Targets: stealthy (S0 = 0), power law S0 = (|n|/K)^2, and a peaked ring of Gaussian
+  peaks of height N/10 (the "10-petaled flower" target of Fig. 1).
+
+Random numbers come from numpy's Philox counter-based generator, which gives the same
+stream on every platform.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    """Philox-backed generator for a seed (platform independent)."""
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def uniform_points(n_points: int, dim: int, seed: int, dtype=np.float64,
+                   box: float = 1.0) -> np.ndarray:
+    """[n_points, dim] i.i.d. uniform positions in [0, box)^dim, row-major.
+
+    Drawn directly in `dtype`, so FP32 inputs are uniform FP32 values in [0, 1) times box.
+    """
+    g = rng(seed)
+    if np.dtype(dtype) == np.float32:
+        x = g.random((n_points, dim), dtype=np.float32)
+        if box != 1.0:
+            x *= np.float32(box)
+        return x
+    x = g.random((n_points, dim), dtype=np.float64)
+    if box != 1.0:
+        x *= box
+    return x.astype(dtype, copy=False)
+
+
+def lattice_points(m: int, dim: int, box: float = 1.0, dtype=np.float64,
+                   offset: float = 0.0) -> np.ndarray:
+    """The m^dim points of a simple square (2D) / cubic (3D) lattice of spacing box/m.
+
+    Point (i_0, ..., i_{d-1}) sits at ((i + offset) * box / m) in each coordinate.
+    """
+    axes = [np.arange(m, dtype=np.float64)] * dim
+    grid = np.meshgrid(*axes, indexing="ij")
+    pts = np.stack([g.reshape(-1) for g in grid], axis=1)
+    return ((pts + offset) * (box / m)).astype(dtype)
+
+
+def ball_count(K: int, dim: int) -> int:
+    """Number of integer vectors n != 0 with |n|^2 <= K^2 (the full ball, origin excluded)."""
+    K = int(K)
+    K2 = K * K
+    total = 0
+    if dim == 2:
+        for nx in range(-K, K + 1):
+            total += 2 * math.isqrt(K2 - nx * nx) + 1
+    elif dim == 3:
+        for nx in range(-K, K + 1):
+            rx = K2 - nx * nx
+            my = math.isqrt(rx)
+            for ny in range(-my, my + 1):
+                total += 2 * math.isqrt(rx - ny * ny) + 1
+    else:
+        raise ValueError("dim must be 2 or 3")
+    return total - 1
+
+
+def radius_for_chi(n_points: int, dim: int, chi: float) -> int:
+    """Integer K whose full-ball count N_K is closest to 2 d N chi.
+
+    The ratio chi = N_K / (2 d N) is the one of Methods "Algorithm parameters"; N_K counts
+    both members of each +-n pair. With this reading the paper's own sizes come out:
+    K = 5050 at N = 5e7 (2D, chi ~ 0.4), K = 142 at N = 5e6 (3D) and K ~ 71 at N = 1e4.
+    """
+    target = 2.0 * dim * n_points * chi
+    if dim == 2:
+        k0 = math.sqrt(target / math.pi)
+    else:
+        k0 = (3.0 * target / (4.0 * math.pi)) ** (1.0 / 3.0)
+    best_k, best_err = None, None
+    for K in range(max(1, int(k0) - 3), int(k0) + 5):
+        err = abs(ball_count(K, dim) - target)
+        if best_err is None or err < best_err:
+            best_k, best_err = K, err
+    return best_k
+
+
+def ball_mask(K: int, dim: int) -> np.ndarray:
+    """int32 [N_K, dim]: every n != 0 with |n| <= K, in lexicographic order of (n_0, n_1, ...).
+
+    Column a is the component along coordinate a of the points (column 0 pairs with x).
+    """
+    K = int(K)
+    K2 = K * K
+    chunks = []
+    if dim == 2:
+        for n0 in range(-K, K + 1):
+            m = math.isqrt(K2 - n0 * n0)
+            n1 = np.arange(-m, m + 1, dtype=np.int32)
+            c = np.empty((n1.size, 2), dtype=np.int32)
+            c[:, 0] = n0
+            c[:, 1] = n1
+            chunks.append(c)
+    elif dim == 3:
+        for n0 in range(-K, K + 1):
+            r0 = K2 - n0 * n0
+            m1 = math.isqrt(r0)
+            for n1 in range(-m1, m1 + 1):
+                m2 = math.isqrt(r0 - n1 * n1)
+                n2 = np.arange(-m2, m2 + 1, dtype=np.int32)
+                c = np.empty((n2.size, 3), dtype=np.int32)
+                c[:, 0] = n0
+                c[:, 1] = n1
+                c[:, 2] = n2
+                chunks.append(c)
+    else:
+        raise ValueError("dim must be 2 or 3")
+    mask = np.concatenate(chunks, axis=0)
+    keep = np.any(mask != 0, axis=1)
+    return np.ascontiguousarray(mask[keep])
+
+
+def half_space(mask: np.ndarray) -> np.ndarray:
+    """Boolean selector of the entries whose first nonzero component, scanning from column 0,
+    is positive: exactly one of each +-n pair. Used by tests to build one-sided masks."""
+    sel = np.zeros(mask.shape[0], dtype=bool)
+    undecided = np.ones(mask.shape[0], dtype=bool)
+    for a in range(mask.shape[1]):
+        c = mask[:, a]
+        sel |= undecided & (c > 0)
+        undecided &= c == 0
+    return sel
+
+
+def stealthy_target(mask: np.ndarray) -> np.ndarray:
+    """S0 = 0 on the whole mask (stealthy hyperuniform target)."""
+    return np.zeros(mask.shape[0], dtype=np.float64)
+
+
+def power_law_target(mask: np.ndarray, K: float, exponent: float = 2.0) -> np.ndarray:
+    """S0(n) = (|n| / K)^exponent (power-law hyperuniform target)."""
+    nn = np.sqrt(np.sum(mask.astype(np.float64) ** 2, axis=1))
+    return (nn / float(K)) ** exponent
+
+
+def peaked_target(mask: np.ndarray, n_points: int, K: float, n_peaks: int = 10,
+                  width: float = 1.0) -> np.ndarray:
+    """Ring of n_peaks Gaussian peaks of height N/10 and width `width` (grid units) at |n| = K/2.
+
+    Peak p sits at (K/2)(cos 2 pi p / n_peaks, sin 2 pi p / n_peaks) in the (n_0, n_1)
+    plane; with an even n_peaks the set is centrosymmetric, so S0(n) = S0(-n).
+    """
+    m = mask.astype(np.float64)
+    out = np.zeros(mask.shape[0], dtype=np.float64)
+    h = n_points / 10.0
+    for p in range(n_peaks):
+        a = 2.0 * math.pi * p / n_peaks
+        c = np.zeros(mask.shape[1])
+        c[0] = 0.5 * K * math.cos(a)
+        c[1] = 0.5 * K * math.sin(a)
+        d2 = np.sum((m - c) ** 2, axis=1)
+        out += h * np.exp(-d2 / (2.0 * width * width))
+    return out
+
+
+def unit_weights(mask: np.ndarray) -> np.ndarray:
+    """w = 1 on the whole mask."""
+    return np.ones(mask.shape[0], dtype=np.float64)
+
+
+@dataclass
+class Workload:
+    """One synthetic problem: N points in a periodic box with a ball mask and a target."""
+    name: str
+    dim: int
+    n_points: int
+    K: int
+    target: str            # "stealthy" | "power_law" | "peaked"
+    dtype: str             # "f64" | "f32"
+    seed: int = 0
+    box: float = 1.0
+    tol: float = 1e-6
+    upsample: float = 2.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.dtype == "f64" else np.float32
+
+    def points(self) -> np.ndarray:
+        return uniform_points(self.n_points, self.dim, self.seed, self.np_dtype, self.box)
+
+    def mask(self) -> np.ndarray:
+        return ball_mask(self.K, self.dim)
+
+    def targets(self, mask: np.ndarray):
+        if self.target == "stealthy":
+            s0 = stealthy_target(mask)
+        elif self.target == "power_law":
+            s0 = power_law_target(mask, self.K)
+        elif self.target == "peaked":
+            s0 = peaked_target(mask, self.n_points, self.K)
+        else:
+            raise ValueError(self.target)
+        return s0, unit_weights(mask)
+
+
+def workload(name: str) -> Workload:
+    """The named synthetic workloads (sizes in the name; see the module docstring)."""
+    if name == "stealthy2d_n1024_k20_f64":
+        return Workload(name, 2, 1024, 20, "stealthy", "f64", seed=0, tol=1e-12)
+    if name == "stealthy2d_n1e6_chi045_f32":
+        return Workload(name, 2, 10**6, radius_for_chi(10**6, 2, 0.45), "stealthy", "f32",
+                        seed=0, tol=1e-6)
+    if name == "powerlaw3d_n2p24_chi03_f32":
+        return Workload(name, 3, 2**24, radius_for_chi(2**24, 3, 0.3), "power_law", "f32",
+                        seed=0, tol=1e-6)
+    if name == "peaked2d_n1e8_chi03_f32":
+        return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f32",
+                        seed=0, tol=1e-6)
+    if name == "peaked2d_n1e8_chi03_f64":
+        return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f64",
+                        seed=0, tol=1e-12)
+    raise KeyError(name)

@@ -1,0 +1,172 @@
+"""Pins for the CPU oracle: facts fixed by the paper and by mathematics, not by the oracle.
+
+Each test below would fail for a plausible mistake in the oracle (a dropped term, a wrong
+sign or index, a transposed operand, a wrong factor in the gradient):
+
+* rho(0) = N (S(0) = N, Eq. 1);
+* points on an M x M (x M) grid with random occupancy: rho equals numpy's FFT of the
+  occupancy array (catches a wrong exponent sign, swapped axes or a wrong box scaling);
+* square / cubic lattices: Bragg peaks S = N on the reciprocal lattice and 0 elsewhere
+  (SI "Saturating peaks");
+* Poisson points: E[S(n)] = 1 for integer n != 0;
+* N = 1: S = 1 and zero gradient; N = 2: closed forms for S, the loss and the gradient;
+* central finite differences of the oracle's own loss against its gradient;
+* translation invariance: sum_j dL/dr_j = 0;
+* lattice with spacing finer than the mask (m > K): L = 0 and dL/dr = 0 (stealthy ground
+  state).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_15693_gb300 import inputs
+
+
+def test_rho_at_origin_is_n():
+    pts = inputs.uniform_points(333, 2, seed=3)
+    mask = np.array([[0, 0], [1, 0]], dtype=np.int32)
+    rho = oracle.rho(pts, mask)
+    assert rho[0].real == pytest.approx(333.0, abs=1e-9)
+    assert abs(rho[0].imag) < 1e-9
+
+
+@pytest.mark.parametrize("dim,M,box", [(2, 12, (1.0, 2.5)), (3, 6, (1.5, 1.0, 0.75))])
+def test_grid_occupancy_equals_numpy_fft(dim, M, box):
+    g = inputs.rng(11)
+    occ = g.random((M,) * dim) < 0.4          # occ[i_{d-1}, ..., i_0] (numpy axis 0 = last coord)
+    idx = np.argwhere(occ)                    # rows (i_{d-1}, ..., i_0)
+    coords = idx[:, ::-1].astype(np.float64)  # (i_0, ..., i_{d-1}) -> coordinate a uses i_a
+    pts = coords / M * np.asarray(box)
+    mask = g.integers(-2 * M, 2 * M, size=(40, dim)).astype(np.int32)
+    rho = oracle.rho(pts, mask, box=box)
+    F = np.fft.fftn(occ.astype(np.float64))   # sum occ[i] exp(-2 pi i k.i / M)
+    want = np.array([F[tuple((n[::-1]) % M)] for n in mask])
+    np.testing.assert_allclose(rho, want, rtol=0, atol=1e-9)
+
+
+def test_square_lattice_bragg_peaks():
+    m = 8
+    pts = inputs.lattice_points(m, 2, offset=0.3)
+    N = pts.shape[0]
+    mask = inputs.ball_mask(20, 2)
+    S0 = np.zeros(mask.shape[0])
+    W = np.ones(mask.shape[0])
+    _, _, S, _ = oracle.loss_grad(pts, mask, S0, W, want_grad=False)
+    on = np.all(mask % m == 0, axis=1)
+    assert on.sum() > 0
+    np.testing.assert_allclose(S[on], N, rtol=1e-12)
+    assert np.max(np.abs(S[~on])) < 1e-12 * N
+
+
+def test_cubic_lattice_bragg_peaks():
+    m = 5
+    pts = inputs.lattice_points(m, 3, box=2.0, offset=0.1)
+    N = pts.shape[0]
+    mask = inputs.ball_mask(8, 3)
+    S0 = np.zeros(mask.shape[0])
+    W = np.ones(mask.shape[0])
+    _, _, S, _ = oracle.loss_grad(pts, mask, S0, W, box=2.0, want_grad=False)
+    on = np.all(mask % m == 0, axis=1)
+    np.testing.assert_allclose(S[on], N, rtol=1e-12)
+    assert np.max(np.abs(S[~on])) < 1e-12 * N
+
+
+def test_poisson_mean_structure_factor_is_one():
+    mask = inputs.ball_mask(20, 2)
+    keep = inputs.half_space(mask)            # S(n) = S(-n): count each pair once
+    half = mask[keep]
+    vals = []
+    for seed in range(64):
+        pts = inputs.uniform_points(1024, 2, seed=1000 + seed)
+        r = oracle.rho(pts, half)
+        vals.append(np.abs(r) ** 2 / 1024.0)
+    s = np.concatenate(vals)
+    sigma = 1.0 / math.sqrt(s.size)           # S ~ Exp(1) for i.i.d. uniform points
+    assert abs(s.mean() - 1.0) < 4.0 * sigma
+
+
+def test_single_point():
+    pts = np.array([[0.37, 0.81]])
+    mask = inputs.ball_mask(5, 2)
+    S0 = np.full(mask.shape[0], 0.25)
+    W = np.linspace(0.5, 2.0, mask.shape[0])
+    loss, grad, S, _ = oracle.loss_grad(pts, mask, S0, W)
+    np.testing.assert_allclose(S, 1.0, rtol=1e-13)
+    assert loss == pytest.approx(np.sum(W * 0.75 ** 2), rel=1e-13)
+    assert np.max(np.abs(grad)) < 1e-10
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_two_points_closed_form(dim):
+    g = inputs.rng(5)
+    pts = g.random((2, dim))
+    box = 1.0 + g.random(dim)
+    mask = inputs.ball_mask(3, dim)
+    S0 = g.random(mask.shape[0]) * 2.0
+    W = 0.5 + g.random(mask.shape[0])
+    loss, grad, S, _ = oracle.loss_grad(pts, mask, S0, W, box=box)
+    k = 2.0 * np.pi * mask / box                           # [n_k, dim]
+    phi = k @ (pts[0] - pts[1])                            # k . (r_1 - r_2)
+    S_cf = 1.0 + np.cos(phi)                               # |1 + e^{-i phi}|^2 / 2
+    L_cf = np.sum(W * (S_cf - S0) ** 2)
+    dS_dr1 = -np.sin(phi)[:, None] * k                     # d/dr_1 of 1 + cos(k.(r_1 - r_2))
+    g1 = np.sum((2.0 * W * (S_cf - S0))[:, None] * dS_dr1, axis=0)
+    np.testing.assert_allclose(S, S_cf, rtol=1e-12, atol=1e-12)
+    assert loss == pytest.approx(L_cf, rel=1e-12)
+    np.testing.assert_allclose(grad[0], g1, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(grad[1], -g1, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("dim,N,K", [(2, 16, 4), (3, 12, 3)])
+def test_gradient_matches_central_differences(dim, N, K):
+    g = inputs.rng(17 + dim)
+    pts = g.random((N, dim))
+    box = np.linspace(1.0, 1.3, dim)
+    pts *= box
+    mask = inputs.ball_mask(K, dim)
+    S0 = g.random(mask.shape[0])
+    W = 0.2 + g.random(mask.shape[0])
+    _, grad, _, _ = oracle.loss_grad(pts, mask, S0, W, box=box)
+    h = 1e-6
+    fd = np.zeros_like(pts)
+    for j in range(N):
+        for a in range(dim):
+            p = pts.copy()
+            p[j, a] += h
+            lp, _, _, _ = oracle.loss_grad(p, mask, S0, W, box=box, want_grad=False)
+            p[j, a] -= 2 * h
+            lm, _, _, _ = oracle.loss_grad(p, mask, S0, W, box=box, want_grad=False)
+            fd[j, a] = (lp - lm) / (2 * h)
+    err = np.linalg.norm(fd - grad) / np.linalg.norm(grad)
+    assert err < 1e-7
+
+
+def test_translation_invariance_and_selection():
+    g = inputs.rng(23)
+    pts = g.random((200, 2))
+    mask = inputs.ball_mask(6, 2)
+    S0 = g.random(mask.shape[0])
+    W = g.random(mask.shape[0])
+    loss, grad, _, _ = oracle.loss_grad(pts, mask, S0, W)
+    assert np.linalg.norm(grad.sum(axis=0)) < 1e-11 * np.linalg.norm(grad)
+    sel = np.array([5, 0, 199, 42])
+    loss2, gsel, _, _ = oracle.loss_grad(pts, mask, S0, W, sel=sel)
+    assert loss2 == loss
+    np.testing.assert_array_equal(gsel, grad[sel])
+    shifted = pts + np.array([0.3, -1.7])
+    loss3, grad3, _, _ = oracle.loss_grad(shifted, mask, S0, W)
+    assert loss3 == pytest.approx(loss, rel=1e-11)
+    np.testing.assert_allclose(grad3, grad, rtol=1e-8, atol=1e-9 * np.abs(grad).max())
+
+
+def test_lattice_ground_state_is_stealthy():
+    m = 16
+    pts = inputs.lattice_points(m, 2, offset=0.5)
+    mask = inputs.ball_mask(10, 2)            # every |n| <= 10 < m: no reciprocal-lattice point
+    loss, grad, S, _ = oracle.loss_grad(pts, mask, np.zeros(mask.shape[0]),
+                                        np.ones(mask.shape[0]))
+    assert loss < 1e-20
+    assert np.max(np.abs(grad)) < 1e-9
