@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Throughput of one FReSCo loss+gradient evaluation on the GPU (points/s), FP32 against the
+all-FP64 GPU path, with per-stage CUDA-event timing, the HBM roofline of the dominant kernel,
+an end-to-end figure through the host-buffer C entry point, and the CPU oracle as baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Default workload: 2D, N = 1e8 uniform FP32 points, ball mask |n| <= K with chi = 0.3 (K = 6180),
+peaked ring target of 10 Gaussian peaks of height N/10, W = 1. Under torchrun each rank runs an
+independent replica of the workload on its own GPU (no data-path collective; weak scaling); the
+barrier and the max over ranks only frame the timing.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "peaked2d_n1e8_chi03_f32"
+METRIC = "points/s per loss+grad eval (FP32 vs FP64 GPU, 2D N=1e8); % HBM roofline"
+L2_BYTES = 129 * 2 ** 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.rows = []
+        self.proc = None
+        self.device_id = device_id
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.device_id:
+            cmd += ["-i", self.device_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _device_selector(dev_index: int) -> str | None:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic bytes per launch of every stage (the minimum each stage must move through HBM)
+
+def stage_bytes(info: dict, n_points: int, esize: int) -> dict:
+    d = info["dim"]
+    nf = info["n_fine"][:d]
+    cells = int(np.prod(nf))
+    rows = cells // nf[0]
+    half = nf[0] // 2 + 1
+    kx = info["k_max"][0]
+    hc_row = 2 * kx + 2
+    pd = 4 if d == 3 else 2           # words per packed coordinate
+    n_pipes = 1 if d == 2 else 2
+    nrep = info["n_rep"]
+    N = n_points
+    c2 = 2 * esize                    # complex element
+    return {
+        "sort": N * d * esize + N * pd * esize + 4 * N,
+        "spread": N * pd * esize + cells * esize,
+        "fft_fwd": cells * esize + rows * half * c2,
+        "mask": nrep * (4 * d + 2 * esize + c2 + n_pipes * 2 * c2),
+        "loss": 0,
+        "fft_inv": n_pipes * (rows * hc_row * c2 + cells * c2),
+        "interp": n_pipes * cells * c2 + N * pd * esize + 4 * N + N * d * esize,
+    }
+
+
+def load_peaks():
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------------------------------------
+
+def make_inputs(wl):
+    t0 = time.time()
+    pts = wl.points()
+    mask = wl.mask()
+    S0, W = wl.targets(mask)
+    log("inputs: N=%d K=%d N_K=%d (%.1f s)" % (wl.n_points, wl.K, mask.shape[0], time.time() - t0))
+    return pts, mask, S0, W
+
+
+def time_device(plan, pts, steps, warmup, dist_on, profile=True):
+    """Device-resident timing: W untimed steps, then K steps bracketed by barrier + sync."""
+    import torch
+    stream = torch.cuda.current_stream()
+    loss = torch.empty((), dtype=torch.float64, device=pts.device)
+    grad = torch.empty_like(pts)
+    from paper_2305_15693_gb300 import fresco
+    for _ in range(warmup):
+        fresco.fresco_loss_grad(plan.handle, pts, loss, grad)
+    torch.cuda.synchronize()
+    if profile:
+        plan.profile_read()           # drop warm-up records
+        plan.profile(True)
+    n0 = plan.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        fresco.fresco_loss_grad(plan.handle, pts, loss, grad)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = plan.launch_count() - n0
+    stages = plan.profile_read() if profile else None
+    plan.profile(False)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError("device status after timing: %d" % st)
+    return ms, launches, stages, float(loss.item())
+
+
+def time_e2e(plan, pts_np, steps, warmup):
+    """Through fresco_loss_grad_host on pinned host buffers: H2D of the points, evaluation,
+    D2H of the loss and the gradient, every step."""
+    import torch
+    h_pts = torch.from_numpy(pts_np).pin_memory()
+    h_grad = torch.empty(pts_np.shape, dtype=h_pts.dtype).pin_memory()
+    a_pts = h_pts.numpy()
+    a_grad = h_grad.numpy()
+    for _ in range(warmup):
+        plan.loss_grad_host(a_pts, a_grad)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.loss_grad_host(a_pts, a_grad)
+    dt = (time.perf_counter() - t0) / steps
+    return dt, a_pts.nbytes, a_grad.nbytes + 8
+
+
+def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2):
+    """The oracle timed on the host cores on a bounded sample: rho at a seeded sample of mask rows
+    over all N points (direct sums). A full evaluation costs rho over all N_K rows plus the
+    gradient over all N points x N_K rows: about 2 N N_K pair terms at the same per-term cost."""
+    import oracle
+    N = pts_np.shape[0]
+    n_k = mask.shape[0]
+    g = np.random.Generator(np.random.Philox(seed))
+    r64 = np.ascontiguousarray(pts_np, dtype=np.float64)
+    probe = mask[g.choice(n_k, 2, replace=False)]
+    t0 = time.perf_counter()
+    oracle.rho(r64, probe, box)
+    t_probe = max(time.perf_counter() - t0, 1e-6)
+    per_row = t_probe / 2
+    n_s = int(max(2, min(256, budget_s / per_row)))
+    sample = mask[g.choice(n_k, n_s, replace=False)]
+    t0 = time.perf_counter()
+    oracle.rho(r64, sample, box)
+    t = time.perf_counter() - t0
+    rate = N * n_s / t                                  # pair terms / s
+    t_eval = 2.0 * N * n_k / rate
+    return {"value": N / t_eval, "unit": "points/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": "rho at %d of %d mask rows over all %d points (%.1f s); full evaluation "
+                      "extrapolated as 2*N*N_K pair terms at the measured %.3e terms/s"
+                      % (n_s, n_k, N, t, rate),
+            "seconds_per_eval_extrapolated": t_eval}
+
+
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args, wl, rank, world):
+    """The oracle as the reference arm: each step is one bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pts, mask, S0, W = make_inputs(wl)
+    r64 = np.ascontiguousarray(pts, dtype=np.float64)
+    g = np.random.Generator(np.random.Philox(3))
+    n_s = max(1, int(args.ref_rows))
+    N, n_k = pts.shape[0], mask.shape[0]
+    for _ in range(args.warmup):
+        oracle.rho(r64, mask[g.choice(n_k, n_s, replace=False)], wl.box)
+    times = []
+    for _ in range(args.steps):
+        sample = mask[g.choice(n_k, n_s, replace=False)]
+        t0 = time.perf_counter()
+        oracle.rho(r64, sample, wl.box)
+        times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    rate = N * n_s / t
+    t_eval = 2.0 * N * n_k / rate
+    value = N / t_eval
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_eval, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_points": N, "K": wl.K, "n_modes": n_k,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": "per step: rho at %d seeded mask rows over all %d points by "
+                                   "direct sums; evaluation extrapolated as 2*N*N_K pair terms"
+                                   % (n_s, N)},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--f64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-rows", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warmup raised to 3")
+        args.warmup = 3
+
+    from paper_2305_15693_gb300 import inputs
+    wl = inputs.workload(args.workload)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+
+    import torch
+    from paper_2305_15693_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    dist_on = world > 1
+    if dist_on:
+        torch.distributed.init_process_group("nccl")
+        _build.build()
+    torch.cuda.set_device(local_rank)
+    from paper_2305_15693_gb300 import fresco
+    fresco.load()
+
+    pts_np, mask, S0, W = make_inputs(wl)
+    N = wl.n_points
+    pts = torch.from_numpy(pts_np).cuda()
+
+    # ---- FP32 path: the headline -------------------------------------------------------------
+    plan = fresco.Plan(wl.box, mask, S0, W, N, precision=wl.dtype, tol=wl.tol,
+                       upsample=wl.upsample)
+    info = plan.info
+    log("plan: n_fine=%s w=%d tiles=%s n_rep=%d device_bytes=%.2f GB" % (
+        info["n_fine"][:wl.dim], info["width"], info["n_tiles"][:wl.dim], info["n_rep"],
+        info["device_bytes"] / 1e9))
+    clocks = ClockSampler(_device_selector(local_rank))
+    clocks.start()
+    ms, launches, stages, loss_val = time_device(plan, pts, args.steps, args.warmup, dist_on)
+    clk = clocks.stop()
+    t_step = ms / args.steps / 1e3
+    if dist_on:
+        t = torch.tensor([t_step], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    value = world * N / t_step
+
+    # e2e through the host-buffer entry point
+    dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
+    if dist_on:
+        t = torch.tensor([dt_e2e], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt_e2e = float(t.item())
+    plan.close()
+
+    # ---- per-stage roofline ------------------------------------------------------------------
+    esize = 4 if wl.dtype == "f32" else 8
+    sb = stage_bytes(info, N, esize)
+    peaks = load_peaks() if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per_stage = {}
+    for name, (tot_ms, cnt) in stages.items():
+        if cnt == 0:
+            continue
+        avg = tot_ms / cnt
+        gbs = sb[name] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        per_stage[name] = {"ms": round(avg, 4), "alg_bytes": int(sb[name]),
+                           "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
+    ours = {k: v for k, v in per_stage.items() if k not in ("fft_fwd", "fft_inv")}
+    dom = max(ours, key=lambda k: ours[k]["ms"])
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tr = json.load(f)
+        entry = tr.get(wl.name, {}).get(dom)
+        if entry and entry.get("source_hash") == _kernel_source_hash():
+            traffic = entry.get("bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": per_stage[dom]["GB/s"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": per_stage[dom]["frac"], "traffic": traffic,
+                "kernel": dom, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+
+    # ---- all-FP64 GPU path on the same workload ----------------------------------------------
+    f64 = None
+    if wl.dtype == "f32" and args.f64_steps > 0:
+        pts64 = pts.double()
+        plan64 = fresco.Plan(wl.box, mask, S0, W, N, precision="f64", tol=1e-12,
+                             upsample=wl.upsample)
+        ms64, _, st64, loss64 = time_device(plan64, pts64, args.f64_steps, 3, dist_on)
+        plan64.close()
+        del pts64
+        t64 = ms64 / args.f64_steps / 1e3
+        f64 = {"value": world * N / t64, "ms_per_step": 1e3 * t64, "width": None,
+               "speedup_f32_over_f64": t64 / t_step,
+               "loss_rel_diff_f32_vs_f64": abs(loss_val - loss64) / abs(loss64),
+               "stages_ms": {k: round(v[0] / max(v[1], 1), 3) for k, v in st64.items()}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pts_np, mask, wl.box)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": wl.dtype, "data": "synthetic",
+            "config": {"workload": wl.name, "n_points": N, "dim": wl.dim, "K": wl.K,
+                       "n_modes": int(mask.shape[0]), "target": wl.target, "tol": wl.tol,
+                       "upsample": wl.upsample, "width": info["width"],
+                       "n_fine": info["n_fine"][:wl.dim], "tiles": info["n_tiles"][:wl.dim],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (fine grid %.2f GB > %d MB)"
+                             % (np.prod(info["n_fine"][:wl.dim]) * esize / 1e9,
+                                L2_BYTES // 2 ** 20)},
+            "roofline": roofline,
+            "stages": per_stage,
+            "fp64": f64,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * N / dt_e2e, "unit": "points/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt_e2e},
+            "clocks": clk,
+            "gpu_launches": launches,
+            "loss": loss_val,
+        }
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def _kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

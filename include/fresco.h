@@ -1,0 +1,186 @@
+/*
+ * fresco.h -- C ABI of libfresco: one evaluation of the FReSCo structure-factor loss and its
+ * position gradient on a GB300 GPU (sm_103a), through a type-1 / type-2 nonuniform FFT pair.
+ *
+ * What is computed (arXiv 2305.15693):
+ *   points r_j in a periodic box [0, L_0) x ... x [0, L_{d-1}), d = 2 or 3, weights c_j = 1;
+ *   mask: integer wavevectors n (k = 2 pi n / L, componentwise), given with S0(n) and W(n);
+ *   rho(n)  = sum_j exp(-i k . r_j)                      (Eq. 1 and Methods Eq. M-ft; e^{-ik.r}
+ *                                                          convention, i.e. the paper's rho conjugated)
+ *   S(n)    = |rho(n)|^2 / N                               (Eq. 1)
+ *   L       = sum_{n in mask} W(n) (S(n) - S0(n))^2        (Eq. 2, with W = w / S0^2 for the
+ *                                                          relative form of Eq. 3, Methods
+ *                                                          "Analytical gradients")
+ *   dL/dr_j = Re sum_n 4 i k W (S - S0) rho(n) / N e^{+i k . r_j}    (Eq. 4)
+ * rho is obtained by a type-1 NUFFT (spread with the exponential-of-semicircle kernel, FFT,
+ * deconvolve), the gradient by d type-2 NUFFTs (deconvolve, inverse FFT, interpolate), the
+ * transforms of Methods "Algorithm parameters" and "NUwU".
+ *
+ * Conventions shared by every entry point:
+ *   - Arrays are row-major. Points are [N][d]: column a is the coordinate along axis a, which
+ *     pairs with box[a] and with column a of the mask.
+ *   - Precision: a plan is FRESCO_F32 or FRESCO_F64. Device point and gradient arrays have that
+ *     element type (float or double). The loss is always a device double.
+ *   - All calls that take a plan run asynchronously on the plan's stream (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream) and perform no host synchronisation, except
+ *     fresco_status_check, fresco_get_info and the *_host variants.
+ *   - Errors: argument errors are returned synchronously. Launch failures return
+ *     FRESCO_ERR_CUDA / FRESCO_ERR_CUFFT. Problems only the device sees (non-finite coordinates)
+ *     are latched in a device error word that fresco_status_check reads. No C++ exception
+ *     crosses this interface.
+ *   - Ownership: the caller owns every pointer it passes (points, gradient, loss, stream);
+ *     a plan owns copies of the mask, S0 and W, all grids, cuFFT plans and workspaces, and
+ *     frees them in fresco_destroy. A plan is not thread safe; use one plan per host thread.
+ */
+#ifndef FRESCO_H
+#define FRESCO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fresco_plan_s *fresco_plan_t;
+
+typedef enum {
+    FRESCO_OK = 0,
+    FRESCO_ERR_ARG = 1,          /* invalid argument (null pointer, size, dimension, mask) */
+    FRESCO_ERR_OOM = 2,          /* a device or host allocation failed */
+    FRESCO_ERR_CUFFT = 3,        /* a cuFFT call failed */
+    FRESCO_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    FRESCO_ERR_NONFINITE = 5,    /* a coordinate was NaN or infinite (device-detected) */
+    FRESCO_ERR_BOUNDS = 6,       /* an index check failed (device-detected) */
+    FRESCO_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
+    FRESCO_ERR_UNSUPPORTED = 8   /* valid request this build does not handle */
+} fresco_status;
+
+enum { FRESCO_F32 = 0, FRESCO_F64 = 1 };
+
+/* Plan options. Zero-initialise (or call fresco_opts_default) and set what you need. */
+typedef struct {
+    int precision;       /* FRESCO_F32 (default) or FRESCO_F64 */
+    double tol;          /* NUFFT relative tolerance eps; 0 -> 1e-6 (F32) or 1e-12 (F64). Sets the
+                            kernel width w = ceil(ln(1/eps) / (pi sqrt(1 - 1/sigma))), at least 2;
+                            a tolerance needing w > 16 is FRESCO_ERR_UNSUPPORTED */
+    double upsample;     /* fine-grid oversampling sigma; 0 -> 2.0; must be in [1.25, 3] */
+    int width_override;  /* kernel width w in fine-grid cells (2..16); 0 -> from tol */
+    int tile[3];         /* spread/interp tile edge per axis in fine cells; 0 -> default */
+    int reserved[4];     /* must be zero */
+} fresco_opts;
+
+/* Plan parameters, filled by fresco_plan_query and fresco_get_info. */
+typedef struct {
+    int dim;
+    int precision;
+    int width;             /* kernel width w (fine cells) */
+    int n_fine[3];         /* fine grid size per axis (axis 0 = x, the contiguous one) */
+    int k_max[3];          /* max |n_a| over the mask */
+    int tile[3];           /* tile edge per axis used by spread / interp */
+    int n_tiles[3];        /* tiles per axis */
+    double beta;           /* ES kernel shape: psi(u) = exp(beta (sqrt(1 - (2u/w)^2) - 1)) */
+    double upsample;
+    double loss_const;     /* constant added back after folding +-n pairs (see fresco_plan) */
+    int64_t n_points;
+    int64_t n_modes;       /* mask entries as given */
+    int64_t n_rep;         /* half-space representatives after folding */
+    int64_t device_bytes;  /* device memory the plan holds (0 from fresco_plan_query) */
+} fresco_info;
+
+/* Fill *opts with the defaults (F32, eps = 1e-6, sigma = 2). */
+void fresco_opts_default(fresco_opts *opts);
+
+/* Create a plan for N points in a periodic box with a fixed wavevector mask (Eq. 2's region K).
+ *   out      : receives the plan handle (set to NULL on failure)
+ *   dim      : 2 or 3
+ *   box      : host [dim] box side lengths L_a > 0
+ *   n_points : N >= 1
+ *   mask     : host int32 [n_k][dim], integer wavevectors n; any order; n = 0 is rejected (S(0) = N
+ *              is fixed, cannot be constrained); |n_a| must stay below n_fine[a] / 2
+ *   n_k      : number of mask rows, >= 1; duplicates are allowed and count separately
+ *   S0, W    : host double [n_k] target and weight per row; W >= 0 and finite, S0 finite
+ *   opts     : NULL for defaults
+ *   stream   : cudaStream_t (as void*) every later call runs on; NULL = default stream
+ * Folding (S(n) = S(-n) for real weights, Friedel's law, Eq. 3 text): rows n and -n share S, so
+ * the plan merges them into one half-space representative with W' = sum W, S0' = sum W S0 / W'.
+ * The loss is unchanged up to the constant sum W S0^2 - sum W' S0'^2, which the plan adds back.
+ * Copies mask, S0 and W; allocates every device buffer and cuFFT plan the evaluations need, so
+ * later calls allocate nothing. Synchronous. Returns FRESCO_ERR_ARG, _OOM, _CUFFT or _CUDA. */
+fresco_status fresco_plan(fresco_plan_t *out, int dim, const double *box, int64_t n_points,
+                          const int32_t *mask, int64_t n_k, const double *S0, const double *W,
+                          const fresco_opts *opts, void *stream);
+
+/* Host only (no GPU touched): validate the same arguments as fresco_plan and report the plan
+ * parameters it would choose (fine grid, kernel width and shape, folded count, loss constant). */
+fresco_status fresco_plan_query(int dim, const double *box, int64_t n_points, const int32_t *mask,
+                                int64_t n_k, const double *S0, const double *W,
+                                const fresco_opts *opts, fresco_info *info);
+
+/* Host only: Fourier transform of the ES kernel on the fine grid,
+ *   out[i] = integral_{-w/2}^{w/2} psi(u) cos(2 pi nu_i u / n_fine) du,  nu_i = i, i < n_nu,
+ * by Gauss-Legendre quadrature in FP64 (the deconvolution factors of the type-1/type-2 NUFFT). */
+fresco_status fresco_kernel_ft(int width, double beta, int n_fine, int64_t n_nu, double *out);
+
+/* Copy the plan parameters into *info. */
+fresco_status fresco_get_info(fresco_plan_t p, fresco_info *info);
+
+/* Run later calls on another stream (cudaStream_t as void*). */
+fresco_status fresco_set_stream(fresco_plan_t p, void *stream);
+
+/* Loss and gradient in one call (Eq. 2 and Eq. 4).
+ *   d_points: device [N][dim] positions (float for F32 plans, double for F64); any real values,
+ *             wrapped into the box modulo L internally; the array is not modified
+ *   d_loss  : device double, receives L
+ *   d_grad  : device [N][dim] same type as d_points, receives dL/dr in the caller's point order;
+ *             may be NULL (loss only) */
+fresco_status fresco_loss_grad(fresco_plan_t p, const void *d_points, double *d_loss,
+                               void *d_grad);
+
+/* First half of fresco_loss_grad: sort, spread, FFT, deconvolve, S and the loss (type-1 NUFFT,
+ * Eq. 1-2). Also prepares the gradient coefficients C(k) of Eq. 4 inside the plan, so a
+ * fresco_backward on the same plan can follow. d_points must stay unchanged until then. */
+fresco_status fresco_forward(fresco_plan_t p, const void *d_points, double *d_loss);
+
+/* Second half: d_grad = g * dL/dr, g = *d_grad_out (device double; NULL means 1), by the
+ * inverse FFT and interpolation of the type-2 NUFFT (Eq. 4). Requires a preceding fresco_forward. */
+fresco_status fresco_backward(fresco_plan_t p, const double *d_grad_out, void *d_grad);
+
+/* After fresco_forward: rho (interleaved re, im: device [n_k][2]) and S (device [n_k]) for the
+ * mask rows in the order given to fresco_plan, in the plan's precision. Either may be NULL.
+ * The first call uploads the mask (allocates once). */
+fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S);
+
+/* End-to-end variant on host buffers: copies h_points (host, [N][dim] plan type) to the device,
+ * evaluates, and copies the loss (host double) and, if h_grad is not NULL, the gradient back.
+ * Synchronises the plan's stream before returning. Uses staging buffers the plan allocates on
+ * first use. */
+fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, double *h_loss,
+                                    void *h_grad);
+
+/* Synchronise the plan's stream and return the first device-detected error, clearing it
+ * (FRESCO_ERR_NONFINITE for a NaN/inf coordinate), or a pending CUDA error. */
+fresco_status fresco_status_check(fresco_plan_t p);
+
+/* Per-stage timing with CUDA events on the plan's stream. enable != 0 records events around
+ * each stage of every later call; fresco_profile_read returns accumulated milliseconds and
+ * call counts per stage (synchronises first) and resets them. Stages, in order:
+ * 0 sort, 1 spread, 2 forward FFT, 3 mask/loss, 4 loss finalize, 5 inverse FFT, 6 interpolate.
+ * ms and counts have room for FRESCO_N_STAGES entries each (counts may be NULL). */
+#define FRESCO_N_STAGES 7
+fresco_status fresco_profile(fresco_plan_t p, int enable);
+fresco_status fresco_profile_read(fresco_plan_t p, double *ms, int64_t *counts);
+
+/* Number of libfresco kernels launched through this plan so far (cuFFT's own not included). */
+int64_t fresco_launch_count(fresco_plan_t p);
+
+/* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
+fresco_status fresco_destroy(fresco_plan_t p);
+
+/* Static description of a status code. */
+const char *fresco_status_string(fresco_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRESCO_H */

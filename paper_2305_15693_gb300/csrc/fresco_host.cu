@@ -1,0 +1,923 @@
+// Host side of libfresco: plan construction (kernel parameters, mask folding, deconvolution
+// tables, cuFFT plans, device buffers) and the C ABI declared in include/fresco.h.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fresco.h"
+#include "fresco_internal.h"
+
+using namespace fresco;
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr size_t kSmemOptin = 227 * 1024;   // opt-in shared memory per block on sm_100 / sm_103
+
+// ---- fine grid and kernel parameters --------------------------------------------------------
+
+bool is_smooth_even(int64_t n) {
+    if (n < 2 || (n & 1)) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Smallest even 2-3-5-7-smooth integer >= n.
+int64_t next_smooth_even(int64_t n) {
+    if (n < 2) n = 2;
+    while (!is_smooth_even(n)) ++n;
+    return n;
+}
+
+// Kernel width and shape for tolerance eps at oversampling sigma, from the error estimate of the
+// exponential-of-semicircle kernel (Barnett, Magland, af Klinteberg, SIAM J. Sci. Comput. 2019,
+// the NUFFT the paper uses, Methods "Algorithm parameters"): the aliasing error decays like
+// exp(-pi w sqrt(1 - 1/sigma)); beta ~ 0.976 pi (1 - 1/(2 sigma)) w, i.e. 2.30 w at sigma = 2.
+// Returns a width above kMaxWidth when eps cannot be reached at this sigma; the caller rejects it.
+int es_width(double eps, double sigma) {
+    double w = std::ceil(std::log(1.0 / eps) / (kPi * std::sqrt(1.0 - 1.0 / sigma)));
+    if (w > 1000.0) w = 1000.0;
+    int wi = (int)w;
+    if (wi < kMinWidth) wi = kMinWidth;
+    return wi;
+}
+double es_beta(int w, double sigma) { return 0.976 * kPi * (1.0 - 0.5 / sigma) * w; }
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n from the three-term
+// recurrence, starting from the asymptotic root estimates).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &wts) {
+    x.assign(n, 0.0);
+    wts.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double t = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        {   // final derivative at the converged root
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+        }
+        x[i] = -t;
+        x[n - 1 - i] = t;
+        double wq = 2.0 / ((1.0 - t * t) * dp * dp);
+        wts[i] = wq;
+        wts[n - 1 - i] = wq;
+    }
+}
+
+// Psi(nu) = integral_{-w/2}^{w/2} psi(u) cos(2 pi nu u / nf) du for nu = 0..n_nu-1.
+// With u = (w/2) sin(theta) the kernel becomes exp(beta (cos(theta) - 1)), analytic on
+// theta in [0, pi/2] (the square-root edge of psi disappears), so Gauss-Legendre in theta
+// converges geometrically.
+void kernel_ft(int w, double beta, int nf, int64_t n_nu, double *out) {
+    const int nq = 200;
+    std::vector<double> x, wq;
+    gauss_legendre(nq, x, wq);
+    const double h = 0.25 * kPi;  // theta in [0, pi/2] = h (1 + t), t in [-1, 1]
+    std::vector<double> u(nq), f(nq);
+    for (int q = 0; q < nq; ++q) {
+        const double th = h * (1.0 + x[q]);
+        u[q] = 0.5 * w * std::sin(th);
+        // factor 2: even integrand; du = (w/2) cos(theta) dtheta
+        f[q] = 2.0 * h * wq[q] * std::exp(beta * (std::cos(th) - 1.0)) * 0.5 * w * std::cos(th);
+    }
+    for (int64_t nu = 0; nu < n_nu; ++nu) {
+        double s = 0.0;
+        for (int q = 0; q < nq; ++q) s += f[q] * std::cos(2.0 * kPi * (double)nu * u[q] / nf);
+        out[nu] = s;
+    }
+}
+
+// ---- argument checks, parameters and mask folding -------------------------------------------
+
+struct Folded {
+    std::vector<int32_t> n;     // [n_rep][dim]
+    std::vector<double> s0;     // S0'
+    std::vector<double> w;      // W'
+    double loss_const = 0.0;
+};
+
+struct Params {
+    int dim, precision, width;
+    double beta, sigma, tol;
+    int kmax[3];
+    int nf[3];
+    int nb[3];
+    int tmax[3];
+};
+
+bool canonical(const int32_t *n, int dim) {
+    if (n[0] != 0) return n[0] > 0;
+    if (n[1] != 0) return n[1] > 0;
+    return dim == 3 && n[2] > 0;
+}
+
+int choose_tiles(int nf, int target, int w) {
+    int minw = (w + 1) / 2;
+    if (target < minw) target = minw;
+    int best = std::max(1, (int)std::lround((double)nf / target));
+    // prefer an exact divisor of nf near the target edge
+    for (int d = 0; d <= target / 4; ++d) {
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int e = target + sgn * d;
+            if (e >= minw && e <= kMaxTileEdge && e <= nf && nf % e == 0) return nf / e;
+        }
+    }
+    while (best > 1 && nf / best < minw) --best;
+    while ((nf + best - 1) / best > kMaxTileEdge) ++best;
+    return best;
+}
+
+fresco_status check_and_params(int dim, const double *box, int64_t n_points, const int32_t *mask,
+                               int64_t n_k, const double *S0, const double *W,
+                               const fresco_opts *opts_in, Params &P) {
+    if (dim != 2 && dim != 3) return FRESCO_ERR_ARG;
+    if (!box || !mask || !S0 || !W) return FRESCO_ERR_ARG;
+    if (n_points < 1 || n_points > 2147483647LL) return FRESCO_ERR_ARG;
+    if (n_k < 1) return FRESCO_ERR_ARG;
+    fresco_opts o;
+    fresco_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    for (int i = 0; i < 4; ++i)
+        if (o.reserved[i] != 0) return FRESCO_ERR_ARG;
+    if (o.precision != FRESCO_F32 && o.precision != FRESCO_F64) return FRESCO_ERR_ARG;
+    double sigma = o.upsample == 0.0 ? 2.0 : o.upsample;
+    if (!(sigma >= 1.25 && sigma <= 3.0)) return FRESCO_ERR_ARG;
+    double tol = o.tol == 0.0 ? (o.precision == FRESCO_F64 ? 1e-12 : 1e-6) : o.tol;
+    if (!(tol > 0.0 && tol < 1.0)) return FRESCO_ERR_ARG;
+    for (int a = 0; a < dim; ++a)
+        if (!(box[a] > 0.0) || !std::isfinite(box[a])) return FRESCO_ERR_ARG;
+    int w = o.width_override ? o.width_override : es_width(tol, sigma);
+    if (o.width_override && (w < kMinWidth || w > kMaxWidth)) return FRESCO_ERR_ARG;
+    if (w > kMaxWidth) return FRESCO_ERR_UNSUPPORTED;   // tol unreachable at this sigma
+
+    int kmax[3] = {0, 0, 0};
+    for (int64_t q = 0; q < n_k; ++q) {
+        const int32_t *n = mask + q * dim;
+        bool zero = true;
+        for (int a = 0; a < dim; ++a) {
+            if (n[a] != 0) zero = false;
+            if (n[a] <= -(1 << 28) || n[a] >= (1 << 28)) return FRESCO_ERR_ARG;
+            kmax[a] = std::max(kmax[a], std::abs(n[a]));
+        }
+        if (zero) return FRESCO_ERR_ARG;
+        if (!std::isfinite(S0[q]) || !std::isfinite(W[q]) || W[q] < 0.0) return FRESCO_ERR_ARG;
+    }
+    P.dim = dim;
+    P.precision = o.precision;
+    P.width = w;
+    P.sigma = sigma;
+    P.tol = tol;
+    P.beta = es_beta(w, sigma);
+    for (int a = 0; a < 3; ++a) {
+        P.kmax[a] = a < dim ? kmax[a] : 0;
+        if (a < dim) {
+            int64_t need = (int64_t)std::ceil(sigma * (2.0 * kmax[a] + 1.0));
+            need = std::max<int64_t>(need, 2 * w);
+            need = std::max<int64_t>(need, 2 * (int64_t)kmax[a] + 2);
+            int64_t nf = next_smooth_even(need);
+            if (nf > (1 << 26)) return FRESCO_ERR_UNSUPPORTED;
+            P.nf[a] = (int)nf;
+        } else {
+            P.nf[a] = 1;
+            P.nb[a] = 1;
+            P.tmax[a] = 1;
+        }
+    }
+    // Tiles: the requested (or default) edge per axis, shrunk while the interpolation tile plus
+    // its halo would not fit the shared-memory budget (2 blocks per SM by default, the opt-in
+    // maximum when the caller fixed the tiles).
+    const size_t es = o.precision == FRESCO_F64 ? 8 : 4;
+    const bool user_tiles = o.tile[0] > 0 || o.tile[1] > 0 || o.tile[2] > 0;
+    size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
+    int target[3];
+    auto reset_targets = [&]() {
+        for (int a = 0; a < dim; ++a) {
+            int deft = dim == 2 ? 48 : (a < 2 ? 16 : 8);
+            target[a] = o.tile[a] > 0 ? o.tile[a] : deft;
+        }
+    };
+    reset_targets();
+    for (int a = 0; a < dim; ++a)
+        if (target[a] > kMaxTileEdge) return FRESCO_ERR_ARG;
+    for (int iter = 0;; ++iter) {
+        for (int a = 0; a < dim; ++a) {
+            P.nb[a] = choose_tiles(P.nf[a], target[a], w);
+            P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
+        }
+        size_t halo_cells = 1, cells = 1;
+        for (int a = 0; a < dim; ++a) {
+            halo_cells *= (size_t)(P.tmax[a] + w);
+            cells *= (size_t)P.tmax[a];
+        }
+        const size_t interp = halo_cells * (2 * es + (dim == 3 ? es : 0));
+        const size_t spread = cells * es;
+        if (interp <= budget && spread <= budget) break;
+        int amax = 0;
+        for (int a = 1; a < dim; ++a)
+            if (P.tmax[a] > P.tmax[amax]) amax = a;
+        const int minw = (w + 1) / 2;
+        if (target[amax] <= minw || iter > 256) {
+            if (budget >= kSmemOptin) return FRESCO_ERR_UNSUPPORTED;
+            budget = kSmemOptin;   // one block per SM rather than no plan
+            reset_targets();
+            iter = 0;
+            continue;
+        }
+        target[amax] = std::max(minw, std::min(target[amax] - 1, (P.tmax[amax] * 3) / 4));
+    }
+    int64_t cells = (int64_t)P.nf[0] * P.nf[1] * P.nf[2];
+    if (cells > (int64_t)1 << 36) return FRESCO_ERR_UNSUPPORTED;
+    int64_t tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
+    if (tiles >= 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
+    return FRESCO_OK;
+}
+
+// Merge each +-n pair onto its half-space representative (first nonzero component > 0):
+// W' = W(n) + W(-n), S0' = (W(n) S0(n) + W(-n) S0(-n)) / W', and the loss constant
+// sum W S0^2 - W' S0'^2, so that sum_mask W (S - S0)^2 = sum_rep W' (S - S0')^2 + const
+// whenever S(n) = S(-n). Representatives come out ordered by their address in the forward
+// half spectrum. Entries whose folded weight is zero are dropped (their terms are constants).
+fresco_status fold_mask(const Params &P, const int32_t *mask, int64_t n_k, const double *S0,
+                        const double *W, Folded &F) {
+    const int dim = P.dim;
+    const int kx = P.kmax[0], ky = P.kmax[1], kz = P.kmax[2];
+    const int64_t ex = kx + 1, ey = 2 * (int64_t)ky + 1, ez = 2 * (int64_t)kz + 1;
+    const int64_t box = ex * ey * ez;
+    if (box > ((int64_t)1 << 31)) return FRESCO_ERR_UNSUPPORTED;
+    std::vector<int32_t> slot;
+    try {
+        slot.assign((size_t)box, -1);
+    } catch (...) {
+        return FRESCO_ERR_OOM;
+    }
+    std::vector<double> sw, sws, sws2;
+    std::vector<int32_t> nrep;
+    for (int64_t q = 0; q < n_k; ++q) {
+        int32_t n[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) n[a] = mask[q * dim + a];
+        if (!canonical(n, dim))
+            for (int a = 0; a < 3; ++a) n[a] = -n[a];
+        const int64_t idx = ((int64_t)(n[2] + kz) * ey + (n[1] + ky)) * ex + n[0];
+        int32_t s = slot[idx];
+        if (s < 0) {
+            s = (int32_t)sw.size();
+            slot[idx] = s;
+            sw.push_back(0.0);
+            sws.push_back(0.0);
+            sws2.push_back(0.0);
+            for (int a = 0; a < dim; ++a) nrep.push_back(n[a]);
+        }
+        sw[s] += W[q];
+        sws[s] += W[q] * S0[q];
+        sws2[s] += W[q] * S0[q] * S0[q];
+    }
+    // emit in spectrum-address order: z rows 0..kz then -kz..-1, same for y, x ascending
+    F.n.clear();
+    F.s0.clear();
+    F.w.clear();
+    F.loss_const = 0.0;
+    F.n.reserve(nrep.size());
+    auto order = [](int k, int i) { return i <= k ? i : i - (2 * k + 1); };
+    for (int64_t iz = 0; iz < ez; ++iz) {
+        const int z = order(kz, (int)iz);
+        for (int64_t iy = 0; iy < ey; ++iy) {
+            const int y = order(ky, (int)iy);
+            const int64_t base = ((int64_t)(z + kz) * ey + (y + ky)) * ex;
+            for (int x = 0; x <= kx; ++x) {
+                const int32_t s = slot[base + x];
+                if (s < 0) continue;
+                const double wp = sw[s];
+                if (wp > 0.0) {
+                    const double s0p = sws[s] / wp;
+                    F.loss_const += sws2[s] - wp * s0p * s0p;
+                    for (int a = 0; a < dim; ++a) F.n.push_back(nrep[(size_t)s * dim + a]);
+                    F.s0.push_back(s0p);
+                    F.w.push_back(wp);
+                } else {
+                    F.loss_const += sws2[s];
+                }
+            }
+        }
+    }
+    return FRESCO_OK;
+}
+
+void fill_info(const Params &P, int64_t n_points, int64_t n_k, const Folded &F, fresco_info *info) {
+    std::memset(info, 0, sizeof(*info));
+    info->dim = P.dim;
+    info->precision = P.precision;
+    info->width = P.width;
+    for (int a = 0; a < 3; ++a) {
+        info->n_fine[a] = P.nf[a];
+        info->k_max[a] = P.kmax[a];
+        info->tile[a] = P.tmax[a];
+        info->n_tiles[a] = P.nb[a];
+    }
+    info->beta = P.beta;
+    info->upsample = P.sigma;
+    info->loss_const = F.loss_const;
+    info->n_points = n_points;
+    info->n_modes = n_k;
+    info->n_rep = (int64_t)F.s0.size();
+}
+
+// ---- device helpers --------------------------------------------------------------------------
+
+fresco_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FRESCO_OK;
+    if (e == cudaErrorMemoryAllocation) return FRESCO_ERR_OOM;
+    return FRESCO_ERR_CUDA;
+}
+
+#define FR_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            fresco_status st_ = cuda_status(e_);              \
+            return st_;                                       \
+        }                                                     \
+    } while (0)
+
+#define FR_CUFFT(call)                                        \
+    do {                                                      \
+        cufftResult r_ = (call);                              \
+        if (r_ != CUFFT_SUCCESS)                              \
+            return r_ == CUFFT_ALLOC_FAILED ? FRESCO_ERR_OOM : FRESCO_ERR_CUFFT; \
+    } while (0)
+
+template <typename P>
+fresco_status dalloc(fresco_plan_s *p, P **ptr, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return FRESCO_ERR_OOM;
+    }
+    p->device_bytes += (int64_t)bytes;
+    *ptr = (P *)v;
+    return FRESCO_OK;
+}
+
+void release(fresco_plan_s *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    void *bufs[] = {p->d_sorted, p->d_perm, p->d_key, p->d_slot, p->d_cnt, p->d_off,
+                    p->d_block_sums, p->d_grid, p->d_spec, p->d_hc[0], p->d_hc[1], p->d_r[0],
+                    p->d_r[1], p->d_g[0], p->d_g[1], p->d_rep_n, p->d_rep_s0, p->d_rep_w,
+                    p->d_ip[0], p->d_ip[1], p->d_ip[2], p->d_partial, p->d_err,
+                    p->d_mask_orig, p->d_fft_work, p->d_stage_pts, p->d_stage_grad,
+                    p->d_stage_loss};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    cufftHandle hs[] = {p->fft_rows, p->fft_cols, p->ifft_cols, p->ifft_rows};
+    for (int i = 0; i < 4; ++i)
+        if (p->have_fft[i]) cufftDestroy(hs[i]);
+    for (auto &r : p->ev_used) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : p->ev_free) cudaEventDestroy(e);
+    delete p;
+}
+
+template <typename T>
+cufftType r2c_type();
+template <>
+cufftType r2c_type<float>() { return CUFFT_R2C; }
+template <>
+cufftType r2c_type<double>() { return CUFFT_D2Z; }
+template <typename T>
+cufftType c2c_type();
+template <>
+cufftType c2c_type<float>() { return CUFFT_C2C; }
+template <>
+cufftType c2c_type<double>() { return CUFFT_Z2Z; }
+
+// Four batched 1D / (d-1)-D plans implement the pruned d-dimensional transforms:
+//   forward: R2C along x for every row, then C2C over (z, y) only for columns x in [0, kx];
+//   inverse: C2C over (z, y) for the kx + 1 nonzero columns of each sign of n_x (the compact
+//            spectrum is read, the full-width buffer R is written; columns of R that no mask
+//            entry reaches are zero from plan time and are never written), then C2C along x.
+template <typename T>
+fresco_status make_ffts(fresco_plan_s *p) {
+    const Params *unused = nullptr;
+    (void)unused;
+    const int dim = p->dim;
+    const int nf0 = p->geom.nf[0], nf1 = p->geom.nf[1], nf2 = p->geom.nf[2];
+    const long long rows = (long long)nf1 * nf2;
+    const long long half = nf0 / 2 + 1;
+    const long long kx = p->mgeom.kx;
+    const long long hcw = p->mgeom.hc_row;
+    size_t ws[4] = {0, 0, 0, 0};
+    cufftHandle *hs[4] = {&p->fft_rows, &p->fft_cols, &p->ifft_cols, &p->ifft_rows};
+    for (int i = 0; i < 4; ++i) {
+        FR_CUFFT(cufftCreate(hs[i]));
+        p->have_fft[i] = true;
+        FR_CUFFT(cufftSetAutoAllocation(*hs[i], 0));
+    }
+    {   // rows, forward R2C
+        long long n[1] = {nf0};
+        FR_CUFFT(cufftMakePlanMany64(p->fft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, half,
+                                     r2c_type<T>(), rows, &ws[0]));
+    }
+    long long cn[2], emb[2];
+    int crank = dim - 1;
+    if (dim == 2) {
+        cn[0] = nf1;
+        emb[0] = nf1;
+    } else {
+        cn[0] = nf2;
+        cn[1] = nf1;
+        emb[0] = nf2;
+        emb[1] = nf1;
+    }
+    FR_CUFFT(cufftMakePlanMany64(p->fft_cols, crank, cn, emb, half, 1, emb, half, 1, c2c_type<T>(),
+                                 kx + 1, &ws[1]));
+    FR_CUFFT(cufftMakePlanMany64(p->ifft_cols, crank, cn, emb, hcw, 1, emb, nf0, 1, c2c_type<T>(),
+                                 kx + 1, &ws[2]));
+    {
+        long long n[1] = {nf0};
+        FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, nf0,
+                                     c2c_type<T>(), rows, &ws[3]));
+    }
+    size_t wmax = std::max(std::max(ws[0], ws[1]), std::max(ws[2], ws[3]));
+    fresco_status st = dalloc(p, &p->d_fft_work, wmax);
+    if (st) return st;
+    for (int i = 0; i < 4; ++i) {
+        FR_CUFFT(cufftSetWorkArea(*hs[i], p->d_fft_work));
+        FR_CUFFT(cufftSetStream(*hs[i], p->stream));
+    }
+    return FRESCO_OK;
+}
+
+template <typename T>
+fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const int dim = p->dim;
+    Geom &g = p->geom;
+    g.dim = dim;
+    for (int a = 0; a < 3; ++a) {
+        g.nf[a] = P.nf[a];
+        g.nb[a] = P.nb[a];
+        g.tmax[a] = P.tmax[a];
+        double s = a < dim ? (double)P.nf[a] / p->box[a] : 0.0;
+        double shi = (double)(T)s;
+        long double slo = (long double)P.nf[a] / (long double)(a < dim ? p->box[a] : 1.0) -
+                          (long double)shi;
+        g.s_hi[a] = shi;
+        g.s_lo[a] = a < dim ? (double)(T)(double)slo : 0.0;
+    }
+    g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
+    g.n_points = p->n_points;
+    g.width = P.width;
+    g.beta = P.beta;
+
+    MaskGeom &m = p->mgeom;
+    m.dim = dim;
+    for (int a = 0; a < 3; ++a) {
+        m.nf[a] = P.nf[a];
+        m.kscale[a] = a < dim ? 2.0 * kPi / p->box[a] : 0.0;
+    }
+    m.kx = P.kmax[0];
+    m.n_rep = (int64_t)F.s0.size();
+    m.half_row = P.nf[0] / 2 + 1;
+    m.hc_row = 2 * (int64_t)P.kmax[0] + 2;
+    m.inv_n = 1.0 / (double)p->n_points;
+    p->n_pipes = dim == 2 ? 1 : 2;
+
+    // shared memory budget
+    int dev = 0;
+    FR_CUDA(cudaGetDevice(&dev));
+    int smem_optin = 0;
+    FR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (Launch<T>::spread_smem(g) > smem_optin || Launch<T>::interp_smem(g) > smem_optin)
+        return FRESCO_ERR_UNSUPPORTED;
+
+    const int64_t N = p->n_points;
+    const int64_t cells = (int64_t)P.nf[0] * P.nf[1] * P.nf[2];
+    const int64_t rows = (int64_t)P.nf[1] * P.nf[2];
+    const int pw = dim == 3 ? 4 : 2;
+    fresco_status st;
+    if ((st = dalloc(p, &p->d_sorted, sizeof(T) * (size_t)N * pw))) return st;
+    if ((st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)N))) return st;
+    if ((st = dalloc(p, &p->d_key, sizeof(int) * (size_t)N))) return st;
+    if ((st = dalloc(p, &p->d_slot, sizeof(int) * (size_t)N))) return st;
+    if ((st = dalloc(p, &p->d_cnt, sizeof(int) * (size_t)g.n_tiles))) return st;
+    if ((st = dalloc(p, &p->d_off, sizeof(int) * (size_t)(g.n_tiles + 1)))) return st;
+    if ((st = dalloc(p, &p->d_block_sums, sizeof(int) * (size_t)((g.n_tiles + 1023) / 1024 + 1))))
+        return st;
+    if ((st = dalloc(p, &p->d_grid, sizeof(T) * (size_t)cells))) return st;
+    if ((st = dalloc(p, &p->d_spec, sizeof(C2) * (size_t)(rows * m.half_row)))) return st;
+    for (int q = 0; q < p->n_pipes; ++q) {
+        if ((st = dalloc(p, &p->d_hc[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
+        if ((st = dalloc(p, &p->d_r[q], sizeof(C2) * (size_t)cells))) return st;
+        if ((st = dalloc(p, &p->d_g[q], sizeof(C2) * (size_t)cells))) return st;
+        FR_CUDA(cudaMemsetAsync(p->d_hc[q], 0, sizeof(C2) * (size_t)(rows * m.hc_row), p->stream));
+        FR_CUDA(cudaMemsetAsync(p->d_r[q], 0, sizeof(C2) * (size_t)cells, p->stream));
+    }
+    const int64_t nrep = m.n_rep;
+    if ((st = dalloc(p, &p->d_rep_n, sizeof(int) * (size_t)(nrep * dim)))) return st;
+    if ((st = dalloc(p, &p->d_rep_s0, sizeof(T) * (size_t)nrep))) return st;
+    if ((st = dalloc(p, &p->d_rep_w, sizeof(T) * (size_t)nrep))) return st;
+    p->n_mask_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((nrep + 255) / 256, 152 * 8));
+    if ((st = dalloc(p, &p->d_partial, sizeof(double) * (size_t)p->n_mask_blocks))) return st;
+    if ((st = dalloc(p, &p->d_err, sizeof(int)))) return st;
+    FR_CUDA(cudaMemsetAsync(p->d_err, 0, sizeof(int), p->stream));
+
+    {   // representatives
+        std::vector<T> s0(nrep), w(nrep);
+        for (int64_t i = 0; i < nrep; ++i) {
+            s0[i] = (T)F.s0[i];
+            w[i] = (T)F.w[i];
+        }
+        FR_CUDA(cudaMemcpy(p->d_rep_n, F.n.data(), sizeof(int) * (size_t)(nrep * dim),
+                           cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(p->d_rep_s0, s0.data(), sizeof(T) * (size_t)nrep, cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(p->d_rep_w, w.data(), sizeof(T) * (size_t)nrep, cudaMemcpyHostToDevice));
+    }
+    for (int a = 0; a < dim; ++a) {   // 1 / Psi_a(nu), nu = 0..kmax[a]
+        const int64_t n_nu = P.kmax[a] + 1;
+        std::vector<double> ft(n_nu);
+        kernel_ft(P.width, P.beta, P.nf[a], n_nu, ft.data());
+        std::vector<T> ip(n_nu);
+        for (int64_t i = 0; i < n_nu; ++i) ip[i] = (T)(1.0 / ft[i]);
+        if ((st = dalloc(p, &p->d_ip[a], sizeof(T) * (size_t)n_nu))) return st;
+        FR_CUDA(cudaMemcpy(p->d_ip[a], ip.data(), sizeof(T) * (size_t)n_nu, cudaMemcpyHostToDevice));
+    }
+    if ((st = make_ffts<T>(p))) return st;
+    FR_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    return FRESCO_OK;
+}
+
+// ---- evaluation ------------------------------------------------------------------------------
+
+struct StageScope {
+    fresco_plan_s *p;
+    int stage;
+    cudaEvent_t b = nullptr;
+    StageScope(fresco_plan_s *p_, int s_) : p(p_), stage(s_) {
+        if (!p->profiling) return;
+        cudaEvent_t a = p->take_event();
+        b = p->take_event();
+        if (a && b) {
+            cudaEventRecord(a, p->stream);
+            p->ev_used.push_back({stage, a, b});
+        }
+    }
+    ~StageScope() {
+        if (b && p->profiling) cudaEventRecord(b, p->stream);
+    }
+};
+
+template <typename T>
+fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const Geom &g = p->geom;
+    const MaskGeom &m = p->mgeom;
+    cudaStream_t s = p->stream;
+    {
+        StageScope sc(p, ST_SORT);
+        FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_tiles, s));
+        FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
+        int nl = 0;
+        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_tiles, s, &nl));
+        FR_CUDA(Launch<T>::scatter(g, pts, p->d_key, p->d_slot, p->d_off, p->d_sorted, p->d_perm, s));
+        p->launches += 2 + nl;
+    }
+    {
+        StageScope sc(p, ST_SPREAD);
+        FR_CUDA(Launch<T>::spread(g, p->d_sorted, p->d_off, (T *)p->d_grid, s));
+        p->launches += 1;
+    }
+    {
+        StageScope sc(p, ST_FFT_FWD);
+        if (sizeof(T) == 4) {
+            FR_CUFFT(cufftExecR2C(p->fft_rows, (cufftReal *)p->d_grid, (cufftComplex *)p->d_spec));
+            FR_CUFFT(cufftExecC2C(p->fft_cols, (cufftComplex *)p->d_spec, (cufftComplex *)p->d_spec,
+                                  CUFFT_FORWARD));
+        } else {
+            FR_CUFFT(cufftExecD2Z(p->fft_rows, (cufftDoubleReal *)p->d_grid,
+                                  (cufftDoubleComplex *)p->d_spec));
+            FR_CUFFT(cufftExecZ2Z(p->fft_cols, (cufftDoubleComplex *)p->d_spec,
+                                  (cufftDoubleComplex *)p->d_spec, CUFFT_FORWARD));
+        }
+    }
+    {
+        StageScope sc(p, ST_MASK);
+        FR_CUDA(Launch<T>::mask(m, p->d_rep_n, (const T *)p->d_rep_s0, (const T *)p->d_rep_w,
+                                p->d_spec, (const T *)p->d_ip[0], (const T *)p->d_ip[1],
+                                (const T *)p->d_ip[2], p->d_hc[0], p->d_hc[1], p->d_partial,
+                                p->n_mask_blocks, s));
+        p->launches += 1;
+    }
+    {
+        StageScope sc(p, ST_LOSS);
+        FR_CUDA(Launch<T>::finalize(p->d_partial, p->n_mask_blocks, p->info.loss_const, loss, s));
+        p->launches += 1;
+    }
+    (void)sizeof(C2);
+    p->forward_done = true;
+    return FRESCO_OK;
+}
+
+template <typename T>
+fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
+    const Geom &g = p->geom;
+    const MaskGeom &m = p->mgeom;
+    cudaStream_t s = p->stream;
+    {
+        StageScope sc(p, ST_FFT_INV);
+        const int64_t kx = m.kx;
+        const int64_t nf0 = g.nf[0];
+        for (int q = 0; q < p->n_pipes; ++q) {
+            if (sizeof(T) == 4) {
+                cufftComplex *hc = (cufftComplex *)p->d_hc[q];
+                cufftComplex *r = (cufftComplex *)p->d_r[q];
+                FR_CUFFT(cufftExecC2C(p->ifft_cols, hc + (kx + 1), r, CUFFT_INVERSE));
+                FR_CUFFT(cufftExecC2C(p->ifft_cols, hc, r + (nf0 - kx - 1), CUFFT_INVERSE));
+                FR_CUFFT(cufftExecC2C(p->ifft_rows, r, (cufftComplex *)p->d_g[q], CUFFT_INVERSE));
+            } else {
+                cufftDoubleComplex *hc = (cufftDoubleComplex *)p->d_hc[q];
+                cufftDoubleComplex *r = (cufftDoubleComplex *)p->d_r[q];
+                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, hc + (kx + 1), r, CUFFT_INVERSE));
+                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, hc, r + (nf0 - kx - 1), CUFFT_INVERSE));
+                FR_CUFFT(cufftExecZ2Z(p->ifft_rows, r, (cufftDoubleComplex *)p->d_g[q],
+                                      CUFFT_INVERSE));
+            }
+        }
+    }
+    {
+        StageScope sc(p, ST_INTERP);
+        FR_CUDA(Launch<T>::interp(g, p->d_sorted, p->d_perm, p->d_off, p->d_g[0], p->d_g[1],
+                                  grad_out, grad, s));
+        p->launches += 1;
+    }
+    return FRESCO_OK;
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+fresco_status check_point_ptr(fresco_plan_s *p, const void *ptr) {
+    if (!ptr) return FRESCO_ERR_ARG;
+    size_t a = p->esize * (p->dim == 2 ? 2 : 1);
+    return aligned(ptr, a) ? FRESCO_OK : FRESCO_ERR_ARG;
+}
+
+}  // namespace
+
+// ---- profiling event pool (members used above) ----------------------------------------------
+cudaEvent_t fresco_plan_s::take_event() {
+    if (!ev_free.empty()) {
+        cudaEvent_t e = ev_free.back();
+        ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+void fresco_opts_default(fresco_opts *opts) {
+    if (!opts) return;
+    std::memset(opts, 0, sizeof(*opts));
+    opts->precision = FRESCO_F32;
+    opts->tol = 0.0;
+    opts->upsample = 2.0;
+}
+
+const char *fresco_status_string(fresco_status s) {
+    switch (s) {
+        case FRESCO_OK: return "ok";
+        case FRESCO_ERR_ARG: return "invalid argument";
+        case FRESCO_ERR_OOM: return "out of memory";
+        case FRESCO_ERR_CUFFT: return "cuFFT error";
+        case FRESCO_ERR_CUDA: return "CUDA error";
+        case FRESCO_ERR_NONFINITE: return "non-finite coordinate";
+        case FRESCO_ERR_BOUNDS: return "index out of bounds";
+        case FRESCO_ERR_TIMEOUT: return "device wait timed out";
+        case FRESCO_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+fresco_status fresco_kernel_ft(int width, double beta, int n_fine, int64_t n_nu, double *out) {
+    if (width < kMinWidth || width > kMaxWidth || !(beta > 0.0) || n_fine < 2 * width ||
+        n_nu < 0 || (n_nu > 0 && !out))
+        return FRESCO_ERR_ARG;
+    kernel_ft(width, beta, n_fine, n_nu, out);
+    return FRESCO_OK;
+}
+
+fresco_status fresco_plan_query(int dim, const double *box, int64_t n_points, const int32_t *mask,
+                                int64_t n_k, const double *S0, const double *W,
+                                const fresco_opts *opts, fresco_info *info) {
+    if (!info) return FRESCO_ERR_ARG;
+    Params P;
+    fresco_status st = check_and_params(dim, box, n_points, mask, n_k, S0, W, opts, P);
+    if (st) return st;
+    Folded F;
+    if ((st = fold_mask(P, mask, n_k, S0, W, F))) return st;
+    fill_info(P, n_points, n_k, F, info);
+    return FRESCO_OK;
+}
+
+fresco_status fresco_plan(fresco_plan_t *out, int dim, const double *box, int64_t n_points,
+                          const int32_t *mask, int64_t n_k, const double *S0, const double *W,
+                          const fresco_opts *opts, void *stream) {
+    if (!out) return FRESCO_ERR_ARG;
+    *out = nullptr;
+    Params P;
+    fresco_status st = check_and_params(dim, box, n_points, mask, n_k, S0, W, opts, P);
+    if (st) return st;
+    Folded F;
+    if ((st = fold_mask(P, mask, n_k, S0, W, F))) return st;
+    if (F.s0.empty()) return FRESCO_ERR_ARG;   // every weight zero: nothing to evaluate
+    fresco_plan_s *p = new (std::nothrow) fresco_plan_s();
+    if (!p) return FRESCO_ERR_OOM;
+    p->dim = dim;
+    p->precision = P.precision;
+    p->esize = P.precision == FRESCO_F64 ? 8 : 4;
+    for (int a = 0; a < dim; ++a) p->box[a] = box[a];
+    p->n_points = n_points;
+    p->n_k = n_k;
+    p->stream = (cudaStream_t)stream;
+    fill_info(P, n_points, n_k, F, &p->info);
+    try {
+        p->h_mask.assign(mask, mask + n_k * dim);
+    } catch (...) {
+        delete p;
+        return FRESCO_ERR_OOM;
+    }
+    st = P.precision == FRESCO_F64 ? build_plan<double>(p, P, F) : build_plan<float>(p, P, F);
+    if (st) {
+        release(p);
+        return st;
+    }
+    p->info.device_bytes = p->device_bytes;
+    *out = p;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_get_info(fresco_plan_t p, fresco_info *info) {
+    if (!p || !info) return FRESCO_ERR_ARG;
+    *info = p->info;
+    info->device_bytes = p->device_bytes;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_set_stream(fresco_plan_t p, void *stream) {
+    if (!p) return FRESCO_ERR_ARG;
+    p->stream = (cudaStream_t)stream;
+    cufftHandle hs[] = {p->fft_rows, p->fft_cols, p->ifft_cols, p->ifft_rows};
+    for (int i = 0; i < 4; ++i)
+        if (p->have_fft[i] && cufftSetStream(hs[i], p->stream) != CUFFT_SUCCESS)
+            return FRESCO_ERR_CUFFT;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_forward(fresco_plan_t p, const void *d_points, double *d_loss) {
+    if (!p || !d_loss) return FRESCO_ERR_ARG;
+    fresco_status st = check_point_ptr(p, d_points);
+    if (st) return st;
+    if (p->precision == FRESCO_F64) return forward_impl<double>(p, (const double *)d_points, d_loss);
+    return forward_impl<float>(p, (const float *)d_points, d_loss);
+}
+
+fresco_status fresco_backward(fresco_plan_t p, const double *d_grad_out, void *d_grad) {
+    if (!p || !p->forward_done) return FRESCO_ERR_ARG;
+    fresco_status st = check_point_ptr(p, d_grad);
+    if (st) return st;
+    if (p->precision == FRESCO_F64) return backward_impl<double>(p, d_grad_out, (double *)d_grad);
+    return backward_impl<float>(p, d_grad_out, (float *)d_grad);
+}
+
+fresco_status fresco_loss_grad(fresco_plan_t p, const void *d_points, double *d_loss, void *d_grad) {
+    fresco_status st = fresco_forward(p, d_points, d_loss);
+    if (st || !d_grad) return st;
+    return fresco_backward(p, nullptr, d_grad);
+}
+
+fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S) {
+    if (!p || !p->forward_done) return FRESCO_ERR_ARG;
+    if (!d_rho && !d_S) return FRESCO_OK;
+    if (!p->d_mask_orig) {
+        fresco_status st = dalloc(p, &p->d_mask_orig, sizeof(int) * p->h_mask.size());
+        if (st) return st;
+        FR_CUDA(cudaMemcpyAsync(p->d_mask_orig, p->h_mask.data(), sizeof(int) * p->h_mask.size(),
+                                cudaMemcpyHostToDevice, p->stream));
+    }
+    cudaError_t e;
+    if (p->precision == FRESCO_F64)
+        e = Launch<double>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_spec,
+                                  (const double *)p->d_ip[0], (const double *)p->d_ip[1],
+                                  (const double *)p->d_ip[2], (double *)d_rho, (double *)d_S,
+                                  p->stream);
+    else
+        e = Launch<float>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_spec,
+                                 (const float *)p->d_ip[0], (const float *)p->d_ip[1],
+                                 (const float *)p->d_ip[2], (float *)d_rho, (float *)d_S,
+                                 p->stream);
+    p->launches += 1;
+    return cuda_status(e);
+}
+
+fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, double *h_loss,
+                                    void *h_grad) {
+    if (!p || !h_points || !h_loss) return FRESCO_ERR_ARG;
+    const size_t bytes = p->esize * (size_t)p->n_points * p->dim;
+    fresco_status st;
+    if (!p->d_stage_pts && (st = dalloc(p, &p->d_stage_pts, bytes))) return st;
+    if (!p->d_stage_grad && (st = dalloc(p, &p->d_stage_grad, bytes))) return st;
+    if (!p->d_stage_loss && (st = dalloc(p, &p->d_stage_loss, sizeof(double)))) return st;
+    FR_CUDA(cudaMemcpyAsync(p->d_stage_pts, h_points, bytes, cudaMemcpyHostToDevice, p->stream));
+    st = fresco_loss_grad(p, p->d_stage_pts, p->d_stage_loss, h_grad ? p->d_stage_grad : nullptr);
+    if (st) return st;
+    FR_CUDA(cudaMemcpyAsync(h_loss, p->d_stage_loss, sizeof(double), cudaMemcpyDeviceToHost,
+                            p->stream));
+    if (h_grad)
+        FR_CUDA(cudaMemcpyAsync(h_grad, p->d_stage_grad, bytes, cudaMemcpyDeviceToHost, p->stream));
+    FR_CUDA(cudaStreamSynchronize(p->stream));
+    return FRESCO_OK;
+}
+
+fresco_status fresco_status_check(fresco_plan_t p) {
+    if (!p) return FRESCO_ERR_ARG;
+    FR_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    int err = 0;
+    FR_CUDA(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        int zero = 0;
+        FR_CUDA(cudaMemcpy(p->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        if (err & 1) return FRESCO_ERR_NONFINITE;
+        return FRESCO_ERR_BOUNDS;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+fresco_status fresco_profile(fresco_plan_t p, int enable) {
+    if (!p) return FRESCO_ERR_ARG;
+    p->profiling = enable != 0;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_profile_read(fresco_plan_t p, double *ms, int64_t *counts) {
+    if (!p || !ms) return FRESCO_ERR_ARG;
+    FR_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    for (auto &r : p->ev_used) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            p->stage_ms[r.stage] += t;
+            p->stage_calls[r.stage] += 1;
+        }
+        p->ev_free.push_back(r.a);
+        p->ev_free.push_back(r.b);
+    }
+    p->ev_used.clear();
+    for (int i = 0; i < FRESCO_N_STAGES; ++i) {
+        ms[i] = p->stage_ms[i];
+        if (counts) counts[i] = p->stage_calls[i];
+        p->stage_ms[i] = 0.0;
+        p->stage_calls[i] = 0;
+    }
+    return FRESCO_OK;
+}
+
+int64_t fresco_launch_count(fresco_plan_t p) { return p ? p->launches : -1; }
+
+fresco_status fresco_destroy(fresco_plan_t p) {
+    release(p);
+    return FRESCO_OK;
+}
+
+}  // extern "C"

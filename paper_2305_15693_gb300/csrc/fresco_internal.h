@@ -1,0 +1,146 @@
+// Internal declarations shared by the host code and the kernel translation units of libfresco.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "fresco.h"
+
+namespace fresco {
+
+constexpr int kMaxWidth = 16;     // largest ES kernel width instantiated
+constexpr int kMinWidth = 2;
+constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
+
+// Geometry of the fine grid and its tiling, passed by value to kernels.
+// Axis 0 is x, the contiguous axis of every grid. Tile b on axis a covers fine cells
+// [start(b), start(b+1)) with start(b) = floor(b * nf[a] / nb[a]).
+struct Geom {
+    int dim;
+    int nf[3];          // fine grid size per axis (1 for unused axes)
+    int nb[3];          // tiles per axis (1 for unused axes)
+    int tmax[3];        // widest tile per axis (1 for unused axes)
+    int64_t n_tiles;
+    int64_t n_points;
+    int width;          // ES kernel width w
+    double beta;        // ES kernel shape
+    double s_hi[3];     // n_f / L split as s_hi + s_lo (s_hi exact in the working precision)
+    double s_lo[3];
+};
+
+__host__ __device__ inline int tile_start(int b, int nf, int nb) {
+    return (int)(((int64_t)b * nf) / nb);
+}
+__host__ __device__ inline int tile_of_cell(int c, int nf, int nb) {
+    return (int)((((int64_t)c + 1) * nb - 1) / nf);
+}
+
+// Geometry of the mask and the spectra.
+struct MaskGeom {
+    int dim;
+    int nf[3];
+    int kx;              // max n_x over representatives (>= 0)
+    int64_t n_rep;
+    int64_t half_row;    // nf[0] / 2 + 1: row length of the forward half spectrum
+    int64_t hc_row;      // 2 * kx + 2: row length of the compact backward spectrum
+    double inv_n;        // 1 / N
+    double kscale[3];    // 2 pi / L_a
+};
+
+enum Stage { ST_SORT = 0, ST_SPREAD, ST_FFT_FWD, ST_MASK, ST_LOSS, ST_FFT_INV, ST_INTERP,
+             ST_COUNT };
+
+// Launchers, instantiated for T = float and T = double. All take the plan's stream and
+// return the cudaError_t of the launch. Element layouts are documented in fresco_kernels.cuh.
+template <typename T>
+struct Launch {
+    static cudaError_t bin(const Geom &g, const T *points, int *cnt, int *key, int *slot,
+                           int *err, cudaStream_t s);
+    static cudaError_t scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
+                            int *launches);
+    static cudaError_t scatter(const Geom &g, const T *points, const int *key, const int *slot,
+                               const int *off, void *sorted, int *perm, cudaStream_t s);
+    static cudaError_t spread(const Geom &g, const void *sorted, const int *off, T *grid,
+                              cudaStream_t s);
+    static cudaError_t mask(const MaskGeom &m, const int *rep_n, const T *rep_s0, const T *rep_w,
+                            const void *spec, const T *ip0, const T *ip1, const T *ip2,
+                            void *hc0, void *hc1, double *partial, int n_blocks, cudaStream_t s);
+    static cudaError_t finalize(const double *partial, int n_blocks, double loss_const,
+                                double *loss, cudaStream_t s);
+    static cudaError_t interp(const Geom &g, const void *sorted, const int *perm, const int *off,
+                              const void *g0, const void *g1, const double *grad_out, T *grad,
+                              cudaStream_t s);
+    static cudaError_t rho_s(const MaskGeom &m, const int *mask_n, int64_t n_k, const void *spec,
+                             const T *ip0, const T *ip1, const T *ip2, T *rho, T *S,
+                             cudaStream_t s);
+    static int spread_smem(const Geom &g);
+    static int interp_smem(const Geom &g);
+};
+
+}  // namespace fresco
+
+// The plan object behind fresco_plan_t.
+struct fresco_plan_s {
+    int dim = 0;
+    int precision = FRESCO_F32;
+    size_t esize = 4;                // sizeof(T)
+    double box[3] = {1, 1, 1};
+    int64_t n_points = 0;
+    int64_t n_k = 0;
+    fresco::Geom geom{};
+    fresco::MaskGeom mgeom{};
+    fresco_info info{};
+    cudaStream_t stream = nullptr;
+
+    // host copy of the mask as given (for fresco_get_rho_S)
+    std::vector<int32_t> h_mask;
+
+    // device buffers (owned)
+    void *d_sorted = nullptr;        // packed tile-relative coordinates, sorted by tile
+    int *d_perm = nullptr;           // sorted position -> caller index
+    int *d_key = nullptr;            // caller index -> tile id
+    int *d_slot = nullptr;           // caller index -> rank within its tile
+    int *d_cnt = nullptr;            // [n_tiles] points per tile
+    int *d_off = nullptr;            // [n_tiles + 1] exclusive prefix sum of d_cnt
+    int *d_block_sums = nullptr;     // scan scratch
+    void *d_grid = nullptr;          // real fine grid (spread output)
+    void *d_spec = nullptr;          // complex forward half spectrum
+    void *d_hc[2] = {nullptr, nullptr};   // compact backward spectra (gradient coefficients)
+    void *d_r[2] = {nullptr, nullptr};    // after the column pass (middle columns stay zero)
+    void *d_g[2] = {nullptr, nullptr};    // complex gradient grids (components packed re/im)
+    int *d_rep_n = nullptr;          // [n_rep][dim] half-space representatives
+    void *d_rep_s0 = nullptr;        // [n_rep] folded S0'
+    void *d_rep_w = nullptr;         // [n_rep] folded W'
+    void *d_ip[3] = {nullptr, nullptr, nullptr};  // 1 / Psi_a(nu), nu = 0..k_max[a]
+    double *d_partial = nullptr;     // per-block loss partial sums
+    int *d_err = nullptr;            // device error word
+    int *d_mask_orig = nullptr;      // lazily uploaded mask (fresco_get_rho_S)
+    void *d_fft_work = nullptr;
+    void *d_stage_pts = nullptr;     // staging for fresco_loss_grad_host
+    void *d_stage_grad = nullptr;
+    double *d_stage_loss = nullptr;
+    int n_mask_blocks = 0;
+    int n_pipes = 1;                 // complex gradient pipelines: ceil(dim / 2)
+    int64_t device_bytes = 0;
+
+    // cuFFT plans
+    cufftHandle fft_rows = 0;        // R2C along x, all rows
+    cufftHandle fft_cols = 0;        // C2C forward over the other axes, columns x in [0, kx]
+    cufftHandle ifft_cols = 0;       // C2C inverse over the other axes, kx + 1 columns
+    cufftHandle ifft_rows = 0;       // C2C inverse along x, all rows
+    bool have_fft[4] = {false, false, false, false};
+
+    // profiling: a pool of CUDA events, one (start, end) pair per recorded stage
+    struct EvRec { int stage; cudaEvent_t a, b; };
+    bool profiling = false;
+    std::vector<EvRec> ev_used;
+    std::vector<cudaEvent_t> ev_free;
+    cudaEvent_t take_event();
+    double stage_ms[fresco::ST_COUNT] = {};
+    int64_t stage_calls[fresco::ST_COUNT] = {};
+    int64_t launches = 0;
+    bool forward_done = false;
+};

@@ -1,0 +1,759 @@
+// CUDA kernels of libfresco for sm_103a, templated on the working precision T (float / double).
+//
+// Data layouts (axis 0 = x is contiguous everywhere):
+//   points      [N][D] caller order, type T.
+//   sorted      packed tile-relative coordinates in tile order: PD = (D == 3 ? 4 : 2) words of
+//               type U per point (U = uint32 for float, uint64 for double); word a holds the cell
+//               of the point relative to its tile origin in the top 8 bits and the fractional
+//               position inside that cell, frac * 2^FB, in the low FB bits (FB = 24 / 56).
+//   perm        [N] sorted position -> caller index.
+//   off         [n_tiles + 1] first sorted position of each tile.
+//   grid        real fine grid [nf2][nf1][nf0].
+//   spec        forward half spectrum [nf2][nf1][nf0/2 + 1], complex T.
+//   hc          compact backward spectrum [nf2][nf1][2 kx + 2]: column c holds n_x = c - kx - 1.
+//   g           complex gradient grid [nf2][nf1][nf0]: re = d/dr_x, im = d/dr_y (pipeline 0),
+//               re = d/dr_z (pipeline 1, 3D only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fresco_internal.h"
+
+namespace fresco {
+
+template <typename T> struct PT;
+template <> struct PT<float> {
+    using C = float2;
+    using U = uint32_t;
+    static constexpr int FB = 24;
+};
+template <> struct PT<double> {
+    using C = double2;
+    using U = uint64_t;
+    static constexpr int FB = 56;
+};
+
+template <int D> struct PackedWords { static constexpr int value = (D == 3) ? 4 : 2; };
+
+// ---------------------------------------------------------------------------------------------
+// Fine-grid coordinate t = r * n_f / L of one coordinate, split into a cell index in [0, n_f)
+// and a fraction in [0, 1). The product uses the two-term scale s_hi + s_lo and an fma residual,
+// so the fraction is accurate to the working precision even when t is large (for n_f = 25000
+// in float a plain product would carry ~1e-3 cells of error).
+template <typename T>
+__device__ __forceinline__ bool fine_coord(T r, T s_hi, T s_lo, int nf, int &cell, T &frac) {
+    bool ok = isfinite(r);
+    if (!ok) r = T(0);
+    T p = r * s_hi;
+    T e = fma(r, s_hi, -p);
+    T lo = fma(r, s_lo, e);
+    T c = floor(p);
+    T f = (p - c) + lo;
+    if (f < T(0)) { c -= T(1); f += T(1); }
+    if (f >= T(1)) { c += T(1); f -= T(1); }
+    long long ci = (long long)c;
+    ci %= nf;
+    if (ci < 0) ci += nf;
+    cell = (int)ci;
+    frac = f;
+    return ok;
+}
+
+template <typename T>
+__device__ __forceinline__ typename PT<T>::U pack_coord(int rel, T frac) {
+    using U = typename PT<T>::U;
+    const T scale = T((U)1 << PT<T>::FB);
+    return ((U)rel << PT<T>::FB) | (U)(frac * scale);
+}
+
+template <typename T>
+__device__ __forceinline__ void unpack_coord(typename PT<T>::U u, int &rel, T &frac) {
+    using U = typename PT<T>::U;
+    rel = (int)(u >> PT<T>::FB);
+    const U m = ((U)1 << PT<T>::FB) - 1;
+    frac = T(u & m) * (T(1) / T((U)1 << PT<T>::FB));
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void load_packed(const typename PT<T>::U *__restrict__ s, int64_t p,
+                                            typename PT<T>::U (&u)[3]) {
+    if constexpr (sizeof(T) == 4 && D == 2) {
+        uint2 v = reinterpret_cast<const uint2 *>(s)[p];
+        u[0] = v.x; u[1] = v.y; u[2] = 0;
+    } else if constexpr (sizeof(T) == 4) {
+        uint4 v = reinterpret_cast<const uint4 *>(s)[p];
+        u[0] = v.x; u[1] = v.y; u[2] = v.z;
+    } else if constexpr (D == 2) {
+        ulonglong2 v = reinterpret_cast<const ulonglong2 *>(s)[p];
+        u[0] = v.x; u[1] = v.y; u[2] = 0;
+    } else {
+        ulonglong2 v0 = reinterpret_cast<const ulonglong2 *>(s)[2 * p];
+        ulonglong2 v1 = reinterpret_cast<const ulonglong2 *>(s)[2 * p + 1];
+        u[0] = v0.x; u[1] = v0.y; u[2] = v1.x;
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void store_packed(typename PT<T>::U *__restrict__ s, int64_t p,
+                                             const typename PT<T>::U (&u)[3]) {
+    if constexpr (sizeof(T) == 4 && D == 2) {
+        reinterpret_cast<uint2 *>(s)[p] = make_uint2(u[0], u[1]);
+    } else if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<uint4 *>(s)[p] = make_uint4(u[0], u[1], u[2], 0u);
+    } else if constexpr (D == 2) {
+        reinterpret_cast<ulonglong2 *>(s)[p] = make_ulonglong2(u[0], u[1]);
+    } else {
+        reinterpret_cast<ulonglong2 *>(s)[2 * p] = make_ulonglong2(u[0], u[1]);
+        reinterpret_cast<ulonglong2 *>(s)[2 * p + 1] = make_ulonglong2(u[2], 0ull);
+    }
+}
+
+// ES kernel weights psi(x1 + k), k = 0..W-1, psi(u) = exp(beta (sqrt(1 - z^2) - 1)), z = 2u/W.
+// sqrt(1 - z^2) - 1 is evaluated as -z^2 / (1 + sqrt(1 - z^2)), free of cancellation near z = 0.
+template <typename T, int W>
+__device__ __forceinline__ void es_weights(T x1, T beta, T inv_hw, T (&w)[W]) {
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        T z = (x1 + T(k)) * inv_hw;
+        T z2 = z * z;
+        T s = sqrt(fmax(T(1) - z2, T(0)));
+        w[k] = exp(-beta * z2 / (T(1) + s));
+    }
+}
+
+// Start of the kernel support (first cell) relative to the cell holding the point, and the
+// offset x1 = start - t in [-W/2, -W/2 + 1).
+template <typename T, int W>
+__device__ __forceinline__ int support_start(T frac, T &x1) {
+    T c = ceil(frac - T(0.5) * T(W));
+    x1 = c - frac;
+    return (int)c;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K1a: wrap, fine cell, tile id and the rank of each point within its tile.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_bin(Geom g, const T *__restrict__ pts,
+                                             int *__restrict__ cnt, int *__restrict__ key,
+                                             int *__restrict__ slot, int *__restrict__ err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.n_points;
+         j += stride) {
+        bool ok = true;
+        int t[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int cell;
+            T frac;
+            ok &= fine_coord<T>(pts[j * D + a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+            t[a] = tile_of_cell(cell, g.nf[a], g.nb[a]);
+        }
+        if (!ok) atomicOr(err, 1);
+        int lin = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
+        key[j] = lin;
+        slot[j] = atomicAdd(&cnt[lin], 1);
+    }
+}
+
+// K1b: exclusive prefix sum of the tile counts, in three passes over blocks of 1024.
+static __global__ void __launch_bounds__(1024) k_scan_blocks(const int *__restrict__ cnt,
+                                                      int *__restrict__ off,
+                                                      int *__restrict__ bsum, int64_t n) {
+    __shared__ int warp_tot[32];
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    int v = (i < n) ? cnt[i] : 0;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int w = warp_tot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
+    if (i < n) off[i] = incl - v;
+    if (threadIdx.x == 1023) bsum[blockIdx.x] = incl;
+}
+
+static __global__ void __launch_bounds__(1024) k_scan_sums(int *__restrict__ bsum, int64_t nb,
+                                                    int *__restrict__ off_end) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += 1024) {
+        int64_t i = base + threadIdx.x;
+        int v = (i < nb) ? bsum[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
+        if (i < nb) bsum[i] = carry + incl - v;  // exclusive
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *off_end = carry;
+}
+
+static __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ off,
+                                                   const int *__restrict__ bsum, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    if (i < n) off[i] += bsum[blockIdx.x];
+}
+
+// K1c: scatter every point to its tile's slice of the sorted arrays.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ pts,
+                                                 const int *__restrict__ key,
+                                                 const int *__restrict__ slot,
+                                                 const int *__restrict__ off,
+                                                 typename PT<T>::U *__restrict__ sorted,
+                                                 int *__restrict__ perm) {
+    using U = typename PT<T>::U;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.n_points;
+         j += stride) {
+        int lin = key[j];
+        int64_t pos = (int64_t)off[lin] + slot[j];
+        int tc[3] = {lin % g.nb[0], (lin / g.nb[0]) % g.nb[1], lin / (g.nb[0] * g.nb[1])};
+        U u[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int cell;
+            T frac;
+            fine_coord<T>(pts[j * D + a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+            int rel = cell - tile_start(tc[a], g.nf[a], g.nb[a]);
+            u[a] = pack_coord<T>(rel, frac);
+        }
+        store_packed<T, D>(sorted, pos, u);
+        perm[pos] = (int)j;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K2: type-1 spreading. One block owns one tile of the fine grid: it accumulates, in shared
+// memory, the kernel contributions of every point (from its own tile and the 3^D neighbouring
+// tiles, periodic images included) that land inside the tile, then writes the tile to the grid
+// with plain coalesced stores. Every cell is written exactly once per call: no zero fill of the
+// grid and no global atomics.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256) k_spread(Geom g, const typename PT<T>::U *__restrict__ sorted,
+                                                const int *__restrict__ off, T *__restrict__ grid) {
+    using U = typename PT<T>::U;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *tile = reinterpret_cast<T *>(sm_raw);
+
+    const int64_t t = blockIdx.x;
+    const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
+                       (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
+    int s[3], wd[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            s[a] = tile_start(tc[a], g.nf[a], g.nb[a]);
+            wd[a] = tile_start(tc[a] + 1, g.nf[a], g.nb[a]) - s[a];
+        } else {
+            s[a] = 0;
+            wd[a] = 1;
+        }
+    }
+    const int sx = wd[0], sxy = wd[0] * wd[1], cells = sxy * wd[2];
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = T(0);
+    __syncthreads();
+
+    const T beta = (T)g.beta;
+    const T inv_hw = T(2) / T(W);
+    const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int dd[3] = {dx, dy, dz};
+                int nt[3], org[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (a < D) {
+                        int b = tc[a] + dd[a], shift = 0;
+                        if (b < 0) { b += g.nb[a]; shift = -g.nf[a]; }
+                        else if (b >= g.nb[a]) { b -= g.nb[a]; shift = g.nf[a]; }
+                        nt[a] = b;
+                        org[a] = tile_start(b, g.nf[a], g.nb[a]) + shift - s[a];
+                    } else {
+                        nt[a] = 0;
+                        org[a] = 0;
+                    }
+                }
+                const int64_t nl = nt[0] + (int64_t)g.nb[0] * (nt[1] + (int64_t)g.nb[1] * nt[2]);
+                const int p0 = off[nl], p1 = off[nl + 1];
+                for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                    U u[3];
+                    load_packed<T, D>(sorted, p, u);
+                    int i0[3] = {0, 0, 0};
+                    T x1[3] = {T(0), T(0), T(0)};
+                    bool hit = true;
+#pragma unroll
+                    for (int a = 0; a < D; ++a) {
+                        int rel;
+                        T f;
+                        unpack_coord<T>(u[a], rel, f);
+                        i0[a] = org[a] + rel + support_start<T, W>(f, x1[a]);
+                        hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
+                    }
+                    if (!hit) continue;
+                    T wx[W], wy[W];
+                    es_weights<T, W>(x1[0], beta, inv_hw, wx);
+                    es_weights<T, W>(x1[1], beta, inv_hw, wy);
+                    if constexpr (D == 2) {
+#pragma unroll
+                        for (int b = 0; b < W; ++b) {
+                            const int yy = i0[1] + b;
+                            if ((unsigned)yy < (unsigned)wd[1]) {
+                                T *row = tile + yy * sx;
+#pragma unroll
+                                for (int a = 0; a < W; ++a) {
+                                    const int xx = i0[0] + a;
+                                    if ((unsigned)xx < (unsigned)wd[0])
+                                        atomicAdd(row + xx, wy[b] * wx[a]);
+                                }
+                            }
+                        }
+                    } else {
+                        T wz[W];
+                        es_weights<T, W>(x1[2], beta, inv_hw, wz);
+#pragma unroll 1
+                        for (int c = 0; c < W; ++c) {
+                            const int zz = i0[2] + c;
+                            if ((unsigned)zz >= (unsigned)wd[2]) continue;
+#pragma unroll
+                            for (int b = 0; b < W; ++b) {
+                                const int yy = i0[1] + b;
+                                if ((unsigned)yy < (unsigned)wd[1]) {
+                                    T *row = tile + zz * sxy + yy * sx;
+                                    const T wzy = wz[c] * wy[b];
+#pragma unroll
+                                    for (int a = 0; a < W; ++a) {
+                                        const int xx = i0[0] + a;
+                                        if ((unsigned)xx < (unsigned)wd[0])
+                                            atomicAdd(row + xx, wzy * wx[a]);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+        const int x = i % sx, y = (i / sx) % wd[1], z = i / sxy;
+        grid[((int64_t)(s[2] + z) * g.nf[1] + (s[1] + y)) * g.nf[0] + s[0] + x] = tile[i];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// K4: deconvolve and crop to the mask, S, the loss partial sums and the gradient coefficients.
+// For each half-space representative n (n_x >= 0), with ip = 1 / Psi(n):
+//   rho = F(n) ip, S = |rho|^2 / N, loss += W' (S - S0')^2 (FP64),
+//   E = 4 W' (S - S0') / N, a_d = i k_d E rho (Eq. 4 coefficient, both members of the +-n pair),
+//   H[n] = (a_x + i a_y) ip / 2 and H[-n] = (conj a_x + i conj a_y) ip / 2 (pipeline 0),
+//   H1[n] = a_z ip / 2, H1[-n] = conj(a_z) ip / 2 (pipeline 1, 3D).
+// The inverse FFT of H then gives d/dr_x + i d/dr_y on the grid (before interpolation).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict__ rep_n,
+                                              const T *__restrict__ rep_s0,
+                                              const T *__restrict__ rep_w,
+                                              const typename PT<T>::C *__restrict__ spec,
+                                              const T *__restrict__ ip0, const T *__restrict__ ip1,
+                                              const T *__restrict__ ip2,
+                                              typename PT<T>::C *__restrict__ hc0,
+                                              typename PT<T>::C *__restrict__ hc1,
+                                              double *__restrict__ partial) {
+    using C = typename PT<T>::C;
+    double lsum = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T inv_n = (T)m.inv_n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m.n_rep; e += stride) {
+        const int nx = rep_n[e * D + 0];
+        const int ny = rep_n[e * D + 1];
+        const int nz = (D == 3) ? rep_n[e * D + 2] : 0;
+        const int ry = ny < 0 ? ny + m.nf[1] : ny;
+        const int rz = nz < 0 ? nz + m.nf[2] : nz;
+        const int64_t row = (int64_t)rz * m.nf[1] + ry;
+        const C F = spec[row * m.half_row + nx];
+        T ip = ip0[nx] * ip1[ny < 0 ? -ny : ny];
+        if (D == 3) ip *= ip2[nz < 0 ? -nz : nz];
+        const T re = F.x * ip, im = F.y * ip;
+        const T S = (re * re + im * im) * inv_n;
+        const double d = (double)S - (double)rep_s0[e];
+        const double wgt = (double)rep_w[e];
+        lsum += wgt * d * d;
+        const T E = (T)(4.0 * wgt * d * m.inv_n);
+        const T h = T(0.5) * ip * E;
+        const T er = re * h, ei = im * h;
+        const T kx = (T)(m.kscale[0] * nx), ky = (T)(m.kscale[1] * ny);
+        const int my = ny > 0 ? m.nf[1] - ny : -ny;
+        const int mz = nz > 0 ? m.nf[2] - nz : -nz;
+        const int64_t rowm = (int64_t)mz * m.nf[1] + my;
+        const int64_t cp = row * m.hc_row + (nx + m.kx + 1);
+        const int64_t cm = rowm * m.hc_row + (-nx + m.kx + 1);
+        hc0[cp] = C{-er * ky - ei * kx, er * kx - ei * ky};
+        hc0[cm] = C{er * ky - ei * kx, -er * kx - ei * ky};
+        if (D == 3) {
+            const T kz = (T)(m.kscale[2] * nz);
+            hc1[cp] = C{-kz * ei, kz * er};
+            hc1[cm] = C{-kz * ei, -kz * er};
+        }
+    }
+    // block reduction of the FP64 loss partials (fixed order: deterministic)
+    __shared__ double wsum[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w];
+        partial[blockIdx.x] = b;
+    }
+}
+
+// K5: second-stage loss sum in a fixed order, plus the folding constant.
+static __global__ void __launch_bounds__(512) k_finalize(const double *__restrict__ partial, int nb,
+                                                  double loss_const, double *__restrict__ loss) {
+    __shared__ double sm[512];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 512) v += partial[i];
+    sm[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 256; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = sm[0] + loss_const;
+}
+
+// ---------------------------------------------------------------------------------------------
+// K7: type-2 interpolation. One block per tile stages the tile plus a halo of the complex
+// gradient grid(s) in shared memory, then every point of the tile sums its W^D kernel-weighted
+// cells; the result, scaled by the incoming gradient, goes to the caller's order through perm.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U *__restrict__ sorted,
+                                                const int *__restrict__ perm,
+                                                const int *__restrict__ off,
+                                                const typename PT<T>::C *__restrict__ g0,
+                                                const typename PT<T>::C *__restrict__ g1,
+                                                const double *__restrict__ grad_out,
+                                                T *__restrict__ grad) {
+    using U = typename PT<T>::U;
+    using C = typename PT<T>::C;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+
+    const int64_t t = blockIdx.x;
+    const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
+                       (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
+    constexpr int HL = W / 2;  // halo before the tile; W - HL after it
+    int s[3], rw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            s[a] = tile_start(tc[a], g.nf[a], g.nb[a]);
+            rw[a] = tile_start(tc[a] + 1, g.nf[a], g.nb[a]) - s[a] + W;
+        } else {
+            s[a] = 0;
+            rw[a] = 1;
+        }
+    }
+    const int rxy = rw[0] * rw[1], cells = rxy * rw[2];
+    C *sg0 = reinterpret_cast<C *>(sm_raw);
+    T *sg1 = reinterpret_cast<T *>(sm_raw + sizeof(C) * (size_t)cells);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+        const int x = i % rw[0], y = (i / rw[0]) % rw[1], z = i / rxy;
+        int gx = s[0] - HL + x, gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
+        gx = (gx % g.nf[0] + g.nf[0]) % g.nf[0];
+        gy = (gy % g.nf[1] + g.nf[1]) % g.nf[1];
+        if (D == 3) gz = (gz % g.nf[2] + g.nf[2]) % g.nf[2];
+        const int64_t gi = ((int64_t)gz * g.nf[1] + gy) * g.nf[0] + gx;
+        sg0[i] = g0[gi];
+        if (D == 3) sg1[i] = g1[gi].x;
+    }
+    __syncthreads();
+
+    const T scale = grad_out ? (T)(*grad_out) : T(1);
+    const T beta = (T)g.beta;
+    const T inv_hw = T(2) / T(W);
+    const int p0 = off[t], p1 = off[t + 1];
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        U u[3];
+        load_packed<T, D>(sorted, p, u);
+        int i0[3] = {0, 0, 0};
+        T x1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int rel;
+            T f;
+            unpack_coord<T>(u[a], rel, f);
+            i0[a] = rel + support_start<T, W>(f, x1[a]) + HL;
+        }
+        T wx[W], wy[W];
+        es_weights<T, W>(x1[0], beta, inv_hw, wx);
+        es_weights<T, W>(x1[1], beta, inv_hw, wy);
+        T ax = T(0), ay = T(0), az = T(0);
+        if constexpr (D == 2) {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const C *row = sg0 + (i0[1] + b) * rw[0] + i0[0];
+                T rx = T(0), ry = T(0);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const C v = row[a];
+                    rx = fma(wx[a], v.x, rx);
+                    ry = fma(wx[a], v.y, ry);
+                }
+                ax = fma(wy[b], rx, ax);
+                ay = fma(wy[b], ry, ay);
+            }
+            const int64_t j = perm[p];
+            using T2 = typename PT<T>::C;
+            reinterpret_cast<T2 *>(grad)[j] = T2{scale * ax, scale * ay};
+        } else {
+            T wz[W];
+            es_weights<T, W>(x1[2], beta, inv_hw, wz);
+#pragma unroll 1
+            for (int c = 0; c < W; ++c) {
+                T px = T(0), py = T(0), pz = T(0);
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const int base = (i0[2] + c) * rxy + (i0[1] + b) * rw[0] + i0[0];
+                    T rx = T(0), ry = T(0), rz = T(0);
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const C v = sg0[base + a];
+                        rx = fma(wx[a], v.x, rx);
+                        ry = fma(wx[a], v.y, ry);
+                        rz = fma(wx[a], sg1[base + a], rz);
+                    }
+                    px = fma(wy[b], rx, px);
+                    py = fma(wy[b], ry, py);
+                    pz = fma(wy[b], rz, pz);
+                }
+                ax = fma(wz[c], px, ax);
+                ay = fma(wz[c], py, ay);
+                az = fma(wz[c], pz, az);
+            }
+            const int64_t j = perm[p];
+            grad[j * 3 + 0] = scale * ax;
+            grad[j * 3 + 1] = scale * ay;
+            grad[j * 3 + 2] = scale * az;
+        }
+    }
+}
+
+// rho and S for the mask rows as given to the plan (diagnostic output).
+template <typename T, int D>
+__global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
+                        const typename PT<T>::C *__restrict__ spec, const T *__restrict__ ip0,
+                        const T *__restrict__ ip1, const T *__restrict__ ip2, T *__restrict__ rho,
+                        T *__restrict__ S) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_k) return;
+    int nx = mask_n[q * D + 0], ny = mask_n[q * D + 1], nz = (D == 3) ? mask_n[q * D + 2] : 0;
+    T sgn = T(1);
+    if (nx < 0) { nx = -nx; ny = -ny; nz = -nz; sgn = T(-1); }   // rho(-n) = conj rho(n)
+    const int ry = ny < 0 ? ny + m.nf[1] : ny;
+    const int rz = nz < 0 ? nz + m.nf[2] : nz;
+    const auto F = spec[((int64_t)rz * m.nf[1] + ry) * m.half_row + nx];
+    T ip = ip0[nx] * ip1[ny < 0 ? -ny : ny];
+    if (D == 3) ip *= ip2[nz < 0 ? -nz : nz];
+    const T re = F.x * ip, im = sgn * F.y * ip;
+    if (rho) { rho[2 * q] = re; rho[2 * q + 1] = im; }
+    if (S) S[q] = (re * re + im * im) * (T)m.inv_n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launchers
+
+inline int grid_for(int64_t n, int threads, int cap) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename T>
+cudaError_t Launch<T>::bin(const Geom &g, const T *points, int *cnt, int *key, int *slot,
+                           int *err, cudaStream_t s) {
+    const int grid = grid_for(g.n_points, 256, 152 * 32);
+    if (g.dim == 2) k_bin<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
+    else k_bin<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
+                            int *launches) {
+    const int64_t nb = (n + 1023) / 1024;
+    k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(cnt, off, block_sums, n);
+    k_scan_sums<<<1, 1024, 0, s>>>(block_sums, nb, off + n);
+    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(off, block_sums, n);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::scatter(const Geom &g, const T *points, const int *key, const int *slot,
+                               const int *off, void *sorted, int *perm, cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int grid = grid_for(g.n_points, 256, 152 * 32);
+    if (g.dim == 2)
+        k_scatter<T, 2><<<grid, 256, 0, s>>>(g, points, key, slot, off, (U *)sorted, perm);
+    else
+        k_scatter<T, 3><<<grid, 256, 0, s>>>(g, points, key, slot, off, (U *)sorted, perm);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int Launch<T>::spread_smem(const Geom &g) {
+    return (int)(sizeof(T) * (size_t)g.tmax[0] * g.tmax[1] * (g.dim == 3 ? g.tmax[2] : 1));
+}
+
+template <typename T>
+int Launch<T>::interp_smem(const Geom &g) {
+    const int w = g.width;
+    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
+    size_t per = sizeof(typename PT<T>::C) + (g.dim == 3 ? sizeof(T) : 0);
+    return (int)(cells * per);
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_spread_w(const Geom &g, const void *sorted, const int *off, T *grid,
+                                   cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int smem = Launch<T>::spread_smem(g);
+    auto kern = k_spread<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, (const U *)sorted, off, grid);
+    return cudaGetLastError();
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_interp_w(const Geom &g, const void *sorted, const int *perm,
+                                   const int *off, const void *g0, const void *g1,
+                                   const double *grad_out, T *grad, cudaStream_t s) {
+    using U = typename PT<T>::U;
+    using C = typename PT<T>::C;
+    const int smem = Launch<T>::interp_smem(g);
+    auto kern = k_interp<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, (const U *)sorted, perm, off, (const C *)g0,
+                                                (const C *)g1, grad_out, grad);
+    return cudaGetLastError();
+}
+
+#define FRESCO_WIDTH_SWITCH(W_, CALL)                                                          \
+    switch (W_) {                                                                              \
+        case 2: { constexpr int WW = 2; CALL; }                                                \
+        case 3: { constexpr int WW = 3; CALL; }                                                \
+        case 4: { constexpr int WW = 4; CALL; }                                                \
+        case 5: { constexpr int WW = 5; CALL; }                                                \
+        case 6: { constexpr int WW = 6; CALL; }                                                \
+        case 7: { constexpr int WW = 7; CALL; }                                                \
+        case 8: { constexpr int WW = 8; CALL; }                                                \
+        case 9: { constexpr int WW = 9; CALL; }                                                \
+        case 10: { constexpr int WW = 10; CALL; }                                              \
+        case 11: { constexpr int WW = 11; CALL; }                                              \
+        case 12: { constexpr int WW = 12; CALL; }                                              \
+        case 13: { constexpr int WW = 13; CALL; }                                              \
+        case 14: { constexpr int WW = 14; CALL; }                                              \
+        case 15: { constexpr int WW = 15; CALL; }                                              \
+        case 16: { constexpr int WW = 16; CALL; }                                              \
+        default: return cudaErrorInvalidValue;                                                 \
+    }
+
+template <typename T>
+cudaError_t Launch<T>::spread(const Geom &g, const void *sorted, const int *off, T *grid,
+                              cudaStream_t s) {
+    if (g.dim == 2) {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_spread_w<T, WW, 2>(g, sorted, off, grid, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_spread_w<T, WW, 3>(g, sorted, off, grid, s)));
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::interp(const Geom &g, const void *sorted, const int *perm, const int *off,
+                              const void *g0, const void *g1, const double *grad_out, T *grad,
+                              cudaStream_t s) {
+    if (g.dim == 2) {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 2>(g, sorted, perm, off, g0,
+                                                                      g1, grad_out, grad, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 3>(g, sorted, perm, off, g0,
+                                                                      g1, grad_out, grad, s)));
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::mask(const MaskGeom &m, const int *rep_n, const T *rep_s0, const T *rep_w,
+                            const void *spec, const T *ip0, const T *ip1, const T *ip2, void *hc0,
+                            void *hc1, double *partial, int n_blocks, cudaStream_t s) {
+    using C = typename PT<T>::C;
+    if (m.dim == 2)
+        k_mask<T, 2><<<n_blocks, 256, 0, s>>>(m, rep_n, rep_s0, rep_w, (const C *)spec, ip0, ip1,
+                                               ip2, (C *)hc0, (C *)hc1, partial);
+    else
+        k_mask<T, 3><<<n_blocks, 256, 0, s>>>(m, rep_n, rep_s0, rep_w, (const C *)spec, ip0, ip1,
+                                               ip2, (C *)hc0, (C *)hc1, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::finalize(const double *partial, int n_blocks, double loss_const,
+                                double *loss, cudaStream_t s) {
+    k_finalize<<<1, 512, 0, s>>>(partial, n_blocks, loss_const, loss);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::rho_s(const MaskGeom &m, const int *mask_n, int64_t n_k, const void *spec,
+                             const T *ip0, const T *ip1, const T *ip2, T *rho, T *S,
+                             cudaStream_t s) {
+    using C = typename PT<T>::C;
+    const unsigned grid = (unsigned)((n_k + 255) / 256);
+    if (m.dim == 2)
+        k_rho_s<T, 2><<<grid, 256, 0, s>>>(m, mask_n, n_k, (const C *)spec, ip0, ip1, ip2, rho, S);
+    else
+        k_rho_s<T, 3><<<grid, 256, 0, s>>>(m, mask_n, n_k, (const C *)spec, ip0, ip1, ip2, rho, S);
+    return cudaGetLastError();
+}
+
+}  // namespace fresco

@@ -1,0 +1,6 @@
+// double instantiation of the libfresco kernels.
+#include "fresco_kernels.cuh"
+
+namespace fresco {
+template struct Launch<double>;
+}

@@ -1,0 +1,367 @@
+"""Thin Python binding of libfresco (include/fresco.h): argument marshalling only.
+
+Every function keeps the C name and forwards to the shared library; all numerical work runs in
+the library's CUDA kernels and cuFFT. Device arrays are passed as torch CUDA tensors (or raw
+integer addresses); torch serves only as the device allocator and stream provider. There is no
+fallback path: if libfresco.so is missing or cannot be loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfresco.so")
+
+FRESCO_OK = 0
+FRESCO_ERR_ARG = 1
+FRESCO_ERR_OOM = 2
+FRESCO_ERR_CUFFT = 3
+FRESCO_ERR_CUDA = 4
+FRESCO_ERR_NONFINITE = 5
+FRESCO_ERR_BOUNDS = 6
+FRESCO_ERR_TIMEOUT = 7
+FRESCO_ERR_UNSUPPORTED = 8
+FRESCO_F32 = 0
+FRESCO_F64 = 1
+FRESCO_N_STAGES = 7
+STAGES = ("sort", "spread", "fft_fwd", "mask", "loss", "fft_inv", "interp")
+
+# every entry point declared in include/fresco.h
+EXPORTS = (
+    "fresco_opts_default", "fresco_plan", "fresco_plan_query", "fresco_kernel_ft",
+    "fresco_get_info", "fresco_set_stream", "fresco_loss_grad", "fresco_forward",
+    "fresco_backward", "fresco_get_rho_S", "fresco_loss_grad_host", "fresco_status_check",
+    "fresco_profile", "fresco_profile_read", "fresco_launch_count", "fresco_destroy",
+    "fresco_status_string",
+)
+
+
+class FrescoError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+        self.status = status
+
+
+class fresco_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("upsample", ctypes.c_double), ("width_override", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("reserved", ctypes.c_int * 4)]
+
+
+class fresco_info(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("precision", ctypes.c_int), ("width", ctypes.c_int),
+                ("n_fine", ctypes.c_int * 3), ("k_max", ctypes.c_int * 3),
+                ("tile", ctypes.c_int * 3), ("n_tiles", ctypes.c_int * 3),
+                ("beta", ctypes.c_double), ("upsample", ctypes.c_double),
+                ("loss_const", ctypes.c_double), ("n_points", ctypes.c_int64),
+                ("n_modes", ctypes.c_int64), ("n_rep", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return d
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfresco.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(
+                "libfresco.so not built: run paper_2305_15693_gb300._build.build() "
+                "(or __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "fresco_opts_default": (None, [P]),
+            "fresco_plan": (I, [P, I, P, I64, P, I64, P, P, P, P]),
+            "fresco_plan_query": (I, [I, P, I64, P, I64, P, P, P, P]),
+            "fresco_kernel_ft": (I, [I, D, I, I64, P]),
+            "fresco_get_info": (I, [P, P]),
+            "fresco_set_stream": (I, [P, P]),
+            "fresco_loss_grad": (I, [P, P, P, P]),
+            "fresco_forward": (I, [P, P, P]),
+            "fresco_backward": (I, [P, P, P]),
+            "fresco_get_rho_S": (I, [P, P, P]),
+            "fresco_loss_grad_host": (I, [P, P, P, P]),
+            "fresco_status_check": (I, [P]),
+            "fresco_profile": (I, [P, I]),
+            "fresco_profile_read": (I, [P, P, P]),
+            "fresco_launch_count": (I64, [P]),
+            "fresco_destroy": (I, [P]),
+            "fresco_status_string": (ctypes.c_char_p, [I]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    return load().fresco_status_string(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != FRESCO_OK:
+        raise FrescoError(status, what)
+
+
+def _addr(x):
+    """Device or host address of a torch tensor, numpy array or integer (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def _host_arrays(box, mask, S0, W):
+    mask = np.ascontiguousarray(np.asarray(mask, dtype=np.int32))
+    if mask.ndim != 2:
+        raise ValueError("mask must be [n_k, dim]")
+    dim = mask.shape[1]
+    box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)))
+    S0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    if S0.size != mask.shape[0] or W.size != mask.shape[0]:
+        raise ValueError("S0 and W need one value per mask row")
+    return dim, box, mask, S0, W
+
+
+def make_opts(precision="f32", tol=0.0, upsample=2.0, width=0, tile=None) -> fresco_opts:
+    o = fresco_opts()
+    load().fresco_opts_default(ctypes.byref(o))
+    o.precision = FRESCO_F64 if precision in ("f64", FRESCO_F64, "float64") else FRESCO_F32
+    o.tol = float(tol)
+    o.upsample = float(upsample)
+    o.width_override = int(width)
+    if tile is not None:
+        for a, t in enumerate(tile):
+            o.tile[a] = int(t)
+    return o
+
+
+# ---- the C entry points, same names -----------------------------------------------------------
+
+def fresco_plan(box, mask, S0, W, n_points, opts=None, stream=None):
+    """Create a plan; returns the opaque handle (an int). See fresco_plan in include/fresco.h."""
+    lib = load()
+    dim, box, mask, S0, W = _host_arrays(box, mask, S0, W)
+    h = ctypes.c_void_p()
+    st = lib.fresco_plan(ctypes.byref(h), dim, box.ctypes.data, int(n_points), mask.ctypes.data,
+                         mask.shape[0], S0.ctypes.data, W.ctypes.data,
+                         ctypes.byref(opts) if opts is not None else None, _stream_handle(stream))
+    _check(st, "fresco_plan")
+    return h.value
+
+
+def fresco_plan_query(box, mask, S0, W, n_points, opts=None) -> dict:
+    """Host-only parameter query (no GPU touched)."""
+    lib = load()
+    dim, box, mask, S0, W = _host_arrays(box, mask, S0, W)
+    info = fresco_info()
+    st = lib.fresco_plan_query(dim, box.ctypes.data, int(n_points), mask.ctypes.data,
+                               mask.shape[0], S0.ctypes.data, W.ctypes.data,
+                               ctypes.byref(opts) if opts is not None else None,
+                               ctypes.byref(info))
+    _check(st, "fresco_plan_query")
+    return info.as_dict()
+
+
+def fresco_kernel_ft(width: int, beta: float, n_fine: int, n_nu: int) -> np.ndarray:
+    out = np.empty(int(n_nu))
+    _check(load().fresco_kernel_ft(int(width), float(beta), int(n_fine), int(n_nu),
+                                   out.ctypes.data), "fresco_kernel_ft")
+    return out
+
+
+def fresco_get_info(plan) -> dict:
+    info = fresco_info()
+    _check(load().fresco_get_info(plan, ctypes.byref(info)), "fresco_get_info")
+    return info.as_dict()
+
+
+def fresco_set_stream(plan, stream):
+    _check(load().fresco_set_stream(plan, _stream_handle(stream)), "fresco_set_stream")
+
+
+def fresco_loss_grad(plan, points, loss, grad=None):
+    _check(load().fresco_loss_grad(plan, _addr(points), _addr(loss), _addr(grad)),
+           "fresco_loss_grad")
+
+
+def fresco_forward(plan, points, loss):
+    _check(load().fresco_forward(plan, _addr(points), _addr(loss)), "fresco_forward")
+
+
+def fresco_backward(plan, grad_out, grad):
+    _check(load().fresco_backward(plan, _addr(grad_out), _addr(grad)), "fresco_backward")
+
+
+def fresco_get_rho_S(plan, rho, S):
+    _check(load().fresco_get_rho_S(plan, _addr(rho), _addr(S)), "fresco_get_rho_S")
+
+
+def fresco_loss_grad_host(plan, points: np.ndarray, grad: np.ndarray | None = None) -> float:
+    loss = np.zeros(1)
+    _check(load().fresco_loss_grad_host(plan, _addr(points), loss.ctypes.data, _addr(grad)),
+           "fresco_loss_grad_host")
+    return float(loss[0])
+
+
+def fresco_status_check(plan) -> int:
+    """Returns the status code (does not raise)."""
+    return int(load().fresco_status_check(plan))
+
+
+def fresco_profile(plan, enable: bool):
+    _check(load().fresco_profile(plan, 1 if enable else 0), "fresco_profile")
+
+
+def fresco_profile_read(plan):
+    ms = np.zeros(FRESCO_N_STAGES)
+    cnt = np.zeros(FRESCO_N_STAGES, dtype=np.int64)
+    _check(load().fresco_profile_read(plan, ms.ctypes.data, cnt.ctypes.data),
+           "fresco_profile_read")
+    return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(STAGES)}
+
+
+def fresco_launch_count(plan) -> int:
+    return int(load().fresco_launch_count(plan))
+
+
+def fresco_destroy(plan):
+    if plan:
+        _check(load().fresco_destroy(plan), "fresco_destroy")
+
+
+def fresco_status_string(status: int) -> str:
+    return status_string(status)
+
+
+# ---- convenience wrapper ------------------------------------------------------------------------
+
+class Plan:
+    """Owning wrapper around a plan handle, with torch-tensor helpers.
+
+    Points and gradients are torch CUDA tensors of shape [N, dim] in the plan's dtype
+    (float32 or float64); the loss is a CUDA float64 tensor of shape [] or [1].
+    """
+
+    def __init__(self, box, mask, S0, W, n_points, precision="f32", tol=0.0, upsample=2.0,
+                 width=0, tile=None, stream=None):
+        import torch  # device memory and streams only
+        self._torch = torch
+        self.opts = make_opts(precision, tol, upsample, width, tile)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.handle = fresco_plan(box, mask, S0, W, n_points, self.opts, stream)
+        self.info = fresco_get_info(self.handle)
+        self.dim = self.info["dim"]
+        self.n_points = int(n_points)
+        self.n_k = int(np.asarray(mask).shape[0])
+        self.dtype = torch.float64 if self.info["precision"] == FRESCO_F64 else torch.float32
+
+    def _check_points(self, x):
+        t = self._torch
+        if not (isinstance(x, t.Tensor) and x.is_cuda and x.dtype == self.dtype
+                and x.is_contiguous() and tuple(x.shape) == (self.n_points, self.dim)):
+            raise ValueError("points must be a contiguous CUDA %s tensor of shape (%d, %d)"
+                             % (self.dtype, self.n_points, self.dim))
+
+    def loss_grad(self, points, want_grad=True):
+        t = self._torch
+        self._check_points(points)
+        loss = t.empty((), dtype=t.float64, device=points.device)
+        grad = t.empty_like(points) if want_grad else None
+        fresco_loss_grad(self.handle, points, loss, grad)
+        return loss, grad
+
+    def forward(self, points):
+        t = self._torch
+        self._check_points(points)
+        loss = t.empty((), dtype=t.float64, device=points.device)
+        fresco_forward(self.handle, points, loss)
+        return loss
+
+    def backward(self, grad_out=None, out=None):
+        t = self._torch
+        dev = t.device("cuda", t.cuda.current_device())
+        grad = out if out is not None else t.empty((self.n_points, self.dim), dtype=self.dtype,
+                                                   device=dev)
+        go = None
+        if grad_out is not None:
+            go = grad_out.to(dtype=t.float64).reshape(())
+            if not go.is_contiguous():
+                go = go.contiguous()
+        fresco_backward(self.handle, go, grad)
+        return grad
+
+    def rho_S(self):
+        t = self._torch
+        dev = t.device("cuda", t.cuda.current_device())
+        rho = t.empty((self.n_k, 2), dtype=self.dtype, device=dev)
+        S = t.empty((self.n_k,), dtype=self.dtype, device=dev)
+        fresco_get_rho_S(self.handle, rho, S)
+        return rho, S
+
+    def loss_grad_host(self, points: np.ndarray, grad: np.ndarray | None = None) -> float:
+        return fresco_loss_grad_host(self.handle, points, grad)
+
+    def status(self) -> int:
+        return fresco_status_check(self.handle)
+
+    def profile(self, enable=True):
+        fresco_profile(self.handle, enable)
+
+    def profile_read(self):
+        return fresco_profile_read(self.handle)
+
+    def launch_count(self) -> int:
+        return fresco_launch_count(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -164,16 +164,20 @@ def peaked_target(mask: np.ndarray, n_points: int, K: float, n_peaks: int = 10,
     Peak p sits at (K/2)(cos 2 pi p / n_peaks, sin 2 pi p / n_peaks) in the (n_0, n_1)
     plane; with an even n_peaks the set is centrosymmetric, so S0(n) = S0(-n).
     """
-    m = mask.astype(np.float64)
     out = np.zeros(mask.shape[0], dtype=np.float64)
     h = n_points / 10.0
+    # h exp(-d^2 / (2 width^2)) is exactly 0.0 in double once d^2 / (2 width^2) > 745 + ln h, so
+    # evaluating it only inside that radius gives the same array as evaluating it everywhere.
+    cut2 = 2.0 * width * width * (746.0 + math.log(max(h, 1.0)))
     for p in range(n_peaks):
         a = 2.0 * math.pi * p / n_peaks
-        c = np.zeros(mask.shape[1])
-        c[0] = 0.5 * K * math.cos(a)
-        c[1] = 0.5 * K * math.sin(a)
-        d2 = np.sum((m - c) ** 2, axis=1)
-        out += h * np.exp(-d2 / (2.0 * width * width))
+        c0 = 0.5 * K * math.cos(a)
+        c1 = 0.5 * K * math.sin(a)
+        d2 = (mask[:, 0] - c0) ** 2 + (mask[:, 1] - c1) ** 2
+        if mask.shape[1] == 3:
+            d2 = d2 + mask[:, 2].astype(np.float64) ** 2
+        near = np.nonzero(d2 < cut2)[0]
+        out[near] += h * np.exp(-d2[near] / (2.0 * width * width))
     return out
 
 
