@@ -173,6 +173,30 @@ fresco_status fresco_profile_read(fresco_plan_t p, double *ms, int64_t *counts);
 /* Number of libfresco kernels launched through this plan so far (cuFFT's own not included). */
 int64_t fresco_launch_count(fresco_plan_t p);
 
+/* Allocation-free loss: *d_loss = sum_{q < n_k} W[q] (S[q] - S0[q])^2, summed in FP64 in a fixed
+ * order (the same two-stage reduction a plan uses for Eq. 2, but without a plan).
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate device
+ * memory at call time -- code running under a device-memory budget fixed at start-up, or inside
+ * a framework whose allocator already owns the device memory, where a cudaMalloc would fail or
+ * is not allowed. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   precision : FRESCO_F32 (d_S is float) or FRESCO_F64 (d_S is double)
+ *   n_k       : number of rows, 1 <= n_k <= FRESCO_LOSS_NOALLOC_MAX_ROWS; larger sizes return
+ *               FRESCO_ERR_UNSUPPORTED before any device work
+ *   d_S       : device [n_k] structure factor (e.g. from fresco_get_rho_S)
+ *   d_S0, d_W : device double [n_k] target and weight
+ *   d_loss    : device double, receives the loss
+ *   stream    : cudaStream_t (as void*), NULL = default stream
+ * Its scratch (512 KiB of per-block partial sums) is one array compiled into the library, held
+ * by every GPU that loads the library until the process exits. The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress, with the device current); make
+ * that first call before any stream capture. All calls on a device share the array: calls that
+ * overlap on the GPU (different streams, no ordering between them) race and give wrong results;
+ * calls ordered on one stream are safe. Asynchronous; returns FRESCO_ERR_ARG for bad arguments,
+ * FRESCO_ERR_CUDA if the address lookup or a launch fails. */
+#define FRESCO_LOSS_NOALLOC_MAX_ROWS ((int64_t)65536 * 4096)
+fresco_status fresco_loss_noalloc(int precision, int64_t n_k, const void *d_S, const double *d_S0,
+                                  const double *d_W, double *d_loss, void *stream);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

@@ -37,8 +37,9 @@ EXPORTS = (
     "fresco_get_info", "fresco_set_stream", "fresco_loss_grad", "fresco_forward",
     "fresco_backward", "fresco_get_rho_S", "fresco_loss_grad_host", "fresco_status_check",
     "fresco_profile", "fresco_profile_read", "fresco_launch_count", "fresco_destroy",
-    "fresco_status_string",
+    "fresco_status_string", "fresco_loss_noalloc",
 )
+FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
 
 class FrescoError(RuntimeError):
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
             "fresco_launch_count": (I64, [P]),
             "fresco_destroy": (I, [P]),
             "fresco_status_string": (ctypes.c_char_p, [I]),
+            "fresco_loss_noalloc": (I, [I, I64, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -265,6 +267,15 @@ def fresco_destroy(plan):
 
 def fresco_status_string(status: int) -> str:
     return status_string(status)
+
+
+def fresco_loss_noalloc(precision, n_k, S, S0, W, loss, stream=None):
+    """sum W (S - S0)^2 into the device double `loss`, allocating nothing (see include/fresco.h:
+    for callers that cannot allocate device memory at call time). S is float (precision "f32")
+    or double ("f64"); S0 and W are device doubles."""
+    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    _check(load().fresco_loss_noalloc(prec, int(n_k), _addr(S), _addr(S0), _addr(W), _addr(loss),
+                                      _stream_handle(stream)), "fresco_loss_noalloc")
 
 
 # ---- convenience wrapper ------------------------------------------------------------------------
