@@ -111,6 +111,47 @@ void kernel_ft(int w, double beta, int nf, int64_t n_nu, double *out) {
     }
 }
 
+// Chebyshev interpolation of psi on each unit interval of its support, converted to monomial
+// coefficients in tau = 2 t - 1, t = x1 + w/2 in [0, 1): c[k][j], j = 0..deg.
+template <typename T>
+void es_poly(int w, double beta, EsPoly<T> &out) {
+    const int deg = PolyDeg<T>::value;
+    const int n = deg + 1;
+    std::memset(&out, 0, sizeof(out));
+    std::vector<double> nodes(n), f(n), a(n), tk(n), tkm1(n), tkp1(n), mono(n);
+    for (int i = 0; i < n; ++i) nodes[i] = std::cos(kPi * (i + 0.5) / n);
+    for (int k = 0; k < w; ++k) {
+        for (int i = 0; i < n; ++i) {
+            const double u = 0.5 * (nodes[i] + 1.0) - 0.5 * w + k;
+            const double z = 2.0 * u / w;
+            const double q = 1.0 - z * z;
+            f[i] = q > 0.0 ? std::exp(beta * (std::sqrt(q) - 1.0)) : 0.0;
+        }
+        for (int j = 0; j < n; ++j) {   // Chebyshev coefficients
+            double sj = 0.0;
+            for (int i = 0; i < n; ++i) sj += f[i] * std::cos(j * kPi * (i + 0.5) / n);
+            a[j] = (j == 0 ? 1.0 : 2.0) * sj / n;
+        }
+        // sum_j a_j T_j(tau) in monomials: T_0 = 1, T_1 = tau, T_{j+1} = 2 tau T_j - T_{j-1}
+        std::fill(mono.begin(), mono.end(), 0.0);
+        std::fill(tkm1.begin(), tkm1.end(), 0.0);
+        std::fill(tk.begin(), tk.end(), 0.0);
+        tkm1[0] = 1.0;   // T_0
+        tk[1 < n ? 1 : 0] = 1.0;   // T_1
+        mono[0] += a[0];
+        if (n > 1)
+            for (int m = 0; m < n; ++m) mono[m] += a[1] * tk[m];
+        for (int j = 1; j + 1 < n; ++j) {
+            for (int m = 0; m < n; ++m)
+                tkp1[m] = (m > 0 ? 2.0 * tk[m - 1] : 0.0) - tkm1[m];
+            for (int m = 0; m < n; ++m) mono[m] += a[j + 1] * tkp1[m];
+            tkm1.swap(tk);
+            tk.swap(tkp1);
+        }
+        for (int m = 0; m < n; ++m) out.c[k][m] = (T)mono[m];
+    }
+}
+
 // ---- argument checks, parameters and mask folding -------------------------------------------
 
 struct Folded {
@@ -234,7 +275,10 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
             cells *= (size_t)P.tmax[a];
         }
         const size_t interp = halo_cells * (2 * es + (dim == 3 ? es : 0));
-        const size_t spread = cells * es;
+        // tile (at least 4-byte cells) plus the compacted point list (2048 float / 1024 double
+        // entries of one int and dim coordinates)
+        const size_t spread = ((cells * std::max<size_t>(es, 4) + 15) & ~(size_t)15) +
+                              (es == 8 ? 1024 : 2048) * (es * dim + 4);
         if (interp <= budget && spread <= budget) break;
         int amax = 0;
         for (int a = 1; a < dim; ++a)
@@ -259,8 +303,9 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
 // Merge each +-n pair onto its half-space representative (first nonzero component > 0):
 // W' = W(n) + W(-n), S0' = (W(n) S0(n) + W(-n) S0(-n)) / W', and the loss constant
 // sum W S0^2 - W' S0'^2, so that sum_mask W (S - S0)^2 = sum_rep W' (S - S0')^2 + const
-// whenever S(n) = S(-n). Representatives come out ordered by their address in the forward
-// half spectrum. Entries whose folded weight is zero are dropped (their terms are constants).
+// whenever S(n) = S(-n). Representatives come out ordered by their address in the transposed
+// forward spectrum (n_x major, then z, then y, each axis 0..k then -k..-1). Entries whose folded
+// weight is zero are dropped (their terms are constants).
 fresco_status fold_mask(const Params &P, const int32_t *mask, int64_t n_k, const double *S0,
                         const double *W, Folded &F) {
     const int dim = P.dim;
@@ -295,20 +340,19 @@ fresco_status fold_mask(const Params &P, const int32_t *mask, int64_t n_k, const
         sws[s] += W[q] * S0[q];
         sws2[s] += W[q] * S0[q] * S0[q];
     }
-    // emit in spectrum-address order: z rows 0..kz then -kz..-1, same for y, x ascending
+    // emit in transposed-spectrum address order
     F.n.clear();
     F.s0.clear();
     F.w.clear();
     F.loss_const = 0.0;
     F.n.reserve(nrep.size());
     auto order = [](int k, int i) { return i <= k ? i : i - (2 * k + 1); };
-    for (int64_t iz = 0; iz < ez; ++iz) {
-        const int z = order(kz, (int)iz);
-        for (int64_t iy = 0; iy < ey; ++iy) {
-            const int y = order(ky, (int)iy);
-            const int64_t base = ((int64_t)(z + kz) * ey + (y + ky)) * ex;
-            for (int x = 0; x <= kx; ++x) {
-                const int32_t s = slot[base + x];
+    for (int x = 0; x <= kx; ++x) {
+        for (int64_t iz = 0; iz < ez; ++iz) {
+            const int z = order(kz, (int)iz);
+            for (int64_t iy = 0; iy < ey; ++iy) {
+                const int y = order(ky, (int)iy);
+                const int32_t s = slot[((int64_t)(z + kz) * ey + (y + ky)) * ex + x];
                 if (s < 0) continue;
                 const double wp = sw[s];
                 if (wp > 0.0) {
@@ -388,7 +432,8 @@ void release(fresco_plan_s *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     void *bufs[] = {p->d_sorted, p->d_perm, p->d_key, p->d_slot, p->d_cnt, p->d_off,
-                    p->d_block_sums, p->d_grid, p->d_spec, p->d_hc[0], p->d_hc[1], p->d_r[0],
+                    p->d_block_sums, p->d_grid, p->d_spec, p->d_specT, p->d_bt[0], p->d_bt[1],
+                    p->d_hc[0], p->d_hc[1], p->d_r[0],
                     p->d_r[1], p->d_g[0], p->d_g[1], p->d_rep_n, p->d_rep_s0, p->d_rep_w,
                     p->d_ip[0], p->d_ip[1], p->d_ip[2], p->d_partial, p->d_err,
                     p->d_mask_orig, p->d_fft_work, p->d_stage_pts, p->d_stage_grad,
@@ -419,15 +464,15 @@ cufftType c2c_type<float>() { return CUFFT_C2C; }
 template <>
 cufftType c2c_type<double>() { return CUFFT_Z2Z; }
 
-// Four batched 1D / (d-1)-D plans implement the pruned d-dimensional transforms:
-//   forward: R2C along x for every row, then C2C over (z, y) only for columns x in [0, kx];
-//   inverse: C2C over (z, y) for the kx + 1 nonzero columns of each sign of n_x (the compact
-//            spectrum is read, the full-width buffer R is written; columns of R that no mask
-//            entry reaches are zero from plan time and are never written), then C2C along x.
+// Four cuFFT plans implement the pruned d-dimensional transforms, every one a batch of
+// contiguous transforms (our transposes move the data in between):
+//   forward: R2C along x for every row; columns x = 0..kx transposed to [kx+1][plane]; C2C over
+//            the contiguous (z,)y plane of each, in place;
+//   inverse: C2C over (z,)y for the 2kx+2 transposed columns n_x = -kx-1..kx of the compact
+//            spectrum (out of place, so its zeros survive); transposed back into R, whose other
+//            columns were zeroed at plan time and are never written; C2C along x.
 template <typename T>
 fresco_status make_ffts(fresco_plan_s *p) {
-    const Params *unused = nullptr;
-    (void)unused;
     const int dim = p->dim;
     const int nf0 = p->geom.nf[0], nf1 = p->geom.nf[1], nf2 = p->geom.nf[2];
     const long long rows = (long long)nf1 * nf2;
@@ -446,21 +491,20 @@ fresco_status make_ffts(fresco_plan_s *p) {
         FR_CUFFT(cufftMakePlanMany64(p->fft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, half,
                                      r2c_type<T>(), rows, &ws[0]));
     }
-    long long cn[2], emb[2];
-    int crank = dim - 1;
+    long long cn[2];
+    const int crank = dim - 1;
     if (dim == 2) {
         cn[0] = nf1;
-        emb[0] = nf1;
     } else {
         cn[0] = nf2;
         cn[1] = nf1;
-        emb[0] = nf2;
-        emb[1] = nf1;
     }
-    FR_CUFFT(cufftMakePlanMany64(p->fft_cols, crank, cn, emb, half, 1, emb, half, 1, c2c_type<T>(),
-                                 kx + 1, &ws[1]));
-    FR_CUFFT(cufftMakePlanMany64(p->ifft_cols, crank, cn, emb, hcw, 1, emb, nf0, 1, c2c_type<T>(),
-                                 kx + 1, &ws[2]));
+    const long long plane = rows;
+    // (z,)y transforms over contiguous planes of the transposed spectra
+    FR_CUFFT(cufftMakePlanMany64(p->fft_cols, crank, cn, nullptr, 1, plane, nullptr, 1, plane,
+                                 c2c_type<T>(), kx + 1, &ws[1]));
+    FR_CUFFT(cufftMakePlanMany64(p->ifft_cols, crank, cn, nullptr, 1, plane, nullptr, 1, plane,
+                                 c2c_type<T>(), hcw, &ws[2]));
     {
         long long n[1] = {nf0};
         FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, nf0,
@@ -493,6 +537,8 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
         g.s_hi[a] = shi;
         g.s_lo[a] = a < dim ? (double)(T)(double)slo : 0.0;
     }
+    es_poly<float>(P.width, P.beta, p->poly32);
+    es_poly<double>(P.width, P.beta, p->poly64);
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
     g.n_points = p->n_points;
     g.width = P.width;
@@ -508,6 +554,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     m.n_rep = (int64_t)F.s0.size();
     m.half_row = P.nf[0] / 2 + 1;
     m.hc_row = 2 * (int64_t)P.kmax[0] + 2;
+    m.plane = (int64_t)P.nf[1] * P.nf[2];
     m.inv_n = 1.0 / (double)p->n_points;
     p->n_pipes = dim == 2 ? 1 : 2;
 
@@ -534,8 +581,10 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
         return st;
     if ((st = dalloc(p, &p->d_grid, sizeof(T) * (size_t)cells))) return st;
     if ((st = dalloc(p, &p->d_spec, sizeof(C2) * (size_t)(rows * m.half_row)))) return st;
+    if ((st = dalloc(p, &p->d_specT, sizeof(C2) * (size_t)(rows * (m.kx + 1))))) return st;
     for (int q = 0; q < p->n_pipes; ++q) {
         if ((st = dalloc(p, &p->d_hc[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
+        if ((st = dalloc(p, &p->d_bt[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
         if ((st = dalloc(p, &p->d_r[q], sizeof(C2) * (size_t)cells))) return st;
         if ((st = dalloc(p, &p->d_g[q], sizeof(C2) * (size_t)cells))) return st;
         FR_CUDA(cudaMemsetAsync(p->d_hc[q], 0, sizeof(C2) * (size_t)(rows * m.hc_row), p->stream));
@@ -596,6 +645,13 @@ struct StageScope {
 };
 
 template <typename T>
+const EsPoly<T> &poly_of(const fresco_plan_s *p);
+template <>
+const EsPoly<float> &poly_of<float>(const fresco_plan_s *p) { return p->poly32; }
+template <>
+const EsPoly<double> &poly_of<double>(const fresco_plan_s *p) { return p->poly64; }
+
+template <typename T>
 fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
     using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     const Geom &g = p->geom;
@@ -612,26 +668,30 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
     }
     {
         StageScope sc(p, ST_SPREAD);
-        FR_CUDA(Launch<T>::spread(g, p->d_sorted, p->d_off, (T *)p->d_grid, s));
+        FR_CUDA(Launch<T>::spread(g, poly_of<T>(p), p->d_sorted, p->d_off, (T *)p->d_grid, s));
         p->launches += 1;
     }
     {
         StageScope sc(p, ST_FFT_FWD);
-        if (sizeof(T) == 4) {
+        const int64_t rows = m.plane;
+        if (sizeof(T) == 4)
             FR_CUFFT(cufftExecR2C(p->fft_rows, (cufftReal *)p->d_grid, (cufftComplex *)p->d_spec));
-            FR_CUFFT(cufftExecC2C(p->fft_cols, (cufftComplex *)p->d_spec, (cufftComplex *)p->d_spec,
-                                  CUFFT_FORWARD));
-        } else {
+        else
             FR_CUFFT(cufftExecD2Z(p->fft_rows, (cufftDoubleReal *)p->d_grid,
                                   (cufftDoubleComplex *)p->d_spec));
-            FR_CUFFT(cufftExecZ2Z(p->fft_cols, (cufftDoubleComplex *)p->d_spec,
-                                  (cufftDoubleComplex *)p->d_spec, CUFFT_FORWARD));
-        }
+        FR_CUDA(Launch<T>::cols_to_rows(p->d_spec, p->d_specT, rows, m.half_row, m.kx + 1, s));
+        p->launches += 1;
+        if (sizeof(T) == 4)
+            FR_CUFFT(cufftExecC2C(p->fft_cols, (cufftComplex *)p->d_specT,
+                                  (cufftComplex *)p->d_specT, CUFFT_FORWARD));
+        else
+            FR_CUFFT(cufftExecZ2Z(p->fft_cols, (cufftDoubleComplex *)p->d_specT,
+                                  (cufftDoubleComplex *)p->d_specT, CUFFT_FORWARD));
     }
     {
         StageScope sc(p, ST_MASK);
         FR_CUDA(Launch<T>::mask(m, p->d_rep_n, (const T *)p->d_rep_s0, (const T *)p->d_rep_w,
-                                p->d_spec, (const T *)p->d_ip[0], (const T *)p->d_ip[1],
+                                p->d_specT, (const T *)p->d_ip[0], (const T *)p->d_ip[1],
                                 (const T *)p->d_ip[2], p->d_hc[0], p->d_hc[1], p->d_partial,
                                 p->n_mask_blocks, s));
         p->launches += 1;
@@ -653,29 +713,27 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
     cudaStream_t s = p->stream;
     {
         StageScope sc(p, ST_FFT_INV);
-        const int64_t kx = m.kx;
-        const int64_t nf0 = g.nf[0];
         for (int q = 0; q < p->n_pipes; ++q) {
-            if (sizeof(T) == 4) {
-                cufftComplex *hc = (cufftComplex *)p->d_hc[q];
-                cufftComplex *r = (cufftComplex *)p->d_r[q];
-                FR_CUFFT(cufftExecC2C(p->ifft_cols, hc + (kx + 1), r, CUFFT_INVERSE));
-                FR_CUFFT(cufftExecC2C(p->ifft_cols, hc, r + (nf0 - kx - 1), CUFFT_INVERSE));
-                FR_CUFFT(cufftExecC2C(p->ifft_rows, r, (cufftComplex *)p->d_g[q], CUFFT_INVERSE));
-            } else {
-                cufftDoubleComplex *hc = (cufftDoubleComplex *)p->d_hc[q];
-                cufftDoubleComplex *r = (cufftDoubleComplex *)p->d_r[q];
-                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, hc + (kx + 1), r, CUFFT_INVERSE));
-                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, hc, r + (nf0 - kx - 1), CUFFT_INVERSE));
-                FR_CUFFT(cufftExecZ2Z(p->ifft_rows, r, (cufftDoubleComplex *)p->d_g[q],
-                                      CUFFT_INVERSE));
-            }
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(p->ifft_cols, (cufftComplex *)p->d_hc[q],
+                                      (cufftComplex *)p->d_bt[q], CUFFT_INVERSE));
+            else
+                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, (cufftDoubleComplex *)p->d_hc[q],
+                                      (cufftDoubleComplex *)p->d_bt[q], CUFFT_INVERSE));
+            FR_CUDA(Launch<T>::rows_to_cols(p->d_bt[q], p->d_r[q], m.plane, g.nf[0], m.kx, s));
+            p->launches += 1;
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(p->ifft_rows, (cufftComplex *)p->d_r[q],
+                                      (cufftComplex *)p->d_g[q], CUFFT_INVERSE));
+            else
+                FR_CUFFT(cufftExecZ2Z(p->ifft_rows, (cufftDoubleComplex *)p->d_r[q],
+                                      (cufftDoubleComplex *)p->d_g[q], CUFFT_INVERSE));
         }
     }
     {
         StageScope sc(p, ST_INTERP);
-        FR_CUDA(Launch<T>::interp(g, p->d_sorted, p->d_perm, p->d_off, p->d_g[0], p->d_g[1],
-                                  grad_out, grad, s));
+        FR_CUDA(Launch<T>::interp(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off, p->d_g[0],
+                                  p->d_g[1], grad_out, grad, s));
         p->launches += 1;
     }
     return FRESCO_OK;
@@ -839,12 +897,12 @@ fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S) {
     }
     cudaError_t e;
     if (p->precision == FRESCO_F64)
-        e = Launch<double>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_spec,
+        e = Launch<double>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_specT,
                                   (const double *)p->d_ip[0], (const double *)p->d_ip[1],
                                   (const double *)p->d_ip[2], (double *)d_rho, (double *)d_S,
                                   p->stream);
     else
-        e = Launch<float>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_spec,
+        e = Launch<float>::rho_s(p->mgeom, p->d_mask_orig, p->n_k, p->d_specT,
                                  (const float *)p->d_ip[0], (const float *)p->d_ip[1],
                                  (const float *)p->d_ip[2], (float *)d_rho, (float *)d_S,
                                  p->stream);

@@ -45,9 +45,22 @@ struct MaskGeom {
     int kx;              // max n_x over representatives (>= 0)
     int64_t n_rep;
     int64_t half_row;    // nf[0] / 2 + 1: row length of the forward half spectrum
-    int64_t hc_row;      // 2 * kx + 2: row length of the compact backward spectrum
+    int64_t hc_row;      // 2 * kx + 2: columns n_x = -kx-1 .. kx of the compact backward spectrum
+    int64_t plane;       // nf[1] * nf[2]: length of one transposed column (all (z, y) for one x)
     double inv_n;        // 1 / N
     double kscale[3];    // 2 pi / L_a
+};
+
+// Piecewise-polynomial form of the ES kernel: on the k-th unit interval of its support,
+// psi(x1 + k) = sum_j c[k][j] tau^j with tau = 2 (x1 + W/2) - 1 in [-1, 1), fitted at plan time by
+// Chebyshev interpolation in FP64 (degree 8 for float, 14 for double; maximum deviation from
+// psi about 4e-8 for w = 7 and 5e-14 for w = 13). Passed by value to the spread/interp kernels,
+// so the coefficients are read from the kernel parameter bank.
+template <typename T> struct PolyDeg { static constexpr int value = 8; };
+template <> struct PolyDeg<double> { static constexpr int value = 14; };
+template <typename T>
+struct EsPoly {
+    T c[kMaxWidth][PolyDeg<T>::value + 1];
 };
 
 enum Stage { ST_SORT = 0, ST_SPREAD, ST_FFT_FWD, ST_MASK, ST_LOSS, ST_FFT_INV, ST_INTERP,
@@ -63,16 +76,20 @@ struct Launch {
                             int *launches);
     static cudaError_t scatter(const Geom &g, const T *points, const int *key, const int *slot,
                                const int *off, void *sorted, int *perm, cudaStream_t s);
-    static cudaError_t spread(const Geom &g, const void *sorted, const int *off, T *grid,
-                              cudaStream_t s);
+    static cudaError_t spread(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                              const int *off, T *grid, cudaStream_t s);
     static cudaError_t mask(const MaskGeom &m, const int *rep_n, const T *rep_s0, const T *rep_w,
                             const void *spec, const T *ip0, const T *ip1, const T *ip2,
                             void *hc0, void *hc1, double *partial, int n_blocks, cudaStream_t s);
     static cudaError_t finalize(const double *partial, int n_blocks, double loss_const,
                                 double *loss, cudaStream_t s);
-    static cudaError_t interp(const Geom &g, const void *sorted, const int *perm, const int *off,
-                              const void *g0, const void *g1, const double *grad_out, T *grad,
-                              cudaStream_t s);
+    static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const double *grad_out, T *grad, cudaStream_t s);
+    static cudaError_t cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda,
+                                    int ncols, cudaStream_t s);
+    static cudaError_t rows_to_cols(const void *bt, void *r, int64_t rows, int nf0, int kx,
+                                    cudaStream_t s);
     static cudaError_t rho_s(const MaskGeom &m, const int *mask_n, int64_t n_k, const void *spec,
                              const T *ip0, const T *ip1, const T *ip2, T *rho, T *S,
                              cudaStream_t s);
@@ -107,9 +124,11 @@ struct fresco_plan_s {
     int *d_off = nullptr;            // [n_tiles + 1] exclusive prefix sum of d_cnt
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
-    void *d_spec = nullptr;          // complex forward half spectrum
-    void *d_hc[2] = {nullptr, nullptr};   // compact backward spectra (gradient coefficients)
-    void *d_r[2] = {nullptr, nullptr};    // after the column pass (middle columns stay zero)
+    void *d_spec = nullptr;          // complex forward half spectrum after the x pass
+    void *d_specT = nullptr;         // its columns x = 0..kx transposed: [kx+1][plane]
+    void *d_hc[2] = {nullptr, nullptr};   // transposed compact backward spectra [2kx+2][plane]
+    void *d_bt[2] = {nullptr, nullptr};   // after the (z,)y pass, still transposed
+    void *d_r[2] = {nullptr, nullptr};    // transposed back to [plane][nf0]; other columns zero
     void *d_g[2] = {nullptr, nullptr};    // complex gradient grids (components packed re/im)
     int *d_rep_n = nullptr;          // [n_rep][dim] half-space representatives
     void *d_rep_s0 = nullptr;        // [n_rep] folded S0'
@@ -122,6 +141,8 @@ struct fresco_plan_s {
     void *d_stage_pts = nullptr;     // staging for fresco_loss_grad_host
     void *d_stage_grad = nullptr;
     double *d_stage_loss = nullptr;
+    fresco::EsPoly<float> poly32{};
+    fresco::EsPoly<double> poly64{};
     int n_mask_blocks = 0;
     int n_pipes = 1;                 // complex gradient pipelines: ceil(dim / 2)
     int64_t device_bytes = 0;

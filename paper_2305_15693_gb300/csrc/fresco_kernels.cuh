@@ -9,8 +9,11 @@
 //   perm        [N] sorted position -> caller index.
 //   off         [n_tiles + 1] first sorted position of each tile.
 //   grid        real fine grid [nf2][nf1][nf0].
-//   spec        forward half spectrum [nf2][nf1][nf0/2 + 1], complex T.
-//   hc          compact backward spectrum [nf2][nf1][2 kx + 2]: column c holds n_x = c - kx - 1.
+//   spec        forward half spectrum after the x pass [nf2][nf1][nf0/2 + 1], complex T.
+//   specT       its columns x = 0..kx, transposed: [kx + 1][nf2][nf1] ("plane" = nf2 * nf1),
+//               transformed over (z, y) in place: specT[n_x][n_z][n_y] is the forward spectrum.
+//   hc          transposed compact backward spectrum [2 kx + 2][nf2][nf1]: column c holds
+//               n_x = c - kx - 1.
 //   g           complex gradient grid [nf2][nf1][nf0]: re = d/dr_x, im = d/dr_y (pipeline 0),
 //               re = d/dr_z (pipeline 1, 3D only).
 #pragma once
@@ -110,16 +113,18 @@ __device__ __forceinline__ void store_packed(typename PT<T>::U *__restrict__ s, 
     }
 }
 
-// ES kernel weights psi(x1 + k), k = 0..W-1, psi(u) = exp(beta (sqrt(1 - z^2) - 1)), z = 2u/W.
-// sqrt(1 - z^2) - 1 is evaluated as -z^2 / (1 + sqrt(1 - z^2)), free of cancellation near z = 0.
+// ES kernel weights psi(x1 + k), k = 0..W-1, from the plan's piecewise polynomials (Horner in
+// tau = 2 (x1 + W/2) - 1 in [-1, 1)); coefficients come from the kernel parameter bank.
 template <typename T, int W>
-__device__ __forceinline__ void es_weights(T x1, T beta, T inv_hw, T (&w)[W]) {
+__device__ __forceinline__ void es_weights(const EsPoly<T> &ep, T x1, T (&w)[W]) {
+    constexpr int P = PolyDeg<T>::value;
+    const T tau = T(2) * x1 + T(W - 1);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        T z = (x1 + T(k)) * inv_hw;
-        T z2 = z * z;
-        T s = sqrt(fmax(T(1) - z2, T(0)));
-        w[k] = exp(-beta * z2 / (T(1) + s));
+        T acc = ep.c[k][P];
+#pragma unroll
+        for (int j = P - 1; j >= 0; --j) acc = fma(acc, tau, ep.c[k][j]);
+        w[k] = acc;
     }
 }
 
@@ -266,12 +271,117 @@ __global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ p
 // tiles, periodic images included) that land inside the tile, then writes the tile to the grid
 // with plain coalesced stores. Every cell is written exactly once per call: no zero fill of the
 // grid and no global atomics.
+//
+// The block first scans the neighbouring tiles' point lists and compacts the points that reach
+// it into a shared list (support start and kernel offsets, already decoded), so the expensive
+// weight/accumulate loop runs with full warps.
+//
+// Float plans accumulate in 32-bit fixed point (shared-memory integer atomics are several times
+// faster than float ones on this part): each contribution is rounded to a multiple of 2^-s with
+// s chosen per tile from the number P of points that reach the tile, so that P * 2^s < 2^31 and
+// no sum can overflow (every weight is at most 1); s is capped at 21 (resolution 4.8e-7). Integer
+// sums are order independent, so the float result is bitwise reproducible. A tile reached by more
+// points than the shared list holds falls back to float atomics straight from the point lists.
+// Double plans always use double atomics.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256) k_spread(Geom g, const typename PT<T>::U *__restrict__ sorted,
+__device__ __forceinline__ void spread_point(const EsPoly<T> &ep, int i0x, int i0y, int i0z,
+                                             T x1x, T x1y, T x1z, int wdx, int wdy, int wdz,
+                                             int sx, int sxy, T *ftile, int *itile, bool fixed,
+                                             float fscale) {
+    const int i0[3] = {i0x, i0y, i0z};
+    const int wd[3] = {wdx, wdy, wdz};
+    T wx[W], wy[W];
+    es_weights<T, W>(ep, x1x, wx);
+    es_weights<T, W>(ep, x1y, wy);
+    if constexpr (D == 2) {
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const int yy = i0[1] + b;
+            if ((unsigned)yy >= (unsigned)wd[1]) continue;
+            if constexpr (sizeof(T) == 4) {
+                if (fixed) {
+                    int *row = itile + yy * sx;
+                    const float wys = wy[b] * fscale;
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const int xx = i0[0] + a;
+                        const int qv = __float_as_int(fmaf(wys, wx[a], 12582912.0f)) - 0x4B400000;
+                        if ((unsigned)xx < (unsigned)wd[0] && qv != 0) atomicAdd(row + xx, qv);
+                    }
+                    continue;
+                }
+            }
+            T *row = ftile + yy * sx;
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const int xx = i0[0] + a;
+                if ((unsigned)xx < (unsigned)wd[0]) atomicAdd(row + xx, wy[b] * wx[a]);
+            }
+        }
+    } else {
+        T wz[W];
+        es_weights<T, W>(ep, x1z, wz);
+#pragma unroll 1
+        for (int c = 0; c < W; ++c) {
+            const int zz = i0[2] + c;
+            if ((unsigned)zz >= (unsigned)wd[2]) continue;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const int yy = i0[1] + b;
+                if ((unsigned)yy >= (unsigned)wd[1]) continue;
+                const T wzy = wz[c] * wy[b];
+                if constexpr (sizeof(T) == 4) {
+                    if (fixed) {
+                        int *row = itile + zz * sxy + yy * sx;
+                        const float wzys = wzy * fscale;
+#pragma unroll
+                        for (int a = 0; a < W; ++a) {
+                            const int xx = i0[0] + a;
+                            const int qv =
+                                __float_as_int(fmaf(wzys, wx[a], 12582912.0f)) - 0x4B400000;
+                            if ((unsigned)xx < (unsigned)wd[0] && qv != 0)
+                                atomicAdd(row + xx, qv);
+                        }
+                        continue;
+                    }
+                }
+                T *row = ftile + zz * sxy + yy * sx;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const int xx = i0[0] + a;
+                    if ((unsigned)xx < (unsigned)wd[0]) atomicAdd(row + xx, wzy * wx[a]);
+                }
+            }
+        }
+    }
+}
+
+// compacted points per tile held in (dynamic) shared memory after the tile itself
+template <typename T> struct SpreadList { static constexpr int value = 2048; };
+template <> struct SpreadList<double> { static constexpr int value = 1024; };
+
+__host__ __device__ inline size_t spread_tile_bytes(const Geom &g, size_t esize) {
+    size_t cells = (size_t)g.tmax[0] * g.tmax[1] * (g.dim == 3 ? g.tmax[2] : 1);
+    size_t b = cells * (esize > 4 ? esize : 4);
+    return (b + 15) & ~(size_t)15;
+}
+
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, EsPoly<T> ep,
+                                                const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ off, T *__restrict__ grid) {
     using U = typename PT<T>::U;
+    constexpr int NNB = (D == 3) ? 27 : 9;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    T *tile = reinterpret_cast<T *>(sm_raw);
+    __shared__ int nb_p0[NNB], nb_p1[NNB], nb_org[NNB][3];
+    __shared__ int s_hits;
+    constexpr int kSpreadList = SpreadList<T>::value;
+    T *ftile = reinterpret_cast<T *>(sm_raw);
+    int *itile = reinterpret_cast<int *>(sm_raw);
+    // compacted list: support starts (packed 3 x 10 bits) and kernel offsets per axis
+    const size_t tb = spread_tile_bytes(g, sizeof(T));
+    T *l_x1 = reinterpret_cast<T *>(sm_raw + tb);                       // [D][kSpreadList]
+    int *l_i0 = reinterpret_cast<int *>(sm_raw + tb + sizeof(T) * D * kSpreadList);
 
     const int64_t t = blockIdx.x;
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
@@ -287,94 +397,124 @@ __global__ void __launch_bounds__(256) k_spread(Geom g, const typename PT<T>::U 
             wd[a] = 1;
         }
     }
-    const int sx = wd[0], sxy = wd[0] * wd[1], cells = sxy * wd[2];
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) tile[i] = T(0);
+    if (threadIdx.x < NNB) {
+        const int q = threadIdx.x;
+        const int dd[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+        int nt[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a < D) {
+                int b = tc[a] + dd[a], shift = 0;
+                if (b < 0) { b += g.nb[a]; shift = -g.nf[a]; }
+                else if (b >= g.nb[a]) { b -= g.nb[a]; shift = g.nf[a]; }
+                nt[a] = b;
+                nb_org[q][a] = tile_start(b, g.nf[a], g.nb[a]) + shift - s[a];
+            } else {
+                nt[a] = 0;
+                nb_org[q][a] = 0;
+            }
+        }
+        const int64_t nl = nt[0] + (int64_t)g.nb[0] * (nt[1] + (int64_t)g.nb[1] * nt[2]);
+        nb_p0[q] = off[nl];
+        nb_p1[q] = off[nl + 1];
+    }
+    if (threadIdx.x == 0) s_hits = 0;
     __syncthreads();
 
-    const T beta = (T)g.beta;
-    const T inv_hw = T(2) / T(W);
-    const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
-    for (int dz = zlo; dz <= zhi; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int dd[3] = {dx, dy, dz};
-                int nt[3], org[3];
+    // 1. compact the points that reach this tile (support starts are >= -W, < tile width; the
+    //    packed form stores i0 + W in 10 bits per axis: tile edges are at most 255 cells)
+    const int lane = threadIdx.x & 31;
+    for (int q = 0; q < NNB; ++q) {
+        const int p0 = nb_p0[q], p1 = nb_p1[q];
+        for (int pb = p0; pb < p1; pb += blockDim.x) {
+            const int p = pb + threadIdx.x;
+            bool hit = p < p1;
+            int i0[3] = {0, 0, 0};
+            T x1[3] = {T(0), T(0), T(0)};
+            if (hit) {
+                U u[3];
+                load_packed<T, D>(sorted, p, u);
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    if (a < D) {
-                        int b = tc[a] + dd[a], shift = 0;
-                        if (b < 0) { b += g.nb[a]; shift = -g.nf[a]; }
-                        else if (b >= g.nb[a]) { b -= g.nb[a]; shift = g.nf[a]; }
-                        nt[a] = b;
-                        org[a] = tile_start(b, g.nf[a], g.nb[a]) + shift - s[a];
-                    } else {
-                        nt[a] = 0;
-                        org[a] = 0;
-                    }
-                }
-                const int64_t nl = nt[0] + (int64_t)g.nb[0] * (nt[1] + (int64_t)g.nb[1] * nt[2]);
-                const int p0 = off[nl], p1 = off[nl + 1];
-                for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-                    U u[3];
-                    load_packed<T, D>(sorted, p, u);
-                    int i0[3] = {0, 0, 0};
-                    T x1[3] = {T(0), T(0), T(0)};
-                    bool hit = true;
-#pragma unroll
-                    for (int a = 0; a < D; ++a) {
-                        int rel;
-                        T f;
-                        unpack_coord<T>(u[a], rel, f);
-                        i0[a] = org[a] + rel + support_start<T, W>(f, x1[a]);
-                        hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
-                    }
-                    if (!hit) continue;
-                    T wx[W], wy[W];
-                    es_weights<T, W>(x1[0], beta, inv_hw, wx);
-                    es_weights<T, W>(x1[1], beta, inv_hw, wy);
-                    if constexpr (D == 2) {
-#pragma unroll
-                        for (int b = 0; b < W; ++b) {
-                            const int yy = i0[1] + b;
-                            if ((unsigned)yy < (unsigned)wd[1]) {
-                                T *row = tile + yy * sx;
-#pragma unroll
-                                for (int a = 0; a < W; ++a) {
-                                    const int xx = i0[0] + a;
-                                    if ((unsigned)xx < (unsigned)wd[0])
-                                        atomicAdd(row + xx, wy[b] * wx[a]);
-                                }
-                            }
-                        }
-                    } else {
-                        T wz[W];
-                        es_weights<T, W>(x1[2], beta, inv_hw, wz);
-#pragma unroll 1
-                        for (int c = 0; c < W; ++c) {
-                            const int zz = i0[2] + c;
-                            if ((unsigned)zz >= (unsigned)wd[2]) continue;
-#pragma unroll
-                            for (int b = 0; b < W; ++b) {
-                                const int yy = i0[1] + b;
-                                if ((unsigned)yy < (unsigned)wd[1]) {
-                                    T *row = tile + zz * sxy + yy * sx;
-                                    const T wzy = wz[c] * wy[b];
-#pragma unroll
-                                    for (int a = 0; a < W; ++a) {
-                                        const int xx = i0[0] + a;
-                                        if ((unsigned)xx < (unsigned)wd[0])
-                                            atomicAdd(row + xx, wzy * wx[a]);
-                                    }
-                                }
-                            }
-                        }
-                    }
+                for (int a = 0; a < D; ++a) {
+                    int rel;
+                    T f;
+                    unpack_coord<T>(u[a], rel, f);
+                    i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
+                    hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
                 }
             }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            int base = 0;
+            if (lane == 0 && m) base = atomicAdd(&s_hits, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (hit) {
+                const int slot = base + __popc(m & ((1u << lane) - 1u));
+                if (slot < kSpreadList) {
+                    l_i0[slot] = (i0[0] + W) | ((i0[1] + W) << 10) | ((i0[2] + W) << 20);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) l_x1[a * kSpreadList + slot] = x1[a];
+                }
+            }
+        }
+    }
+    const int sx = wd[0], sxy = wd[0] * wd[1], cells = sxy * wd[2];
     __syncthreads();
+    const int hits = s_hits;
+    const bool listed = hits <= kSpreadList;
+    bool fixed = false;
+    int sc = 0;
+    if constexpr (sizeof(T) == 4) {
+        fixed = listed;
+        sc = fixed ? min(21, __clz(max(hits, 1)) - 1) : 0;
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) itile[i] = 0;
+    } else {
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) ftile[i] = T(0);
+    }
+    __syncthreads();
+    const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
+
+    if (listed) {
+        // 2. accumulate the compacted points with full warps
+        for (int h = threadIdx.x; h < hits; h += blockDim.x) {
+            const int pk = l_i0[h];
+            const T x1x = l_x1[h], x1y = l_x1[kSpreadList + h];
+            const T x1z = D == 3 ? l_x1[(D - 1) * kSpreadList + h] : T(0);
+            spread_point<T, W, D>(ep, (pk & 1023) - W, ((pk >> 10) & 1023) - W,
+                                  ((pk >> 20) & 1023) - W, x1x, x1y, x1z, wd[0], wd[1], wd[2],
+                                  sx, sxy, ftile, itile, fixed, fscale);
+        }
+    } else {
+        // 2'. crowded tile: float atomics straight from the point lists
+        for (int q = 0; q < NNB; ++q) {
+            const int p0 = nb_p0[q], p1 = nb_p1[q];
+            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                U u[3];
+                load_packed<T, D>(sorted, p, u);
+                int i0[3] = {0, 0, 0};
+                T x1[3] = {T(0), T(0), T(0)};
+                bool hit = true;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    int rel;
+                    T f;
+                    unpack_coord<T>(u[a], rel, f);
+                    i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
+                    hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
+                }
+                if (hit)
+                    spread_point<T, W, D>(ep, i0[0], i0[1], i0[2], x1[0], x1[1], x1[2], wd[0],
+                                          wd[1], wd[2], sx, sxy, ftile, itile, false, fscale);
+            }
+        }
+    }
+    __syncthreads();
+    const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
         const int x = i % sx, y = (i / sx) % wd[1], z = i / sxy;
-        grid[((int64_t)(s[2] + z) * g.nf[1] + (s[1] + y)) * g.nf[0] + s[0] + x] = tile[i];
+        T v;
+        if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i] * finv : ftile[i];
+        else v = ftile[i];
+        grid[((int64_t)(s[2] + z) * g.nf[1] + (s[1] + y)) * g.nf[0] + s[0] + x] = v;
     }
 }
 
@@ -407,7 +547,7 @@ __global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict_
         const int ry = ny < 0 ? ny + m.nf[1] : ny;
         const int rz = nz < 0 ? nz + m.nf[2] : nz;
         const int64_t row = (int64_t)rz * m.nf[1] + ry;
-        const C F = spec[row * m.half_row + nx];
+        const C F = spec[(int64_t)nx * m.plane + row];
         T ip = ip0[nx] * ip1[ny < 0 ? -ny : ny];
         if (D == 3) ip *= ip2[nz < 0 ? -nz : nz];
         const T re = F.x * ip, im = F.y * ip;
@@ -422,8 +562,8 @@ __global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict_
         const int my = ny > 0 ? m.nf[1] - ny : -ny;
         const int mz = nz > 0 ? m.nf[2] - nz : -nz;
         const int64_t rowm = (int64_t)mz * m.nf[1] + my;
-        const int64_t cp = row * m.hc_row + (nx + m.kx + 1);
-        const int64_t cm = rowm * m.hc_row + (-nx + m.kx + 1);
+        const int64_t cp = (int64_t)(nx + m.kx + 1) * m.plane + row;
+        const int64_t cm = (int64_t)(-nx + m.kx + 1) * m.plane + rowm;
         hc0[cp] = C{-er * ky - ei * kx, er * kx - ei * ky};
         hc0[cm] = C{er * ky - ei * kx, -er * kx - ei * ky};
         if (D == 3) {
@@ -465,7 +605,8 @@ static __global__ void __launch_bounds__(512) k_finalize(const double *__restric
 // gradient grid(s) in shared memory, then every point of the tile sums its W^D kernel-weighted
 // cells; the result, scaled by the incoming gradient, goes to the caller's order through perm.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U *__restrict__ sorted,
+__global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
+                                                const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ perm,
                                                 const int *__restrict__ off,
                                                 const typename PT<T>::C *__restrict__ g0,
@@ -496,10 +637,11 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U 
     T *sg1 = reinterpret_cast<T *>(sm_raw + sizeof(C) * (size_t)cells);
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
         const int x = i % rw[0], y = (i / rw[0]) % rw[1], z = i / rxy;
+        // the staged region is narrower than the grid, so it wraps at most once per axis
         int gx = s[0] - HL + x, gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
-        gx = (gx % g.nf[0] + g.nf[0]) % g.nf[0];
-        gy = (gy % g.nf[1] + g.nf[1]) % g.nf[1];
-        if (D == 3) gz = (gz % g.nf[2] + g.nf[2]) % g.nf[2];
+        gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+        gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+        if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
         const int64_t gi = ((int64_t)gz * g.nf[1] + gy) * g.nf[0] + gx;
         sg0[i] = g0[gi];
         if (D == 3) sg1[i] = g1[gi].x;
@@ -507,8 +649,6 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U 
     __syncthreads();
 
     const T scale = grad_out ? (T)(*grad_out) : T(1);
-    const T beta = (T)g.beta;
-    const T inv_hw = T(2) / T(W);
     const int p0 = off[t], p1 = off[t + 1];
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
@@ -523,8 +663,8 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U 
             i0[a] = rel + support_start<T, W>(f, x1[a]) + HL;
         }
         T wx[W], wy[W];
-        es_weights<T, W>(x1[0], beta, inv_hw, wx);
-        es_weights<T, W>(x1[1], beta, inv_hw, wy);
+        es_weights<T, W>(ep, x1[0], wx);
+        es_weights<T, W>(ep, x1[1], wy);
         T ax = T(0), ay = T(0), az = T(0);
         if constexpr (D == 2) {
 #pragma unroll
@@ -545,7 +685,7 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, const typename PT<T>::U 
             reinterpret_cast<T2 *>(grad)[j] = T2{scale * ax, scale * ay};
         } else {
             T wz[W];
-            es_weights<T, W>(x1[2], beta, inv_hw, wz);
+            es_weights<T, W>(ep, x1[2], wz);
 #pragma unroll 1
             for (int c = 0; c < W; ++c) {
                 T px = T(0), py = T(0), pz = T(0);
@@ -589,12 +729,60 @@ __global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
     if (nx < 0) { nx = -nx; ny = -ny; nz = -nz; sgn = T(-1); }   // rho(-n) = conj rho(n)
     const int ry = ny < 0 ? ny + m.nf[1] : ny;
     const int rz = nz < 0 ? nz + m.nf[2] : nz;
-    const auto F = spec[((int64_t)rz * m.nf[1] + ry) * m.half_row + nx];
+    const auto F = spec[(int64_t)nx * m.plane + (int64_t)rz * m.nf[1] + ry];
     T ip = ip0[nx] * ip1[ny < 0 ? -ny : ny];
     if (D == 3) ip *= ip2[nz < 0 ? -nz : nz];
     const T re = F.x * ip, im = sgn * F.y * ip;
     if (rho) { rho[2 * q] = re; rho[2 * q + 1] = im; }
     if (S) S[q] = (re * re + im * im) * (T)m.inv_n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Transposes around the (z,)y FFT pass, so that every cuFFT call is a batch of contiguous
+// transforms (32 x 32 tiles through shared memory; coalesced on both sides).
+
+// at[c][r] = a[r][c] for r < rows, c < ncols (a has row stride lda)
+template <typename C>
+__global__ void __launch_bounds__(256) k_cols_to_rows(const C *__restrict__ a, C *__restrict__ at,
+                                                      int64_t rows, int64_t lda, int ncols) {
+    __shared__ C tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t r = r0 + k;
+        const int c = c0 + threadIdx.x;
+        if (r < rows && c < ncols) tile[k][threadIdx.x] = a[r * lda + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t r = r0 + threadIdx.x;
+        if (c < ncols && r < rows) at[(int64_t)c * rows + r] = tile[threadIdx.x][k];
+    }
+}
+
+// r[row][x(c)] = bt[c][row] for c < 2 kx + 2, x(c) = c - kx - 1 taken modulo nf0
+template <typename C>
+__global__ void __launch_bounds__(256) k_rows_to_cols(const C *__restrict__ bt, C *__restrict__ r,
+                                                      int64_t rows, int nf0, int kx) {
+    __shared__ C tile[32][33];
+    const int ncols = 2 * kx + 2;
+    const int c0 = blockIdx.y * 32;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t row = r0 + threadIdx.x;
+        if (c < ncols && row < rows) tile[k][threadIdx.x] = bt[(int64_t)c * rows + row];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t row = r0 + k;
+        const int c = c0 + threadIdx.x;
+        if (row < rows && c < ncols) {
+            const int x = c <= kx ? nf0 - kx - 1 + c : c - kx - 1;
+            r[row * nf0 + x] = tile[threadIdx.x][k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -641,7 +829,9 @@ cudaError_t Launch<T>::scatter(const Geom &g, const T *points, const int *key, c
 
 template <typename T>
 int Launch<T>::spread_smem(const Geom &g) {
-    return (int)(sizeof(T) * (size_t)g.tmax[0] * g.tmax[1] * (g.dim == 3 ? g.tmax[2] : 1));
+    const int D = g.dim;
+    return (int)(spread_tile_bytes(g, sizeof(T)) +
+                 (sizeof(T) * D + sizeof(int)) * (size_t)SpreadList<T>::value);
 }
 
 template <typename T>
@@ -653,29 +843,30 @@ int Launch<T>::interp_smem(const Geom &g) {
 }
 
 template <typename T, int W, int D>
-static cudaError_t launch_spread_w(const Geom &g, const void *sorted, const int *off, T *grid,
-                                   cudaStream_t s) {
+static cudaError_t launch_spread_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                   const int *off, T *grid, cudaStream_t s) {
     using U = typename PT<T>::U;
     const int smem = Launch<T>::spread_smem(g);
     auto kern = k_spread<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, (const U *)sorted, off, grid);
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid);
     return cudaGetLastError();
 }
 
 template <typename T, int W, int D>
-static cudaError_t launch_interp_w(const Geom &g, const void *sorted, const int *perm,
-                                   const int *off, const void *g0, const void *g1,
-                                   const double *grad_out, T *grad, cudaStream_t s) {
+static cudaError_t launch_interp_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                   const int *perm, const int *off, const void *g0,
+                                   const void *g1, const double *grad_out, T *grad,
+                                   cudaStream_t s) {
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
     const int smem = Launch<T>::interp_smem(g);
     auto kern = k_interp<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, (const U *)sorted, perm, off, (const C *)g0,
-                                                (const C *)g1, grad_out, grad);
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, off,
+                                                (const C *)g0, (const C *)g1, grad_out, grad);
     return cudaGetLastError();
 }
 
@@ -700,25 +891,27 @@ static cudaError_t launch_interp_w(const Geom &g, const void *sorted, const int 
     }
 
 template <typename T>
-cudaError_t Launch<T>::spread(const Geom &g, const void *sorted, const int *off, T *grid,
-                              cudaStream_t s) {
+cudaError_t Launch<T>::spread(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                              const int *off, T *grid, cudaStream_t s) {
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_spread_w<T, WW, 2>(g, sorted, off, grid, s)));
+        FRESCO_WIDTH_SWITCH(g.width,
+                            return (launch_spread_w<T, WW, 2>(g, ep, sorted, off, grid, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_spread_w<T, WW, 3>(g, sorted, off, grid, s)));
+        FRESCO_WIDTH_SWITCH(g.width,
+                            return (launch_spread_w<T, WW, 3>(g, ep, sorted, off, grid, s)));
     }
 }
 
 template <typename T>
-cudaError_t Launch<T>::interp(const Geom &g, const void *sorted, const int *perm, const int *off,
-                              const void *g0, const void *g1, const double *grad_out, T *grad,
-                              cudaStream_t s) {
+cudaError_t Launch<T>::interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const double *grad_out, T *grad, cudaStream_t s) {
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 2>(g, sorted, perm, off, g0,
-                                                                      g1, grad_out, grad, s)));
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 2>(g, ep, sorted, perm, off,
+                                                                      g0, g1, grad_out, grad, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 3>(g, sorted, perm, off, g0,
-                                                                      g1, grad_out, grad, s)));
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 3>(g, ep, sorted, perm, off,
+                                                                      g0, g1, grad_out, grad, s)));
     }
 }
 
@@ -740,6 +933,24 @@ template <typename T>
 cudaError_t Launch<T>::finalize(const double *partial, int n_blocks, double loss_const,
                                 double *loss, cudaStream_t s) {
     k_finalize<<<1, 512, 0, s>>>(partial, n_blocks, loss_const, loss);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda, int ncols,
+                                    cudaStream_t s) {
+    using C = typename PT<T>::C;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((ncols + 31) / 32));
+    k_cols_to_rows<C><<<grid, dim3(32, 8), 0, s>>>((const C *)a, (C *)at, rows, lda, ncols);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::rows_to_cols(const void *bt, void *r, int64_t rows, int nf0, int kx,
+                                    cudaStream_t s) {
+    using C = typename PT<T>::C;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((2 * kx + 2 + 31) / 32));
+    k_rows_to_cols<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, nf0, kx);
     return cudaGetLastError();
 }
 

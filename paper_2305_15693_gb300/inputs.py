@@ -236,6 +236,9 @@ def workload(name: str) -> Workload:
     if name == "peaked2d_n1e8_chi03_f32":
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f32",
                         seed=0, tol=1e-6)
+    if name == "peaked2d_n1e7_chi03_f32":
+        return Workload(name, 2, 10**7, radius_for_chi(10**7, 2, 0.3), "peaked", "f32",
+                        seed=0, tol=1e-6)
     if name == "peaked2d_n1e8_chi03_f64":
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f64",
                         seed=0, tol=1e-12)
