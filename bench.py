@@ -282,6 +282,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ref-rows", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--upsample", type=float, default=0.0,
+                    help="override the workload's fine-grid oversampling sigma")
+    ap.add_argument("--tile", type=int, nargs="*", default=None,
+                    help="override the spread/interp tile edge per axis")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3")
@@ -289,6 +293,8 @@ def main():
 
     from paper_2305_15693_gb300 import inputs
     wl = inputs.workload(args.workload)
+    if args.upsample:
+        wl.upsample = args.upsample
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,7 +322,7 @@ def main():
 
     # ---- FP32 path: the headline -------------------------------------------------------------
     plan = fresco.Plan(wl.box, mask, S0, W, N, precision=wl.dtype, tol=wl.tol,
-                       upsample=wl.upsample)
+                       upsample=wl.upsample, tile=args.tile)
     info = plan.info
     log("plan: n_fine=%s w=%d tiles=%s n_rep=%d device_bytes=%.2f GB" % (
         info["n_fine"][:wl.dim], info["width"], info["n_tiles"][:wl.dim], info["n_rep"],

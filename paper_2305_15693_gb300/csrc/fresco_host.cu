@@ -530,6 +530,9 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
         g.nf[a] = P.nf[a];
         g.nb[a] = P.nb[a];
         g.tmax[a] = P.tmax[a];
+        g.tq[a] = P.nf[a] / P.nb[a];
+        g.tr[a] = P.nf[a] % P.nb[a];
+        g.tinv[a] = (float)P.nb[a] / (float)P.nf[a];
         double s = a < dim ? (double)P.nf[a] / p->box[a] : 0.0;
         double shi = (double)(T)s;
         long double slo = (long double)P.nf[a] / (long double)(a < dim ? p->box[a] : 1.0) -
@@ -540,6 +543,10 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     es_poly<float>(P.width, P.beta, p->poly32);
     es_poly<double>(P.width, P.beta, p->poly64);
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
+    g.sub = dim == 3 ? 27 : 9;
+    for (int a = 0; a < 3; ++a) g.strips[a] = a < dim && P.nf[a] / P.nb[a] >= P.width ? 1 : 0;
+    g.n_bins = g.n_tiles * g.sub;
+    if (g.n_bins >= 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
     g.n_points = p->n_points;
     g.width = P.width;
     g.beta = P.beta;
@@ -569,16 +576,18 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     const int64_t N = p->n_points;
     const int64_t cells = (int64_t)P.nf[0] * P.nf[1] * P.nf[2];
     const int64_t rows = (int64_t)P.nf[1] * P.nf[2];
-    const int pw = dim == 3 ? 4 : 2;
+    // sorted records: float plans keep the caller index inside each 16-byte record
+    const int pw = sizeof(T) == 4 ? 4 : (dim == 3 ? 4 : 2);
     fresco_status st;
     if ((st = dalloc(p, &p->d_sorted, sizeof(T) * (size_t)N * pw))) return st;
-    if ((st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)N))) return st;
+    if (sizeof(T) == 8 && (st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)N))) return st;
     if ((st = dalloc(p, &p->d_key, sizeof(int) * (size_t)N))) return st;
     if ((st = dalloc(p, &p->d_slot, sizeof(int) * (size_t)N))) return st;
-    if ((st = dalloc(p, &p->d_cnt, sizeof(int) * (size_t)g.n_tiles))) return st;
-    if ((st = dalloc(p, &p->d_off, sizeof(int) * (size_t)(g.n_tiles + 1)))) return st;
-    if ((st = dalloc(p, &p->d_block_sums, sizeof(int) * (size_t)((g.n_tiles + 1023) / 1024 + 1))))
+    if ((st = dalloc(p, &p->d_cnt, sizeof(int) * (size_t)g.n_bins))) return st;
+    if ((st = dalloc(p, &p->d_off, sizeof(int) * (size_t)(g.n_bins + 1)))) return st;
+    if ((st = dalloc(p, &p->d_block_sums, sizeof(int) * (size_t)((g.n_bins + 1023) / 1024 + 1))))
         return st;
+
     if ((st = dalloc(p, &p->d_grid, sizeof(T) * (size_t)cells))) return st;
     if ((st = dalloc(p, &p->d_spec, sizeof(C2) * (size_t)(rows * m.half_row)))) return st;
     if ((st = dalloc(p, &p->d_specT, sizeof(C2) * (size_t)(rows * (m.kx + 1))))) return st;
@@ -659,12 +668,14 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
     cudaStream_t s = p->stream;
     {
         StageScope sc(p, ST_SORT);
-        FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_tiles, s));
+        FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_bins, s));
         FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
         int nl = 0;
-        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_tiles, s, &nl));
-        FR_CUDA(Launch<T>::scatter(g, pts, p->d_key, p->d_slot, p->d_off, p->d_sorted, p->d_perm, s));
-        p->launches += 2 + nl;
+        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl));
+        FR_CUDA(Launch<T>::scatter(g, pts, p->d_key, p->d_slot, p->d_off, p->d_sorted, p->d_perm,
+                                   s));
+        nl += 1;
+        p->launches += 1 + nl;
     }
     {
         StageScope sc(p, ST_SPREAD);

@@ -16,14 +16,21 @@ constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
 
 // Geometry of the fine grid and its tiling, passed by value to kernels.
-// Axis 0 is x, the contiguous axis of every grid. Tile b on axis a covers fine cells
-// [start(b), start(b+1)) with start(b) = floor(b * nf[a] / nb[a]).
+// Axis 0 is x, the contiguous axis of every grid. With q = nf / nb and r = nf % nb, tile b on an
+// axis covers fine cells [start(b), start(b+1)), start(b) = b q + min(b, r): the first r tiles
+// are q + 1 cells wide, the others q.
 struct Geom {
     int dim;
     int nf[3];          // fine grid size per axis (1 for unused axes)
     int nb[3];          // tiles per axis (1 for unused axes)
     int tmax[3];        // widest tile per axis (1 for unused axes)
+    int tq[3], tr[3];   // nf / nb and nf % nb per axis
+    float tinv[3];      // nb / nf (estimate of the tile of a cell, corrected exactly)
     int64_t n_tiles;
+    int sub;            // sub-bins per tile, 3^dim: per axis the low border strip (cells that can
+                        // reach the previous tile), the interior, the high border strip
+    int strips[3];      // 1 if every tile on the axis is at least w cells wide (strips disjoint)
+    int64_t n_bins;     // n_tiles * sub: the sort key space
     int64_t n_points;
     int width;          // ES kernel width w
     double beta;        // ES kernel shape
@@ -31,11 +38,12 @@ struct Geom {
     double s_lo[3];
 };
 
-__host__ __device__ inline int tile_start(int b, int nf, int nb) {
-    return (int)(((int64_t)b * nf) / nb);
-}
-__host__ __device__ inline int tile_of_cell(int c, int nf, int nb) {
-    return (int)((((int64_t)c + 1) * nb - 1) / nf);
+__host__ __device__ inline int tile_start(int b, int q, int r) { return b * q + (b < r ? b : r); }
+__host__ __device__ inline int tile_of_cell(int c, int q, int r, float inv) {
+    int b = (int)((float)c * inv);
+    while (b > 0 && tile_start(b, q, r) > c) --b;
+    while (tile_start(b + 1, q, r) <= c) ++b;
+    return b;
 }
 
 // Geometry of the mask and the spectra.
@@ -76,6 +84,7 @@ struct Launch {
                             int *launches);
     static cudaError_t scatter(const Geom &g, const T *points, const int *key, const int *slot,
                                const int *off, void *sorted, int *perm, cudaStream_t s);
+
     static cudaError_t spread(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                               const int *off, T *grid, cudaStream_t s);
     static cudaError_t mask(const MaskGeom &m, const int *rep_n, const T *rep_s0, const T *rep_w,
@@ -116,12 +125,13 @@ struct fresco_plan_s {
     std::vector<int32_t> h_mask;
 
     // device buffers (owned)
-    void *d_sorted = nullptr;        // packed tile-relative coordinates, sorted by tile
-    int *d_perm = nullptr;           // sorted position -> caller index
+    void *d_sorted = nullptr;        // sorted records: packed tile-relative coordinates (and, for
+                                     // float plans, the caller index)
+    int *d_perm = nullptr;           // double plans: sorted position -> caller index
     int *d_key = nullptr;            // caller index -> tile id
     int *d_slot = nullptr;           // caller index -> rank within its tile
-    int *d_cnt = nullptr;            // [n_tiles] points per tile
-    int *d_off = nullptr;            // [n_tiles + 1] exclusive prefix sum of d_cnt
+    int *d_cnt = nullptr;            // [n_bins] points per sub-bin
+    int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of d_cnt
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
     void *d_spec = nullptr;          // complex forward half spectrum after the x pass

@@ -2,11 +2,12 @@
 //
 // Data layouts (axis 0 = x is contiguous everywhere):
 //   points      [N][D] caller order, type T.
-//   sorted      packed tile-relative coordinates in tile order: PD = (D == 3 ? 4 : 2) words of
-//               type U per point (U = uint32 for float, uint64 for double); word a holds the cell
-//               of the point relative to its tile origin in the top 8 bits and the fractional
-//               position inside that cell, frac * 2^FB, in the low FB bits (FB = 24 / 56).
-//   perm        [N] sorted position -> caller index.
+//   sorted      one record per point in sub-bin order, words of type U (uint32 for float, uint64
+//               for double): word a holds the cell of the point relative to its tile origin in
+//               the top 8 bits and the fractional position inside that cell, frac * 2^FB, in the
+//               low FB bits (FB = 24 / 56). Float records are 16 bytes {u0, u1, u2 or 0, caller
+//               index}; double records are 2 (2D) or 4 (3D) words.
+//   perm        [N] sorted position -> caller index (double plans only).
 //   off         [n_tiles + 1] first sorted position of each tile.
 //   grid        real fine grid [nf2][nf1][nf0].
 //   spec        forward half spectrum after the x pass [nf2][nf1][nf0/2 + 1], complex T.
@@ -37,8 +38,6 @@ template <> struct PT<double> {
     using U = uint64_t;
     static constexpr int FB = 56;
 };
-
-template <int D> struct PackedWords { static constexpr int value = (D == 3) ? 4 : 2; };
 
 // ---------------------------------------------------------------------------------------------
 // Fine-grid coordinate t = r * n_f / L of one coordinate, split into a cell index in [0, n_f)
@@ -79,14 +78,14 @@ __device__ __forceinline__ void unpack_coord(typename PT<T>::U u, int &rel, T &f
     frac = T(u & m) * (T(1) / T((U)1 << PT<T>::FB));
 }
 
+// Sorted records. Float plans store one 16-byte record per point, {u0, u1, u2 (3D) or 0, caller
+// index}, so the scatter costs one partial-sector write per point; double plans store D (2D) or
+// 4 (3D) 64-bit words and keep the caller index in the separate perm array.
 template <typename T, int D>
 __device__ __forceinline__ void load_packed(const typename PT<T>::U *__restrict__ s, int64_t p,
                                             typename PT<T>::U (&u)[3]) {
-    if constexpr (sizeof(T) == 4 && D == 2) {
-        uint2 v = reinterpret_cast<const uint2 *>(s)[p];
-        u[0] = v.x; u[1] = v.y; u[2] = 0;
-    } else if constexpr (sizeof(T) == 4) {
-        uint4 v = reinterpret_cast<const uint4 *>(s)[p];
+    if constexpr (sizeof(T) == 4) {
+        const uint4 v = reinterpret_cast<const uint4 *>(s)[p];
         u[0] = v.x; u[1] = v.y; u[2] = v.z;
     } else if constexpr (D == 2) {
         ulonglong2 v = reinterpret_cast<const ulonglong2 *>(s)[p];
@@ -98,19 +97,41 @@ __device__ __forceinline__ void load_packed(const typename PT<T>::U *__restrict_
     }
 }
 
+// as load_packed, plus the caller index of the point
 template <typename T, int D>
-__device__ __forceinline__ void store_packed(typename PT<T>::U *__restrict__ s, int64_t p,
-                                             const typename PT<T>::U (&u)[3]) {
-    if constexpr (sizeof(T) == 4 && D == 2) {
-        reinterpret_cast<uint2 *>(s)[p] = make_uint2(u[0], u[1]);
-    } else if constexpr (sizeof(T) == 4) {
-        reinterpret_cast<uint4 *>(s)[p] = make_uint4(u[0], u[1], u[2], 0u);
+__device__ __forceinline__ int load_record(const typename PT<T>::U *__restrict__ s,
+                                           const int *__restrict__ perm, int64_t p,
+                                           typename PT<T>::U (&u)[3]) {
+    if constexpr (sizeof(T) == 4) {
+        const uint4 v = reinterpret_cast<const uint4 *>(s)[p];
+        u[0] = v.x; u[1] = v.y; u[2] = v.z;
+        return (int)v.w;
+    } else {
+        load_packed<T, D>(s, p, u);
+        return perm[p];
+    }
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void store_record(typename PT<T>::U *__restrict__ s,
+                                             int *__restrict__ perm, int64_t p,
+                                             const typename PT<T>::U (&u)[3], int j) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<uint4 *>(s)[p] = make_uint4(u[0], u[1], D == 3 ? u[2] : 0u, (unsigned)j);
     } else if constexpr (D == 2) {
         reinterpret_cast<ulonglong2 *>(s)[p] = make_ulonglong2(u[0], u[1]);
+        perm[p] = j;
     } else {
         reinterpret_cast<ulonglong2 *>(s)[2 * p] = make_ulonglong2(u[0], u[1]);
         reinterpret_cast<ulonglong2 *>(s)[2 * p + 1] = make_ulonglong2(u[2], 0ull);
+        perm[p] = j;
     }
+}
+
+// words of type U per sorted record
+template <typename T, int D>
+__host__ __device__ constexpr int record_words() {
+    return sizeof(T) == 4 ? 4 : (D == 3 ? 4 : 2);
 }
 
 // ES kernel weights psi(x1 + k), k = 0..W-1, from the plan's piecewise polynomials (Horner in
@@ -138,27 +159,66 @@ __device__ __forceinline__ int support_start(T frac, T &x1) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// K1a: wrap, fine cell, tile id and the rank of each point within its tile.
+// Sub-bin part of a tile-relative cell along one axis: 0 for the low border strip (cells whose
+// kernel support can reach the previous tile), 2 for the high border strip (support can reach
+// the next tile), 1 otherwise; always 1 when the axis's tiles are narrower than w.
+__device__ __forceinline__ int strip_part(int rel, int wd, int w, int strips) {
+    if (!strips) return 1;
+    if (rel < w / 2) return 0;
+    if (rel >= wd - (w + 1) / 2) return 2;
+    return 1;
+}
+
+// K1a: wrap, fine cell, sub-bin (tile x 3^D border parts) and the rank of each point within it.
+// Each thread handles 4 points per iteration (independent loads and atomics in flight).
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_bin(Geom g, const T *__restrict__ pts,
                                              int *__restrict__ cnt, int *__restrict__ key,
                                              int *__restrict__ slot, int *__restrict__ err) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.n_points;
-         j += stride) {
-        bool ok = true;
-        int t[3] = {0, 0, 0};
+    constexpr int IL = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
+         j0 += stride) {
+        T r[IL][3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            int cell;
-            T frac;
-            ok &= fine_coord<T>(pts[j * D + a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
-            t[a] = tile_of_cell(cell, g.nf[a], g.nb[a]);
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+#pragma unroll
+            for (int a = 0; a < D; ++a) r[k][a] = j < g.n_points ? pts[j * D + a] : T(0);
+        }
+        int bin[IL];
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            int t[3] = {0, 0, 0}, part[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                int cell;
+                T frac;
+                ok &= fine_coord<T>(r[k][a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+                t[a] = tile_of_cell(cell, g.tq[a], g.tr[a], g.tinv[a]);
+                const int st = tile_start(t[a], g.tq[a], g.tr[a]);
+                const int wd = tile_start(t[a] + 1, g.tq[a], g.tr[a]) - st;
+                part[a] = strip_part(cell - st, wd, g.width, g.strips[a]);
+            }
+            const int lin = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
+            bin[k] = lin * g.sub + (part[0] + 3 * part[1] + 9 * part[2]);
         }
         if (!ok) atomicOr(err, 1);
-        int lin = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
-        key[j] = lin;
-        slot[j] = atomicAdd(&cnt[lin], 1);
+        int sl[IL];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            sl[k] = j < g.n_points ? atomicAdd(&cnt[bin[k]], 1) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            if (j < g.n_points) {
+                key[j] = bin[k];
+                slot[j] = sl[k];
+            }
+        }
     }
 }
 
@@ -236,7 +296,8 @@ static __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ off,
     if (i < n) off[i] += bsum[blockIdx.x];
 }
 
-// K1c: scatter every point to its tile's slice of the sorted arrays.
+// K1c: scatter every point to its sub-bin's slice of the sorted arrays (4 points per thread per
+// iteration, loads issued before the dependent offset lookups and stores).
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ pts,
                                                  const int *__restrict__ key,
@@ -245,23 +306,41 @@ __global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ p
                                                  typename PT<T>::U *__restrict__ sorted,
                                                  int *__restrict__ perm) {
     using U = typename PT<T>::U;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.n_points;
-         j += stride) {
-        int lin = key[j];
-        int64_t pos = (int64_t)off[lin] + slot[j];
-        int tc[3] = {lin % g.nb[0], (lin / g.nb[0]) % g.nb[1], lin / (g.nb[0] * g.nb[1])};
-        U u[3] = {0, 0, 0};
+    constexpr int IL = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
+         j0 += stride) {
+        int bin[IL], sl[IL];
+        T r[IL][3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-            int cell;
-            T frac;
-            fine_coord<T>(pts[j * D + a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
-            int rel = cell - tile_start(tc[a], g.nf[a], g.nb[a]);
-            u[a] = pack_coord<T>(rel, frac);
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            const bool in = j < g.n_points;
+            bin[k] = in ? key[j] : 0;
+            sl[k] = in ? slot[j] : 0;
+#pragma unroll
+            for (int a = 0; a < D; ++a) r[k][a] = in ? pts[j * D + a] : T(0);
         }
-        store_packed<T, D>(sorted, pos, u);
-        perm[pos] = (int)j;
+        int64_t pos[IL];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) pos[k] = (int64_t)off[bin[k]] + sl[k];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            if (j >= g.n_points) continue;
+            const int lin = bin[k] / g.sub;
+            const int tc[3] = {lin % g.nb[0], (lin / g.nb[0]) % g.nb[1],
+                               lin / (g.nb[0] * g.nb[1])};
+            U u[3] = {0, 0, 0};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                int cell;
+                T frac;
+                fine_coord<T>(r[k][a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+                u[a] = pack_coord<T>(cell - tile_start(tc[a], g.tq[a], g.tr[a]), frac);
+            }
+            store_record<T, D>(sorted, perm, pos[k], u, (int)j);
+        }
     }
 }
 
@@ -293,6 +372,21 @@ __device__ __forceinline__ void spread_point(const EsPoly<T> &ep, int i0x, int i
     T wx[W], wy[W];
     es_weights<T, W>(ep, x1x, wx);
     es_weights<T, W>(ep, x1y, wy);
+    if constexpr (sizeof(T) == 4 && D == 2) {
+        // footprint entirely inside the tile (most points): no per-cell bounds checks
+        if (fixed && i0x >= 0 && i0x + W <= wdx && i0y >= 0 && i0y + W <= wdy) {
+            int *base = itile + i0y * sx + i0x;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const float wys = wy[b] * fscale;
+#pragma unroll
+                for (int a = 0; a < W; ++a)
+                    atomicAdd(base + b * sx + a,
+                              __float_as_int(fmaf(wys, wx[a], 12582912.0f)) - 0x4B400000);
+            }
+            return;
+        }
+    }
     if constexpr (D == 2) {
 #pragma unroll
         for (int b = 0; b < W; ++b) {
@@ -371,10 +465,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
                                                 const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ off, T *__restrict__ grid) {
     using U = typename PT<T>::U;
-    constexpr int NNB = (D == 3) ? 27 : 9;
+    constexpr int NNB = (D == 3) ? 27 : 9;     // neighbouring tiles, this one included
+    constexpr int S = (D == 3) ? 27 : 9;       // sub-bins per tile
+    constexpr int MAXR = NNB * S;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ int nb_p0[NNB], nb_p1[NNB], nb_org[NNB][3];
-    __shared__ int s_hits;
+    __shared__ int nb_org[NNB][3], nb_tile[NNB];
+    __shared__ int r_p0[MAXR], r_start[MAXR + 1], r_q[MAXR];
+    __shared__ int s_nr, s_hits, s_edge;
     constexpr int kSpreadList = SpreadList<T>::value;
     T *ftile = reinterpret_cast<T *>(sm_raw);
     int *itile = reinterpret_cast<int *>(sm_raw);
@@ -390,8 +487,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < D) {
-            s[a] = tile_start(tc[a], g.nf[a], g.nb[a]);
-            wd[a] = tile_start(tc[a] + 1, g.nf[a], g.nb[a]) - s[a];
+            s[a] = tile_start(tc[a], g.tq[a], g.tr[a]);
+            wd[a] = tile_start(tc[a] + 1, g.tq[a], g.tr[a]) - s[a];
         } else {
             s[a] = 0;
             wd[a] = 1;
@@ -408,58 +505,123 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
                 if (b < 0) { b += g.nb[a]; shift = -g.nf[a]; }
                 else if (b >= g.nb[a]) { b -= g.nb[a]; shift = g.nf[a]; }
                 nt[a] = b;
-                nb_org[q][a] = tile_start(b, g.nf[a], g.nb[a]) + shift - s[a];
+                nb_org[q][a] = tile_start(b, g.tq[a], g.tr[a]) + shift - s[a];
             } else {
                 nt[a] = 0;
                 nb_org[q][a] = 0;
             }
         }
-        const int64_t nl = nt[0] + (int64_t)g.nb[0] * (nt[1] + (int64_t)g.nb[1] * nt[2]);
-        nb_p0[q] = off[nl];
-        nb_p1[q] = off[nl + 1];
+        nb_tile[q] = nt[0] + g.nb[0] * (nt[1] + g.nb[1] * nt[2]);
     }
-    if (threadIdx.x == 0) s_hits = 0;
+    if (threadIdx.x == 0) {
+        s_nr = 0;
+        s_hits = 0;
+        s_edge = 0;
+    }
     __syncthreads();
 
-    // 1. compact the points that reach this tile (support starts are >= -W, < tile width; the
-    //    packed form stores i0 + W in 10 bits per axis: tile edges are at most 255 cells)
-    const int lane = threadIdx.x & 31;
-    for (int q = 0; q < NNB; ++q) {
-        const int p0 = nb_p0[q], p1 = nb_p1[q];
-        for (int pb = p0; pb < p1; pb += blockDim.x) {
-            const int p = pb + threadIdx.x;
-            bool hit = p < p1;
-            int i0[3] = {0, 0, 0};
-            T x1[3] = {T(0), T(0), T(0)};
-            if (hit) {
-                U u[3];
-                load_packed<T, D>(sorted, p, u);
+    // 1. candidate ranges: every sub-bin of this tile, and of each neighbour only the border
+    //    strips that face this tile
+    for (int e = threadIdx.x; e < MAXR; e += blockDim.x) {
+        const int q = e / S, sb = e % S;
+        const int dd[3] = {q % 3 - 1, (q / 3) % 3 - 1, q / 9 - 1};
+        const int pp[3] = {sb % 3, (sb / 3) % 3, sb / 9};
+        bool ok = true;
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    int rel;
-                    T f;
-                    unpack_coord<T>(u[a], rel, f);
-                    i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
-                    hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
-                }
+        for (int a = 0; a < D; ++a)
+            if (g.strips[a]) ok = ok && (dd[a] == 0 || (dd[a] < 0 ? pp[a] == 2 : pp[a] == 0));
+        if (ok) {
+            const int64_t bin = (int64_t)nb_tile[q] * S + sb;
+            const int p0 = off[bin], p1 = off[bin + 1];
+            if (p1 > p0) {
+                const int r = atomicAdd(&s_nr, 1);
+                r_p0[r] = p0;
+                r_start[r] = p1 - p0;
+                r_q[r] = q;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, hit);
-            int base = 0;
-            if (lane == 0 && m) base = atomicAdd(&s_hits, __popc(m));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (hit) {
-                const int slot = base + __popc(m & ((1u << lane) - 1u));
-                if (slot < kSpreadList) {
-                    l_i0[slot] = (i0[0] + W) | ((i0[1] + W) << 10) | ((i0[2] + W) << 20);
+        }
+    }
+    __syncthreads();
+    const int nr = s_nr;
+    if (threadIdx.x < 32) {   // lengths -> exclusive starts, total in r_start[nr]
+        int carry = 0;
+        for (int base = 0; base < nr; base += 32) {
+            const int i = base + threadIdx.x;
+            const int v = i < nr ? r_start[i] : 0;
+            int x = v;
 #pragma unroll
-                    for (int a = 0; a < D; ++a) l_x1[a * kSpreadList + slot] = x1[a];
-                }
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if ((int)threadIdx.x >= o) x += y;
+            }
+            if (i < nr) r_start[i] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (threadIdx.x == 0) r_start[nr] = carry;
+    }
+    __syncthreads();
+    const int total = r_start[nr];
+
+    // candidate e -> (range, point); ranges are few (<= 25 in 2D), binary search over starts
+    auto candidate = [&](int e, int &q) -> int {
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (r_start[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        q = r_q[lo];
+        return r_p0[lo] + (e - r_start[lo]);
+    };
+
+    // 2. compact the candidates that reach this tile (support starts are >= -W and < the tile
+    //    width; the packed form stores i0 + W in 10 bits per axis, tile edges are <= 255).
+    //    Points whose whole support lies inside the tile go to the front of the list, the others
+    //    to the back, so warps run the unchecked and the checked accumulate separately.
+    const int lane = threadIdx.x & 31;
+    for (int eb = 0; eb < total; eb += blockDim.x) {
+        const int e = eb + threadIdx.x;
+        bool hit = e < total, inner = true;
+        int i0[3] = {0, 0, 0};
+        T x1[3] = {T(0), T(0), T(0)};
+        if (hit) {
+            int q;
+            const int p = candidate(e, q);
+            U u[3];
+            load_packed<T, D>(sorted, p, u);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                int rel;
+                T f;
+                unpack_coord<T>(u[a], rel, f);
+                i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
+                hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
+                inner = inner && (i0[a] >= 0) && (i0[a] + W <= wd[a]);
+            }
+        }
+        const unsigned mi = __ballot_sync(0xffffffffu, hit && inner);
+        const unsigned me = __ballot_sync(0xffffffffu, hit && !inner);
+        int bi = 0, be = 0;
+        if (lane == 0) {
+            if (mi) bi = atomicAdd(&s_hits, __popc(mi));
+            if (me) be = atomicAdd(&s_edge, __popc(me));
+        }
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        be = __shfl_sync(0xffffffffu, be, 0);
+        if (hit) {
+            const unsigned lt = (1u << lane) - 1u;
+            const int slot = inner ? bi + __popc(mi & lt) : kSpreadList - 1 - (be + __popc(me & lt));
+            if (slot >= 0 && slot < kSpreadList) {
+                l_i0[slot] = (i0[0] + W) | ((i0[1] + W) << 10) | ((i0[2] + W) << 20);
+#pragma unroll
+                for (int a = 0; a < D; ++a) l_x1[a * kSpreadList + slot] = x1[a];
             }
         }
     }
     const int sx = wd[0], sxy = wd[0] * wd[1], cells = sxy * wd[2];
     __syncthreads();
-    const int hits = s_hits;
+    const int n_inner = s_hits, n_edge = s_edge;
+    const int hits = n_inner + n_edge;
     const bool listed = hits <= kSpreadList;
     bool fixed = false;
     int sc = 0;
@@ -474,8 +636,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
     const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
 
     if (listed) {
-        // 2. accumulate the compacted points with full warps
-        for (int h = threadIdx.x; h < hits; h += blockDim.x) {
+        // 3. accumulate the compacted points with full warps: interior entries [0, n_inner),
+        //    edge entries [kSpreadList - n_edge, kSpreadList)
+        for (int k = threadIdx.x; k < hits; k += blockDim.x) {
+            const int h = k < n_inner ? k : kSpreadList - hits + k;
             const int pk = l_i0[h];
             const T x1x = l_x1[h], x1y = l_x1[kSpreadList + h];
             const T x1z = D == 3 ? l_x1[(D - 1) * kSpreadList + h] : T(0);
@@ -484,37 +648,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
                                   sx, sxy, ftile, itile, fixed, fscale);
         }
     } else {
-        // 2'. crowded tile: float atomics straight from the point lists
-        for (int q = 0; q < NNB; ++q) {
-            const int p0 = nb_p0[q], p1 = nb_p1[q];
-            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-                U u[3];
-                load_packed<T, D>(sorted, p, u);
-                int i0[3] = {0, 0, 0};
-                T x1[3] = {T(0), T(0), T(0)};
-                bool hit = true;
+        // 3'. crowded tile: float atomics straight from the candidate ranges
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            int q;
+            const int p = candidate(e, q);
+            U u[3];
+            load_packed<T, D>(sorted, p, u);
+            int i0[3] = {0, 0, 0};
+            T x1[3] = {T(0), T(0), T(0)};
+            bool hit = true;
 #pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    int rel;
-                    T f;
-                    unpack_coord<T>(u[a], rel, f);
-                    i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
-                    hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
-                }
-                if (hit)
-                    spread_point<T, W, D>(ep, i0[0], i0[1], i0[2], x1[0], x1[1], x1[2], wd[0],
-                                          wd[1], wd[2], sx, sxy, ftile, itile, false, fscale);
+            for (int a = 0; a < D; ++a) {
+                int rel;
+                T f;
+                unpack_coord<T>(u[a], rel, f);
+                i0[a] = nb_org[q][a] + rel + support_start<T, W>(f, x1[a]);
+                hit = hit && (i0[a] < wd[a]) && (i0[a] + W > 0);
             }
+            if (hit)
+                spread_point<T, W, D>(ep, i0[0], i0[1], i0[2], x1[0], x1[1], x1[2], wd[0], wd[1],
+                                      wd[2], sx, sxy, ftile, itile, false, fscale);
         }
     }
     __syncthreads();
     const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-        const int x = i % sx, y = (i / sx) % wd[1], z = i / sxy;
-        T v;
-        if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i] * finv : ftile[i];
-        else v = ftile[i];
-        grid[((int64_t)(s[2] + z) * g.nf[1] + (s[1] + y)) * g.nf[0] + s[0] + x] = v;
+    const int nrows = wd[1] * wd[2];
+    for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
+        const int z = D == 3 ? row / wd[1] : 0, y = D == 3 ? row - z * wd[1] : row;
+        T *dst = grid + ((int64_t)(s[2] + z) * g.nf[1] + (s[1] + y)) * g.nf[0] + s[0];
+        const int i0 = row * sx;
+        for (int x = lane; x < sx; x += 32) {
+            T v;
+            if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i0 + x] * finv : ftile[i0 + x];
+            else v = ftile[i0 + x];
+            dst[x] = v;
+        }
     }
 }
 
@@ -552,10 +720,10 @@ __global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict_
         if (D == 3) ip *= ip2[nz < 0 ? -nz : nz];
         const T re = F.x * ip, im = F.y * ip;
         const T S = (re * re + im * im) * inv_n;
-        const double d = (double)S - (double)rep_s0[e];
-        const double wgt = (double)rep_w[e];
-        lsum += wgt * d * d;
-        const T E = (T)(4.0 * wgt * d * m.inv_n);
+        const T wgt = rep_w[e];
+        const double d = (double)S - (double)rep_s0[e];   // exact difference of two T values
+        lsum = fma((double)wgt * d, d, lsum);
+        const T E = T(4) * wgt * (T)d * inv_n;
         const T h = T(0.5) * ip * E;
         const T er = re * h, ei = im * h;
         const T kx = (T)(m.kscale[0] * nx), ky = (T)(m.kscale[1] * ny);
@@ -605,7 +773,7 @@ static __global__ void __launch_bounds__(512) k_finalize(const double *__restric
 // gradient grid(s) in shared memory, then every point of the tile sums its W^D kernel-weighted
 // cells; the result, scaled by the incoming gradient, goes to the caller's order through perm.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp(Geom g, EsPoly<T> ep,
                                                 const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ perm,
                                                 const int *__restrict__ off,
@@ -625,8 +793,8 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < D) {
-            s[a] = tile_start(tc[a], g.nf[a], g.nb[a]);
-            rw[a] = tile_start(tc[a] + 1, g.nf[a], g.nb[a]) - s[a] + W;
+            s[a] = tile_start(tc[a], g.tq[a], g.tr[a]);
+            rw[a] = tile_start(tc[a] + 1, g.tq[a], g.tr[a]) - s[a] + W;
         } else {
             s[a] = 0;
             rw[a] = 1;
@@ -635,24 +803,32 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
     const int rxy = rw[0] * rw[1], cells = rxy * rw[2];
     C *sg0 = reinterpret_cast<C *>(sm_raw);
     T *sg1 = reinterpret_cast<T *>(sm_raw + sizeof(C) * (size_t)cells);
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) {
-        const int x = i % rw[0], y = (i / rw[0]) % rw[1], z = i / rxy;
-        // the staged region is narrower than the grid, so it wraps at most once per axis
-        int gx = s[0] - HL + x, gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
-        gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
-        gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
-        if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
-        const int64_t gi = ((int64_t)gz * g.nf[1] + gy) * g.nf[0] + gx;
-        sg0[i] = g0[gi];
-        if (D == 3) sg1[i] = g1[gi].x;
+    {   // stage row by row; the staged region is narrower than the grid, so it wraps at most
+        // once per axis
+        const int lane = threadIdx.x & 31;
+        const int nrows = rw[1] * rw[2];
+        for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
+            const int z = D == 3 ? row / rw[1] : 0, y = D == 3 ? row - z * rw[1] : row;
+            int gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
+            gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+            if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
+            const int64_t rbase = ((int64_t)gz * g.nf[1] + gy) * g.nf[0];
+            for (int x = lane; x < rw[0]; x += 32) {
+                int gx = s[0] - HL + x;
+                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+                const int i = row * rw[0] + x;
+                sg0[i] = g0[rbase + gx];
+                if (D == 3) sg1[i] = g1[rbase + gx].x;
+            }
+        }
     }
     __syncthreads();
 
     const T scale = grad_out ? (T)(*grad_out) : T(1);
-    const int p0 = off[t], p1 = off[t + 1];
+    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
-        load_packed<T, D>(sorted, p, u);
+        const int64_t j = load_record<T, D>(sorted, perm, p, u);
         int i0[3] = {0, 0, 0};
         T x1[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -680,7 +856,6 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
                 ax = fma(wy[b], rx, ax);
                 ay = fma(wy[b], ry, ay);
             }
-            const int64_t j = perm[p];
             using T2 = typename PT<T>::C;
             reinterpret_cast<T2 *>(grad)[j] = T2{scale * ax, scale * ay};
         } else {
@@ -708,7 +883,6 @@ __global__ void __launch_bounds__(256) k_interp(Geom g, EsPoly<T> ep,
                 ay = fma(wz[c], py, ay);
                 az = fma(wz[c], pz, az);
             }
-            const int64_t j = perm[p];
             grad[j * 3 + 0] = scale * ax;
             grad[j * 3 + 1] = scale * ay;
             grad[j * 3 + 2] = scale * az;
@@ -798,7 +972,7 @@ inline int grid_for(int64_t n, int threads, int cap) {
 template <typename T>
 cudaError_t Launch<T>::bin(const Geom &g, const T *points, int *cnt, int *key, int *slot,
                            int *err, cudaStream_t s) {
-    const int grid = grid_for(g.n_points, 256, 152 * 32);
+    const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
     if (g.dim == 2) k_bin<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
     else k_bin<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
     return cudaGetLastError();
@@ -819,7 +993,7 @@ template <typename T>
 cudaError_t Launch<T>::scatter(const Geom &g, const T *points, const int *key, const int *slot,
                                const int *off, void *sorted, int *perm, cudaStream_t s) {
     using U = typename PT<T>::U;
-    const int grid = grid_for(g.n_points, 256, 152 * 32);
+    const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
     if (g.dim == 2)
         k_scatter<T, 2><<<grid, 256, 0, s>>>(g, points, key, slot, off, (U *)sorted, perm);
     else

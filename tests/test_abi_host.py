@@ -93,7 +93,8 @@ def test_tiles_cover_the_grid(fr):
         info = _query(fr, inputs.ball_mask(K, 2), tile=tile)
         for a in range(2):
             nf, nb, tmax = info["n_fine"][a], info["n_tiles"][a], info["tile"][a]
-            starts = [b * nf // nb for b in range(nb + 1)]
+            q, r = divmod(nf, nb)
+            starts = [b * q + min(b, r) for b in range(nb + 1)]
             widths = np.diff(starts)
             assert starts[-1] == nf and widths.max() == tmax <= 255
             assert widths.min() >= (info["width"] + 1) // 2
