@@ -197,6 +197,54 @@ int64_t fresco_launch_count(fresco_plan_t p);
 fresco_status fresco_loss_noalloc(int precision, int64_t n_k, const void *d_S, const double *d_S0,
                                   const double *d_W, double *d_loss, void *stream);
 
+/* ---- Minimisation (the optimiser of the main text after Eq. 4: L-BFGS with a maximal step
+ * size and a backtracking line search) ------------------------------------------------------
+ * A solver owns device vectors (gradient, direction, trial point, m (s, y) pairs) in the plan's
+ * precision and runs on the plan's stream; inner products are accumulated in FP64. Each
+ * iteration: d = -H g by the two-loop recursion (H0 = (s.y)/(y.y) I; steepest descent when the
+ * history is empty or d is not a descent direction); step t0 = min(1, max_step / max_j |d_j|);
+ * backtracking t = t0, t0/2, ... until L(x + t d) <= L(x) + c1 t g.d; the pair (s, y) is kept when
+ * s.y > 0. The host reads one or two scalars per line-search trial. */
+typedef struct fresco_lbfgs_s *fresco_lbfgs_t;
+
+typedef struct {
+    int history;          /* stored pairs m, 1..64 (default 10) */
+    double max_step;      /* largest displacement of any coordinate per iteration; 0 -> a tenth
+                             of the mean point spacing, 0.1 min(L) N^(-1/d) */
+    double c1;            /* Armijo constant in (0, 1) (default 1e-4) */
+    int max_backtrack;    /* halvings per line search, 0..60 (default 20) */
+    double gtol;          /* stop when the RMS gradient sqrt(g.g / (N d)) < gtol (0: off) */
+    double ftol;          /* stop when the loss < ftol (0: off) */
+    int reserved[4];      /* must be zero */
+} fresco_lbfgs_opts;
+
+typedef struct {
+    int64_t iterations;   /* accepted steps since create / reset */
+    int64_t evaluations;  /* loss+gradient evaluations since create / reset */
+    double loss;          /* loss at the returned points */
+    double grad_rms;      /* RMS gradient at the returned points */
+    int status;           /* 1 gradient below gtol (or zero step), 2 loss below ftol,
+                             3 iteration limit, 4 line search failed */
+} fresco_lbfgs_report;
+
+void fresco_lbfgs_opts_default(fresco_lbfgs_opts *opts);
+
+/* Create a solver for a plan (the plan must outlive it). Allocates (2m + 4) vectors of N * dim
+ * elements of the plan's precision. Returns FRESCO_ERR_ARG or FRESCO_ERR_OOM. */
+fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
+                                  const fresco_lbfgs_opts *opts);
+
+/* Run up to max_iter iterations from the device points d_points ([N][dim], plan precision),
+ * which are updated in place; the history persists across calls (continue a run by calling
+ * again). report (host) may be NULL. Synchronises the plan's stream. */
+fresco_status fresco_lbfgs_run(fresco_lbfgs_t s, void *d_points, int64_t max_iter,
+                               fresco_lbfgs_report *report);
+
+/* Drop the stored pairs and zero the counters. */
+fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s);
+
+fresco_status fresco_lbfgs_destroy(fresco_lbfgs_t s);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

@@ -37,7 +37,8 @@ EXPORTS = (
     "fresco_get_info", "fresco_set_stream", "fresco_loss_grad", "fresco_forward",
     "fresco_backward", "fresco_get_rho_S", "fresco_loss_grad_host", "fresco_status_check",
     "fresco_profile", "fresco_profile_read", "fresco_launch_count", "fresco_destroy",
-    "fresco_status_string", "fresco_loss_noalloc",
+    "fresco_status_string", "fresco_loss_noalloc", "fresco_lbfgs_opts_default",
+    "fresco_lbfgs_create", "fresco_lbfgs_run", "fresco_lbfgs_reset", "fresco_lbfgs_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -52,6 +53,20 @@ class fresco_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("upsample", ctypes.c_double), ("width_override", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("reserved", ctypes.c_int * 4)]
+
+
+class fresco_lbfgs_opts(ctypes.Structure):
+    _fields_ = [("history", ctypes.c_int), ("max_step", ctypes.c_double), ("c1", ctypes.c_double),
+                ("max_backtrack", ctypes.c_int), ("gtol", ctypes.c_double),
+                ("ftol", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+
+class fresco_lbfgs_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("evaluations", ctypes.c_int64),
+                ("loss", ctypes.c_double), ("grad_rms", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class fresco_info(ctypes.Structure):
@@ -106,6 +121,11 @@ def load(path: str = LIB_PATH):
             "fresco_destroy": (I, [P]),
             "fresco_status_string": (ctypes.c_char_p, [I]),
             "fresco_loss_noalloc": (I, [I, I64, P, P, P, P, P]),
+            "fresco_lbfgs_opts_default": (None, [P]),
+            "fresco_lbfgs_create": (I, [P, P, P]),
+            "fresco_lbfgs_run": (I, [P, P, I64, P]),
+            "fresco_lbfgs_reset": (I, [P]),
+            "fresco_lbfgs_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -276,6 +296,67 @@ def fresco_loss_noalloc(precision, n_k, S, S0, W, loss, stream=None):
     prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
     _check(load().fresco_loss_noalloc(prec, int(n_k), _addr(S), _addr(S0), _addr(W), _addr(loss),
                                       _stream_handle(stream)), "fresco_loss_noalloc")
+
+
+def fresco_lbfgs_opts_default() -> fresco_lbfgs_opts:
+    o = fresco_lbfgs_opts()
+    load().fresco_lbfgs_opts_default(ctypes.byref(o))
+    return o
+
+
+def fresco_lbfgs_create(plan, opts=None):
+    h = ctypes.c_void_p()
+    _check(load().fresco_lbfgs_create(ctypes.byref(h), plan,
+                                      ctypes.byref(opts) if opts is not None else None),
+           "fresco_lbfgs_create")
+    return h.value
+
+
+def fresco_lbfgs_run(solver, points, max_iter) -> dict:
+    rep = fresco_lbfgs_report()
+    _check(load().fresco_lbfgs_run(solver, _addr(points), int(max_iter), ctypes.byref(rep)),
+           "fresco_lbfgs_run")
+    return rep.as_dict()
+
+
+def fresco_lbfgs_reset(solver):
+    _check(load().fresco_lbfgs_reset(solver), "fresco_lbfgs_reset")
+
+
+def fresco_lbfgs_destroy(solver):
+    if solver:
+        _check(load().fresco_lbfgs_destroy(solver), "fresco_lbfgs_destroy")
+
+
+class LBFGS:
+    """Device-resident L-BFGS over a Plan (see fresco_lbfgs_* in include/fresco.h)."""
+
+    def __init__(self, plan, history=10, max_step=0.0, c1=1e-4, max_backtrack=20, gtol=0.0,
+                 ftol=0.0):
+        o = fresco_lbfgs_opts_default()
+        o.history, o.max_step, o.c1 = int(history), float(max_step), float(c1)
+        o.max_backtrack, o.gtol, o.ftol = int(max_backtrack), float(gtol), float(ftol)
+        self.plan = plan
+        self.handle = fresco_lbfgs_create(plan.handle, o)
+
+    def run(self, points, max_iter) -> dict:
+        """Minimise in place (points: contiguous CUDA tensor [N, dim] of the plan's dtype)."""
+        self.plan._check_points(points)
+        return fresco_lbfgs_run(self.handle, points, max_iter)
+
+    def reset(self):
+        fresco_lbfgs_reset(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_lbfgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- convenience wrapper ------------------------------------------------------------------------
