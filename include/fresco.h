@@ -197,6 +197,28 @@ int64_t fresco_launch_count(fresco_plan_t p);
 fresco_status fresco_loss_noalloc(int precision, int64_t n_k, const void *d_S, const double *d_S0,
                                   const double *d_W, double *d_loss, void *stream);
 
+/* ---- Repulsive pair term of the hybrid loss (Eq. 6) ----------------------------------------
+ * E = sum_{m<n} U(|r_m - r_n|), minimum-image distance in the periodic box,
+ * U(r) = (eps / alpha)(1 - r / sigma)^alpha for r < sigma, 0 beyond (alpha = 2.5: the Hertzian
+ * potential of Eq. 6; alpha = 2: harmonic soft spheres), by a cell list (cells >= sigma wide). */
+typedef struct fresco_pair_s *fresco_pair_t;
+
+/* dim 2 or 3; box host [dim]; sigma < min(L) / 2; eps >= 0; alpha > 1; precision FRESCO_F32 or
+ * FRESCO_F64 (type of points and gradient); stream as for fresco_plan. Allocates the cell list
+ * (one int per cell, five per point) and a sorted copy of the points. */
+fresco_status fresco_pair_plan(fresco_pair_t *out, int dim, const double *box, int64_t n_points,
+                               double sigma, double eps, double alpha, int precision,
+                               void *stream);
+
+/* *d_energy = E and d_grad = dE/dr (device, [N][dim], caller order); with accumulate != 0 both
+ * are added to what the arrays hold (e.g. after fresco_loss_grad, for the hybrid loss of Eq. 6).
+ * The energy is summed in FP64 in a fixed order. Asynchronous. */
+fresco_status fresco_pair_energy_grad(fresco_pair_t p, const void *d_points, double *d_energy,
+                                      void *d_grad, int accumulate);
+
+fresco_status fresco_pair_set_stream(fresco_pair_t p, void *stream);
+fresco_status fresco_pair_destroy(fresco_pair_t p);
+
 /* ---- Minimisation (the optimiser of the main text after Eq. 4: L-BFGS with a maximal step
  * size and a backtracking line search) ------------------------------------------------------
  * A solver owns device vectors (gradient, direction, trial point, m (s, y) pairs) in the plan's
@@ -239,6 +261,10 @@ fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
  * again). report (host) may be NULL. Synchronises the plan's stream. */
 fresco_status fresco_lbfgs_run(fresco_lbfgs_t s, void *d_points, int64_t max_iter,
                                fresco_lbfgs_report *report);
+
+/* Minimise the hybrid loss of Eq. 6 from now on: every evaluation adds the pair term of p (same
+ * points, precision and stream as the plan) to the structure-factor loss. NULL removes it. */
+fresco_status fresco_lbfgs_set_pair(fresco_lbfgs_t s, fresco_pair_t p);
 
 /* Drop the stored pairs and zero the counters. */
 fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s);

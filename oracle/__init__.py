@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the bench's
 CPU-baseline leg; never by the GPU library. It shares no code with the CUDA path. The C
 source (fresco_oracle.c) writes the definitions of Eq. 1, Eq. 2 and Eq. 4 of arXiv
-2305.15693 out as plain sums; this wrapper only marshals numpy arrays.
+2305.15693 (and the pair term of the hybrid loss, Eq. 6) out as plain sums; this wrapper only
+marshals numpy arrays.
 
 Points stored in FP32 are promoted exactly to FP64, so both sides see identical inputs.
 """
@@ -47,6 +48,10 @@ def _load():
             lib.oracle_loss_grad.argtypes = [ctypes.c_int, i64, p, p, i64, p, p, p,
                                              p, p, p, p, i64, p, p]
             lib.oracle_loss_grad.restype = ctypes.c_int
+            lib.oracle_pair_energy_grad.argtypes = [ctypes.c_int, i64, p, p, ctypes.c_double,
+                                                    ctypes.c_double, ctypes.c_double, p, i64, p,
+                                                    p]
+            lib.oracle_pair_energy_grad.restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
@@ -116,3 +121,30 @@ def loss_grad(points, mask, S0, W, box=1.0, sel=None, want_grad=True):
     if rc != 0:
         raise ValueError("oracle_loss_grad failed (%d)" % rc)
     return float(loss[0]), grad, S, re + 1j * im
+
+
+def pair_energy_grad(points, sigma, eps=1.0, alpha=2.0, box=1.0, sel=None, want_grad=True,
+                     want_energy=True):
+    """Repulsive pair term of the hybrid loss (Eq. 6) by the direct double loop: returns
+    (E, grad); grad is [len(sel), dim] when `sel` is given; E is None without want_energy."""
+    r = np.ascontiguousarray(np.asarray(points).astype(np.float64))
+    dim = r.shape[1]
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)))
+    e = np.zeros(1)
+    grad = None
+    sel_arr = None
+    n_sel = 0
+    if want_grad:
+        if sel is not None:
+            sel_arr = np.ascontiguousarray(np.asarray(sel, dtype=np.int64).reshape(-1))
+            n_sel = sel_arr.size
+            grad = np.empty((n_sel, dim))
+        else:
+            grad = np.empty((r.shape[0], dim))
+    rc = _load().oracle_pair_energy_grad(dim, r.shape[0], _ptr(r), _ptr(b), float(sigma),
+                                         float(eps), float(alpha),
+                                         _ptr(e) if want_energy else None, n_sel, _ptr(sel_arr),
+                                         _ptr(grad))
+    if rc != 0:
+        raise ValueError("oracle_pair_energy_grad failed (%d)" % rc)
+    return (float(e[0]) if want_energy else None), grad

@@ -118,6 +118,59 @@ int oracle_loss_grad(int dim, int64_t n_points, const double *r, const double *b
     return 0;
 }
 
+/* Repulsive pair term of the hybrid loss (Eq. 6): E = sum_{m<n} U(|r_m - r_n|) with the
+ * minimum-image distance in the periodic box and U(r) = (eps / alpha) (1 - r / sigma)^alpha for
+ * r < sigma, 0 otherwise (alpha = 2.5: the Hertzian potential of Eq. 6; alpha = 2: harmonic).
+ * grad[j] = dE/dr_j = sum_{n != j} U'(r) (r_j - r_n) / r, U'(r) = -(eps / sigma)(1 - r/sigma)^(alpha-1).
+ * Direct O(N^2) double loop; energy or grad may be NULL; sel/n_sel select the points whose
+ * gradient is wanted (sel == NULL: all). */
+int oracle_pair_energy_grad(int dim, int64_t n_points, const double *r, const double *box,
+                            double sigma, double eps, double alpha, double *energy,
+                            int64_t n_sel, const int64_t *sel, double *grad)
+{
+    if (dim < 1 || dim > 3 || n_points < 0 || !(sigma > 0.0) || !(alpha > 1.0)) return 1;
+    double e = 0.0;
+    int64_t n_e = energy ? n_points : 0;   /* energy == NULL: gradient rows only */
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : e)
+    for (int64_t m = 0; m < n_e; ++m) {
+        for (int64_t n = m + 1; n < n_points; ++n) {
+            double d2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                double dx = r[m * dim + a] - r[n * dim + a];
+                dx -= box[a] * nearbyint(dx / box[a]);
+                d2 += dx * dx;
+            }
+            double rr = sqrt(d2);
+            if (rr < sigma) e += eps / alpha * pow(1.0 - rr / sigma, alpha);
+        }
+    }
+    if (energy) *energy = e;
+    if (grad) {
+        int64_t n_out = sel ? n_sel : n_points;
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int64_t t = 0; t < n_out; ++t) {
+            int64_t j = sel ? sel[t] : t;
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int64_t n = 0; n < n_points; ++n) {
+                if (n == j) continue;
+                double dx[3] = {0.0, 0.0, 0.0}, d2 = 0.0;
+                for (int a = 0; a < dim; ++a) {
+                    dx[a] = r[j * dim + a] - r[n * dim + a];
+                    dx[a] -= box[a] * nearbyint(dx[a] / box[a]);
+                    d2 += dx[a] * dx[a];
+                }
+                double rr = sqrt(d2);
+                if (rr < sigma && rr > 0.0) {
+                    double du = -eps / sigma * pow(1.0 - rr / sigma, alpha - 1.0);
+                    for (int a = 0; a < dim; ++a) g[a] += du * dx[a] / rr;
+                }
+            }
+            for (int a = 0; a < dim; ++a) grad[t * dim + a] = g[a];
+        }
+    }
+    return 0;
+}
+
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
 int oracle_threads(void)
 {

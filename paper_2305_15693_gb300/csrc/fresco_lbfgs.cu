@@ -137,6 +137,7 @@ __global__ void k_set(double *__restrict__ p, double v) { *p = v; }
 
 struct fresco_lbfgs_s {
     fresco_plan_t plan = nullptr;
+    fresco_pair_t pair = nullptr;
     fresco_lbfgs_opts opts{};
     int64_t n = 0;          // N * dim
     size_t es = 4;
@@ -194,6 +195,13 @@ double host_read(fresco_lbfgs_s *s, const double *dev) {
     return v;
 }
 
+// loss and gradient of the minimised function: the structure-factor loss, plus the pair term
+fresco_status evaluate(fresco_lbfgs_s *s, const void *x, double *loss, void *grad) {
+    fresco_status st = fresco_loss_grad(s->plan, x, loss, grad);
+    if (st || !s->pair) return st;
+    return fresco_pair_energy_grad(s->pair, x, loss, grad, 1);
+}
+
 template <typename T>
 fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfgs_report *rep) {
     Ops<T> op{s};
@@ -201,7 +209,7 @@ fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfg
     double *sc = s->scal;
     fresco_status st;
     // loss and gradient at the start point
-    if ((st = fresco_loss_grad(s->plan, x, s->loss_x, s->g))) return st;
+    if ((st = evaluate(s, x, s->loss_x, s->g))) return st;
     ++s->evals;
     double fx = host_read(s, s->loss_x);
     int status = 0;
@@ -249,7 +257,7 @@ fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfg
         double ft = fx;
         for (int k = 0; k <= s->opts.max_backtrack; ++k) {
             op.lincomb(s->xt, x, s->d, t);
-            if ((st = fresco_loss_grad(s->plan, s->xt, s->loss_t, s->gt))) return st;
+            if ((st = evaluate(s, s->xt, s->loss_t, s->gt))) return st;
             ++s->evals;
             ft = host_read(s, s->loss_t);
             if (std::isfinite(ft) && ft <= fx + s->opts.c1 * t * gd) {
@@ -380,6 +388,12 @@ fresco_status fresco_lbfgs_run(fresco_lbfgs_t s, void *d_points, int64_t max_ite
     s->stream = s->plan->stream;
     if (s->es == 8) return run_impl<double>(s, d_points, max_iter, report);
     return run_impl<float>(s, d_points, max_iter, report);
+}
+
+fresco_status fresco_lbfgs_set_pair(fresco_lbfgs_t s, fresco_pair_t p) {
+    if (!s) return FRESCO_ERR_ARG;
+    s->pair = p;
+    return FRESCO_OK;
 }
 
 fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s) {

@@ -39,6 +39,8 @@ EXPORTS = (
     "fresco_profile", "fresco_profile_read", "fresco_launch_count", "fresco_destroy",
     "fresco_status_string", "fresco_loss_noalloc", "fresco_lbfgs_opts_default",
     "fresco_lbfgs_create", "fresco_lbfgs_run", "fresco_lbfgs_reset", "fresco_lbfgs_destroy",
+    "fresco_lbfgs_set_pair", "fresco_pair_plan", "fresco_pair_energy_grad",
+    "fresco_pair_set_stream", "fresco_pair_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -126,6 +128,11 @@ def load(path: str = LIB_PATH):
             "fresco_lbfgs_run": (I, [P, P, I64, P]),
             "fresco_lbfgs_reset": (I, [P]),
             "fresco_lbfgs_destroy": (I, [P]),
+            "fresco_lbfgs_set_pair": (I, [P, P]),
+            "fresco_pair_plan": (I, [P, I, P, I64, D, D, D, I, P]),
+            "fresco_pair_energy_grad": (I, [P, P, P, P, I]),
+            "fresco_pair_set_stream": (I, [P, P]),
+            "fresco_pair_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -328,6 +335,75 @@ def fresco_lbfgs_destroy(solver):
         _check(load().fresco_lbfgs_destroy(solver), "fresco_lbfgs_destroy")
 
 
+def fresco_pair_plan(box, dim, n_points, sigma, eps=1.0, alpha=2.0, precision="f32",
+                     stream=None):
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)))
+    h = ctypes.c_void_p()
+    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    _check(load().fresco_pair_plan(ctypes.byref(h), int(dim), b.ctypes.data, int(n_points),
+                                   float(sigma), float(eps), float(alpha), prec,
+                                   _stream_handle(stream)), "fresco_pair_plan")
+    return h.value
+
+
+def fresco_pair_energy_grad(pair, points, energy, grad, accumulate=False):
+    _check(load().fresco_pair_energy_grad(pair, _addr(points), _addr(energy), _addr(grad),
+                                          1 if accumulate else 0), "fresco_pair_energy_grad")
+
+
+def fresco_pair_set_stream(pair, stream):
+    _check(load().fresco_pair_set_stream(pair, _stream_handle(stream)), "fresco_pair_set_stream")
+
+
+def fresco_pair_destroy(pair):
+    if pair:
+        _check(load().fresco_pair_destroy(pair), "fresco_pair_destroy")
+
+
+def fresco_lbfgs_set_pair(solver, pair):
+    _check(load().fresco_lbfgs_set_pair(solver, pair), "fresco_lbfgs_set_pair")
+
+
+class PairTerm:
+    """Repulsive pair term of the hybrid loss (Eq. 6) over torch CUDA tensors."""
+
+    def __init__(self, box, dim, n_points, sigma, eps=1.0, alpha=2.0, precision="f32",
+                 stream=None):
+        import torch
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.dim, self.n_points = int(dim), int(n_points)
+        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.handle = fresco_pair_plan(box, dim, n_points, sigma, eps, alpha, precision, stream)
+
+    def energy_grad(self, points, energy=None, grad=None, accumulate=False):
+        t = self._torch
+        if energy is None:
+            energy = t.zeros((), dtype=t.float64, device=points.device)
+        if grad is None:
+            grad = t.zeros_like(points)
+        fresco_pair_energy_grad(self.handle, points, energy, grad, accumulate)
+        return energy, grad
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_pair_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 class LBFGS:
     """Device-resident L-BFGS over a Plan (see fresco_lbfgs_* in include/fresco.h)."""
 
@@ -338,6 +414,11 @@ class LBFGS:
         o.max_backtrack, o.gtol, o.ftol = int(max_backtrack), float(gtol), float(ftol)
         self.plan = plan
         self.handle = fresco_lbfgs_create(plan.handle, o)
+
+    def set_pair(self, pair):
+        """Minimise the hybrid loss of Eq. 6 (a PairTerm, or None to drop it)."""
+        self.pair = pair
+        fresco_lbfgs_set_pair(self.handle, pair.handle if pair is not None else None)
 
     def run(self, points, max_iter) -> dict:
         """Minimise in place (points: contiguous CUDA tensor [N, dim] of the plan's dtype)."""

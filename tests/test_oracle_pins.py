@@ -170,3 +170,47 @@ def test_lattice_ground_state_is_stealthy():
                                         np.ones(mask.shape[0]))
     assert loss < 1e-20
     assert np.max(np.abs(grad)) < 1e-9
+
+
+# ---- repulsive pair term of the hybrid loss (Eq. 6) ------------------------------------------
+
+@pytest.mark.parametrize("alpha", [2.0, 2.5])
+def test_pair_two_points_closed_form_and_periodic_image(alpha):
+    sigma, eps = 0.2, 1.7
+    # direct distance 0.12 along y; 0.12 again through the periodic image along x for the second
+    for pts, r in ((np.array([[0.3, 0.40], [0.3, 0.52]]), 0.12),
+                   (np.array([[0.04, 0.5], [0.92, 0.5]]), 0.12)):
+        e, g = oracle.pair_energy_grad(pts, sigma, eps, alpha, box=1.0)
+        assert e == pytest.approx(eps / alpha * (1 - r / sigma) ** alpha, rel=1e-12)
+        du = -eps / sigma * (1 - r / sigma) ** (alpha - 1)
+        dx = pts[0] - pts[1]
+        dx -= np.round(dx)
+        np.testing.assert_allclose(g[0], du * dx / r, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(g[1], -g[0], rtol=1e-12, atol=1e-14)
+    e, g = oracle.pair_energy_grad(np.array([[0.1, 0.1], [0.1, 0.35]]), sigma, eps, alpha)
+    assert e == 0.0 and np.all(g == 0.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_pair_gradient_central_differences_and_invariance(dim):
+    g = inputs.rng(90 + dim)
+    N = 40
+    box = np.linspace(1.0, 1.2, dim)
+    pts = g.random((N, dim)) * box
+    sigma = 0.6 * (np.prod(box) / N) ** (1.0 / dim) * 2
+    e, grad = oracle.pair_energy_grad(pts, sigma, 1.3, 2.5, box=box)
+    assert e > 0
+    h = 1e-7
+    fd = np.zeros_like(pts)
+    for j in range(N):
+        for a in range(dim):
+            p = pts.copy()
+            p[j, a] += h
+            ep, _ = oracle.pair_energy_grad(p, sigma, 1.3, 2.5, box=box, want_grad=False)
+            p[j, a] -= 2 * h
+            em, _ = oracle.pair_energy_grad(p, sigma, 1.3, 2.5, box=box, want_grad=False)
+            fd[j, a] = (ep - em) / (2 * h)
+    assert np.linalg.norm(fd - grad) / np.linalg.norm(grad) < 1e-6
+    assert np.linalg.norm(grad.sum(axis=0)) < 1e-10 * np.linalg.norm(grad)
+    e2, _ = oracle.pair_energy_grad(pts + 0.37, sigma, 1.3, 2.5, box=box, want_grad=False)
+    assert e2 == pytest.approx(e, rel=1e-12)
