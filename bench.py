@@ -138,6 +138,22 @@ def load_peaks():
 
 # ---------------------------------------------------------------------------------------------
 
+def max_over_ranks(value: float, dist_on: bool, device=None) -> float:
+    """Largest value over all ranks (the slowest replica sets the step time)."""
+    if not dist_on:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(n_points: int, world: int, t_step: float) -> float:
+    """Whole-job points/s when each of `world` ranks evaluates its own n_points-point replica in
+    t_step seconds (weak scaling: no data crosses ranks)."""
+    return world * n_points / t_step
+
+
 def make_inputs(wl):
     t0 = time.time()
     pts = wl.points()
@@ -331,19 +347,12 @@ def main():
     clocks.start()
     ms, launches, stages, loss_val = time_device(plan, pts, args.steps, args.warmup, dist_on)
     clk = clocks.stop()
-    t_step = ms / args.steps / 1e3
-    if dist_on:
-        t = torch.tensor([t_step], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
-    value = world * N / t_step
+    t_step = max_over_ranks(ms / args.steps / 1e3, dist_on, "cuda")
+    value = replica_throughput(N, world, t_step)
 
     # e2e through the host-buffer entry point
     dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
-    if dist_on:
-        t = torch.tensor([dt_e2e], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt_e2e = float(t.item())
+    dt_e2e = max_over_ranks(dt_e2e, dist_on, "cuda")
     plan.close()
 
     # ---- per-stage roofline ------------------------------------------------------------------
@@ -413,7 +422,8 @@ def main():
             "stages": per_stage,
             "fp64": f64,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * N / dt_e2e, "unit": "points/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": replica_throughput(N, world, dt_e2e), "unit": "points/s",
+                    "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * dt_e2e},
             "clocks": clk,
             "gpu_launches": launches,
