@@ -271,6 +271,41 @@ fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s);
 
 fresco_status fresco_lbfgs_destroy(fresco_lbfgs_t s);
 
+/* ---- Ensembles: many independent problems in one set of launches ---------------------------
+ * A batch plan holds n_inst independent 2D problems (points, box, mask, S0, W each their own,
+ * the same precision and tolerance). Their points are packed one instance after the other in a
+ * single device array; every stage (sort, spread, mask, interpolation) runs as one launch over
+ * all instances, and the uniform FFTs run per size class (fine grids rounded up to 2^k or 3 2^k),
+ * one batched cuFFT call per class and direction. The result for instance i is exactly what
+ * fresco_plan / fresco_loss_grad give for that problem alone (up to the larger fine grid). */
+typedef struct fresco_batch_s *fresco_batch_t;
+
+/* boxes: host [n_inst][dim]; n_points, n_modes: host [n_inst]; masks: host int32, the instances'
+ * masks concatenated ([sum n_modes][dim]); S0, W: host double, concatenated. dim must be 2
+ * (3D returns FRESCO_ERR_UNSUPPORTED). Argument rules as for fresco_plan, per instance. */
+fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const double *boxes,
+                                const int64_t *n_points, const int64_t *n_modes,
+                                const int32_t *masks, const double *S0, const double *W,
+                                const fresco_opts *opts, void *stream);
+
+/* d_points: device [sum N][dim] (instance after instance); d_losses: device double [n_inst];
+ * d_grad: device [sum N][dim] or NULL (losses only). Asynchronous. */
+fresco_status fresco_batch_loss_grad(fresco_batch_t b, const void *d_points, double *d_losses,
+                                     void *d_grad);
+
+/* Record one fresco_batch_loss_grad on these (fixed) pointers as a CUDA graph, after running it
+ * once normally; fresco_batch_graph_launch replays it on the plan's stream. The plan needs a
+ * non-default stream for capture. */
+fresco_status fresco_batch_graph_capture(fresco_batch_t b, const void *d_points, double *d_losses,
+                                         void *d_grad);
+fresco_status fresco_batch_graph_launch(fresco_batch_t b);
+
+/* Any argument may be NULL. */
+fresco_status fresco_batch_info(fresco_batch_t b, int64_t *total_points, int *n_classes,
+                                int64_t *device_bytes, int64_t *launches);
+fresco_status fresco_batch_status_check(fresco_batch_t b);
+fresco_status fresco_batch_destroy(fresco_batch_t b);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

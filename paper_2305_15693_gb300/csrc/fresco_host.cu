@@ -192,6 +192,61 @@ int choose_tiles(int nf, int target, int w) {
     return best;
 }
 
+// Tiles: the requested (or default) edge per axis, shrunk while the interpolation tile plus its
+// halo, or the spread tile plus its point list, would not fit the shared-memory budget (2 blocks
+// per SM by default, the opt-in maximum when the caller fixed the tiles). Needs P.nf, P.width,
+// P.dim, P.precision.
+fresco_status choose_tiling(Params &P, const int tile_req[3]) {
+    const int dim = P.dim, w = P.width;
+    const size_t es = P.precision == FRESCO_F64 ? 8 : 4;
+    const bool user_tiles = tile_req[0] > 0 || tile_req[1] > 0 || tile_req[2] > 0;
+    size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
+    int target[3];
+    auto reset_targets = [&]() {
+        for (int a = 0; a < dim; ++a) {
+            int deft = dim == 2 ? 48 : (a < 2 ? 16 : 8);
+            target[a] = tile_req[a] > 0 ? tile_req[a] : deft;
+        }
+    };
+    reset_targets();
+    for (int a = 0; a < dim; ++a)
+        if (target[a] > kMaxTileEdge) return FRESCO_ERR_ARG;
+    for (int iter = 0;; ++iter) {
+        for (int a = 0; a < dim; ++a) {
+            P.nb[a] = choose_tiles(P.nf[a], target[a], w);
+            P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
+        }
+        size_t halo_cells = 1, cells = 1;
+        for (int a = 0; a < dim; ++a) {
+            halo_cells *= (size_t)(P.tmax[a] + w);
+            cells *= (size_t)P.tmax[a];
+        }
+        const size_t interp = halo_cells * (2 * es + (dim == 3 ? es : 0));
+        // tile (at least 4-byte cells) plus the compacted point list (2048 float / 1024 double
+        // entries of one int and dim coordinates)
+        const size_t spread = ((cells * std::max<size_t>(es, 4) + 15) & ~(size_t)15) +
+                              (es == 8 ? 1024 : 2048) * (es * dim + 4);
+        if (interp <= budget && spread <= budget) break;
+        int amax = 0;
+        for (int a = 1; a < dim; ++a)
+            if (P.tmax[a] > P.tmax[amax]) amax = a;
+        const int minw = (w + 1) / 2;
+        if (target[amax] <= minw || iter > 256) {
+            if (budget >= kSmemOptin) return FRESCO_ERR_UNSUPPORTED;
+            budget = kSmemOptin;   // one block per SM rather than no plan
+            reset_targets();
+            iter = 0;
+            continue;
+        }
+        target[amax] = std::max(minw, std::min(target[amax] - 1, (P.tmax[amax] * 3) / 4));
+    }
+    for (int a = P.dim; a < 3; ++a) {
+        P.nb[a] = 1;
+        P.tmax[a] = 1;
+    }
+    return FRESCO_OK;
+}
+
 fresco_status check_and_params(int dim, const double *box, int64_t n_points, const int32_t *mask,
                                int64_t n_k, const double *S0, const double *W,
                                const fresco_opts *opts_in, Params &P) {
@@ -248,51 +303,8 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
             P.tmax[a] = 1;
         }
     }
-    // Tiles: the requested (or default) edge per axis, shrunk while the interpolation tile plus
-    // its halo would not fit the shared-memory budget (2 blocks per SM by default, the opt-in
-    // maximum when the caller fixed the tiles).
-    const size_t es = o.precision == FRESCO_F64 ? 8 : 4;
-    const bool user_tiles = o.tile[0] > 0 || o.tile[1] > 0 || o.tile[2] > 0;
-    size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
-    int target[3];
-    auto reset_targets = [&]() {
-        for (int a = 0; a < dim; ++a) {
-            int deft = dim == 2 ? 48 : (a < 2 ? 16 : 8);
-            target[a] = o.tile[a] > 0 ? o.tile[a] : deft;
-        }
-    };
-    reset_targets();
-    for (int a = 0; a < dim; ++a)
-        if (target[a] > kMaxTileEdge) return FRESCO_ERR_ARG;
-    for (int iter = 0;; ++iter) {
-        for (int a = 0; a < dim; ++a) {
-            P.nb[a] = choose_tiles(P.nf[a], target[a], w);
-            P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
-        }
-        size_t halo_cells = 1, cells = 1;
-        for (int a = 0; a < dim; ++a) {
-            halo_cells *= (size_t)(P.tmax[a] + w);
-            cells *= (size_t)P.tmax[a];
-        }
-        const size_t interp = halo_cells * (2 * es + (dim == 3 ? es : 0));
-        // tile (at least 4-byte cells) plus the compacted point list (2048 float / 1024 double
-        // entries of one int and dim coordinates)
-        const size_t spread = ((cells * std::max<size_t>(es, 4) + 15) & ~(size_t)15) +
-                              (es == 8 ? 1024 : 2048) * (es * dim + 4);
-        if (interp <= budget && spread <= budget) break;
-        int amax = 0;
-        for (int a = 1; a < dim; ++a)
-            if (P.tmax[a] > P.tmax[amax]) amax = a;
-        const int minw = (w + 1) / 2;
-        if (target[amax] <= minw || iter > 256) {
-            if (budget >= kSmemOptin) return FRESCO_ERR_UNSUPPORTED;
-            budget = kSmemOptin;   // one block per SM rather than no plan
-            reset_targets();
-            iter = 0;
-            continue;
-        }
-        target[amax] = std::max(minw, std::min(target[amax] - 1, (P.tmax[amax] * 3) / 4));
-    }
+    fresco_status st = choose_tiling(P, o.tile);
+    if (st) return st;
     int64_t cells = (int64_t)P.nf[0] * P.nf[1] * P.nf[2];
     if (cells > (int64_t)1 << 36) return FRESCO_ERR_UNSUPPORTED;
     int64_t tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
@@ -986,6 +998,513 @@ int64_t fresco_launch_count(fresco_plan_t p) { return p ? p->launches : -1; }
 
 fresco_status fresco_destroy(fresco_plan_t p) {
     release(p);
+    return FRESCO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Ensembles: many independent problems evaluated by one set of launches
+// ============================================================================================
+
+struct fresco_batch_s {
+    struct Cls {
+        int nf[2] = {0, 0};
+        int kx = 0;
+        int count = 0;
+        int64_t go0 = 0, ao0 = 0, ato0 = 0, hco0 = 0, ro0 = 0;
+        cufftHandle h[4] = {0, 0, 0, 0};   // rows R2C, cols fwd, cols inv, rows inv
+        bool have[4] = {false, false, false, false};
+    };
+    int dim = 0;
+    int precision = FRESCO_F32;
+    size_t esize = 4;
+    int n_inst = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<BInst> inst;
+    std::vector<Cls> cls;
+    std::vector<int64_t> pt_first, tile_first, mblk_first;
+    BTables tab{};
+    EsPoly<float> poly32{};
+    EsPoly<double> poly64{};
+    int64_t n_points = 0, n_bins = 0, n_rep = 0;
+    int64_t cells = 0, n_spec = 0, n_specT = 0, n_hc = 0;
+    // device
+    BInst *d_inst = nullptr;
+    int64_t *d_pt_first = nullptr, *d_tile_first = nullptr, *d_mblk_first = nullptr;
+    void *sorted = nullptr;
+    int *perm = nullptr, *key = nullptr, *slot = nullptr, *cnt = nullptr, *off = nullptr;
+    int *bsum = nullptr, *err = nullptr;
+    void *grid = nullptr, *spec = nullptr, *specT = nullptr, *hc = nullptr, *bt = nullptr;
+    void *r = nullptr, *g = nullptr;
+    int *rep_n = nullptr;
+    void *rep_s0 = nullptr, *rep_w = nullptr, *ip = nullptr;
+    double *partial = nullptr;
+    void *work = nullptr;
+    std::vector<void *> allocs;
+    int64_t device_bytes = 0;
+    int64_t launches = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+bool balloc(fresco_batch_s *b, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    b->allocs.push_back(*p);
+    b->device_bytes += (int64_t)bytes;
+    return true;
+}
+
+void batch_free(fresco_batch_s *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto &c : b->cls)
+        for (int i = 0; i < 4; ++i)
+            if (c.have[i]) cufftDestroy(c.h[i]);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+// FFT size class of a fine-grid size: the smallest 2^k or 3 * 2^k (k >= 3) not below it
+int class_size(int nf) {
+    int best = 1 << 30;
+    for (int64_t p = 8; p < (1 << 27); p *= 2) {
+        if (p >= nf && p < best) best = (int)p;
+        if (3 * p / 2 >= nf && 3 * p / 2 < best && (3 * p / 2) % 2 == 0) best = (int)(3 * p / 2);
+    }
+    return best;
+}
+
+template <typename T>
+fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
+                          const std::vector<Folded> &F, const double *boxes,
+                          const int64_t *n_points) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const int dim = b->dim;
+    const int n = b->n_inst;
+    // ---- classes (by fine grid size), per-class kx
+    std::vector<int> cls_of(n);
+    for (int i = 0; i < n; ++i) {
+        int found = -1;
+        for (size_t c = 0; c < b->cls.size(); ++c)
+            if (b->cls[c].nf[0] == P[i].nf[0] && b->cls[c].nf[1] == P[i].nf[1]) found = (int)c;
+        if (found < 0) {
+            fresco_batch_s::Cls c;
+            c.nf[0] = P[i].nf[0];
+            c.nf[1] = P[i].nf[1];
+            b->cls.push_back(c);
+            found = (int)b->cls.size() - 1;
+        }
+        cls_of[i] = found;
+        b->cls[found].kx = std::max(b->cls[found].kx, P[i].kmax[0]);
+        b->cls[found].count += 1;
+    }
+    // ---- caller-order offsets
+    b->inst.assign(n, BInst{});
+    b->pt_first.assign(n + 1, 0);
+    b->tile_first.assign(n + 1, 0);
+    b->mblk_first.assign(n + 1, 0);
+    int64_t bo = 0, reo = 0, ipo = 0;
+    int tmax[3] = {1, 1, 1};
+    for (int i = 0; i < n; ++i) {
+        BInst &I = b->inst[i];
+        const Params &p = P[i];
+        const int64_t nt = (int64_t)p.nb[0] * p.nb[1] * p.nb[2];
+        const int64_t nrep = (int64_t)F[i].s0.size();
+        b->pt_first[i + 1] = b->pt_first[i] + n_points[i];
+        b->tile_first[i + 1] = b->tile_first[i] + nt;
+        b->mblk_first[i + 1] =
+            b->mblk_first[i] + std::max<int64_t>(1, std::min<int64_t>((nrep + 1023) / 1024, 64));
+        I.po = b->pt_first[i];
+        I.bo = bo;
+        I.reo = reo;
+        for (int a = 0; a < 3; ++a) {
+            I.ipo[a] = ipo;
+            if (a < dim) ipo += p.kmax[a] + 1;
+            tmax[a] = std::max(tmax[a], p.tmax[a]);
+        }
+        bo += nt * (dim == 3 ? 27 : 9);
+        reo += nrep;
+        I.loss_const = F[i].loss_const;
+    }
+    b->n_points = b->pt_first[n];
+    b->n_bins = bo;
+    b->n_rep = reo;
+    if (b->n_points > 2147483647LL || b->n_bins > 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
+    // ---- class-order offsets (grids and spectra of a class are contiguous)
+    int64_t go = 0, ao = 0, ato = 0, hco = 0, ro = 0;
+    for (size_t c = 0; c < b->cls.size(); ++c) {
+        auto &K = b->cls[c];
+        K.go0 = go; K.ao0 = ao; K.ato0 = ato; K.hco0 = hco; K.ro0 = ro;
+        const int64_t plane = K.nf[1], cells = (int64_t)K.nf[0] * K.nf[1];
+        const int64_t half = K.nf[0] / 2 + 1;
+        for (int i = 0; i < n; ++i) {
+            if (cls_of[i] != (int)c) continue;
+            BInst &I = b->inst[i];
+            I.go = go; I.ao = ao; I.ato = ato; I.hco = hco; I.ro = ro;
+            go += cells;
+            ao += plane * half;
+            ato += plane * (K.kx + 1);
+            hco += plane * (2 * (int64_t)K.kx + 2);
+            ro += cells;
+        }
+    }
+    b->cells = go;
+    b->n_spec = ao;
+    b->n_specT = ato;
+    b->n_hc = hco;
+    // ---- per-instance geometry
+    std::vector<double> ip_h((size_t)std::max<int64_t>(ipo, 1));
+    for (int i = 0; i < n; ++i) {
+        BInst &I = b->inst[i];
+        const Params &p = P[i];
+        const auto &K = b->cls[cls_of[i]];
+        Geom &g = I.g;
+        g.dim = dim;
+        for (int a = 0; a < 3; ++a) {
+            g.nf[a] = p.nf[a];
+            g.nb[a] = p.nb[a];
+            g.tmax[a] = p.tmax[a];
+            g.tq[a] = p.nf[a] / p.nb[a];
+            g.tr[a] = p.nf[a] % p.nb[a];
+            g.tinv[a] = (float)p.nb[a] / (float)p.nf[a];
+            const double L = a < dim ? boxes[(size_t)i * dim + a] : 1.0;
+            double sc = a < dim ? (double)p.nf[a] / L : 0.0;
+            double shi = (double)(T)sc;
+            long double slo = (long double)p.nf[a] / (long double)L - (long double)shi;
+            g.s_hi[a] = shi;
+            g.s_lo[a] = a < dim ? (double)(T)(double)slo : 0.0;
+            I.m.nf[a] = p.nf[a];
+            I.m.kscale[a] = a < dim ? 2.0 * kPi / L : 0.0;
+        }
+        g.n_tiles = (int64_t)p.nb[0] * p.nb[1] * p.nb[2];
+        g.sub = dim == 3 ? 27 : 9;
+        for (int a = 0; a < 3; ++a) g.strips[a] = a < dim && p.nf[a] / p.nb[a] >= p.width ? 1 : 0;
+        g.n_bins = g.n_tiles * g.sub;
+        g.n_points = n_points[i];
+        g.width = p.width;
+        g.beta = p.beta;
+        I.m.dim = dim;
+        I.m.kx = K.kx;
+        I.m.n_rep = (int64_t)F[i].s0.size();
+        I.m.half_row = p.nf[0] / 2 + 1;
+        I.m.hc_row = 2 * (int64_t)K.kx + 2;
+        I.m.plane = (int64_t)p.nf[1] * p.nf[2];
+        I.m.inv_n = 1.0 / (double)n_points[i];
+        for (int a = 0; a < dim; ++a) {
+            std::vector<double> ft(p.kmax[a] + 1);
+            kernel_ft(p.width, p.beta, p.nf[a], (int64_t)ft.size(), ft.data());
+            for (size_t k = 0; k < ft.size(); ++k) ip_h[I.ipo[a] + k] = 1.0 / ft[k];
+        }
+    }
+    es_poly<float>(P[0].width, P[0].beta, b->poly32);
+    es_poly<double>(P[0].width, P[0].beta, b->poly64);
+    // ---- device buffers
+    const size_t N = (size_t)b->n_points;
+    const int rw = sizeof(T) == 4 ? 4 : (dim == 3 ? 4 : 2);
+    bool ok = balloc(b, (void **)&b->d_inst, sizeof(BInst) * n) &&
+              balloc(b, (void **)&b->d_pt_first, sizeof(int64_t) * (n + 1)) &&
+              balloc(b, (void **)&b->d_tile_first, sizeof(int64_t) * (n + 1)) &&
+              balloc(b, (void **)&b->d_mblk_first, sizeof(int64_t) * (n + 1)) &&
+              balloc(b, &b->sorted, sizeof(T) * N * rw) &&
+              (sizeof(T) == 4 || balloc(b, (void **)&b->perm, sizeof(int) * N)) &&
+              balloc(b, (void **)&b->key, sizeof(int) * N) &&
+              balloc(b, (void **)&b->slot, sizeof(int) * N) &&
+              balloc(b, (void **)&b->cnt, sizeof(int) * b->n_bins) &&
+              balloc(b, (void **)&b->off, sizeof(int) * (b->n_bins + 1)) &&
+              balloc(b, (void **)&b->bsum, sizeof(int) * ((b->n_bins + 1023) / 1024 + 1)) &&
+              balloc(b, (void **)&b->err, sizeof(int)) &&
+              balloc(b, &b->grid, sizeof(T) * b->cells) &&
+              balloc(b, &b->spec, sizeof(C2) * b->n_spec) &&
+              balloc(b, &b->specT, sizeof(C2) * b->n_specT) &&
+              balloc(b, &b->hc, sizeof(C2) * b->n_hc) && balloc(b, &b->bt, sizeof(C2) * b->n_hc) &&
+              balloc(b, &b->r, sizeof(C2) * b->cells) && balloc(b, &b->g, sizeof(C2) * b->cells) &&
+              balloc(b, (void **)&b->rep_n, sizeof(int) * b->n_rep * dim) &&
+              balloc(b, &b->rep_s0, sizeof(T) * b->n_rep) &&
+              balloc(b, &b->rep_w, sizeof(T) * b->n_rep) &&
+              balloc(b, &b->ip, sizeof(T) * ip_h.size()) &&
+              balloc(b, (void **)&b->partial, sizeof(double) * b->mblk_first[n]);
+    if (!ok) return FRESCO_ERR_OOM;
+    {
+        std::vector<int32_t> rn;
+        std::vector<T> s0, w;
+        rn.reserve((size_t)b->n_rep * dim);
+        s0.reserve((size_t)b->n_rep);
+        w.reserve((size_t)b->n_rep);
+        for (int i = 0; i < n; ++i) {
+            rn.insert(rn.end(), F[i].n.begin(), F[i].n.end());
+            for (size_t k = 0; k < F[i].s0.size(); ++k) {
+                s0.push_back((T)F[i].s0[k]);
+                w.push_back((T)F[i].w[k]);
+            }
+        }
+        std::vector<T> ipt(ip_h.size());
+        for (size_t k = 0; k < ip_h.size(); ++k) ipt[k] = (T)ip_h[k];
+        FR_CUDA(cudaMemcpy(b->rep_n, rn.data(), sizeof(int) * rn.size(), cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->rep_s0, s0.data(), sizeof(T) * s0.size(), cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->rep_w, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->ip, ipt.data(), sizeof(T) * ipt.size(), cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->d_pt_first, b->pt_first.data(), sizeof(int64_t) * (n + 1),
+                           cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->d_tile_first, b->tile_first.data(), sizeof(int64_t) * (n + 1),
+                           cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemcpy(b->d_mblk_first, b->mblk_first.data(), sizeof(int64_t) * (n + 1),
+                           cudaMemcpyHostToDevice));
+        FR_CUDA(cudaMemset(b->hc, 0, sizeof(C2) * b->n_hc));
+        FR_CUDA(cudaMemset(b->r, 0, sizeof(C2) * b->cells));
+        FR_CUDA(cudaMemset(b->err, 0, sizeof(int)));
+    }
+    BTables &t = b->tab;
+    t.inst = b->d_inst;
+    t.pt_first = b->d_pt_first;
+    t.tile_first = b->d_tile_first;
+    t.mblk_first = b->d_mblk_first;
+    t.n_inst = n;
+    t.dim = dim;
+    t.width = P[0].width;
+    t.n_points = b->n_points;
+    t.n_tiles = b->tile_first[n];
+    t.n_mblk = b->mblk_first[n];
+    for (int a = 0; a < 3; ++a) t.tmax[a] = tmax[a];
+    {   // shared memory of the ensemble kernels must fit every instance's tiles
+        int dev = 0, optin = 0;
+        FR_CUDA(cudaGetDevice(&dev));
+        FR_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        Geom tg{};
+        tg.dim = dim;
+        tg.width = t.width;
+        for (int a = 0; a < 3; ++a) tg.tmax[a] = tmax[a];
+        if (Launch<T>::spread_smem(tg) > optin || Launch<T>::interp_smem(tg) > optin)
+            return FRESCO_ERR_UNSUPPORTED;
+    }
+    // ---- cuFFT plans per class (all transforms of a class in one batch)
+    size_t wmax = 0;
+    for (auto &K : b->cls) {
+        size_t ws = 0;
+        for (int i = 0; i < 4; ++i) {
+            FR_CUFFT(cufftCreate(&K.h[i]));
+            K.have[i] = true;
+            FR_CUFFT(cufftSetAutoAllocation(K.h[i], 0));
+        }
+        long long n0 = K.nf[0], n1 = K.nf[1], half = K.nf[0] / 2 + 1, cnt = K.count;
+        FR_CUFFT(cufftMakePlanMany64(K.h[0], 1, &n0, nullptr, 1, n0, nullptr, 1, half,
+                                     r2c_type<T>(), cnt * n1, &ws));
+        wmax = std::max(wmax, ws);
+        FR_CUFFT(cufftMakePlanMany64(K.h[1], 1, &n1, nullptr, 1, n1, nullptr, 1, n1, c2c_type<T>(),
+                                     cnt * (K.kx + 1), &ws));
+        wmax = std::max(wmax, ws);
+        FR_CUFFT(cufftMakePlanMany64(K.h[2], 1, &n1, nullptr, 1, n1, nullptr, 1, n1, c2c_type<T>(),
+                                     cnt * (2 * (long long)K.kx + 2), &ws));
+        wmax = std::max(wmax, ws);
+        FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, n0, nullptr, 1, n0, c2c_type<T>(),
+                                     cnt * n1, &ws));
+        wmax = std::max(wmax, ws);
+    }
+    if (!balloc(b, &b->work, wmax)) return FRESCO_ERR_OOM;
+    for (auto &K : b->cls)
+        for (int i = 0; i < 4; ++i) {
+            FR_CUFFT(cufftSetWorkArea(K.h[i], b->work));
+            FR_CUFFT(cufftSetStream(K.h[i], b->stream));
+        }
+    FR_CUDA(cudaDeviceSynchronize());
+    return FRESCO_OK;
+}
+
+template <typename T>
+const EsPoly<T> &bpoly(const fresco_batch_s *b);
+template <>
+const EsPoly<float> &bpoly<float>(const fresco_batch_s *b) { return b->poly32; }
+template <>
+const EsPoly<double> &bpoly<double>(const fresco_batch_s *b) { return b->poly64; }
+
+template <typename T>
+fresco_status batch_eval(fresco_batch_s *b, const T *pts, double *losses, T *grad) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    cudaStream_t s = b->stream;
+    const BTables &t = b->tab;
+    FR_CUDA(cudaMemsetAsync(b->cnt, 0, sizeof(int) * (size_t)b->n_bins, s));
+    FR_CUDA(Launch<T>::bin_b(t, pts, b->cnt, b->key, b->slot, b->err, s));
+    int nl = 0;
+    FR_CUDA(Launch<T>::scan(b->cnt, b->off, b->bsum, b->n_bins, s, &nl));
+    FR_CUDA(Launch<T>::scatter_b(t, pts, b->key, b->slot, b->off, b->sorted, b->perm, s));
+    FR_CUDA(Launch<T>::spread_b(t, bpoly<T>(b), b->sorted, b->off, (T *)b->grid, s));
+    b->launches += 4 + nl;
+    for (auto &K : b->cls) {   // forward FFT of each class
+        const int64_t half = K.nf[0] / 2 + 1, plane = K.nf[1];
+        C2 *A = (C2 *)b->spec + K.ao0, *AT = (C2 *)b->specT + K.ato0;
+        if (sizeof(T) == 4)
+            FR_CUFFT(cufftExecR2C(K.h[0], (cufftReal *)((T *)b->grid + K.go0), (cufftComplex *)A));
+        else
+            FR_CUFFT(cufftExecD2Z(K.h[0], (cufftDoubleReal *)((T *)b->grid + K.go0),
+                                  (cufftDoubleComplex *)A));
+        FR_CUDA(Launch<T>::cols_to_rows(A, AT, plane, half, K.kx + 1, s, K.count, plane * half,
+                                        plane * (K.kx + 1)));
+        if (sizeof(T) == 4)
+            FR_CUFFT(cufftExecC2C(K.h[1], (cufftComplex *)AT, (cufftComplex *)AT, CUFFT_FORWARD));
+        else
+            FR_CUFFT(cufftExecZ2Z(K.h[1], (cufftDoubleComplex *)AT, (cufftDoubleComplex *)AT,
+                                  CUFFT_FORWARD));
+        b->launches += 1;
+    }
+    FR_CUDA(Launch<T>::mask_b(t, b->rep_n, (const T *)b->rep_s0, (const T *)b->rep_w, b->specT,
+                              (const T *)b->ip, b->hc, nullptr, b->partial, s));
+    FR_CUDA(Launch<T>::finalize_b(t, b->partial, losses, s));
+    b->launches += 2;
+    if (!grad) return FRESCO_OK;
+    for (auto &K : b->cls) {   // inverse FFT of each class
+        const int64_t plane = K.nf[1];
+        C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0, *R = (C2 *)b->r + K.ro0;
+        C2 *G = (C2 *)b->g + K.ro0;
+        if (sizeof(T) == 4)
+            FR_CUFFT(cufftExecC2C(K.h[2], (cufftComplex *)H, (cufftComplex *)BT, CUFFT_INVERSE));
+        else
+            FR_CUFFT(cufftExecZ2Z(K.h[2], (cufftDoubleComplex *)H, (cufftDoubleComplex *)BT,
+                                  CUFFT_INVERSE));
+        FR_CUDA(Launch<T>::rows_to_cols(BT, R, plane, K.nf[0], K.kx, s, K.count,
+                                        plane * (2 * (int64_t)K.kx + 2),
+                                        (int64_t)K.nf[0] * plane));
+        if (sizeof(T) == 4)
+            FR_CUFFT(cufftExecC2C(K.h[3], (cufftComplex *)R, (cufftComplex *)G, CUFFT_INVERSE));
+        else
+            FR_CUFFT(cufftExecZ2Z(K.h[3], (cufftDoubleComplex *)R, (cufftDoubleComplex *)G,
+                                  CUFFT_INVERSE));
+        b->launches += 1;
+    }
+    FR_CUDA(Launch<T>::interp_b(t, bpoly<T>(b), b->sorted, b->perm, b->off, b->g, nullptr,
+                                nullptr, grad, s));
+    b->launches += 1;
+    return FRESCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const double *boxes,
+                                const int64_t *n_points, const int64_t *n_modes,
+                                const int32_t *masks, const double *S0, const double *W,
+                                const fresco_opts *opts, void *stream) {
+    if (!out) return FRESCO_ERR_ARG;
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return FRESCO_ERR_ARG;
+    if (dim != 2) return FRESCO_ERR_UNSUPPORTED;
+    if (n_inst < 1 || !boxes || !n_points || !n_modes || !masks || !S0 || !W)
+        return FRESCO_ERR_ARG;
+    std::vector<Params> P(n_inst);
+    std::vector<Folded> F(n_inst);
+    int64_t m0 = 0;
+    fresco_opts o;
+    fresco_opts_default(&o);
+    if (opts) o = *opts;
+    for (int i = 0; i < n_inst; ++i) {
+        if (n_modes[i] < 1) return FRESCO_ERR_ARG;
+        fresco_status st = check_and_params(dim, boxes + (size_t)i * dim, n_points[i],
+                                            masks + m0 * dim, n_modes[i], S0 + m0, W + m0, &o,
+                                            P[i]);
+        if (st) return st;
+        if (i > 0 && P[i].width != P[0].width) return FRESCO_ERR_UNSUPPORTED;
+        for (int a = 0; a < dim; ++a) P[i].nf[a] = class_size(P[i].nf[a]);
+        if ((st = choose_tiling(P[i], o.tile))) return st;
+        if ((st = fold_mask(P[i], masks + m0 * dim, n_modes[i], S0 + m0, W + m0, F[i]))) return st;
+        if (F[i].s0.empty()) return FRESCO_ERR_ARG;
+        m0 += n_modes[i];
+    }
+    fresco_batch_s *b = new (std::nothrow) fresco_batch_s();
+    if (!b) return FRESCO_ERR_OOM;
+    b->dim = dim;
+    b->precision = o.precision;
+    b->esize = o.precision == FRESCO_F64 ? 8 : 4;
+    b->n_inst = n_inst;
+    b->stream = (cudaStream_t)stream;
+    fresco_status st = o.precision == FRESCO_F64 ? batch_build<double>(b, P, F, boxes, n_points)
+                                                 : batch_build<float>(b, P, F, boxes, n_points);
+    if (st) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_batch_loss_grad(fresco_batch_t b, const void *d_points, double *d_losses,
+                                     void *d_grad) {
+    if (!b || !d_points || !d_losses) return FRESCO_ERR_ARG;
+    if (b->precision == FRESCO_F64)
+        return batch_eval<double>(b, (const double *)d_points, d_losses, (double *)d_grad);
+    return batch_eval<float>(b, (const float *)d_points, d_losses, (float *)d_grad);
+}
+
+fresco_status fresco_batch_graph_capture(fresco_batch_t b, const void *d_points, double *d_losses,
+                                         void *d_grad) {
+    if (!b || !d_points || !d_losses || !b->stream) return FRESCO_ERR_ARG;
+    // one ordinary evaluation first (sets kernel attributes, warms the cuFFT plans)
+    fresco_status st = fresco_batch_loss_grad(b, d_points, d_losses, d_grad);
+    if (st) return st;
+    FR_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    FR_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    st = fresco_batch_loss_grad(b, d_points, d_losses, d_grad);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (st) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    FR_CUDA(e);
+    b->graph = graph;
+    FR_CUDA(cudaGraphInstantiate(&b->gexec, graph, 0));
+    return FRESCO_OK;
+}
+
+fresco_status fresco_batch_graph_launch(fresco_batch_t b) {
+    if (!b || !b->gexec) return FRESCO_ERR_ARG;
+    FR_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    return FRESCO_OK;
+}
+
+fresco_status fresco_batch_info(fresco_batch_t b, int64_t *total_points, int *n_classes,
+                                int64_t *device_bytes, int64_t *launches) {
+    if (!b) return FRESCO_ERR_ARG;
+    if (total_points) *total_points = b->n_points;
+    if (n_classes) *n_classes = (int)b->cls.size();
+    if (device_bytes) *device_bytes = b->device_bytes;
+    if (launches) *launches = b->launches;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_batch_status_check(fresco_batch_t b) {
+    if (!b) return FRESCO_ERR_ARG;
+    FR_CUDA(b->stream ? cudaStreamSynchronize(b->stream) : cudaDeviceSynchronize());
+    int err = 0;
+    FR_CUDA(cudaMemcpy(&err, b->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        int zero = 0;
+        FR_CUDA(cudaMemcpy(b->err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return FRESCO_ERR_NONFINITE;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+fresco_status fresco_batch_destroy(fresco_batch_t b) {
+    batch_free(b);
     return FRESCO_OK;
 }
 

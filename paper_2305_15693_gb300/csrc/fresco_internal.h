@@ -71,6 +71,38 @@ struct EsPoly {
     T c[kMaxWidth][PolyDeg<T>::value + 1];
 };
 
+// One instance of an ensemble (batch plan): its geometry and where its data sit in the packed
+// buffers. Instances are listed in the caller's order; point, sub-bin, tile, mask-block and
+// representative offsets grow in that order. Grid and spectrum offsets follow the FFT size classes
+// (instances of a class are contiguous there, so cuFFT transforms a class in one batch).
+struct BInst {
+    Geom g;
+    MaskGeom m;
+    int64_t po;        // first point
+    int64_t bo;        // first sub-bin
+    int64_t go;        // first fine-grid cell (real grid)
+    int64_t ao;        // forward half spectrum (complex elements)
+    int64_t ato;       // transposed forward spectrum
+    int64_t hco;       // transposed compact backward spectrum (and the buffer after its y pass)
+    int64_t ro;        // R and G (complex elements)
+    int64_t reo;       // first representative
+    int64_t ipo[3];    // 1 / Psi tables per axis
+    double loss_const;
+};
+
+// Device tables of a batch plan, passed to the ensemble launchers.
+struct BTables {
+    const BInst *inst;
+    const int64_t *pt_first;     // [n_inst + 1]
+    const int64_t *tile_first;   // [n_inst + 1]
+    const int64_t *mblk_first;   // [n_inst + 1]
+    int n_inst;
+    int dim;
+    int width;
+    int64_t n_points, n_tiles, n_mblk;
+    int tmax[3];                 // widest tile over all instances (shared-memory sizing)
+};
+
 enum Stage { ST_SORT = 0, ST_SPREAD, ST_FFT_FWD, ST_MASK, ST_LOSS, ST_FFT_INV, ST_INTERP,
              ST_COUNT };
 
@@ -96,9 +128,27 @@ struct Launch {
                               const int *perm, const int *off, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s);
     static cudaError_t cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda,
-                                    int ncols, cudaStream_t s);
+                                    int ncols, cudaStream_t s, int batch = 1,
+                                    int64_t a_stride = 0, int64_t at_stride = 0);
     static cudaError_t rows_to_cols(const void *bt, void *r, int64_t rows, int nf0, int kx,
-                                    cudaStream_t s);
+                                    cudaStream_t s, int batch = 1, int64_t bt_stride = 0,
+                                    int64_t r_stride = 0);
+    // ensemble (batched) launchers: one launch over every instance of a batch plan
+    static cudaError_t bin_b(const BTables &b, const T *points, int *cnt, int *key, int *slot,
+                             int *err, cudaStream_t s);
+    static cudaError_t scatter_b(const BTables &b, const T *points, const int *key,
+                                 const int *slot, const int *off, void *sorted, int *perm,
+                                 cudaStream_t s);
+    static cudaError_t spread_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *off, T *grid, cudaStream_t s);
+    static cudaError_t mask_b(const BTables &b, const int *rep_n, const T *rep_s0,
+                              const T *rep_w, const void *spec, const T *ip, void *hc0, void *hc1,
+                              double *partial, cudaStream_t s);
+    static cudaError_t finalize_b(const BTables &b, const double *partial, double *losses,
+                                  cudaStream_t s);
+    static cudaError_t interp_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *perm, const int *off, const void *g0, const void *g1,
+                                const double *grad_out, T *grad, cudaStream_t s);
     static cudaError_t rho_s(const MaskGeom &m, const int *mask_n, int64_t n_k, const void *spec,
                              const T *ip0, const T *ip1, const T *ip2, T *rho, T *S,
                              cudaStream_t s);

@@ -21,6 +21,8 @@
 
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "fresco_internal.h"
@@ -344,6 +346,86 @@ __global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ p
     }
 }
 
+// Largest i with first[i] <= v (first is ascending, first[0] = 0).
+__device__ __forceinline__ int find_segment(const int64_t *__restrict__ first, int n, int64_t v) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched K1a / K1c: the points of all instances, packed in instance order; each point finds its
+// instance by binary search over the first-point offsets and bins with that instance's geometry
+// into the instance's own range of sub-bins.
+template <typename T, int D>
+__device__ __forceinline__ int bin_point(const Geom &g, const T *__restrict__ p, bool &ok) {
+    int t[3] = {0, 0, 0}, part[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int cell;
+        T frac;
+        ok &= fine_coord<T>(p[a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+        t[a] = tile_of_cell(cell, g.tq[a], g.tr[a], g.tinv[a]);
+        const int st = tile_start(t[a], g.tq[a], g.tr[a]);
+        const int wd = tile_start(t[a] + 1, g.tq[a], g.tr[a]) - st;
+        part[a] = strip_part(cell - st, wd, g.width, g.strips[a]);
+    }
+    const int lin = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
+    return lin * g.sub + (part[0] + 3 * part[1] + 9 * part[2]);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_bin_b(const BInst *__restrict__ inst,
+                                               const int64_t *__restrict__ pt_first, int n_inst,
+                                               int64_t n_points, const T *__restrict__ pts,
+                                               int *__restrict__ cnt, int *__restrict__ key,
+                                               int *__restrict__ slot, int *__restrict__ err) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool ok = true;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_points; j += stride) {
+        const int i = find_segment(pt_first, n_inst, j);
+        const BInst &I = inst[i];
+        const int bin = (int)I.bo + bin_point<T, D>(I.g, pts + j * D, ok);
+        key[j] = bin;
+        slot[j] = atomicAdd(&cnt[bin], 1);
+    }
+    if (!ok) atomicOr(err, 1);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_scatter_b(const BInst *__restrict__ inst,
+                                                   const int64_t *__restrict__ pt_first,
+                                                   int n_inst, int64_t n_points,
+                                                   const T *__restrict__ pts,
+                                                   const int *__restrict__ key,
+                                                   const int *__restrict__ slot,
+                                                   const int *__restrict__ off,
+                                                   typename PT<T>::U *__restrict__ sorted,
+                                                   int *__restrict__ perm) {
+    using U = typename PT<T>::U;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n_points; j += stride) {
+        const int i = find_segment(pt_first, n_inst, j);
+        const Geom &g = inst[i].g;
+        const int bin = key[j];
+        const int64_t pos = (int64_t)off[bin] + slot[j];
+        const int lin = (bin - (int)inst[i].bo) / g.sub;
+        const int tc[3] = {lin % g.nb[0], (lin / g.nb[0]) % g.nb[1], lin / (g.nb[0] * g.nb[1])};
+        U u[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int cell;
+            T frac;
+            fine_coord<T>(pts[j * D + a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
+            u[a] = pack_coord<T>(cell - tile_start(tc[a], g.tq[a], g.tr[a]), frac);
+        }
+        store_record<T, D>(sorted, perm, pos, u, (int)j);
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // K2: type-1 spreading. One block owns one tile of the fine grid: it accumulates, in shared
 // memory, the kernel contributions of every point (from its own tile and the 3^D neighbouring
@@ -461,9 +543,10 @@ __host__ __device__ inline size_t spread_tile_bytes(const Geom &g, size_t esize)
 }
 
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, EsPoly<T> ep,
-                                                const typename PT<T>::U *__restrict__ sorted,
-                                                const int *__restrict__ off, T *__restrict__ grid) {
+__device__ __forceinline__ void spread_tile(const Geom &g, const EsPoly<T> &ep,
+                                            const typename PT<T>::U *__restrict__ sorted,
+                                            const int *__restrict__ off, T *__restrict__ grid,
+                                            const int64_t t) {
     using U = typename PT<T>::U;
     constexpr int NNB = (D == 3) ? 27 : 9;     // neighbouring tiles, this one included
     constexpr int S = (D == 3) ? 27 : 9;       // sub-bins per tile
@@ -480,7 +563,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
     T *l_x1 = reinterpret_cast<T *>(sm_raw + tb);                       // [D][kSpreadList]
     int *l_i0 = reinterpret_cast<int *>(sm_raw + tb + sizeof(T) * D * kSpreadList);
 
-    const int64_t t = blockIdx.x;
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
     int s[3], wd[3];
@@ -686,6 +768,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
     }
 }
 
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, EsPoly<T> ep,
+                                                const typename PT<T>::U *__restrict__ sorted,
+                                                const int *__restrict__ off, T *__restrict__ grid) {
+    spread_tile<T, W, D>(g, ep, sorted, off, grid, blockIdx.x);
+}
+
+// Batched spread: a persistent grid walks the tiles of every instance of the ensemble.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_b(
+    const BInst *__restrict__ inst, const int64_t *__restrict__ tile_first, int n_inst,
+    int64_t n_tiles, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ off, T *__restrict__ grid) {
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int i = find_segment(tile_first, n_inst, t);
+        const BInst &I = inst[i];
+        spread_tile<T, W, D>(I.g, ep, sorted, off + I.bo, grid + I.go, t - tile_first[i]);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // K4: deconvolve and crop to the mask, S, the loss partial sums and the gradient coefficients.
 // For each half-space representative n (n_x >= 0), with ip = 1 / Psi(n):
@@ -695,20 +798,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, 
 //   H1[n] = a_z ip / 2, H1[-n] = conj(a_z) ip / 2 (pipeline 1, 3D).
 // The inverse FFT of H then gives d/dr_x + i d/dr_y on the grid (before interpolation).
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict__ rep_n,
-                                              const T *__restrict__ rep_s0,
-                                              const T *__restrict__ rep_w,
-                                              const typename PT<T>::C *__restrict__ spec,
-                                              const T *__restrict__ ip0, const T *__restrict__ ip1,
-                                              const T *__restrict__ ip2,
-                                              typename PT<T>::C *__restrict__ hc0,
-                                              typename PT<T>::C *__restrict__ hc1,
-                                              double *__restrict__ partial) {
+__device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__restrict__ rep_n,
+                                             const T *__restrict__ rep_s0,
+                                             const T *__restrict__ rep_w,
+                                             const typename PT<T>::C *__restrict__ spec,
+                                             const T *__restrict__ ip0, const T *__restrict__ ip1,
+                                             const T *__restrict__ ip2,
+                                             typename PT<T>::C *__restrict__ hc0,
+                                             typename PT<T>::C *__restrict__ hc1, int64_t e0,
+                                             int64_t stride) {
     using C = typename PT<T>::C;
     double lsum = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const T inv_n = (T)m.inv_n;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m.n_rep; e += stride) {
+    for (int64_t e = e0; e < m.n_rep; e += stride) {
         const int nx = rep_n[e * D + 0];
         const int ny = rep_n[e * D + 1];
         const int nz = (D == 3) ? rep_n[e * D + 2] : 0;
@@ -740,17 +842,76 @@ __global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict_
             hc1[cm] = C{-kz * ei, -kz * er};
         }
     }
-    // block reduction of the FP64 loss partials (fixed order: deterministic)
-    __shared__ double wsum[8];
+    return lsum;
+}
+
+// block reduction of FP64 partials (fixed order: deterministic); result in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double wsum[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = lsum;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double b = 0.0;
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double b = 0.0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += wsum[w];
-        partial[blockIdx.x] = b;
-    }
+    return b;
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_mask(MaskGeom m, const int *__restrict__ rep_n,
+                                              const T *__restrict__ rep_s0,
+                                              const T *__restrict__ rep_w,
+                                              const typename PT<T>::C *__restrict__ spec,
+                                              const T *__restrict__ ip0, const T *__restrict__ ip1,
+                                              const T *__restrict__ ip2,
+                                              typename PT<T>::C *__restrict__ hc0,
+                                              typename PT<T>::C *__restrict__ hc1,
+                                              double *__restrict__ partial) {
+    const double lsum = mask_range<T, D>(m, rep_n, rep_s0, rep_w, spec, ip0, ip1, ip2, hc0, hc1,
+                                         (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                         (int64_t)gridDim.x * blockDim.x);
+    const double b = block_sum(lsum);
+    if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
+// Batched mask: blocks [I.mb0, I.mb1) work on instance I only, so every partial belongs to one
+// instance and the per-instance sums stay in a fixed order.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_mask_b(const BInst *__restrict__ inst,
+                                                const int64_t *__restrict__ mblk_first, int n_inst,
+                                                const int *__restrict__ rep_n,
+                                                const T *__restrict__ rep_s0,
+                                                const T *__restrict__ rep_w,
+                                                const typename PT<T>::C *__restrict__ spec,
+                                                const T *__restrict__ ip,
+                                                typename PT<T>::C *__restrict__ hc0,
+                                                typename PT<T>::C *__restrict__ hc1,
+                                                double *__restrict__ partial) {
+    const int i = find_segment(mblk_first, n_inst, blockIdx.x);
+    const BInst &I = inst[i];
+    const int64_t nb = mblk_first[i + 1] - mblk_first[i];
+    const int64_t b = blockIdx.x - mblk_first[i];
+    const double lsum = mask_range<T, D>(
+        I.m, rep_n + I.reo * D, rep_s0 + I.reo, rep_w + I.reo, spec + I.ato, ip + I.ipo[0],
+        ip + I.ipo[1], ip + I.ipo[2], hc0 + I.hco, D == 3 ? hc1 + I.hco : hc1,
+        b * blockDim.x + threadIdx.x, nb * blockDim.x);
+    const double s = block_sum(lsum);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// per-instance second stage: block i sums the partials of instance i in a fixed order
+static __global__ void __launch_bounds__(256) k_finalize_b(const BInst *__restrict__ inst,
+                                                           const int64_t *__restrict__ mblk_first,
+                                                           const double *__restrict__ partial,
+                                                           double *__restrict__ losses) {
+    const int i = blockIdx.x;
+    double v = 0.0;
+    for (int64_t k = mblk_first[i] + threadIdx.x; k < mblk_first[i + 1]; k += blockDim.x)
+        v += partial[k];
+    const double s = block_sum(v);
+    if (threadIdx.x == 0) losses[i] = s + inst[i].loss_const;
 }
 
 // K5: second-stage loss sum in a fixed order, plus the folding constant.
@@ -773,19 +934,18 @@ static __global__ void __launch_bounds__(512) k_finalize(const double *__restric
 // gradient grid(s) in shared memory, then every point of the tile sums its W^D kernel-weighted
 // cells; the result, scaled by the incoming gradient, goes to the caller's order through perm.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp(Geom g, EsPoly<T> ep,
-                                                const typename PT<T>::U *__restrict__ sorted,
-                                                const int *__restrict__ perm,
-                                                const int *__restrict__ off,
-                                                const typename PT<T>::C *__restrict__ g0,
-                                                const typename PT<T>::C *__restrict__ g1,
-                                                const double *__restrict__ grad_out,
-                                                T *__restrict__ grad) {
+__device__ __forceinline__ void interp_tile(const Geom &g, const EsPoly<T> &ep,
+                                            const typename PT<T>::U *__restrict__ sorted,
+                                            const int *__restrict__ perm,
+                                            const int *__restrict__ off,
+                                            const typename PT<T>::C *__restrict__ g0,
+                                            const typename PT<T>::C *__restrict__ g1,
+                                            const double *__restrict__ grad_out,
+                                            T *__restrict__ grad, const int64_t t) {
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
     extern __shared__ __align__(16) unsigned char sm_raw[];
 
-    const int64_t t = blockIdx.x;
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
     constexpr int HL = W / 2;  // halo before the tile; W - HL after it
@@ -890,6 +1050,35 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp(Geom g, 
     }
 }
 
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp(Geom g, EsPoly<T> ep,
+                                                const typename PT<T>::U *__restrict__ sorted,
+                                                const int *__restrict__ perm,
+                                                const int *__restrict__ off,
+                                                const typename PT<T>::C *__restrict__ g0,
+                                                const typename PT<T>::C *__restrict__ g1,
+                                                const double *__restrict__ grad_out,
+                                                T *__restrict__ grad) {
+    interp_tile<T, W, D>(g, ep, sorted, perm, off, g0, g1, grad_out, grad, blockIdx.x);
+}
+
+// Batched interpolation: a persistent grid walks the tiles of every instance.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_b(
+    const BInst *__restrict__ inst, const int64_t *__restrict__ tile_first, int n_inst,
+    int64_t n_tiles, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ perm, const int *__restrict__ off,
+    const typename PT<T>::C *__restrict__ g0, const typename PT<T>::C *__restrict__ g1,
+    const double *__restrict__ grad_out, T *__restrict__ grad) {
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int i = find_segment(tile_first, n_inst, t);
+        const BInst &I = inst[i];
+        interp_tile<T, W, D>(I.g, ep, sorted, perm, off + I.bo, g0 + I.ro,
+                             D == 3 ? g1 + I.ro : g1, grad_out, grad, t - tile_first[i]);
+        __syncthreads();
+    }
+}
+
 // rho and S for the mask rows as given to the plan (diagnostic output).
 template <typename T, int D>
 __global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
@@ -918,8 +1107,11 @@ __global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
 // at[c][r] = a[r][c] for r < rows, c < ncols (a has row stride lda)
 template <typename C>
 __global__ void __launch_bounds__(256) k_cols_to_rows(const C *__restrict__ a, C *__restrict__ at,
-                                                      int64_t rows, int64_t lda, int ncols) {
+                                                      int64_t rows, int64_t lda, int ncols,
+                                                      int64_t a_stride, int64_t at_stride) {
     __shared__ C tile[32][33];
+    a += blockIdx.z * a_stride;
+    at += blockIdx.z * at_stride;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
@@ -938,8 +1130,11 @@ __global__ void __launch_bounds__(256) k_cols_to_rows(const C *__restrict__ a, C
 // r[row][x(c)] = bt[c][row] for c < 2 kx + 2, x(c) = c - kx - 1 taken modulo nf0
 template <typename C>
 __global__ void __launch_bounds__(256) k_rows_to_cols(const C *__restrict__ bt, C *__restrict__ r,
-                                                      int64_t rows, int nf0, int kx) {
+                                                      int64_t rows, int nf0, int kx,
+                                                      int64_t bt_stride, int64_t r_stride) {
     __shared__ C tile[32][33];
+    bt += blockIdx.z * bt_stride;
+    r += blockIdx.z * r_stride;
     const int ncols = 2 * kx + 2;
     const int c0 = blockIdx.y * 32;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
@@ -1112,19 +1307,23 @@ cudaError_t Launch<T>::finalize(const double *partial, int n_blocks, double loss
 
 template <typename T>
 cudaError_t Launch<T>::cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda, int ncols,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int batch, int64_t a_stride,
+                                    int64_t at_stride) {
     using C = typename PT<T>::C;
-    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((ncols + 31) / 32));
-    k_cols_to_rows<C><<<grid, dim3(32, 8), 0, s>>>((const C *)a, (C *)at, rows, lda, ncols);
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((ncols + 31) / 32), (unsigned)batch);
+    k_cols_to_rows<C><<<grid, dim3(32, 8), 0, s>>>((const C *)a, (C *)at, rows, lda, ncols,
+                                                   a_stride, at_stride);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::rows_to_cols(const void *bt, void *r, int64_t rows, int nf0, int kx,
-                                    cudaStream_t s) {
+                                    cudaStream_t s, int batch, int64_t bt_stride,
+                                    int64_t r_stride) {
     using C = typename PT<T>::C;
-    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((2 * kx + 2 + 31) / 32));
-    k_rows_to_cols<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, nf0, kx);
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((2 * kx + 2 + 31) / 32), (unsigned)batch);
+    k_rows_to_cols<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, nf0, kx,
+                                                   bt_stride, r_stride);
     return cudaGetLastError();
 }
 
@@ -1138,6 +1337,121 @@ cudaError_t Launch<T>::rho_s(const MaskGeom &m, const int *mask_n, int64_t n_k, 
         k_rho_s<T, 2><<<grid, 256, 0, s>>>(m, mask_n, n_k, (const C *)spec, ip0, ip1, ip2, rho, S);
     else
         k_rho_s<T, 3><<<grid, 256, 0, s>>>(m, mask_n, n_k, (const C *)spec, ip0, ip1, ip2, rho, S);
+    return cudaGetLastError();
+}
+
+// ---- ensemble launchers ----------------------------------------------------------------------
+
+inline Geom tiles_geom(const BTables &b) {
+    Geom g{};
+    g.dim = b.dim;
+    g.width = b.width;
+    for (int a = 0; a < 3; ++a) g.tmax[a] = b.tmax[a];
+    return g;
+}
+
+template <typename T>
+cudaError_t Launch<T>::bin_b(const BTables &b, const T *points, int *cnt, int *key, int *slot,
+                             int *err, cudaStream_t s) {
+    const int grid = grid_for(b.n_points, 256, 152 * 16);
+    if (b.dim == 2)
+        k_bin_b<T, 2><<<grid, 256, 0, s>>>(b.inst, b.pt_first, b.n_inst, b.n_points, points, cnt,
+                                           key, slot, err);
+    else
+        k_bin_b<T, 3><<<grid, 256, 0, s>>>(b.inst, b.pt_first, b.n_inst, b.n_points, points, cnt,
+                                           key, slot, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::scatter_b(const BTables &b, const T *points, const int *key,
+                                 const int *slot, const int *off, void *sorted, int *perm,
+                                 cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int grid = grid_for(b.n_points, 256, 152 * 16);
+    if (b.dim == 2)
+        k_scatter_b<T, 2><<<grid, 256, 0, s>>>(b.inst, b.pt_first, b.n_inst, b.n_points, points,
+                                               key, slot, off, (U *)sorted, perm);
+    else
+        k_scatter_b<T, 3><<<grid, 256, 0, s>>>(b.inst, b.pt_first, b.n_inst, b.n_points, points,
+                                               key, slot, off, (U *)sorted, perm);
+    return cudaGetLastError();
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_spread_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                    const int *off, T *grid, cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int smem = Launch<T>::spread_smem(tiles_geom(b));
+    auto kern = k_spread_b<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>(b.n_tiles, 152 * 8);
+    kern<<<blocks, 256, smem, s>>>(b.inst, b.tile_first, b.n_inst, b.n_tiles, ep, (const U *)sorted,
+                                   off, grid);
+    return cudaGetLastError();
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_interp_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                    const int *perm, const int *off, const void *g0,
+                                    const void *g1, const double *grad_out, T *grad,
+                                    cudaStream_t s) {
+    using U = typename PT<T>::U;
+    using C = typename PT<T>::C;
+    const int smem = Launch<T>::interp_smem(tiles_geom(b));
+    auto kern = k_interp_b<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>(b.n_tiles, 152 * 8);
+    kern<<<blocks, 256, smem, s>>>(b.inst, b.tile_first, b.n_inst, b.n_tiles, ep, (const U *)sorted,
+                                   perm, off, (const C *)g0, (const C *)g1, grad_out, grad);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::spread_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *off, T *grid, cudaStream_t s) {
+    if (b.dim == 2) {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_spread_bw<T, WW, 2>(b, ep, sorted, off, grid, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_spread_bw<T, WW, 3>(b, ep, sorted, off, grid, s)));
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::interp_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *perm, const int *off, const void *g0, const void *g1,
+                                const double *grad_out, T *grad, cudaStream_t s) {
+    if (b.dim == 2) {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_bw<T, WW, 2>(b, ep, sorted, perm, off,
+                                                                        g0, g1, grad_out, grad, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_bw<T, WW, 3>(b, ep, sorted, perm, off,
+                                                                        g0, g1, grad_out, grad, s)));
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::mask_b(const BTables &b, const int *rep_n, const T *rep_s0, const T *rep_w,
+                              const void *spec, const T *ip, void *hc0, void *hc1,
+                              double *partial, cudaStream_t s) {
+    using C = typename PT<T>::C;
+    if (b.dim == 2)
+        k_mask_b<T, 2><<<(unsigned)b.n_mblk, 256, 0, s>>>(b.inst, b.mblk_first, b.n_inst, rep_n,
+                                                          rep_s0, rep_w, (const C *)spec, ip,
+                                                          (C *)hc0, (C *)hc1, partial);
+    else
+        k_mask_b<T, 3><<<(unsigned)b.n_mblk, 256, 0, s>>>(b.inst, b.mblk_first, b.n_inst, rep_n,
+                                                          rep_s0, rep_w, (const C *)spec, ip,
+                                                          (C *)hc0, (C *)hc1, partial);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::finalize_b(const BTables &b, const double *partial, double *losses,
+                                  cudaStream_t s) {
+    k_finalize_b<<<b.n_inst, 256, 0, s>>>(b.inst, b.mblk_first, partial, losses);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,9 @@ EXPORTS = (
     "fresco_status_string", "fresco_loss_noalloc", "fresco_lbfgs_opts_default",
     "fresco_lbfgs_create", "fresco_lbfgs_run", "fresco_lbfgs_reset", "fresco_lbfgs_destroy",
     "fresco_lbfgs_set_pair", "fresco_pair_plan", "fresco_pair_energy_grad",
-    "fresco_pair_set_stream", "fresco_pair_destroy",
+    "fresco_pair_set_stream", "fresco_pair_destroy", "fresco_batch_plan",
+    "fresco_batch_loss_grad", "fresco_batch_graph_capture", "fresco_batch_graph_launch",
+    "fresco_batch_info", "fresco_batch_status_check", "fresco_batch_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -133,6 +135,13 @@ def load(path: str = LIB_PATH):
             "fresco_pair_energy_grad": (I, [P, P, P, P, I]),
             "fresco_pair_set_stream": (I, [P, P]),
             "fresco_pair_destroy": (I, [P]),
+            "fresco_batch_plan": (I, [P, I, I, P, P, P, P, P, P, P, P]),
+            "fresco_batch_loss_grad": (I, [P, P, P, P]),
+            "fresco_batch_graph_capture": (I, [P, P, P, P]),
+            "fresco_batch_graph_launch": (I, [P]),
+            "fresco_batch_info": (I, [P, P, P, P, P]),
+            "fresco_batch_status_check": (I, [P]),
+            "fresco_batch_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -362,6 +371,144 @@ def fresco_pair_destroy(pair):
 
 def fresco_lbfgs_set_pair(solver, pair):
     _check(load().fresco_lbfgs_set_pair(solver, pair), "fresco_lbfgs_set_pair")
+
+
+def fresco_batch_plan(boxes, n_points, masks, S0s, Ws, opts=None, stream=None):
+    """Batch plan over independent 2D problems: boxes [n_inst][dim] (or scalars), n_points
+    [n_inst], and per instance a mask [n_k, dim], S0 [n_k], W [n_k] (lists of arrays)."""
+    lib = load()
+    n = len(n_points)
+    if not (len(masks) == len(S0s) == len(Ws) == n) or n < 1:
+        raise ValueError("one mask, S0 and W per instance")
+    arrs = [_host_arrays(boxes[i], masks[i], S0s[i], Ws[i]) for i in range(n)]
+    dim = arrs[0][0]
+    if any(a[0] != dim for a in arrs):
+        raise ValueError("all instances need the same dimension")
+    box = np.ascontiguousarray(np.stack([a[1] for a in arrs]))
+    mask = np.ascontiguousarray(np.concatenate([a[2] for a in arrs]))
+    S0 = np.ascontiguousarray(np.concatenate([a[3] for a in arrs]))
+    W = np.ascontiguousarray(np.concatenate([a[4] for a in arrs]))
+    npts = np.ascontiguousarray(np.asarray(n_points, dtype=np.int64))
+    nmod = np.ascontiguousarray(np.array([a[2].shape[0] for a in arrs], dtype=np.int64))
+    h = ctypes.c_void_p()
+    st = lib.fresco_batch_plan(ctypes.byref(h), dim, n, box.ctypes.data, npts.ctypes.data,
+                               nmod.ctypes.data, mask.ctypes.data, S0.ctypes.data, W.ctypes.data,
+                               ctypes.byref(opts) if opts is not None else None,
+                               _stream_handle(stream))
+    _check(st, "fresco_batch_plan")
+    return h.value
+
+
+def fresco_batch_loss_grad(batch, points, losses, grad=None):
+    _check(load().fresco_batch_loss_grad(batch, _addr(points), _addr(losses), _addr(grad)),
+           "fresco_batch_loss_grad")
+
+
+def fresco_batch_graph_capture(batch, points, losses, grad=None):
+    _check(load().fresco_batch_graph_capture(batch, _addr(points), _addr(losses), _addr(grad)),
+           "fresco_batch_graph_capture")
+
+
+def fresco_batch_graph_launch(batch):
+    _check(load().fresco_batch_graph_launch(batch), "fresco_batch_graph_launch")
+
+
+def fresco_batch_info(batch) -> dict:
+    tp, nc = ctypes.c_int64(), ctypes.c_int()
+    db, nl = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fresco_batch_info(batch, ctypes.byref(tp), ctypes.byref(nc), ctypes.byref(db),
+                                    ctypes.byref(nl)), "fresco_batch_info")
+    return {"total_points": tp.value, "n_classes": nc.value, "device_bytes": db.value,
+            "launches": nl.value}
+
+
+def fresco_batch_status_check(batch) -> int:
+    return load().fresco_batch_status_check(batch)
+
+
+def fresco_batch_destroy(batch):
+    _check(load().fresco_batch_destroy(batch), "fresco_batch_destroy")
+
+
+class Batch:
+    """Ensemble of independent 2D problems evaluated together (fresco_batch_* in
+    include/fresco.h). Points of all instances are one CUDA tensor [sum N, dim], instance after
+    instance; losses come back as a float64 tensor [n_inst]. The batch runs on a stream of its
+    own (needed for graph capture), ordered after and before torch's current stream."""
+
+    def __init__(self, boxes, n_points, masks, S0s, Ws, precision="f32", tol=0.0, upsample=2.0,
+                 width=0, tile=None, stream=None):
+        import torch
+        self._torch = torch
+        self.opts = make_opts(precision, tol, upsample, width, tile)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.n_points = [int(n) for n in n_points]
+        self.first = np.concatenate([[0], np.cumsum(self.n_points)]).astype(np.int64)
+        self.dim = np.asarray(masks[0]).shape[1]
+        self.dtype = torch.float64 if self.opts.precision == FRESCO_F64 else torch.float32
+        self.handle = fresco_batch_plan(boxes, n_points, masks, S0s, Ws, self.opts, self.stream)
+        self.info = fresco_batch_info(self.handle)
+
+    @property
+    def n_inst(self):
+        return len(self.n_points)
+
+    def _check_points(self, points):
+        if (not points.is_cuda or points.dtype != self.dtype or not points.is_contiguous()
+                or tuple(points.shape) != (int(self.first[-1]), self.dim)):
+            raise ValueError("points must be a contiguous CUDA %s tensor [%d, %d]"
+                             % (self.dtype, int(self.first[-1]), self.dim))
+
+    def loss_grad(self, points, losses=None, grad=None, want_grad=True):
+        t = self._torch
+        self._check_points(points)
+        if losses is None:
+            losses = t.empty(self.n_inst, dtype=t.float64, device=points.device)
+        if grad is None and want_grad:
+            grad = t.empty_like(points)
+        cur = t.cuda.current_stream()
+        self.stream.wait_stream(cur)
+        fresco_batch_loss_grad(self.handle, points, losses, grad)
+        cur.wait_stream(self.stream)
+        return losses, grad
+
+    def capture(self, points, losses, grad=None):
+        """Record one evaluation on these tensors as a CUDA graph (replay with launch())."""
+        self._check_points(points)
+        t = self._torch
+        self.stream.wait_stream(t.cuda.current_stream())
+        fresco_batch_graph_capture(self.handle, points, losses, grad)
+        self._graph_args = (points, losses, grad)   # keep the captured buffers alive
+
+    def launch(self):
+        t = self._torch
+        self.stream.wait_stream(t.cuda.current_stream())
+        fresco_batch_graph_launch(self.handle)
+        t.cuda.current_stream().wait_stream(self.stream)
+
+    def status(self) -> int:
+        return fresco_batch_status_check(self.handle)
+
+    def split(self, x):
+        """Per-instance views of a [sum N, ...] tensor."""
+        return [x[self.first[i]:self.first[i + 1]] for i in range(self.n_inst)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class PairTerm:

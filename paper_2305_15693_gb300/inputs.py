@@ -245,3 +245,67 @@ def workload(name: str) -> Workload:
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f64",
                         seed=0, tol=1e-12, upsample=1.5)
     raise KeyError(name)
+
+
+@dataclass
+class Ensemble:
+    """Many independent 2D problems: instance i has n_points[i] uniform points in a periodic box
+    boxes[i] (a square of that side) and the ball mask of radius K[i] (from chi[i]), with a
+    stealthy target and unit weights."""
+    name: str
+    n_points: list
+    K: list
+    chi: list
+    boxes: list
+    dtype: str = "f32"
+    seed: int = 7
+    tol: float = 1e-6
+    upsample: float = 2.0
+
+    @property
+    def n_inst(self) -> int:
+        return len(self.n_points)
+
+    @property
+    def np_dtype(self):
+        return np.float64 if self.dtype == "f64" else np.float32
+
+    def instance_points(self, i: int) -> np.ndarray:
+        # instance i draws from its own stream, so any one instance can be rebuilt alone
+        return uniform_points(self.n_points[i], 2, self.seed * 1_000_003 + 1 + i, self.np_dtype,
+                              self.boxes[i])
+
+    def points(self) -> np.ndarray:
+        """All instances' points packed one instance after the other: [sum N, 2]."""
+        return np.ascontiguousarray(np.concatenate(
+            [self.instance_points(i) for i in range(self.n_inst)], axis=0))
+
+    def masks(self) -> list:
+        return [ball_mask(k, 2) for k in self.K]
+
+    def targets(self, masks: list):
+        return [stealthy_target(m) for m in masks], [unit_weights(m) for m in masks]
+
+
+def ensemble(n_inst: int, n_lo: float, n_hi: float, chi_lo: float, chi_hi: float, seed: int,
+             dtype: str = "f32", box_lo: float = 1.0, box_hi: float = 1.0, tol: float = 1e-6,
+             upsample: float = 2.0, name: str = "") -> Ensemble:
+    """n_inst instances with N log-uniform in [n_lo, n_hi], chi uniform in [chi_lo, chi_hi] and
+    box sides uniform in [box_lo, box_hi], all drawn from one seeded stream."""
+    g = rng(seed)
+    n = np.rint(np.exp(g.uniform(math.log(n_lo), math.log(n_hi), n_inst))).astype(np.int64)
+    chi = g.uniform(chi_lo, chi_hi, n_inst)
+    box = g.uniform(box_lo, box_hi, n_inst) if box_hi > box_lo else np.full(n_inst, box_lo)
+    K = [max(1, radius_for_chi(int(n[i]), 2, float(chi[i]))) for i in range(n_inst)]
+    return Ensemble(name or "ensemble%d_seed%d" % (n_inst, seed), [int(x) for x in n], K,
+                    [float(c) for c in chi], [float(b) for b in box], dtype, seed, tol, upsample)
+
+
+def ensemble_workload(name: str) -> Ensemble:
+    """The named ensembles: 512 stealthy 2D configurations, N log-uniform in [1e3, 1e5] and chi
+    uniform in [0.1, 0.5], seed 7, unit square boxes."""
+    if name == "stealthy2d_ens512_n1e3to1e5_f32":
+        return ensemble(512, 1e3, 1e5, 0.1, 0.5, 7, "f32", tol=1e-6, name=name)
+    if name == "stealthy2d_ens512_n1e3to1e5_f64":
+        return ensemble(512, 1e3, 1e5, 0.1, 0.5, 7, "f64", tol=1e-12, name=name)
+    raise KeyError(name)
