@@ -306,6 +306,31 @@ fresco_status fresco_batch_info(fresco_batch_t b, int64_t *total_points, int *n_
 fresco_status fresco_batch_status_check(fresco_batch_t b);
 fresco_status fresco_batch_destroy(fresco_batch_t b);
 
+/* L-BFGS over an ensemble: every instance of a batch plan minimises its own loss (the optimiser
+ * of the main text after Eq. 4, with the rules of fresco_lbfgs_run, per instance), and all
+ * instances advance together. One step = one loss+gradient evaluation of the whole ensemble at
+ * the instances' trial points, then, per instance on the device, the Armijo decision (accept, or
+ * halve the step, or give up after max_backtrack halvings), the new (s, y) pair and the next
+ * direction by the two-loop recursion over that instance's own history. From the second step
+ * on, a step is one replay of a CUDA graph when the batch plan has a non-default stream.
+ * opts: as for fresco_lbfgs_create (NULL = defaults; max_step 0 = a tenth of each instance's
+ * mean spacing L N^(-1/d)); max_iter: accepted iterations per instance (0 = no limit).
+ * The solver owns its trial and history buffers ((5 + 2 history) x sum N x dim values). */
+typedef struct fresco_batch_lbfgs_s *fresco_batch_lbfgs_t;
+fresco_status fresco_batch_lbfgs_create(fresco_batch_lbfgs_t *out, fresco_batch_t b,
+                                        const fresco_lbfgs_opts *opts, int64_t max_iter);
+/* Copy the start points (device, packed like the batch's points) and reset every instance. */
+fresco_status fresco_batch_lbfgs_start(fresco_batch_lbfgs_t s, const void *d_points);
+/* Run n_steps steps, asynchronously on the batch plan's stream. Stopped instances (converged,
+ * max_iter reached, line search failed) stay where they are while the others continue. */
+fresco_status fresco_batch_lbfgs_step(fresco_batch_lbfgs_t s, int64_t n_steps);
+/* Synchronising read-back: the accepted points into d_points (device, may be NULL), one report
+ * per instance into reports (host [n_inst], may be NULL; status 0 = still running, others as in
+ * fresco_lbfgs_report) and the number of instances still running. */
+fresco_status fresco_batch_lbfgs_read(fresco_batch_lbfgs_t s, void *d_points,
+                                      fresco_lbfgs_report *reports, int64_t *n_running);
+fresco_status fresco_batch_lbfgs_destroy(fresco_batch_lbfgs_t s);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

@@ -1007,46 +1007,6 @@ fresco_status fresco_destroy(fresco_plan_t p) {
 // Ensembles: many independent problems evaluated by one set of launches
 // ============================================================================================
 
-struct fresco_batch_s {
-    struct Cls {
-        int nf[2] = {0, 0};
-        int kx = 0;
-        int count = 0;
-        int64_t go0 = 0, ao0 = 0, ato0 = 0, hco0 = 0, ro0 = 0;
-        cufftHandle h[4] = {0, 0, 0, 0};   // rows R2C, cols fwd, cols inv, rows inv
-        bool have[4] = {false, false, false, false};
-    };
-    int dim = 0;
-    int precision = FRESCO_F32;
-    size_t esize = 4;
-    int n_inst = 0;
-    cudaStream_t stream = nullptr;
-    std::vector<BInst> inst;
-    std::vector<Cls> cls;
-    std::vector<int64_t> pt_first, tile_first, mblk_first;
-    BTables tab{};
-    EsPoly<float> poly32{};
-    EsPoly<double> poly64{};
-    int64_t n_points = 0, n_bins = 0, n_rep = 0;
-    int64_t cells = 0, n_spec = 0, n_specT = 0, n_hc = 0;
-    // device
-    BInst *d_inst = nullptr;
-    int64_t *d_pt_first = nullptr, *d_tile_first = nullptr, *d_mblk_first = nullptr;
-    void *sorted = nullptr;
-    int *perm = nullptr, *key = nullptr, *slot = nullptr, *cnt = nullptr, *off = nullptr;
-    int *bsum = nullptr, *err = nullptr;
-    void *grid = nullptr, *spec = nullptr, *specT = nullptr, *hc = nullptr, *bt = nullptr;
-    void *r = nullptr, *g = nullptr;
-    int *rep_n = nullptr;
-    void *rep_s0 = nullptr, *rep_w = nullptr, *ip = nullptr;
-    double *partial = nullptr;
-    void *work = nullptr;
-    std::vector<void *> allocs;
-    int64_t device_bytes = 0;
-    int64_t launches = 0;
-    cudaGraphExec_t gexec = nullptr;
-    cudaGraph_t graph = nullptr;
-};
 
 namespace {
 
@@ -1427,6 +1387,7 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     b->esize = o.precision == FRESCO_F64 ? 8 : 4;
     b->n_inst = n_inst;
     b->stream = (cudaStream_t)stream;
+    b->boxes.assign(boxes, boxes + (size_t)n_inst * dim);
     fresco_status st = o.precision == FRESCO_F64 ? batch_build<double>(b, P, F, boxes, n_points)
                                                  : batch_build<float>(b, P, F, boxes, n_points);
     if (st) {

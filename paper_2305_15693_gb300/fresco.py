@@ -43,6 +43,8 @@ EXPORTS = (
     "fresco_pair_set_stream", "fresco_pair_destroy", "fresco_batch_plan",
     "fresco_batch_loss_grad", "fresco_batch_graph_capture", "fresco_batch_graph_launch",
     "fresco_batch_info", "fresco_batch_status_check", "fresco_batch_destroy",
+    "fresco_batch_lbfgs_create", "fresco_batch_lbfgs_start", "fresco_batch_lbfgs_step",
+    "fresco_batch_lbfgs_read", "fresco_batch_lbfgs_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -142,6 +144,11 @@ def load(path: str = LIB_PATH):
             "fresco_batch_info": (I, [P, P, P, P, P]),
             "fresco_batch_status_check": (I, [P]),
             "fresco_batch_destroy": (I, [P]),
+            "fresco_batch_lbfgs_create": (I, [P, P, P, I64]),
+            "fresco_batch_lbfgs_start": (I, [P, P]),
+            "fresco_batch_lbfgs_step": (I, [P, I64]),
+            "fresco_batch_lbfgs_read": (I, [P, P, P, P]),
+            "fresco_batch_lbfgs_destroy": (I, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -428,6 +435,93 @@ def fresco_batch_status_check(batch) -> int:
 
 def fresco_batch_destroy(batch):
     _check(load().fresco_batch_destroy(batch), "fresco_batch_destroy")
+
+
+def fresco_batch_lbfgs_create(batch, opts=None, max_iter=0):
+    h = ctypes.c_void_p()
+    _check(load().fresco_batch_lbfgs_create(ctypes.byref(h), batch,
+                                            ctypes.byref(opts) if opts is not None else None,
+                                            int(max_iter)), "fresco_batch_lbfgs_create")
+    return h.value
+
+
+def fresco_batch_lbfgs_start(solver, points):
+    _check(load().fresco_batch_lbfgs_start(solver, _addr(points)), "fresco_batch_lbfgs_start")
+
+
+def fresco_batch_lbfgs_step(solver, n_steps=1):
+    _check(load().fresco_batch_lbfgs_step(solver, int(n_steps)), "fresco_batch_lbfgs_step")
+
+
+def fresco_batch_lbfgs_read(solver, n_inst, points=None):
+    """Returns (list of per-instance report dicts, instances still running)."""
+    reps = (fresco_lbfgs_report * n_inst)()
+    run = ctypes.c_int64()
+    _check(load().fresco_batch_lbfgs_read(solver, _addr(points), reps, ctypes.byref(run)),
+           "fresco_batch_lbfgs_read")
+    return [r.as_dict() for r in reps], run.value
+
+
+def fresco_batch_lbfgs_destroy(solver):
+    _check(load().fresco_batch_lbfgs_destroy(solver), "fresco_batch_lbfgs_destroy")
+
+
+class BatchLBFGS:
+    """Per-instance L-BFGS over a Batch, all instances stepping together (fresco_batch_lbfgs_*
+    in include/fresco.h). Steps after the first replay one CUDA graph each."""
+
+    def __init__(self, batch, max_iter=0, history=10, max_step=0.0, c1=1e-4, max_backtrack=20,
+                 gtol=0.0, ftol=0.0):
+        o = fresco_lbfgs_opts_default()
+        o.history, o.max_step, o.c1 = int(history), float(max_step), float(c1)
+        o.max_backtrack, o.gtol, o.ftol = int(max_backtrack), float(gtol), float(ftol)
+        self.batch = batch
+        self.handle = fresco_batch_lbfgs_create(batch.handle, o, max_iter)
+
+    def start(self, points):
+        self.batch._check_points(points)
+        self.batch.stream.wait_stream(self.batch._torch.cuda.current_stream())
+        fresco_batch_lbfgs_start(self.handle, points)
+
+    def step(self, n_steps=1):
+        fresco_batch_lbfgs_step(self.handle, n_steps)
+
+    def read(self, points=None):
+        if points is not None:
+            self.batch._check_points(points)
+        return fresco_batch_lbfgs_read(self.handle, self.batch.n_inst, points)
+
+    def run(self, points, max_steps, check_every=64):
+        """Minimise every instance in place, for at most max_steps steps (evaluations); returns
+        the per-instance reports."""
+        self.start(points)
+        done = 0
+        while done < max_steps:
+            n = min(check_every, max_steps - done)
+            self.step(n)
+            done += n
+            _, running = self.read()
+            if running == 0:
+                break
+        reps, _ = self.read(points)
+        return reps
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_batch_lbfgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Batch:

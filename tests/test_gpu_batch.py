@@ -158,3 +158,56 @@ def test_ensemble_512_full_size():
     l_o, g_o, _, _ = oracle.loss_grad(pts32[sl], masks[i], S0s[i], Ws[i], sel=sel)
     assert abs(l64[i] - l_o) <= TOL["f64"]["loss"] * l_o
     assert rel_l2(g64[sl][sel], g_o) <= TOL["f64"]["grad"]
+
+
+# ---- L-BFGS over the ensemble ----------------------------------------------------------------
+
+def test_batch_lbfgs_follows_reference_per_instance():
+    """Each instance's first iterations on the device follow the numpy L-BFGS driven by the
+    oracle (FP64), although instances accept, backtrack and stop at different steps."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    from _lbfgs_ref import lbfgs as lbfgs_ref
+    ens = inputs.ensemble(5, 40, 400, 0.2, 0.5, 21, "f64", box_lo=0.8, box_hi=1.5, tol=1e-12)
+    masks, S0s, Ws = _problem(ens)
+    pts_np = ens.points()
+    iters, m, step = 8, 5, 2e-3
+    pts = torch.from_numpy(pts_np).cuda()
+    with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision="f64",
+                      tol=1e-12) as b, \
+            fresco.BatchLBFGS(b, max_iter=iters, history=m, max_step=step) as opt:
+        reps = opt.run(pts, 2000)
+        first = b.first
+    x = pts.cpu().numpy()
+    for i in range(ens.n_inst):
+        sl = slice(first[i], first[i + 1])
+
+        def fg(p, i=i):
+            loss, grad, _, _ = oracle.loss_grad(p, masks[i], S0s[i], Ws[i], box=ens.boxes[i])
+            return loss, grad
+
+        x_ref, trace = lbfgs_ref(fg, pts_np[sl], iters, m=m, max_step=step)
+        assert reps[i]["iterations"] == iters and reps[i]["status"] == 3, (i, reps[i])
+        assert reps[i]["loss"] == pytest.approx(trace[-1], rel=1e-8), i
+        assert rel_l2(x[sl] - pts_np[sl], x_ref - pts_np[sl]) < 1e-6, i
+
+
+def test_batch_lbfgs_lowers_every_instance_and_reports_true_losses():
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    ens = inputs.ensemble(48, 500, 20000, 0.1, 0.5, 8, "f32")
+    masks, S0s, Ws = _problem(ens)
+    pts = torch.from_numpy(ens.points()).cuda()
+    with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision="f32") as b:
+        l0, _ = b.loss_grad(pts, want_grad=False)
+        l0 = l0.cpu().numpy()
+        with fresco.BatchLBFGS(b) as opt:
+            reps = opt.run(pts, 150)
+        l1, _ = b.loss_grad(pts, want_grad=False)
+        torch.cuda.synchronize()
+        l1 = l1.cpu().numpy()
+        assert b.status() == fresco.FRESCO_OK
+    for i, r in enumerate(reps):
+        assert r["evaluations"] <= 150
+        assert r["loss"] == l1[i], i            # the reported loss is the loss at the points
+        assert l1[i] < 0.1 * l0[i], (i, l0[i], l1[i])
