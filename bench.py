@@ -287,6 +287,250 @@ def run_reference(args, wl, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------------------
+# ensembles: many independent 2D problems per evaluation (configurations/s)
+
+ENS_METRIC = ("configurations/s per loss+grad eval of a 512-instance 2D ensemble "
+              "(N log-uniform in [1e3, 1e5]); p50/p99 ms per evaluation")
+
+
+def ensemble_inputs(ens):
+    t0 = time.time()
+    masks = ens.masks()
+    S0s, Ws = ens.targets(masks)
+    pts = ens.points()
+    log("ensemble: %d instances, %d points, %d modes (%.1f s)" % (
+        ens.n_inst, pts.shape[0], sum(m.shape[0] for m in masks), time.time() - t0))
+    return pts, masks, S0s, Ws
+
+
+def ensemble_cpu_rate(ens, pts_np, masks, budget_s=12.0, seed=4):
+    """Oracle pair terms per second on the host cores, from rho at sampled mask rows of a few
+    seeded instances; a full ensemble evaluation is sum_i 2 N_i N_K,i such terms."""
+    import oracle
+    g = np.random.Generator(np.random.Philox(seed))
+    first = np.concatenate([[0], np.cumsum(ens.n_points)])
+    picks = g.choice(ens.n_inst, 3, replace=False)
+    terms, t = 0.0, 0.0
+    for i in picks:
+        r64 = np.ascontiguousarray(pts_np[first[i]:first[i + 1]], dtype=np.float64)
+        n_s = max(2, min(masks[i].shape[0], 64))
+        rows = masks[i][g.choice(masks[i].shape[0], n_s, replace=False)]
+        t0 = time.perf_counter()
+        oracle.rho(r64, rows, ens.boxes[i])
+        t += time.perf_counter() - t0
+        terms += r64.shape[0] * n_s
+        if t > budget_s:
+            break
+    rate = terms / t
+    total = sum(2.0 * ens.n_points[i] * masks[i].shape[0] for i in range(ens.n_inst))
+    return rate, total, [int(i) for i in picks]
+
+
+def run_ensemble(args, ens, rank, world, local_rank, dist_on):
+    import torch
+    from paper_2305_15693_gb300 import fresco, tune
+    pts_np, masks, S0s, Ws = ensemble_inputs(ens)
+    pts = torch.from_numpy(pts_np).cuda()
+    n_inst, n_tot = ens.n_inst, pts_np.shape[0]
+    esize = 4 if ens.dtype == "f32" else 8
+
+    # ---- autotuned oversampling and tile edge ----------------------------------------------
+    table = None
+    if args.tile:
+        best = {"upsample": args.upsample or ens.upsample, "tile": tuple(args.tile[:2])}
+    else:
+        best, table = tune.autotune_batch(ens.boxes, ens.n_points, masks, S0s, Ws, pts,
+                                          precision=ens.dtype, tol=ens.tol)
+        log("autotune: %s" % json.dumps(table))
+    b = fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision=ens.dtype, tol=ens.tol,
+                     upsample=best["upsample"], tile=best["tile"])
+    infos = [fresco.fresco_batch_get_info(b.handle, i) for i in range(n_inst)]
+
+    # launches of one evaluation (eager), then per-stage device time
+    l0 = fresco.fresco_batch_info(b.handle)["launches"]
+    b.loss_grad(pts)
+    torch.cuda.synchronize()
+    per_eval_launches = fresco.fresco_batch_info(b.handle)["launches"] - l0
+    b.profile(True)
+    for _ in range(3):
+        b.loss_grad(pts)
+    stages = b.profile_read()
+    b.profile(False)
+
+    # ---- graph replays: K evaluations, each bracketed by events -----------------------------
+    losses = torch.empty(n_inst, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(pts)
+    b.capture(pts, losses, grad)
+    s = b.stream
+    for _ in range(args.warmup):
+        fresco.fresco_batch_graph_launch(b.handle)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    clocks = ClockSampler(_device_selector(local_rank))
+    clocks.start()
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs[0].record(s)
+    for k in range(args.steps):
+        fresco.fresco_batch_graph_launch(b.handle)
+        evs[k + 1].record(s)
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t_step = max_over_ranks(total_ms / args.steps / 1e3, dist_on, "cuda")
+    if b.status() != fresco.FRESCO_OK:
+        raise RuntimeError("device status after timing")
+    value = world * n_inst / t_step
+
+    # ---- e2e: pinned host points in, losses and gradient out, every step --------------------
+    h_pts = torch.from_numpy(pts_np).pin_memory()
+    h_grad = torch.empty(pts_np.shape, dtype=h_pts.dtype).pin_memory()
+    h_loss = torch.empty(n_inst, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        with torch.cuda.stream(s):
+            pts.copy_(h_pts, non_blocking=True)
+            fresco.fresco_batch_graph_launch(b.handle)
+            h_grad.copy_(grad, non_blocking=True)
+            h_loss.copy_(losses, non_blocking=True)
+        s.synchronize()
+    e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    dt_e2e = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist_on, "cuda")
+
+    # ---- one L-BFGS step per graph replay ----------------------------------------------------
+    x = pts.clone()
+    opt = fresco.BatchLBFGS(b)
+    opt.start(x)
+    opt.step(2)                       # the first step runs directly, the second is captured
+    torch.cuda.synchronize()
+    n_lb = max(args.steps, 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    opt.step(n_lb)
+    e1.record(s)
+    torch.cuda.synchronize()
+    lbfgs_ms = e0.elapsed_time(e1) / n_lb
+    reps, running = opt.read()
+    opt.close()
+
+    # ---- roofline of the slowest kernel stage ------------------------------------------------
+    sb = {}
+    for i in range(n_inst):
+        for k, v in stage_bytes(infos[i], ens.n_points[i], esize).items():
+            sb[k] = sb.get(k, 0) + v
+    peaks = load_peaks() if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    per_stage = {}
+    for name, (tot_ms, cnt) in stages.items():
+        if cnt == 0:
+            continue
+        avg = tot_ms / cnt
+        gbs = sb[name] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        per_stage[name] = {"ms": round(avg, 4), "alg_bytes": int(sb[name]),
+                           "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
+    ours = {k: v for k, v in per_stage.items() if k in ("spread", "interp", "mask")}
+    dom = max(ours, key=lambda k: ours[k]["ms"])
+    roofline = {"bound": "hbm", "achieved": per_stage[dom]["GB/s"], "peak": hbm_peak,
+                "unit": "GB/s", "frac": per_stage[dom]["frac"], "traffic": None, "kernel": dom,
+                "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+    b.close()
+
+    # ---- all-FP64 batch on the same ensemble ------------------------------------------------
+    f64 = None
+    if ens.dtype == "f32" and args.f64_steps > 0:
+        p64 = pts.double()
+        b64 = fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision="f64", tol=1e-12,
+                           upsample=best["upsample"], tile=best["tile"])
+        ms64 = tune.time_graph(b64, p64, reps=args.f64_steps, warmup=3)
+        b64.close()
+        t64 = float(np.mean(ms64)) / 1e3
+        f64 = {"value": world * n_inst / t64, "ms_per_step": 1e3 * t64,
+               "speedup_f32_over_f64": t64 / t_step}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, terms, picks = ensemble_cpu_rate(ens, pts_np, masks)
+        cpu = {"value": n_inst / (terms / rate), "unit": "configurations/s",
+               "cores": __import__("oracle").threads(), "kind": "oracle",
+               "sample": "rho at up to 64 sampled mask rows of instances %s by direct sums "
+                         "(%.3e pair terms/s); a full ensemble evaluation extrapolated as "
+                         "sum 2 N_i N_K,i = %.3e terms" % (picks, rate, terms)}
+
+    if rank == 0:
+        line = {
+            "metric": ENS_METRIC, "value": value, "unit": "configurations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ens.dtype, "data": "synthetic",
+            "config": {"workload": ens.name, "n_inst": n_inst, "total_points": n_tot,
+                       "n_modes": int(sum(m.shape[0] for m in masks)), "tol": ens.tol,
+                       "upsample": best["upsample"], "tile": list(best["tile"]),
+                       "width": infos[0]["width"], "autotune": table,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "timing": "CUDA-graph replay per evaluation",
+                       "l2": "inputs larger than L2 (points %.0f MB + grids, %d MB L2)"
+                             % (pts_np.nbytes / 1e6, L2_BYTES // 2 ** 20)},
+            "latency_ms": {"p50": float(np.percentile(per, 50)),
+                           "p99": float(np.percentile(per, 99)), "mean": float(per.mean())},
+            "points_per_s": world * n_tot / t_step,
+            "lbfgs_step_ms": lbfgs_ms,
+            "lbfgs_after": {"steps": n_lb + 2, "running": running,
+                            "iterations_median": float(np.median([r["iterations"]
+                                                                  for r in reps]))},
+            "roofline": roofline,
+            "stages": per_stage,
+            "fp64": f64,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * n_inst / dt_e2e, "unit": "configurations/s",
+                    "h2d_bytes_per_step": int(pts_np.nbytes),
+                    "d2h_bytes_per_step": int(pts_np.nbytes + 8 * n_inst),
+                    "ms_per_step": 1e3 * dt_e2e},
+            "clocks": clk,
+            "gpu_launches": per_eval_launches * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_reference_ensemble(args, ens, rank):
+    """The oracle as the reference arm on an ensemble: each step is a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pts_np, masks, _, _ = ensemble_inputs(ens)
+    times = []
+    for k in range(args.warmup + args.steps):
+        rate, terms, _ = ensemble_cpu_rate(ens, pts_np, masks, budget_s=5.0, seed=10 + k)
+        if k >= args.warmup:
+            times.append(terms / rate)
+    t = float(np.mean(times))
+    value = ens.n_inst / t
+    line = {
+        "impl": "reference", "metric": ENS_METRIC, "value": value, "unit": "configurations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": ens.name, "n_inst": ens.n_inst,
+                   "total_points": int(sum(ens.n_points)), "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "configurations/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": "per step: rho at up to 64 sampled mask rows of 3 seeded "
+                                   "instances; ensemble evaluation extrapolated as "
+                                   "sum 2 N_i N_K,i pair terms"},
+        "e2e": {"value": value, "unit": "configurations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -308,16 +552,23 @@ def main():
         args.warmup = 3
 
     from paper_2305_15693_gb300 import inputs
-    wl = inputs.workload(args.workload)
-    if args.upsample:
-        wl.upsample = args.upsample
+    ens = None
+    try:
+        ens = inputs.ensemble_workload(args.workload)
+    except KeyError:
+        wl = inputs.workload(args.workload)
+        if args.upsample:
+            wl.upsample = args.upsample
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        run_reference(args, wl, rank, world)
+        if ens is not None:
+            run_reference_ensemble(args, ens, rank)
+        else:
+            run_reference(args, wl, rank, world)
         return
 
     import torch
@@ -331,6 +582,13 @@ def main():
     torch.cuda.set_device(local_rank)
     from paper_2305_15693_gb300 import fresco
     fresco.load()
+
+    if ens is not None:
+        run_ensemble(args, ens, rank, world, local_rank, dist_on)
+        if dist_on:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
 
     pts_np, mask, S0, W = make_inputs(wl)
     N = wl.n_points

@@ -303,7 +303,14 @@ fresco_status fresco_batch_graph_launch(fresco_batch_t b);
 /* Any argument may be NULL. */
 fresco_status fresco_batch_info(fresco_batch_t b, int64_t *total_points, int *n_classes,
                                 int64_t *device_bytes, int64_t *launches);
+/* Geometry of instance i (0 <= i < n_inst) as fresco_get_info reports a plan: its own fine
+ * grid (after rounding up to the size class), k_max, tiles, n_rep; device_bytes is 0. */
+fresco_status fresco_batch_get_info(fresco_batch_t b, int i, fresco_info *info);
 fresco_status fresco_batch_status_check(fresco_batch_t b);
+/* Per-stage device time of ordinary (not graph-replayed) evaluations, as fresco_profile /
+ * fresco_profile_read: ms and counts [FRESCO_N_STAGES], summed since the last read. */
+fresco_status fresco_batch_profile(fresco_batch_t b, int enable);
+fresco_status fresco_batch_profile_read(fresco_batch_t b, double *ms, int64_t *counts);
 fresco_status fresco_batch_destroy(fresco_batch_t b);
 
 /* L-BFGS over an ensemble: every instance of a batch plan minimises its own loss (the optimiser

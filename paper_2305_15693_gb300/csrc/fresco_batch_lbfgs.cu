@@ -595,11 +595,17 @@ fresco_status fresco_batch_lbfgs_step(fresco_batch_lbfgs_t s, int64_t n_steps) {
             if (st) return st;
         } else {
             if (!s->gexec) {
+                const bool prof_on = s->b->prof.on;   // no event records inside the graph
+                s->b->prof.on = false;
                 cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
-                if (e != cudaSuccess) return cuda_st(e);
+                if (e != cudaSuccess) {
+                    s->b->prof.on = prof_on;
+                    return cuda_st(e);
+                }
                 fresco_status st = one_step(s);
                 cudaGraph_t graph = nullptr;
                 e = cudaStreamEndCapture(s->stream, &graph);
+                s->b->prof.on = prof_on;
                 if (st) {
                     if (graph) cudaGraphDestroy(graph);
                     return st;

@@ -455,11 +455,7 @@ void release(fresco_plan_s *p) {
     cufftHandle hs[] = {p->fft_rows, p->fft_cols, p->ifft_cols, p->ifft_rows};
     for (int i = 0; i < 4; ++i)
         if (p->have_fft[i]) cufftDestroy(hs[i]);
-    for (auto &r : p->ev_used) {
-        cudaEventDestroy(r.a);
-        cudaEventDestroy(r.b);
-    }
-    for (auto e : p->ev_free) cudaEventDestroy(e);
+    p->prof.release();
     delete p;
 }
 
@@ -647,24 +643,6 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
 
 // ---- evaluation ------------------------------------------------------------------------------
 
-struct StageScope {
-    fresco_plan_s *p;
-    int stage;
-    cudaEvent_t b = nullptr;
-    StageScope(fresco_plan_s *p_, int s_) : p(p_), stage(s_) {
-        if (!p->profiling) return;
-        cudaEvent_t a = p->take_event();
-        b = p->take_event();
-        if (a && b) {
-            cudaEventRecord(a, p->stream);
-            p->ev_used.push_back({stage, a, b});
-        }
-    }
-    ~StageScope() {
-        if (b && p->profiling) cudaEventRecord(b, p->stream);
-    }
-};
-
 template <typename T>
 const EsPoly<T> &poly_of(const fresco_plan_s *p);
 template <>
@@ -679,7 +657,7 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
     const MaskGeom &m = p->mgeom;
     cudaStream_t s = p->stream;
     {
-        StageScope sc(p, ST_SORT);
+        StageScope sc(p->prof, p->stream, ST_SORT);
         FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_bins, s));
         FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
         int nl = 0;
@@ -690,12 +668,12 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
         p->launches += 1 + nl;
     }
     {
-        StageScope sc(p, ST_SPREAD);
+        StageScope sc(p->prof, p->stream, ST_SPREAD);
         FR_CUDA(Launch<T>::spread(g, poly_of<T>(p), p->d_sorted, p->d_off, (T *)p->d_grid, s));
         p->launches += 1;
     }
     {
-        StageScope sc(p, ST_FFT_FWD);
+        StageScope sc(p->prof, p->stream, ST_FFT_FWD);
         const int64_t rows = m.plane;
         if (sizeof(T) == 4)
             FR_CUFFT(cufftExecR2C(p->fft_rows, (cufftReal *)p->d_grid, (cufftComplex *)p->d_spec));
@@ -712,7 +690,7 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
                                   (cufftDoubleComplex *)p->d_specT, CUFFT_FORWARD));
     }
     {
-        StageScope sc(p, ST_MASK);
+        StageScope sc(p->prof, p->stream, ST_MASK);
         FR_CUDA(Launch<T>::mask(m, p->d_rep_n, (const T *)p->d_rep_s0, (const T *)p->d_rep_w,
                                 p->d_specT, (const T *)p->d_ip[0], (const T *)p->d_ip[1],
                                 (const T *)p->d_ip[2], p->d_hc[0], p->d_hc[1], p->d_partial,
@@ -720,7 +698,7 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
         p->launches += 1;
     }
     {
-        StageScope sc(p, ST_LOSS);
+        StageScope sc(p->prof, p->stream, ST_LOSS);
         FR_CUDA(Launch<T>::finalize(p->d_partial, p->n_mask_blocks, p->info.loss_const, loss, s));
         p->launches += 1;
     }
@@ -735,7 +713,7 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
     const MaskGeom &m = p->mgeom;
     cudaStream_t s = p->stream;
     {
-        StageScope sc(p, ST_FFT_INV);
+        StageScope sc(p->prof, p->stream, ST_FFT_INV);
         for (int q = 0; q < p->n_pipes; ++q) {
             if (sizeof(T) == 4)
                 FR_CUFFT(cufftExecC2C(p->ifft_cols, (cufftComplex *)p->d_hc[q],
@@ -754,7 +732,7 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
         }
     }
     {
-        StageScope sc(p, ST_INTERP);
+        StageScope sc(p->prof, p->stream, ST_INTERP);
         FR_CUDA(Launch<T>::interp(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off, p->d_g[0],
                                   p->d_g[1], grad_out, grad, s));
         p->launches += 1;
@@ -772,16 +750,45 @@ fresco_status check_point_ptr(fresco_plan_s *p, const void *ptr) {
 
 }  // namespace
 
-// ---- profiling event pool (members used above) ----------------------------------------------
-cudaEvent_t fresco_plan_s::take_event() {
-    if (!ev_free.empty()) {
-        cudaEvent_t e = ev_free.back();
-        ev_free.pop_back();
+// ---- profiling event pool --------------------------------------------------------------------
+cudaEvent_t fresco::StageProfile::take() {
+    if (!spare.empty()) {
+        cudaEvent_t e = spare.back();
+        spare.pop_back();
         return e;
     }
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
+}
+
+void fresco::StageProfile::read(double *ms_out, int64_t *calls_out) {
+    for (auto &r : used) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            ms[r.stage] += t;
+            calls[r.stage] += 1;
+        }
+        spare.push_back(r.a);
+        spare.push_back(r.b);
+    }
+    used.clear();
+    for (int i = 0; i < ST_COUNT; ++i) {
+        if (ms_out) ms_out[i] = ms[i];
+        if (calls_out) calls_out[i] = calls[i];
+        ms[i] = 0.0;
+        calls[i] = 0;
+    }
+}
+
+void fresco::StageProfile::release() {
+    for (auto &r : used) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    used.clear();
+    for (auto e : spare) cudaEventDestroy(e);
+    spare.clear();
 }
 
 // ============================================================================================
@@ -968,29 +975,14 @@ fresco_status fresco_status_check(fresco_plan_t p) {
 
 fresco_status fresco_profile(fresco_plan_t p, int enable) {
     if (!p) return FRESCO_ERR_ARG;
-    p->profiling = enable != 0;
+    p->prof.on = enable != 0;
     return FRESCO_OK;
 }
 
 fresco_status fresco_profile_read(fresco_plan_t p, double *ms, int64_t *counts) {
     if (!p || !ms) return FRESCO_ERR_ARG;
     FR_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
-    for (auto &r : p->ev_used) {
-        float t = 0.f;
-        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
-            p->stage_ms[r.stage] += t;
-            p->stage_calls[r.stage] += 1;
-        }
-        p->ev_free.push_back(r.a);
-        p->ev_free.push_back(r.b);
-    }
-    p->ev_used.clear();
-    for (int i = 0; i < FRESCO_N_STAGES; ++i) {
-        ms[i] = p->stage_ms[i];
-        if (counts) counts[i] = p->stage_calls[i];
-        p->stage_ms[i] = 0.0;
-        p->stage_calls[i] = 0;
-    }
+    p->prof.read(ms, counts);
     return FRESCO_OK;
 }
 
@@ -1032,6 +1024,7 @@ void batch_free(fresco_batch_s *b) {
         for (int i = 0; i < 4; ++i)
             if (c.have[i]) cufftDestroy(c.h[i]);
     for (void *p : b->allocs) cudaFree(p);
+    b->prof.release();
     delete b;
 }
 
@@ -1293,57 +1286,84 @@ fresco_status batch_eval(fresco_batch_s *b, const T *pts, double *losses, T *gra
     using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     cudaStream_t s = b->stream;
     const BTables &t = b->tab;
-    FR_CUDA(cudaMemsetAsync(b->cnt, 0, sizeof(int) * (size_t)b->n_bins, s));
-    FR_CUDA(Launch<T>::bin_b(t, pts, b->cnt, b->key, b->slot, b->err, s));
-    int nl = 0;
-    FR_CUDA(Launch<T>::scan(b->cnt, b->off, b->bsum, b->n_bins, s, &nl));
-    FR_CUDA(Launch<T>::scatter_b(t, pts, b->key, b->slot, b->off, b->sorted, b->perm, s));
-    FR_CUDA(Launch<T>::spread_b(t, bpoly<T>(b), b->sorted, b->off, (T *)b->grid, s));
-    b->launches += 4 + nl;
-    for (auto &K : b->cls) {   // forward FFT of each class
-        const int64_t half = K.nf[0] / 2 + 1, plane = K.nf[1];
-        C2 *A = (C2 *)b->spec + K.ao0, *AT = (C2 *)b->specT + K.ato0;
-        if (sizeof(T) == 4)
-            FR_CUFFT(cufftExecR2C(K.h[0], (cufftReal *)((T *)b->grid + K.go0), (cufftComplex *)A));
-        else
-            FR_CUFFT(cufftExecD2Z(K.h[0], (cufftDoubleReal *)((T *)b->grid + K.go0),
-                                  (cufftDoubleComplex *)A));
-        FR_CUDA(Launch<T>::cols_to_rows(A, AT, plane, half, K.kx + 1, s, K.count, plane * half,
-                                        plane * (K.kx + 1)));
-        if (sizeof(T) == 4)
-            FR_CUFFT(cufftExecC2C(K.h[1], (cufftComplex *)AT, (cufftComplex *)AT, CUFFT_FORWARD));
-        else
-            FR_CUFFT(cufftExecZ2Z(K.h[1], (cufftDoubleComplex *)AT, (cufftDoubleComplex *)AT,
-                                  CUFFT_FORWARD));
+    {
+        StageScope sc(b->prof, s, ST_SORT);
+        FR_CUDA(cudaMemsetAsync(b->cnt, 0, sizeof(int) * (size_t)b->n_bins, s));
+        FR_CUDA(Launch<T>::bin_b(t, pts, b->cnt, b->key, b->slot, b->err, s));
+        int nl = 0;
+        FR_CUDA(Launch<T>::scan(b->cnt, b->off, b->bsum, b->n_bins, s, &nl));
+        FR_CUDA(Launch<T>::scatter_b(t, pts, b->key, b->slot, b->off, b->sorted, b->perm, s));
+        b->launches += 2 + nl;
+    }
+    {
+        StageScope sc(b->prof, s, ST_SPREAD);
+        FR_CUDA(Launch<T>::spread_b(t, bpoly<T>(b), b->sorted, b->off, (T *)b->grid, s));
         b->launches += 1;
     }
-    FR_CUDA(Launch<T>::mask_b(t, b->rep_n, (const T *)b->rep_s0, (const T *)b->rep_w, b->specT,
-                              (const T *)b->ip, b->hc, nullptr, b->partial, s));
-    FR_CUDA(Launch<T>::finalize_b(t, b->partial, losses, s));
-    b->launches += 2;
+    {
+        StageScope sc(b->prof, s, ST_FFT_FWD);
+        for (auto &K : b->cls) {   // forward FFT of each size class
+            const int64_t half = K.nf[0] / 2 + 1, plane = K.nf[1];
+            C2 *A = (C2 *)b->spec + K.ao0, *AT = (C2 *)b->specT + K.ato0;
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecR2C(K.h[0], (cufftReal *)((T *)b->grid + K.go0),
+                                      (cufftComplex *)A));
+            else
+                FR_CUFFT(cufftExecD2Z(K.h[0], (cufftDoubleReal *)((T *)b->grid + K.go0),
+                                      (cufftDoubleComplex *)A));
+            FR_CUDA(Launch<T>::cols_to_rows(A, AT, plane, half, K.kx + 1, s, K.count,
+                                            plane * half, plane * (K.kx + 1)));
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(K.h[1], (cufftComplex *)AT, (cufftComplex *)AT,
+                                      CUFFT_FORWARD));
+            else
+                FR_CUFFT(cufftExecZ2Z(K.h[1], (cufftDoubleComplex *)AT, (cufftDoubleComplex *)AT,
+                                      CUFFT_FORWARD));
+            b->launches += 1;
+        }
+    }
+    {
+        StageScope sc(b->prof, s, ST_MASK);
+        FR_CUDA(Launch<T>::mask_b(t, b->rep_n, (const T *)b->rep_s0, (const T *)b->rep_w,
+                                  b->specT, (const T *)b->ip, b->hc, nullptr, b->partial, s));
+        b->launches += 1;
+    }
+    {
+        StageScope sc(b->prof, s, ST_LOSS);
+        FR_CUDA(Launch<T>::finalize_b(t, b->partial, losses, s));
+        b->launches += 1;
+    }
     if (!grad) return FRESCO_OK;
-    for (auto &K : b->cls) {   // inverse FFT of each class
-        const int64_t plane = K.nf[1];
-        C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0, *R = (C2 *)b->r + K.ro0;
-        C2 *G = (C2 *)b->g + K.ro0;
-        if (sizeof(T) == 4)
-            FR_CUFFT(cufftExecC2C(K.h[2], (cufftComplex *)H, (cufftComplex *)BT, CUFFT_INVERSE));
-        else
-            FR_CUFFT(cufftExecZ2Z(K.h[2], (cufftDoubleComplex *)H, (cufftDoubleComplex *)BT,
-                                  CUFFT_INVERSE));
-        FR_CUDA(Launch<T>::rows_to_cols(BT, R, plane, K.nf[0], K.kx, s, K.count,
-                                        plane * (2 * (int64_t)K.kx + 2),
-                                        (int64_t)K.nf[0] * plane));
-        if (sizeof(T) == 4)
-            FR_CUFFT(cufftExecC2C(K.h[3], (cufftComplex *)R, (cufftComplex *)G, CUFFT_INVERSE));
-        else
-            FR_CUFFT(cufftExecZ2Z(K.h[3], (cufftDoubleComplex *)R, (cufftDoubleComplex *)G,
-                                  CUFFT_INVERSE));
+    {
+        StageScope sc(b->prof, s, ST_FFT_INV);
+        for (auto &K : b->cls) {   // inverse FFT of each size class
+            const int64_t plane = K.nf[1];
+            C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0, *R = (C2 *)b->r + K.ro0;
+            C2 *G = (C2 *)b->g + K.ro0;
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(K.h[2], (cufftComplex *)H, (cufftComplex *)BT,
+                                      CUFFT_INVERSE));
+            else
+                FR_CUFFT(cufftExecZ2Z(K.h[2], (cufftDoubleComplex *)H, (cufftDoubleComplex *)BT,
+                                      CUFFT_INVERSE));
+            FR_CUDA(Launch<T>::rows_to_cols(BT, R, plane, K.nf[0], K.kx, s, K.count,
+                                            plane * (2 * (int64_t)K.kx + 2),
+                                            (int64_t)K.nf[0] * plane));
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(K.h[3], (cufftComplex *)R, (cufftComplex *)G,
+                                      CUFFT_INVERSE));
+            else
+                FR_CUFFT(cufftExecZ2Z(K.h[3], (cufftDoubleComplex *)R, (cufftDoubleComplex *)G,
+                                      CUFFT_INVERSE));
+            b->launches += 1;
+        }
+    }
+    {
+        StageScope sc(b->prof, s, ST_INTERP);
+        FR_CUDA(Launch<T>::interp_b(t, bpoly<T>(b), b->sorted, b->perm, b->off, b->g, nullptr,
+                                    nullptr, grad, s));
         b->launches += 1;
     }
-    FR_CUDA(Launch<T>::interp_b(t, bpoly<T>(b), b->sorted, b->perm, b->off, b->g, nullptr,
-                                nullptr, grad, s));
-    b->launches += 1;
     return FRESCO_OK;
 }
 
@@ -1388,6 +1408,8 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     b->n_inst = n_inst;
     b->stream = (cudaStream_t)stream;
     b->boxes.assign(boxes, boxes + (size_t)n_inst * dim);
+    b->infos.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i) fill_info(P[i], n_points[i], n_modes[i], F[i], &b->infos[i]);
     fresco_status st = o.precision == FRESCO_F64 ? batch_build<double>(b, P, F, boxes, n_points)
                                                  : batch_build<float>(b, P, F, boxes, n_points);
     if (st) {
@@ -1421,10 +1443,13 @@ fresco_status fresco_batch_graph_capture(fresco_batch_t b, const void *d_points,
         cudaGraphDestroy(b->graph);
         b->graph = nullptr;
     }
+    const bool prof_on = b->prof.on;   // no event records inside the graph
+    b->prof.on = false;
     FR_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     st = fresco_batch_loss_grad(b, d_points, d_losses, d_grad);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    b->prof.on = prof_on;
     if (st) {
         if (graph) cudaGraphDestroy(graph);
         return st;
@@ -1451,6 +1476,12 @@ fresco_status fresco_batch_info(fresco_batch_t b, int64_t *total_points, int *n_
     return FRESCO_OK;
 }
 
+fresco_status fresco_batch_get_info(fresco_batch_t b, int i, fresco_info *info) {
+    if (!b || !info || i < 0 || i >= b->n_inst) return FRESCO_ERR_ARG;
+    *info = b->infos[i];
+    return FRESCO_OK;
+}
+
 fresco_status fresco_batch_status_check(fresco_batch_t b) {
     if (!b) return FRESCO_ERR_ARG;
     FR_CUDA(b->stream ? cudaStreamSynchronize(b->stream) : cudaDeviceSynchronize());
@@ -1462,6 +1493,19 @@ fresco_status fresco_batch_status_check(fresco_batch_t b) {
         return FRESCO_ERR_NONFINITE;
     }
     return cuda_status(cudaGetLastError());
+}
+
+fresco_status fresco_batch_profile(fresco_batch_t b, int enable) {
+    if (!b) return FRESCO_ERR_ARG;
+    b->prof.on = enable != 0;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_batch_profile_read(fresco_batch_t b, double *ms, int64_t *counts) {
+    if (!b || !ms) return FRESCO_ERR_ARG;
+    FR_CUDA(b->stream ? cudaStreamSynchronize(b->stream) : cudaDeviceSynchronize());
+    b->prof.read(ms, counts);
+    return FRESCO_OK;
 }
 
 fresco_status fresco_batch_destroy(fresco_batch_t b) {

@@ -106,6 +106,43 @@ struct BTables {
 enum Stage { ST_SORT = 0, ST_SPREAD, ST_FFT_FWD, ST_MASK, ST_LOSS, ST_FFT_INV, ST_INTERP,
              ST_COUNT };
 
+// Per-stage device time: a pool of CUDA events, one (start, end) pair per recorded stage,
+// accumulated when read.
+struct StageProfile {
+    struct EvRec { int stage; cudaEvent_t a, b; };
+    bool on = false;
+    std::vector<EvRec> used;
+    std::vector<cudaEvent_t> spare;
+    double ms[ST_COUNT] = {};
+    int64_t calls[ST_COUNT] = {};
+    cudaEvent_t take();
+    // fold the recorded pairs into ms / calls (the stream must be synchronised), copy them out
+    // and reset
+    void read(double *ms_out, int64_t *calls_out);
+    void release();
+};
+
+// Records the events around one stage on a stream while it is in scope.
+struct StageScope {
+    StageProfile &p;
+    cudaStream_t s;
+    cudaEvent_t b = nullptr;
+    StageScope(StageProfile &p_, cudaStream_t s_, int stage) : p(p_), s(s_) {
+        if (!p.on) return;
+        cudaEvent_t a = p.take();
+        b = p.take();
+        if (a && b) {
+            cudaEventRecord(a, s);
+            p.used.push_back({stage, a, b});
+        } else {
+            b = nullptr;
+        }
+    }
+    ~StageScope() {
+        if (b) cudaEventRecord(b, s);
+    }
+};
+
 // Launchers, instantiated for T = float and T = double. All take the plan's stream and
 // return the cudaError_t of the launch. Element layouts are documented in fresco_kernels.cuh.
 template <typename T>
@@ -214,14 +251,7 @@ struct fresco_plan_s {
     cufftHandle ifft_rows = 0;       // C2C inverse along x, all rows
     bool have_fft[4] = {false, false, false, false};
 
-    // profiling: a pool of CUDA events, one (start, end) pair per recorded stage
-    struct EvRec { int stage; cudaEvent_t a, b; };
-    bool profiling = false;
-    std::vector<EvRec> ev_used;
-    std::vector<cudaEvent_t> ev_free;
-    cudaEvent_t take_event();
-    double stage_ms[fresco::ST_COUNT] = {};
-    int64_t stage_calls[fresco::ST_COUNT] = {};
+    fresco::StageProfile prof;
     int64_t launches = 0;
     bool forward_done = false;
 };
@@ -242,6 +272,7 @@ struct fresco_batch_s {
     int n_inst = 0;
     cudaStream_t stream = nullptr;
     std::vector<double> boxes;       // [n_inst][dim]
+    std::vector<fresco_info> infos;  // per instance, as fresco_get_info reports a plan
     std::vector<fresco::BInst> inst;
     std::vector<Cls> cls;
     std::vector<int64_t> pt_first, tile_first, mblk_first;
@@ -267,4 +298,5 @@ struct fresco_batch_s {
     int64_t launches = 0;
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
+    fresco::StageProfile prof;
 };

@@ -44,7 +44,8 @@ EXPORTS = (
     "fresco_batch_loss_grad", "fresco_batch_graph_capture", "fresco_batch_graph_launch",
     "fresco_batch_info", "fresco_batch_status_check", "fresco_batch_destroy",
     "fresco_batch_lbfgs_create", "fresco_batch_lbfgs_start", "fresco_batch_lbfgs_step",
-    "fresco_batch_lbfgs_read", "fresco_batch_lbfgs_destroy",
+    "fresco_batch_lbfgs_read", "fresco_batch_lbfgs_destroy", "fresco_batch_profile",
+    "fresco_batch_profile_read", "fresco_batch_get_info",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -149,6 +150,9 @@ def load(path: str = LIB_PATH):
             "fresco_batch_lbfgs_step": (I, [P, I64]),
             "fresco_batch_lbfgs_read": (I, [P, P, P, P]),
             "fresco_batch_lbfgs_destroy": (I, [P]),
+            "fresco_batch_profile": (I, [P, I]),
+            "fresco_batch_profile_read": (I, [P, P, P]),
+            "fresco_batch_get_info": (I, [P, I, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -429,8 +433,27 @@ def fresco_batch_info(batch) -> dict:
             "launches": nl.value}
 
 
+def fresco_batch_get_info(batch, i: int) -> dict:
+    info = fresco_info()
+    _check(load().fresco_batch_get_info(batch, int(i), ctypes.byref(info)),
+           "fresco_batch_get_info")
+    return info.as_dict()
+
+
 def fresco_batch_status_check(batch) -> int:
     return load().fresco_batch_status_check(batch)
+
+
+def fresco_batch_profile(batch, enable: bool):
+    _check(load().fresco_batch_profile(batch, 1 if enable else 0), "fresco_batch_profile")
+
+
+def fresco_batch_profile_read(batch):
+    """Per-stage device time since the last read: {stage: (ms, calls)}."""
+    ms = (ctypes.c_double * FRESCO_N_STAGES)()
+    cnt = (ctypes.c_int64 * FRESCO_N_STAGES)()
+    _check(load().fresco_batch_profile_read(batch, ms, cnt), "fresco_batch_profile_read")
+    return {STAGES[i]: (ms[i], cnt[i]) for i in range(FRESCO_N_STAGES)}
 
 
 def fresco_batch_destroy(batch):
@@ -582,6 +605,12 @@ class Batch:
 
     def status(self) -> int:
         return fresco_batch_status_check(self.handle)
+
+    def profile(self, enable=True):
+        fresco_batch_profile(self.handle, enable)
+
+    def profile_read(self):
+        return fresco_batch_profile_read(self.handle)
 
     def split(self, x):
         """Per-instance views of a [sum N, ...] tensor."""
