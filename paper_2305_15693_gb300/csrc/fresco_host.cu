@@ -249,7 +249,8 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
 
 fresco_status check_and_params(int dim, const double *box, int64_t n_points, const int32_t *mask,
                                int64_t n_k, const double *S0, const double *W,
-                               const fresco_opts *opts_in, Params &P) {
+                               const fresco_opts *opts_in, Params &P,
+                               bool width_from_reached = true) {
     if (dim != 2 && dim != 3) return FRESCO_ERR_ARG;
     if (!box || !mask || !S0 || !W) return FRESCO_ERR_ARG;
     if (n_points < 1 || n_points > 2147483647LL) return FRESCO_ERR_ARG;
@@ -301,6 +302,19 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
             P.nf[a] = 1;
             P.nb[a] = 1;
             P.tmax[a] = 1;
+        }
+    }
+    if (!o.width_override && width_from_reached) {
+        // rounding n_f up to an FFT-friendly size raises the oversampling actually reached; the
+        // width rule applied to that ratio may then need fewer cells (never more)
+        double sig_eff = 1e300;
+        for (int a = 0; a < dim; ++a)
+            sig_eff = std::min(sig_eff, (double)P.nf[a] / (2.0 * kmax[a] + 1.0));
+        const int w_eff = std::max(kMinWidth, es_width(tol, sig_eff));
+        if (w_eff < w) {
+            w = w_eff;
+            P.width = w;
+            P.beta = es_beta(w, sig_eff);
         }
     }
     fresco_status st = choose_tiling(P, o.tile);
@@ -1389,9 +1403,10 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     if (opts) o = *opts;
     for (int i = 0; i < n_inst; ++i) {
         if (n_modes[i] < 1) return FRESCO_ERR_ARG;
+        // one kernel serves every instance: the width rule at the requested oversampling
         fresco_status st = check_and_params(dim, boxes + (size_t)i * dim, n_points[i],
                                             masks + m0 * dim, n_modes[i], S0 + m0, W + m0, &o,
-                                            P[i]);
+                                            P[i], false);
         if (st) return st;
         if (i > 0 && P[i].width != P[0].width) return FRESCO_ERR_UNSUPPORTED;
         for (int a = 0; a < dim; ++a) P[i].nf[a] = class_size(P[i].nf[a]);

@@ -65,19 +65,32 @@ def test_parameters_of_the_named_workloads(fr):
     assert info["k_max"] == [193, 193, 193] and info["n_fine"] == [784, 784, 784]
 
 
+def _width_rule(eps, sigma):
+    return max(2, math.ceil(math.log(1.0 / eps) / (math.pi * math.sqrt(1.0 - 1.0 / sigma))))
+
+
 def test_fine_grid_is_smooth_and_large_enough(fr):
+    """n_f is the smallest even 2-3-5-7-smooth size >= max(sigma (2K+1), 2 w_sigma, 2K+2), w_sigma
+    the width rule at the requested sigma; the kernel then takes the width rule at the
+    oversampling n_f / (2K+1) actually reached, which is never wider."""
     for K in (1, 2, 5, 13, 40, 101):
         for sigma in (1.25, 2.0, 2.5):
             info = _query(fr, inputs.ball_mask(K, 2), upsample=sigma)
             nf = info["n_fine"][0]
-            assert nf % 2 == 0 and nf >= sigma * (2 * K + 1) and nf >= 2 * info["width"]
+            w_sigma = _width_rule(1e-6, sigma)
+            assert info["width"] == min(w_sigma, _width_rule(1e-6, nf / (2 * K + 1)))
+            if info["width"] < w_sigma:
+                reached = nf / (2 * K + 1)
+                assert info["beta"] == pytest.approx(
+                    0.976 * math.pi * (1 - 0.5 / reached) * info["width"], rel=1e-12)
+            assert nf % 2 == 0 and nf >= sigma * (2 * K + 1) and nf >= 2 * w_sigma
             m = nf
             for p in (2, 3, 5, 7):
                 while m % p == 0:
                     m //= p
             assert m == 1
             # smallest such: no smaller even smooth number qualifies
-            for c in range(max(2, math.ceil(max(sigma * (2 * K + 1), 2 * info["width"],
+            for c in range(max(2, math.ceil(max(sigma * (2 * K + 1), 2 * w_sigma,
                                                 2 * K + 2))), nf):
                 if c % 2:
                     continue
