@@ -216,16 +216,14 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
             P.nb[a] = choose_tiles(P.nf[a], target[a], w);
             P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
         }
-        size_t halo_cells = 1, cells = 1;
-        for (int a = 0; a < dim; ++a) {
-            halo_cells *= (size_t)(P.tmax[a] + w);
-            cells *= (size_t)P.tmax[a];
-        }
-        const size_t interp = halo_cells * (2 * es + (dim == 3 ? es : 0));
-        // tile (at least 4-byte cells) plus the compacted point list (2048 float / 1024 double
-        // entries of one int and dim coordinates)
-        const size_t spread = ((cells * std::max<size_t>(es, 4) + 15) & ~(size_t)15) +
-                              (es == 8 ? 1024 : 2048) * (es * dim + 4);
+        Geom tg{};
+        tg.dim = dim;
+        tg.width = w;
+        for (int a = 0; a < 3; ++a) tg.tmax[a] = a < dim ? P.tmax[a] : 1;
+        const size_t interp = es == 8 ? Launch<double>::interp_smem(tg)
+                                      : Launch<float>::interp_smem(tg);
+        const size_t spread = es == 8 ? Launch<double>::spread_smem(tg)
+                                      : Launch<float>::spread_smem(tg);
         if (interp <= budget && spread <= budget) break;
         int amax = 0;
         for (int a = 1; a < dim; ++a)
