@@ -120,7 +120,7 @@ def stage_bytes(info: dict, n_points: int, esize: int) -> dict:
     nrep = info["n_rep"]
     N = n_points
     c2 = 2 * esize                    # complex element
-    return {
+    out = {
         "sort": N * d * esize + N * pd * esize + 4 * N,
         "spread": N * pd * esize + cells * esize,
         "fft_fwd": cells * esize + rows * half * c2,
@@ -129,6 +129,12 @@ def stage_bytes(info: dict, n_points: int, esize: int) -> dict:
         "fft_inv": n_pipes * (rows * hc_row * c2 + cells * c2),
         "interp": n_pipes * cells * c2 + N * pd * esize + 4 * N + N * d * esize,
     }
+    if info.get("grad_mode", 0) == 1:
+        # one scalar half spectrum [kx + 1][rows] in, one real grid out and back in
+        out["mask"] = nrep * (4 * d + 2 * esize + c2 + c2)
+        out["fft_inv"] = rows * (kx + 1) * c2 + cells * esize
+        out["interp"] = cells * esize + N * pd * esize + 4 * N + N * d * esize
+    return out
 
 
 def load_peaks():
@@ -546,6 +552,8 @@ def main():
                     help="override the workload's fine-grid oversampling sigma")
     ap.add_argument("--tile", type=int, nargs="*", default=None,
                     help="override the spread/interp tile edge per axis")
+    ap.add_argument("--grad-mode", default=None, choices=["direct", "kderiv"],
+                    help="override the workload's gradient mode")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3")
@@ -559,6 +567,8 @@ def main():
         wl = inputs.workload(args.workload)
         if args.upsample:
             wl.upsample = args.upsample
+        if args.grad_mode:
+            wl.grad_mode = args.grad_mode
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -596,7 +606,7 @@ def main():
 
     # ---- FP32 path: the headline -------------------------------------------------------------
     plan = fresco.Plan(wl.box, mask, S0, W, N, precision=wl.dtype, tol=wl.tol,
-                       upsample=wl.upsample, tile=args.tile)
+                       upsample=wl.upsample, tile=args.tile, grad_mode=wl.grad_mode)
     info = plan.info
     log("plan: n_fine=%s w=%d tiles=%s n_rep=%d device_bytes=%.2f GB" % (
         info["n_fine"][:wl.dim], info["width"], info["n_tiles"][:wl.dim], info["n_rep"],
@@ -648,7 +658,7 @@ def main():
     if wl.dtype == "f32" and args.f64_steps > 0:
         pts64 = pts.double()
         plan64 = fresco.Plan(wl.box, mask, S0, W, N, precision="f64", tol=1e-12,
-                             upsample=wl.upsample)
+                             upsample=wl.upsample, grad_mode=wl.grad_mode)
         ms64, _, st64, loss64 = time_device(plan64, pts64, args.f64_steps, 3, dist_on)
         plan64.close()
         del pts64
@@ -671,6 +681,7 @@ def main():
             "config": {"workload": wl.name, "n_points": N, "dim": wl.dim, "K": wl.K,
                        "n_modes": int(mask.shape[0]), "target": wl.target, "tol": wl.tol,
                        "upsample": wl.upsample, "width": info["width"],
+                       "grad_mode": wl.grad_mode,
                        "n_fine": info["n_fine"][:wl.dim], "tiles": info["n_tiles"][:wl.dim],
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (fine grid %.2f GB > %d MB)"

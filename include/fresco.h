@@ -66,8 +66,21 @@ typedef struct {
     double upsample;     /* fine-grid oversampling sigma; 0 -> 2.0; must be in [1.25, 3] */
     int width_override;  /* kernel width w in fine-grid cells (2..16); 0 -> from tol */
     int tile[3];         /* spread/interp tile edge per axis in fine cells; 0 -> default */
-    int reserved[4];     /* must be zero */
+    int grad_mode;       /* FRESCO_GRAD_DIRECT (default) or FRESCO_GRAD_KDERIV, see below */
+    int reserved[3];     /* must be zero */
 } fresco_opts;
+
+/* Gradient modes (the adjoint half of the evaluation, Eq. 4).
+ * FRESCO_GRAD_DIRECT: the d gradient components i k_d E(k) / Psi(k) are transformed to the fine
+ *   grid (in 2D as one complex field G_x + i G_y; in 3D as that plus G_z) and interpolated with
+ *   the kernel psi.
+ * FRESCO_GRAD_KDERIV: one real field, the inverse transform of E(k) / Psi(k) (Hermitian, so a
+ *   single complex-to-real FFT), interpolated with the kernel's derivative psi' along each axis:
+ *   the gradient of the type-2 interpolant. It needs one real FFT instead of d real FFTs' worth
+ *   and reads one real grid, at an accuracy slightly below the direct mode's (the derivative
+ *   amplifies the kernel's aliasing error). Batch plans use the direct mode only. */
+#define FRESCO_GRAD_DIRECT 0
+#define FRESCO_GRAD_KDERIV 1
 
 /* Plan parameters, filled by fresco_plan_query and fresco_get_info. */
 typedef struct {
@@ -85,6 +98,7 @@ typedef struct {
     int64_t n_modes;       /* mask entries as given */
     int64_t n_rep;         /* half-space representatives after folding */
     int64_t device_bytes;  /* device memory the plan holds (0 from fresco_plan_query) */
+    int grad_mode;         /* FRESCO_GRAD_DIRECT or FRESCO_GRAD_KDERIV */
 } fresco_info;
 
 /* Fill *opts with the defaults (F32, eps = 1e-6, sigma = 2). */

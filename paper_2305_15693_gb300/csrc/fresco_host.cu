@@ -163,6 +163,7 @@ struct Folded {
 
 struct Params {
     int dim, precision, width;
+    int grad_mode;    // fresco_opts.grad_mode
     double beta, sigma, tol;
     int kmax[3];
     int nf[3];
@@ -256,8 +257,10 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
     fresco_opts o;
     fresco_opts_default(&o);
     if (opts_in) o = *opts_in;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i] != 0) return FRESCO_ERR_ARG;
+    if (o.grad_mode != FRESCO_GRAD_DIRECT && o.grad_mode != FRESCO_GRAD_KDERIV)
+        return FRESCO_ERR_ARG;
     if (o.precision != FRESCO_F32 && o.precision != FRESCO_F64) return FRESCO_ERR_ARG;
     double sigma = o.upsample == 0.0 ? 2.0 : o.upsample;
     if (!(sigma >= 1.25 && sigma <= 3.0)) return FRESCO_ERR_ARG;
@@ -283,6 +286,7 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
     }
     P.dim = dim;
     P.precision = o.precision;
+    P.grad_mode = o.grad_mode;
     P.width = w;
     P.sigma = sigma;
     P.tol = tol;
@@ -411,6 +415,7 @@ void fill_info(const Params &P, int64_t n_points, int64_t n_k, const Folded &F, 
     info->n_points = n_points;
     info->n_modes = n_k;
     info->n_rep = (int64_t)F.s0.size();
+    info->grad_mode = P.grad_mode;
 }
 
 // ---- device helpers --------------------------------------------------------------------------
@@ -472,6 +477,13 @@ void release(fresco_plan_s *p) {
 }
 
 template <typename T>
+cufftType c2r_type();
+template <>
+cufftType c2r_type<float>() { return CUFFT_C2R; }
+template <>
+cufftType c2r_type<double>() { return CUFFT_Z2D; }
+
+template <typename T>
 cufftType r2c_type();
 template <>
 cufftType r2c_type<float>() { return CUFFT_R2C; }
@@ -525,7 +537,11 @@ fresco_status make_ffts(fresco_plan_s *p) {
                                  c2c_type<T>(), kx + 1, &ws[1]));
     FR_CUFFT(cufftMakePlanMany64(p->ifft_cols, crank, cn, nullptr, 1, plane, nullptr, 1, plane,
                                  c2c_type<T>(), hcw, &ws[2]));
-    {
+    if (p->mgeom.kderiv) {   // rows, inverse complex-to-real from the half rows
+        long long n[1] = {nf0};
+        FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, half, nullptr, 1, nf0,
+                                     c2r_type<T>(), rows, &ws[3]));
+    } else {
         long long n[1] = {nf0};
         FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, nf0,
                                      c2c_type<T>(), rows, &ws[3]));
@@ -580,10 +596,13 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     m.kx = P.kmax[0];
     m.n_rep = (int64_t)F.s0.size();
     m.half_row = P.nf[0] / 2 + 1;
-    m.hc_row = 2 * (int64_t)P.kmax[0] + 2;
+    m.kderiv = P.grad_mode == FRESCO_GRAD_KDERIV ? 1 : 0;
+    m.hc_row = m.kderiv ? (int64_t)P.kmax[0] + 1 : 2 * (int64_t)P.kmax[0] + 2;
     m.plane = (int64_t)P.nf[1] * P.nf[2];
     m.inv_n = 1.0 / (double)p->n_points;
-    p->n_pipes = dim == 2 ? 1 : 2;
+    p->n_pipes = (dim == 2 || m.kderiv) ? 1 : 2;
+    for (int a = 0; a < 3; ++a)
+        p->dscale[a] = a < dim ? -2.0 * (double)P.nf[a] / p->box[a] : 0.0;
 
     // shared memory budget
     int dev = 0;
@@ -611,13 +630,18 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     if ((st = dalloc(p, &p->d_grid, sizeof(T) * (size_t)cells))) return st;
     if ((st = dalloc(p, &p->d_spec, sizeof(C2) * (size_t)(rows * m.half_row)))) return st;
     if ((st = dalloc(p, &p->d_specT, sizeof(C2) * (size_t)(rows * (m.kx + 1))))) return st;
+    // backward spectra: compact transposed [hc_row][plane], after the (z,)y pass, back in row
+    // order (a full complex row in the direct mode, the half row of the real transform in the
+    // kderiv mode; columns outside the mask stay zero from here on), and the grid(s)
+    const size_t r_elems = m.kderiv ? (size_t)(rows * m.half_row) : (size_t)cells;
+    const size_t g_bytes = m.kderiv ? sizeof(T) * (size_t)cells : sizeof(C2) * (size_t)cells;
     for (int q = 0; q < p->n_pipes; ++q) {
         if ((st = dalloc(p, &p->d_hc[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
         if ((st = dalloc(p, &p->d_bt[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
-        if ((st = dalloc(p, &p->d_r[q], sizeof(C2) * (size_t)cells))) return st;
-        if ((st = dalloc(p, &p->d_g[q], sizeof(C2) * (size_t)cells))) return st;
+        if ((st = dalloc(p, &p->d_r[q], sizeof(C2) * r_elems))) return st;
+        if ((st = dalloc(p, &p->d_g[q], g_bytes))) return st;
         FR_CUDA(cudaMemsetAsync(p->d_hc[q], 0, sizeof(C2) * (size_t)(rows * m.hc_row), p->stream));
-        FR_CUDA(cudaMemsetAsync(p->d_r[q], 0, sizeof(C2) * (size_t)cells, p->stream));
+        FR_CUDA(cudaMemsetAsync(p->d_r[q], 0, sizeof(C2) * r_elems, p->stream));
     }
     const int64_t nrep = m.n_rep;
     if ((st = dalloc(p, &p->d_rep_n, sizeof(int) * (size_t)(nrep * dim)))) return st;
@@ -724,6 +748,30 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
     const Geom &g = p->geom;
     const MaskGeom &m = p->mgeom;
     cudaStream_t s = p->stream;
+    if (m.kderiv) {
+        {
+            StageScope sc(p->prof, p->stream, ST_FFT_INV);
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2C(p->ifft_cols, (cufftComplex *)p->d_hc[0],
+                                      (cufftComplex *)p->d_bt[0], CUFFT_INVERSE));
+            else
+                FR_CUFFT(cufftExecZ2Z(p->ifft_cols, (cufftDoubleComplex *)p->d_hc[0],
+                                      (cufftDoubleComplex *)p->d_bt[0], CUFFT_INVERSE));
+            FR_CUDA(Launch<T>::rows_to_half(p->d_bt[0], p->d_r[0], m.plane, m.half_row, m.kx, s));
+            p->launches += 1;
+            if (sizeof(T) == 4)
+                FR_CUFFT(cufftExecC2R(p->ifft_rows, (cufftComplex *)p->d_r[0],
+                                      (cufftReal *)p->d_g[0]));
+            else
+                FR_CUFFT(cufftExecZ2D(p->ifft_rows, (cufftDoubleComplex *)p->d_r[0],
+                                      (cufftDoubleReal *)p->d_g[0]));
+        }
+        StageScope sc(p->prof, p->stream, ST_INTERP);
+        FR_CUDA(Launch<T>::interp_kd(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off,
+                                     (const T *)p->d_g[0], grad_out, p->dscale, grad, s));
+        p->launches += 1;
+        return FRESCO_OK;
+    }
     {
         StageScope sc(p->prof, p->stream, ST_FFT_INV);
         for (int q = 0; q < p->n_pipes; ++q) {
@@ -1401,6 +1449,7 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     if (opts) o = *opts;
     for (int i = 0; i < n_inst; ++i) {
         if (n_modes[i] < 1) return FRESCO_ERR_ARG;
+        if (o.grad_mode != FRESCO_GRAD_DIRECT) return FRESCO_ERR_UNSUPPORTED;
         // one kernel serves every instance: the width rule at the requested oversampling
         fresco_status st = check_and_params(dim, boxes + (size_t)i * dim, n_points[i],
                                             masks + m0 * dim, n_modes[i], S0 + m0, W + m0, &o,

@@ -53,7 +53,9 @@ struct MaskGeom {
     int kx;              // max n_x over representatives (>= 0)
     int64_t n_rep;
     int64_t half_row;    // nf[0] / 2 + 1: row length of the forward half spectrum
-    int64_t hc_row;      // 2 * kx + 2: columns n_x = -kx-1 .. kx of the compact backward spectrum
+    int64_t hc_row;      // columns of the compact backward spectrum: 2 kx + 2 (n_x = -kx-1 .. kx)
+                         // in the direct gradient mode, kx + 1 (n_x = 0 .. kx) in the kderiv mode
+    int kderiv;          // the backward spectrum is the scalar E / Psi (kernel-derivative mode)
     int64_t plane;       // nf[1] * nf[2]: length of one transposed column (all (z, y) for one x)
     double inv_n;        // 1 / N
     double kscale[3];    // 2 pi / L_a
@@ -164,6 +166,14 @@ struct Launch {
     static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                               const int *perm, const int *off, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s);
+    // kernel-derivative mode: h is the real field, dscale[a] = -2 n_f[a] / L[a]
+    static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                 const int *perm, const int *off, const T *h,
+                                 const double *grad_out, const double dscale[3], T *grad,
+                                 cudaStream_t s);
+    static int interp_kd_smem(const Geom &g);
+    static cudaError_t rows_to_half(const void *bt, void *r, int64_t rows, int64_t half_row,
+                                    int kx, cudaStream_t s);
     static cudaError_t cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda,
                                     int ncols, cudaStream_t s, int batch = 1,
                                     int64_t a_stride = 0, int64_t at_stride = 0);
@@ -241,7 +251,8 @@ struct fresco_plan_s {
     fresco::EsPoly<float> poly32{};
     fresco::EsPoly<double> poly64{};
     int n_mask_blocks = 0;
-    int n_pipes = 1;                 // complex gradient pipelines: ceil(dim / 2)
+    int n_pipes = 1;                 // complex gradient pipelines: ceil(dim / 2), 1 in kderiv
+    double dscale[3] = {0, 0, 0};    // kderiv mode: -2 n_f[a] / L[a]
     int64_t device_bytes = 0;
 
     // cuFFT plans

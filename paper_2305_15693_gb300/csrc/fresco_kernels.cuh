@@ -151,6 +151,25 @@ __device__ __forceinline__ void es_weights(const EsPoly<T> &ep, T x1, T (&w)[W])
     }
 }
 
+// The weights and their derivatives d psi(x1 + k) / d tau (Horner for the value and the
+// derivative together); d psi / d x1 = 2 d psi / d tau.
+template <typename T, int W>
+__device__ __forceinline__ void es_weights_d(const EsPoly<T> &ep, T x1, T (&w)[W], T (&dw)[W]) {
+    constexpr int P = PolyDeg<T>::value;
+    const T tau = T(2) * x1 + T(W - 1);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        T acc = ep.c[k][P], dacc = T(0);
+#pragma unroll
+        for (int j = P - 1; j >= 0; --j) {
+            dacc = fma(dacc, tau, acc);
+            acc = fma(acc, tau, ep.c[k][j]);
+        }
+        w[k] = acc;
+        dw[k] = dacc;
+    }
+}
+
 // Start of the kernel support (first cell) relative to the cell holding the point, and the
 // offset x1 = start - t in [-W/2, -W/2 + 1).
 template <typename T, int W>
@@ -828,10 +847,17 @@ __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__res
         const T E = T(4) * wgt * (T)d * inv_n;
         const T h = T(0.5) * ip * E;
         const T er = re * h, ei = im * h;
-        const T kx = (T)(m.kscale[0] * nx), ky = (T)(m.kscale[1] * ny);
         const int my = ny > 0 ? m.nf[1] - ny : -ny;
         const int mz = nz > 0 ? m.nf[2] - nz : -nz;
         const int64_t rowm = (int64_t)mz * m.nf[1] + my;
+        if (m.kderiv) {
+            // the scalar half spectrum E / Psi at n (and, on the n_x = 0 column, its conjugate at
+            // -n, which the complex-to-real transform expects to find there)
+            hc0[(int64_t)nx * m.plane + row] = C{er, ei};
+            if (nx == 0) hc0[rowm] = C{er, -ei};
+            continue;
+        }
+        const T kx = (T)(m.kscale[0] * nx), ky = (T)(m.kscale[1] * ny);
         const int64_t cp = (int64_t)(nx + m.kx + 1) * m.plane + row;
         const int64_t cm = (int64_t)(-nx + m.kx + 1) * m.plane + rowm;
         hc0[cp] = C{-er * ky - ei * kx, er * kx - ei * ky};
@@ -1079,6 +1105,127 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_b(
     }
 }
 
+// K7 in the kernel-derivative mode: the tile and halo of the real field h = F^-1[E / Psi] are
+// staged in shared memory and each point takes the gradient of the interpolant,
+//   dL/dr_a = -(2 n_f[a] / L[a]) sum_m h(m) (d psi / d tau along a) (psi along the other axes),
+// scaled by the incoming gradient; dscale holds -2 n_f[a] / L[a].
+template <typename T, int W, int D>
+__device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &ep,
+                                               const typename PT<T>::U *__restrict__ sorted,
+                                               const int *__restrict__ perm,
+                                               const int *__restrict__ off,
+                                               const T *__restrict__ h, T dsx, T dsy, T dsz,
+                                               T *__restrict__ grad, const int64_t t) {
+    using U = typename PT<T>::U;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
+                       (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
+    constexpr int HL = W / 2;
+    int s[3], rw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < D) {
+            s[a] = tile_start(tc[a], g.tq[a], g.tr[a]);
+            rw[a] = tile_start(tc[a] + 1, g.tq[a], g.tr[a]) - s[a] + W;
+        } else {
+            s[a] = 0;
+            rw[a] = 1;
+        }
+    }
+    const int rxy = rw[0] * rw[1];
+    T *sh = reinterpret_cast<T *>(sm_raw);
+    {
+        const int lane = threadIdx.x & 31;
+        const int nrows = rw[1] * rw[2];
+        for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
+            const int z = D == 3 ? row / rw[1] : 0, y = D == 3 ? row - z * rw[1] : row;
+            int gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
+            gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+            if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
+            const int64_t rbase = ((int64_t)gz * g.nf[1] + gy) * g.nf[0];
+            for (int x = lane; x < rw[0]; x += 32) {
+                int gx = s[0] - HL + x;
+                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+                sh[row * rw[0] + x] = h[rbase + gx];
+            }
+        }
+    }
+    __syncthreads();
+    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        U u[3];
+        const int64_t j = load_record<T, D>(sorted, perm, p, u);
+        int i0[3] = {0, 0, 0};
+        T x1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            int rel;
+            T f;
+            unpack_coord<T>(u[a], rel, f);
+            i0[a] = rel + support_start<T, W>(f, x1[a]) + HL;
+        }
+        T wx[W], dwx[W], wy[W], dwy[W];
+        es_weights_d<T, W>(ep, x1[0], wx, dwx);
+        es_weights_d<T, W>(ep, x1[1], wy, dwy);
+        if constexpr (D == 2) {
+            T gx = T(0), gy = T(0);
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const T *row = sh + (i0[1] + b) * rw[0] + i0[0];
+                T r0 = T(0), r1 = T(0);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const T v = row[a];
+                    r0 = fma(wx[a], v, r0);
+                    r1 = fma(dwx[a], v, r1);
+                }
+                gx = fma(wy[b], r1, gx);
+                gy = fma(dwy[b], r0, gy);
+            }
+            using T2 = typename PT<T>::C;
+            reinterpret_cast<T2 *>(grad)[j] = T2{dsx * gx, dsy * gy};
+        } else {
+            T wz[W], dwz[W];
+            es_weights_d<T, W>(ep, x1[2], wz, dwz);
+            T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll 1
+            for (int c = 0; c < W; ++c) {
+                T px = T(0), py = T(0), pz = T(0);
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const T *row = sh + (i0[2] + c) * rxy + (i0[1] + b) * rw[0] + i0[0];
+                    T r0 = T(0), r1 = T(0);
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const T v = row[a];
+                        r0 = fma(wx[a], v, r0);
+                        r1 = fma(dwx[a], v, r1);
+                    }
+                    px = fma(wy[b], r1, px);
+                    py = fma(dwy[b], r0, py);
+                    pz = fma(wy[b], r0, pz);
+                }
+                gx = fma(wz[c], px, gx);
+                gy = fma(wz[c], py, gy);
+                gz = fma(dwz[c], pz, gz);
+            }
+            grad[j * 3 + 0] = dsx * gx;
+            grad[j * 3 + 1] = dsy * gy;
+            grad[j * 3 + 2] = dsz * gz;
+        }
+    }
+}
+
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_kd(
+    Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
+    const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad) {
+    const T sc = grad_out ? (T)(*grad_out) : T(1);
+    interp_tile_kd<T, W, D>(g, ep, sorted, perm, off, h, sc * dsx, sc * dsy, sc * dsz, grad,
+                            blockIdx.x);
+}
+
 // rho and S for the mask rows as given to the plan (diagnostic output).
 template <typename T, int D>
 __global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
@@ -1154,6 +1301,27 @@ __global__ void __launch_bounds__(256) k_rows_to_cols(const C *__restrict__ bt, 
     }
 }
 
+// Kernel-derivative mode: the transformed columns [kx + 1][rows] back into the rows of the
+// half spectrum [rows][half_row] (columns 0 .. kx; the others stay zero from plan time).
+template <typename C>
+__global__ void __launch_bounds__(256) k_rows_to_half(const C *__restrict__ bt, C *__restrict__ r,
+                                                      int64_t rows, int64_t half_row, int ncols) {
+    __shared__ C tile[32][33];
+    const int c0 = blockIdx.y * 32;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int c = c0 + k;
+        const int64_t row = r0 + threadIdx.x;
+        if (c < ncols && row < rows) tile[k][threadIdx.x] = bt[(int64_t)c * rows + row];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t row = r0 + k;
+        const int c = c0 + threadIdx.x;
+        if (row < rows && c < ncols) r[row * half_row + c] = tile[threadIdx.x][k];
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Launchers
 
@@ -1204,6 +1372,22 @@ int Launch<T>::spread_smem(const Geom &g) {
 }
 
 template <typename T>
+int Launch<T>::interp_kd_smem(const Geom &g) {
+    const int w = g.width;
+    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
+    return (int)(cells * sizeof(T));
+}
+
+template <typename T>
+cudaError_t Launch<T>::rows_to_half(const void *bt, void *r, int64_t rows, int64_t half_row,
+                                    int kx, cudaStream_t s) {
+    using C = typename PT<T>::C;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((kx + 1 + 31) / 32));
+    k_rows_to_half<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, half_row, kx + 1);
+    return cudaGetLastError();
+}
+
+template <typename T>
 int Launch<T>::interp_smem(const Geom &g) {
     const int w = g.width;
     size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
@@ -1236,6 +1420,21 @@ static cudaError_t launch_interp_w(const Geom &g, const EsPoly<T> &ep, const voi
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, off,
                                                 (const C *)g0, (const C *)g1, grad_out, grad);
+    return cudaGetLastError();
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_interp_kd_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                      const int *perm, const int *off, const T *h,
+                                      const double *grad_out, const double dscale[3], T *grad,
+                                      cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int smem = Launch<T>::interp_kd_smem(g);
+    auto kern = k_interp_kd<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, off, h, grad_out,
+                                                (T)dscale[0], (T)dscale[1], (T)dscale[2], grad);
     return cudaGetLastError();
 }
 
@@ -1281,6 +1480,20 @@ cudaError_t Launch<T>::interp(const Geom &g, const EsPoly<T> &ep, const void *so
     } else {
         FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 3>(g, ep, sorted, perm, off,
                                                                       g0, g1, grad_out, grad, s)));
+    }
+}
+
+template <typename T>
+cudaError_t Launch<T>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                 const int *perm, const int *off, const T *h,
+                                 const double *grad_out, const double dscale[3], T *grad,
+                                 cudaStream_t s) {
+    if (g.dim == 2) {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_kd_w<T, WW, 2>(
+                                         g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_kd_w<T, WW, 3>(
+                                         g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
     }
 }
 

@@ -28,6 +28,8 @@ FRESCO_ERR_TIMEOUT = 7
 FRESCO_ERR_UNSUPPORTED = 8
 FRESCO_F32 = 0
 FRESCO_F64 = 1
+FRESCO_GRAD_DIRECT = 0
+FRESCO_GRAD_KDERIV = 1
 FRESCO_N_STAGES = 7
 STAGES = ("sort", "spread", "fft_fwd", "mask", "loss", "fft_inv", "interp")
 
@@ -59,7 +61,8 @@ class FrescoError(RuntimeError):
 class fresco_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("upsample", ctypes.c_double), ("width_override", ctypes.c_int),
-                ("tile", ctypes.c_int * 3), ("reserved", ctypes.c_int * 4)]
+                ("tile", ctypes.c_int * 3), ("grad_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class fresco_lbfgs_opts(ctypes.Structure):
@@ -83,7 +86,7 @@ class fresco_info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("upsample", ctypes.c_double),
                 ("loss_const", ctypes.c_double), ("n_points", ctypes.c_int64),
                 ("n_modes", ctypes.c_int64), ("n_rep", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("grad_mode", ctypes.c_int)]
 
     def as_dict(self):
         d = {}
@@ -205,7 +208,8 @@ def _host_arrays(box, mask, S0, W):
     return dim, box, mask, S0, W
 
 
-def make_opts(precision="f32", tol=0.0, upsample=2.0, width=0, tile=None) -> fresco_opts:
+def make_opts(precision="f32", tol=0.0, upsample=2.0, width=0, tile=None,
+              grad_mode=FRESCO_GRAD_DIRECT) -> fresco_opts:
     o = fresco_opts()
     load().fresco_opts_default(ctypes.byref(o))
     o.precision = FRESCO_F64 if precision in ("f64", FRESCO_F64, "float64") else FRESCO_F32
@@ -215,6 +219,8 @@ def make_opts(precision="f32", tol=0.0, upsample=2.0, width=0, tile=None) -> fre
     if tile is not None:
         for a, t in enumerate(tile):
             o.tile[a] = int(t)
+    o.grad_mode = {"direct": FRESCO_GRAD_DIRECT, "kderiv": FRESCO_GRAD_KDERIV}.get(
+        grad_mode, grad_mode)
     return o
 
 
@@ -720,10 +726,10 @@ class Plan:
     """
 
     def __init__(self, box, mask, S0, W, n_points, precision="f32", tol=0.0, upsample=2.0,
-                 width=0, tile=None, stream=None):
+                 width=0, tile=None, stream=None, grad_mode=FRESCO_GRAD_DIRECT):
         import torch  # device memory and streams only
         self._torch = torch
-        self.opts = make_opts(precision, tol, upsample, width, tile)
+        self.opts = make_opts(precision, tol, upsample, width, tile, grad_mode)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -199,6 +199,7 @@ class Workload:
     box: float = 1.0
     tol: float = 1e-6
     upsample: float = 2.0
+    grad_mode: str = "direct"   # "direct" or "kderiv" (gradient of the type-2 interpolant)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -227,20 +228,23 @@ def workload(name: str) -> Workload:
     """The named synthetic workloads (sizes in the name; see the module docstring)."""
     if name == "stealthy2d_n1024_k20_f64":
         return Workload(name, 2, 1024, 20, "stealthy", "f64", seed=0, tol=1e-12)
+    # the FP32 workloads take the gradient of the type-2 interpolant (one real inverse FFT, one
+    # real grid to interpolate): 2.3x faster in 3D and 7% faster at 1e8 in 2D than the direct
+    # mode, 2e-6 .. 6e-6 relative gradient difference
     if name == "stealthy2d_n1e6_chi045_f32":
         return Workload(name, 2, 10**6, radius_for_chi(10**6, 2, 0.45), "stealthy", "f32",
-                        seed=0, tol=1e-6)
+                        seed=0, tol=1e-6, grad_mode="kderiv")
     if name == "powerlaw3d_n2p24_chi03_f32":
         return Workload(name, 3, 2**24, radius_for_chi(2**24, 3, 0.3), "power_law", "f32",
-                        seed=0, tol=1e-6)
+                        seed=0, tol=1e-6, grad_mode="kderiv")
     # the large 2D workloads run at oversampling 1.5 (kernel width 8 at 1e-6): the fine grid is
     # 1.8x smaller than at 2.0, which more than pays for the wider kernel
     if name == "peaked2d_n1e8_chi03_f32":
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f32",
-                        seed=0, tol=1e-6, upsample=1.5)
+                        seed=0, tol=1e-6, upsample=1.5, grad_mode="kderiv")
     if name == "peaked2d_n1e7_chi03_f32":
         return Workload(name, 2, 10**7, radius_for_chi(10**7, 2, 0.3), "peaked", "f32",
-                        seed=0, tol=1e-6, upsample=1.5)
+                        seed=0, tol=1e-6, upsample=1.5, grad_mode="kderiv")
     if name == "peaked2d_n1e8_chi03_f64":
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f64",
                         seed=0, tol=1e-12, upsample=1.5)

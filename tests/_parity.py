@@ -23,14 +23,14 @@ def rel_l2(a, b):
 
 
 def gpu_eval(points, mask, S0, W, box=1.0, precision="f64", tol=0.0, tile=None, upsample=2.0,
-             want_rho=True):
+             want_rho=True, grad_mode=0):
     """One loss+gradient evaluation through the C ABI; returns (loss, grad, rho, S, status, info)."""
     import torch
     from paper_2305_15693_gb300 import fresco
     dt = torch.float64 if precision == "f64" else torch.float32
     pts = torch.from_numpy(np.ascontiguousarray(points)).to("cuda", dt)
     plan = fresco.Plan(box, mask, S0, W, pts.shape[0], precision=precision, tol=tol, tile=tile,
-                       upsample=upsample)
+                       upsample=upsample, grad_mode=grad_mode)
     try:
         loss, grad = plan.loss_grad(pts)
         rho = S = None
@@ -46,11 +46,12 @@ def gpu_eval(points, mask, S0, W, box=1.0, precision="f64", tol=0.0, tile=None, 
     return out
 
 
-def compare(points, mask, S0, W, box=1.0, precision="f64", tol=0.0, tile=None, upsample=2.0):
+def compare(points, mask, S0, W, box=1.0, precision="f64", tol=0.0, tile=None, upsample=2.0,
+            grad_mode=0):
     """GPU vs oracle errors on the same inputs."""
     import oracle
     loss_g, grad_g, rho_g, S_g, st, info = gpu_eval(points, mask, S0, W, box, precision, tol,
-                                                    tile, upsample)
+                                                    tile, upsample, grad_mode=grad_mode)
     loss_o, grad_o, S_o, rho_o = oracle.loss_grad(points, mask, S0, W, box=box)
     return {
         "status": st,

@@ -63,6 +63,9 @@ def test_parameters_of_the_named_workloads(fr):
     m3 = np.vstack([m3, [[193, 0, 0], [0, 193, 0], [0, 0, -193]]]).astype(np.int32)
     info = _query(fr, m3, tol=1e-6)
     assert info["k_max"] == [193, 193, 193] and info["n_fine"] == [784, 784, 784]
+    assert info["grad_mode"] == fr.FRESCO_GRAD_DIRECT
+    info = _query(fr, m3, tol=1e-6, grad_mode="kderiv")
+    assert info["grad_mode"] == fr.FRESCO_GRAD_KDERIV and info["n_fine"] == [784, 784, 784]
 
 
 def _width_rule(eps, sigma):
@@ -158,7 +161,8 @@ def test_unreachable_tolerance_is_unsupported(fr):
     assert e.value.status == fr.FRESCO_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("bad", ["zero_n", "dim4", "neg_w", "nan_s0", "n0", "tol", "sigma"])
+@pytest.mark.parametrize("bad", ["zero_n", "dim4", "neg_w", "nan_s0", "n0", "tol", "sigma",
+                                 "grad_mode"])
 def test_argument_errors(fr, bad):
     mask = inputs.ball_mask(3, 2)
     S0 = np.zeros(mask.shape[0])
@@ -183,6 +187,8 @@ def test_argument_errors(fr, bad):
         kw["tol"] = 2.0
     elif bad == "sigma":
         kw["upsample"] = 1.0
+    elif bad == "grad_mode":
+        kw["grad_mode"] = 2
     with pytest.raises(fr.FrescoError) as e:
         fr.fresco_plan_query(1.0, mask, S0, W, n, fr.make_opts(**kw))
     assert e.value.status == fr.FRESCO_ERR_ARG

@@ -45,7 +45,7 @@ def test_full_size_workload(name):
     pts = torch.from_numpy(pts_np).cuda()
 
     with fresco.Plan(wl.box, mask, S0, W, N, precision="f32", tol=wl.tol,
-                     upsample=wl.upsample) as plan:
+                     upsample=wl.upsample, grad_mode=wl.grad_mode) as plan:
         loss32, grad32 = plan.loss_grad(pts)
         rho32, _ = plan.rho_S()
         torch.cuda.synchronize()
