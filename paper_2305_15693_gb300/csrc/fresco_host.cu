@@ -20,6 +20,7 @@ namespace {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
 constexpr size_t kSmemOptin = 227 * 1024;   // opt-in shared memory per block on sm_100 / sm_103
+constexpr double kTileHits = 2000.0;         // points per 2D tile (with halo) the default aims at
 
 // ---- fine grid and kernel parameters --------------------------------------------------------
 
@@ -163,6 +164,8 @@ struct Folded {
 
 struct Params {
     int dim, precision, width;
+    int64_t n_points;
+    int list_cap;     // spread list entries
     int grad_mode;    // fresco_opts.grad_mode
     double beta, sigma, tol;
     int kmax[3];
@@ -202,10 +205,23 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
     const size_t es = P.precision == FRESCO_F64 ? 8 : 4;
     const bool user_tiles = tile_req[0] > 0 || tile_req[1] > 0 || tile_req[2] > 0;
     size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
+    double cells_all = 1.0;
+    for (int a = 0; a < dim; ++a) cells_all *= (double)P.nf[a];
+    const double density = (double)P.n_points / cells_all;   // points per fine cell
     int target[3];
     auto reset_targets = [&]() {
         for (int a = 0; a < dim; ++a) {
-            int deft = dim == 2 ? 48 : (a < 2 ? 16 : 8);
+            // 2D: a square tile whose halo-extended area holds about kTileHits points on
+            // average (fewer points straddle tile borders than with small tiles; more than that
+            // and the tile's shared memory limits residency), but enough tiles for about twelve
+            // blocks per SM (one and a half waves of the interpolation kernel) where the grid
+            // allows it; 3D: 16 x 16 x 8
+            int deft = a < 2 ? 16 : 8;
+            if (dim == 2) {
+                deft = (int)std::lround(std::sqrt(kTileHits / std::max(density, 1e-9))) - w;
+                deft = std::min(deft, (int)std::sqrt(cells_all / (12.0 * 152.0)));
+                deft = std::min(96, std::max(32, deft));
+            }
             target[a] = tile_req[a] > 0 ? tile_req[a] : deft;
         }
     };
@@ -217,9 +233,17 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
             P.nb[a] = choose_tiles(P.nf[a], target[a], w);
             P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
         }
+        // spread list: the expected points reaching a tile plus five standard deviations
+        // (Poisson), at least 1024; a tile beyond it takes the slower float-atomic path
+        double hits = density;
+        for (int a = 0; a < dim; ++a) hits *= (double)(P.tmax[a] + w);
+        P.list_cap = (int)std::min<double>(
+            16384.0,
+            std::max(1024.0, std::ceil((hits + 5.0 * std::sqrt(hits) + 64.0) / 256.0) * 256.0));
         Geom tg{};
         tg.dim = dim;
         tg.width = w;
+        tg.list_cap = P.list_cap;
         for (int a = 0; a < 3; ++a) tg.tmax[a] = a < dim ? P.tmax[a] : 1;
         const size_t interp = es == 8 ? Launch<double>::interp_smem(tg)
                                       : Launch<float>::interp_smem(tg);
@@ -285,6 +309,7 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
         if (!std::isfinite(S0[q]) || !std::isfinite(W[q]) || W[q] < 0.0) return FRESCO_ERR_ARG;
     }
     P.dim = dim;
+    P.n_points = n_points;
     P.precision = o.precision;
     P.grad_mode = o.grad_mode;
     P.width = w;
@@ -579,6 +604,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     es_poly<float>(P.width, P.beta, p->poly32);
     es_poly<double>(P.width, P.beta, p->poly64);
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
+    g.list_cap = P.list_cap;
     g.sub = dim == 3 ? 27 : 9;
     for (int a = 0; a < 3; ++a) g.strips[a] = a < dim && P.nf[a] / P.nb[a] >= P.width ? 1 : 0;
     g.n_bins = g.n_tiles * g.sub;
@@ -1176,7 +1202,9 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
     b->n_spec = ao;
     b->n_specT = ato;
     b->n_hc = hco;
-    // ---- per-instance geometry
+    // ---- per-instance geometry (one spread list size for all: the largest any instance needs)
+    int cap_max = 1024;
+    for (int i = 0; i < n; ++i) cap_max = std::max(cap_max, P[i].list_cap);
     std::vector<double> ip_h((size_t)std::max<int64_t>(ipo, 1));
     for (int i = 0; i < n; ++i) {
         BInst &I = b->inst[i];
@@ -1201,6 +1229,7 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
             I.m.kscale[a] = a < dim ? 2.0 * kPi / L : 0.0;
         }
         g.n_tiles = (int64_t)p.nb[0] * p.nb[1] * p.nb[2];
+        g.list_cap = cap_max;
         g.sub = dim == 3 ? 27 : 9;
         for (int a = 0; a < 3; ++a) g.strips[a] = a < dim && p.nf[a] / p.nb[a] >= p.width ? 1 : 0;
         g.n_bins = g.n_tiles * g.sub;
@@ -1286,6 +1315,7 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
     t.n_inst = n;
     t.dim = dim;
     t.width = P[0].width;
+    t.list_cap = cap_max;
     t.n_points = b->n_points;
     t.n_tiles = b->tile_first[n];
     t.n_mblk = b->mblk_first[n];
@@ -1297,6 +1327,7 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         Geom tg{};
         tg.dim = dim;
         tg.width = t.width;
+        tg.list_cap = cap_max;
         for (int a = 0; a < 3; ++a) tg.tmax[a] = tmax[a];
         if (Launch<T>::spread_smem(tg) > optin || Launch<T>::interp_smem(tg) > optin)
             return FRESCO_ERR_UNSUPPORTED;

@@ -27,6 +27,7 @@ struct Geom {
     int tq[3], tr[3];   // nf / nb and nf % nb per axis
     float tinv[3];      // nb / nf (estimate of the tile of a cell, corrected exactly)
     int64_t n_tiles;
+    int list_cap;       // entries of the spread kernel's compacted point list (shared memory)
     int sub;            // sub-bins per tile, 3^dim: per axis the low border strip (cells that can
                         // reach the previous tile), the interior, the high border strip
     int strips[3];      // 1 if every tile on the axis is at least w cells wide (strips disjoint)
@@ -101,6 +102,7 @@ struct BTables {
     int n_inst;
     int dim;
     int width;
+    int list_cap;                // spread list entries (the same for every instance)
     int64_t n_points, n_tiles, n_mblk;
     int tmax[3];                 // widest tile over all instances (shared-memory sizing)
 };

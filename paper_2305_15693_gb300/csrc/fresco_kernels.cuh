@@ -551,9 +551,8 @@ __device__ __forceinline__ void spread_point(const EsPoly<T> &ep, int i0x, int i
     }
 }
 
-// compacted points per tile held in (dynamic) shared memory after the tile itself
-template <typename T> struct SpreadList { static constexpr int value = 2048; };
-template <> struct SpreadList<double> { static constexpr int value = 1024; };
+// The compacted points of a tile are held in (dynamic) shared memory after the tile itself;
+// the list has g.list_cap entries, sized at plan time from the expected points per tile.
 
 __host__ __device__ inline size_t spread_tile_bytes(const Geom &g, size_t esize) {
     size_t cells = (size_t)g.tmax[0] * g.tmax[1] * (g.dim == 3 ? g.tmax[2] : 1);
@@ -574,7 +573,7 @@ __device__ __forceinline__ void spread_tile(const Geom &g, const EsPoly<T> &ep,
     __shared__ int nb_org[NNB][3], nb_tile[NNB];
     __shared__ int r_p0[MAXR], r_start[MAXR + 1], r_q[MAXR];
     __shared__ int s_nr, s_hits, s_edge;
-    constexpr int kSpreadList = SpreadList<T>::value;
+    const int kSpreadList = g.list_cap;
     T *ftile = reinterpret_cast<T *>(sm_raw);
     int *itile = reinterpret_cast<int *>(sm_raw);
     // compacted list: support starts (packed 3 x 10 bits) and kernel offsets per axis
@@ -1368,7 +1367,7 @@ template <typename T>
 int Launch<T>::spread_smem(const Geom &g) {
     const int D = g.dim;
     return (int)(spread_tile_bytes(g, sizeof(T)) +
-                 (sizeof(T) * D + sizeof(int)) * (size_t)SpreadList<T>::value);
+                 (sizeof(T) * D + sizeof(int)) * (size_t)g.list_cap);
 }
 
 template <typename T>
@@ -1559,6 +1558,7 @@ inline Geom tiles_geom(const BTables &b) {
     Geom g{};
     g.dim = b.dim;
     g.width = b.width;
+    g.list_cap = b.list_cap;
     for (int a = 0; a < 3; ++a) g.tmax[a] = b.tmax[a];
     return g;
 }
