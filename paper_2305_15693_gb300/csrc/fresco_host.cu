@@ -245,10 +245,11 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
         tg.width = w;
         tg.list_cap = P.list_cap;
         for (int a = 0; a < 3; ++a) tg.tmax[a] = a < dim ? P.tmax[a] : 1;
-        // the larger of the two interpolation forms (direct, kernel derivative)
+        // the interpolation form this plan uses (direct or kernel derivative)
+        const bool kd = P.grad_mode == FRESCO_GRAD_KDERIV;
         const size_t interp =
-            es == 8 ? std::max(Launch<double>::interp_smem(tg), Launch<double>::interp_kd_smem(tg))
-                    : std::max(Launch<float>::interp_smem(tg), Launch<float>::interp_kd_smem(tg));
+            es == 8 ? (kd ? Launch<double>::interp_kd_smem(tg) : Launch<double>::interp_smem(tg))
+                    : (kd ? Launch<float>::interp_kd_smem(tg) : Launch<float>::interp_smem(tg));
         const size_t spread = es == 8 ? Launch<double>::spread_smem(tg)
                                       : Launch<float>::spread_smem(tg);
         if (interp <= budget && spread <= budget) break;
@@ -637,8 +638,9 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     FR_CUDA(cudaGetDevice(&dev));
     int smem_optin = 0;
     FR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (Launch<T>::spread_smem(g) > smem_optin || Launch<T>::interp_smem(g) > smem_optin ||
-        Launch<T>::interp_kd_smem(g) > smem_optin)
+    const int interp_bytes =
+        m.kderiv ? Launch<T>::interp_kd_smem(g) : Launch<T>::interp_smem(g);
+    if (Launch<T>::spread_smem(g) > smem_optin || interp_bytes > smem_optin)
         return FRESCO_ERR_UNSUPPORTED;
 
     const int64_t N = p->n_points;
