@@ -36,7 +36,7 @@
 
 namespace {
 
-constexpr int kChunk = 2048;     // elements of the packed vector per chunk (one block each)
+constexpr int kChunk = 8192;     // elements of the packed vector per chunk (one block each)
 constexpr int kThreads = 256;
 
 enum Act { ACT_BACKTRACK = 0, ACT_ACCEPT = 1, ACT_IDLE = 2, ACT_INIT = 3 };
