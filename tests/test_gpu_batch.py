@@ -211,3 +211,27 @@ def test_batch_lbfgs_lowers_every_instance_and_reports_true_losses():
         assert r["evaluations"] <= 150
         assert r["loss"] == l1[i], i            # the reported loss is the loss at the points
         assert l1[i] < 0.1 * l0[i], (i, l0[i], l1[i])
+
+
+def test_autotuner_times_every_candidate_and_keeps_the_fastest():
+    import torch
+    from paper_2305_15693_gb300 import fresco, tune
+    ens = inputs.ensemble(16, 300, 5000, 0.1, 0.5, 4, "f32")
+    masks, S0s, Ws = _problem(ens)
+    pts = torch.from_numpy(ens.points()).cuda()
+    best, table = tune.autotune_batch(ens.boxes, ens.n_points, masks, S0s, Ws, pts,
+                                      upsamples=(1.5, 2.0), tiles=(32, 64), reps=3, warmup=1)
+    assert len(table) == 4
+    timed = [r for r in table if r["ms"] is not None]
+    assert timed and all(r["ms"] > 0 for r in timed)
+    assert best["ms"] == min(r["ms"] for r in timed)
+    assert {r["width"] for r in timed if r["upsample"] == 1.5} == {8}   # eps 1e-6 at sigma 1.5
+    # the chosen configuration is an ordinary batch plan with the same results as the default
+    with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, upsample=best["upsample"],
+                      tile=best["tile"]) as b, \
+            fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws) as ref:
+        l1, g1 = b.loss_grad(pts)
+        l2, g2 = ref.loss_grad(pts)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(l1.cpu().numpy(), l2.cpu().numpy(), rtol=TOL["f32"]["loss"])
+        assert rel_l2(g1.double().cpu().numpy(), g2.double().cpu().numpy()) <= TOL["f32"]["grad"]
