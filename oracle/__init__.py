@@ -52,6 +52,9 @@ def _load():
                                                     ctypes.c_double, ctypes.c_double, p, i64, p,
                                                     p]
             lib.oracle_pair_energy_grad.restype = ctypes.c_int
+            lib.oracle_weight_loss_grad.argtypes = [ctypes.c_int, i64, p, p, p, i64, p, p, p,
+                                                    p, p, p, p, p]
+            lib.oracle_weight_loss_grad.restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
@@ -121,6 +124,41 @@ def loss_grad(points, mask, S0, W, box=1.0, sel=None, want_grad=True):
     if rc != 0:
         raise ValueError("oracle_loss_grad failed (%d)" % rc)
     return float(loss[0]), grad, S, re + 1j * im
+
+
+def weight_loss_grad(points, weights, mask, S0, W, box=1.0, want_grad=True):
+    """Weighted points (real weights c_j at positions r_j): rho = sum_j c_j e^{-ik.r_j},
+    S = |rho|^2 / sum_j c_j^2. Returns (loss, dL/dc [N] or None, S, rho)."""
+    r, dim, b, m = _prep(points, box, mask)
+    c = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    if c.size != r.shape[0]:
+        raise ValueError("one weight per point")
+    s0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    w = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    n_k = m.shape[0]
+    loss = np.zeros(1)
+    S = np.empty(n_k)
+    re = np.empty(n_k)
+    im = np.empty(n_k)
+    grad = np.empty(r.shape[0]) if want_grad else None
+    rc = _load().oracle_weight_loss_grad(dim, r.shape[0], _ptr(r), _ptr(b), _ptr(c), n_k, _ptr(m),
+                                         _ptr(s0), _ptr(w), _ptr(loss), _ptr(S), _ptr(re),
+                                         _ptr(im), _ptr(grad))
+    if rc != 0:
+        raise ValueError("oracle_weight_loss_grad failed (%d)" % rc)
+    return float(loss[0]), grad, S, re + 1j * im
+
+
+def grid_points(shape, box=1.0):
+    """Positions of the cells of a uniform grid, row-major with the first axis fastest:
+    cell (i_0, ..., i_{d-1}) at (i_a L_a / M_a)_a, flattened index i_0 + M_0 (i_1 + M_1 i_2)."""
+    shape = tuple(int(x) for x in shape)
+    dim = len(shape)
+    b = np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,))
+    axes = [np.arange(m, dtype=np.float64) * (b[a] / m) for a, m in enumerate(shape)]
+    mesh = np.meshgrid(*axes, indexing="ij")          # mesh[a][i_0, ..., i_{d-1}]
+    pts = np.stack([g.transpose(tuple(range(dim))[::-1]).reshape(-1) for g in mesh], axis=1)
+    return np.ascontiguousarray(pts)
 
 
 def pair_energy_grad(points, sigma, eps=1.0, alpha=2.0, box=1.0, sel=None, want_grad=True,

@@ -172,6 +172,63 @@ int oracle_pair_energy_grad(int dim, int64_t n_points, const double *r, const do
 }
 
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
+/* Weighted points (the "UwU" / "UwNU" weight-gradient forms of Methods "Analytical
+ * gradients"): real weights c_j at fixed positions r_j,
+ *   rho(k)   = sum_j c_j exp(-i k . r_j),   rho0 = sum_j c_j^2,   S(k) = |rho(k)|^2 / rho0,
+ *   L_S      = sum_{k in mask} W(k) (S(k) - S0(k))^2,
+ *   dL/dc_j  = sum_k 2 W (S - S0) dS/dc_j,
+ *   dS/dc_j  = (d rho/dc_j conj(rho) + rho conj(d rho/dc_j)) / rho0 - |rho|^2 (2 c_j) / rho0^2
+ *            = 2 Re[rho e^{+i k . r_j}] / rho0 - 2 c_j S / rho0
+ * (the chain rule written out per (point, wavevector) pair, not the paper's regrouped form).
+ *   c: [n_points]; grad: out [n_points] or NULL; other arguments as oracle_loss_grad. */
+int oracle_weight_loss_grad(int dim, int64_t n_points, const double *r, const double *box,
+                            const double *c, int64_t n_k, const int32_t *mask, const double *S0,
+                            const double *W, double *loss, double *S_out, double *rho_re_out,
+                            double *rho_im_out, double *grad)
+{
+    if (dim < 1 || dim > 3 || n_points <= 0 || n_k < 0) return 1;
+    double *re = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *im = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *S = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    if (!re || !im || !S) { free(re); free(im); free(S); return 2; }
+    double rho0 = 0.0;
+    for (int64_t j = 0; j < n_points; ++j) rho0 += c[j] * c[j];
+    if (!(rho0 > 0.0)) { free(re); free(im); free(S); return 3; }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_k; ++q) {
+        double complex acc = 0.0;
+        for (int64_t j = 0; j < n_points; ++j)
+            acc += c[j] * cexp(-I * k_dot_r(dim, mask + q * dim, r + j * dim, box));
+        re[q] = creal(acc);
+        im[q] = cimag(acc);
+    }
+    double total = 0.0;
+    for (int64_t q = 0; q < n_k; ++q) {
+        S[q] = (re[q] * re[q] + im[q] * im[q]) / rho0;
+        double d = S[q] - S0[q];
+        total += W[q] * d * d;
+    }
+    *loss = total;
+    if (grad) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t j = 0; j < n_points; ++j) {
+            double g = 0.0;
+            for (int64_t q = 0; q < n_k; ++q) {
+                double complex rho = re[q] + I * im[q];
+                double complex e = cexp(I * k_dot_r(dim, mask + q * dim, r + j * dim, box));
+                double dS = 2.0 * creal(rho * e) / rho0 - 2.0 * c[j] * S[q] / rho0;
+                g += 2.0 * W[q] * (S[q] - S0[q]) * dS;
+            }
+            grad[j] = g;
+        }
+    }
+    if (S_out) for (int64_t q = 0; q < n_k; ++q) S_out[q] = S[q];
+    if (rho_re_out) for (int64_t q = 0; q < n_k; ++q) rho_re_out[q] = re[q];
+    if (rho_im_out) for (int64_t q = 0; q < n_k; ++q) rho_im_out[q] = im[q];
+    free(re); free(im); free(S);
+    return 0;
+}
+
 int oracle_threads(void)
 {
 #ifdef _OPENMP

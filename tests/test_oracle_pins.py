@@ -214,3 +214,66 @@ def test_pair_gradient_central_differences_and_invariance(dim):
     assert np.linalg.norm(grad.sum(axis=0)) < 1e-10 * np.linalg.norm(grad)
     e2, _ = oracle.pair_energy_grad(pts + 0.37, sigma, 1.3, 2.5, box=box, want_grad=False)
     assert e2 == pytest.approx(e, rel=1e-12)
+
+
+# ---- weighted points: the weight gradient (Methods, "Analytical gradients", UwU / UwNU) -----
+
+def _grid_problem(shape, K, seed):
+    g = inputs.rng(seed)
+    dim = len(shape)
+    c = g.standard_normal(int(np.prod(shape)))
+    mask = inputs.ball_mask(K, dim)
+    S0 = g.random(mask.shape[0])
+    W = 0.5 + g.random(mask.shape[0])
+    return oracle.grid_points(shape), c, mask, S0, W
+
+
+@pytest.mark.parametrize("shape", [(12, 10), (6, 5, 4)])
+def test_weighted_grid_rho_equals_numpy_fft(shape):
+    pts, c, mask, S0, W = _grid_problem(shape, 2, 81)
+    _, _, S, rho = oracle.weight_loss_grad(pts, c, mask, S0, W)
+    F = np.fft.fftn(c.reshape(shape[::-1]))           # numpy axis 0 is the last coordinate
+    want = np.array([F[tuple((n[::-1]) % np.array(shape[::-1]))] for n in mask])
+    np.testing.assert_allclose(rho, want, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(S, np.abs(want) ** 2 / np.sum(c * c), rtol=1e-12)
+
+
+def test_weight_gradient_matches_central_differences():
+    pts, c, mask, S0, W = _grid_problem((8, 7), 3, 82)
+    _, grad, _, _ = oracle.weight_loss_grad(pts, c, mask, S0, W)
+    h = 1e-6
+    fd = np.zeros_like(c)
+    for j in range(c.size):
+        cp, cm = c.copy(), c.copy()
+        cp[j] += h
+        cm[j] -= h
+        lp, _, _, _ = oracle.weight_loss_grad(pts, cp, mask, S0, W, want_grad=False)
+        lm, _, _, _ = oracle.weight_loss_grad(pts, cm, mask, S0, W, want_grad=False)
+        fd[j] = (lp - lm) / (2 * h)
+    assert np.linalg.norm(fd - grad) / np.linalg.norm(grad) < 1e-7
+
+
+def test_weight_gradient_scale_invariance_and_single_weight():
+    pts, c, mask, S0, W = _grid_problem((9, 8), 3, 83)
+    loss, grad, _, _ = oracle.weight_loss_grad(pts, c, mask, S0, W)
+    # S, hence L, is invariant under c -> alpha c, so sum_j c_j dL/dc_j = 0 (Euler)
+    assert abs(np.dot(c, grad)) < 1e-11 * np.linalg.norm(c) * np.linalg.norm(grad)
+    loss2, _, _, _ = oracle.weight_loss_grad(pts, -3.7 * c, mask, S0, W, want_grad=False)
+    assert loss2 == pytest.approx(loss, rel=1e-12)
+    # a single nonzero weight: S = 1 everywhere and no force on that weight
+    one = np.zeros_like(c)
+    one[17] = 2.5
+    _, g1, S1, _ = oracle.weight_loss_grad(pts, one, mask, S0, W)
+    np.testing.assert_allclose(S1, 1.0, rtol=1e-13)
+    assert abs(g1[17]) < 1e-12
+
+
+def test_unit_weights_reproduce_the_point_oracle():
+    pts = inputs.uniform_points(300, 2, 84)
+    mask = inputs.ball_mask(5, 2)
+    g = inputs.rng(84)
+    S0, W = g.random(mask.shape[0]), 0.5 + g.random(mask.shape[0])
+    l1, _, S1, r1 = oracle.weight_loss_grad(pts, np.ones(300), mask, S0, W, want_grad=False)
+    l2, _, S2, r2 = oracle.loss_grad(pts, mask, S0, W, want_grad=False)
+    assert l1 == pytest.approx(l2, rel=1e-13)
+    np.testing.assert_allclose(S1, S2, rtol=1e-12)
