@@ -352,6 +352,26 @@ fresco_status fresco_batch_lbfgs_read(fresco_batch_lbfgs_t s, void *d_points,
                                       fresco_lbfgs_report *reports, int64_t *n_running);
 fresco_status fresco_batch_lbfgs_destroy(fresco_batch_lbfgs_t s);
 
+/* ---- Weights on a uniform grid (UwU, Methods "Analytical gradients") --------------------------
+ * The weight-gradient form of the method: real weights c_m sit at the cells r_m = m L / M of a
+ * periodic grid of M_0 x M_1 (x M_2) cells and the constraints are on integer wavevectors n,
+ *   rho(n) = sum_m c_m e^{-2 pi i n.m / M},  rho0 = sum_m c_m^2,  S = |rho|^2 / rho0,
+ *   L = sum_mask W (S - S0)^2,
+ *   dL/dc_m = Re sum_mask [4 W (S - S0) rho / rho0] e^{+2 pi i n.m / M}
+ *             - (4 c_m / rho0) sum_mask W S (S - S0)
+ * (the weight gradient of Methods, in this library's e^{-ik.r} convention). Both FFTs are exact
+ * transforms of the grid: no NUFFT kernel, so results are exact up to rounding. The box size does
+ * not enter. grid: host [dim] cell counts, even, >= 4; mask entries need |n_a| < M_a / 2 and n != 0
+ * (FRESCO_ERR_ARG otherwise); mask, S0, W as for fresco_plan (folded the same way). */
+typedef struct fresco_uwu_s *fresco_uwu_t;
+fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, const int32_t *mask,
+                              int64_t n_k, const double *S0, const double *W, int precision,
+                              void *stream);
+/* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
+ * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. */
+fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad);
+fresco_status fresco_uwu_destroy(fresco_uwu_t u);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

@@ -1612,3 +1612,330 @@ fresco_status fresco_batch_destroy(fresco_batch_t b) {
 }
 
 }  // extern "C"
+
+// ============================================================================================
+// Weights on a uniform grid with uniform k constraints (UwU, Methods "Analytical gradients"):
+// real weights c_m at the cells r_m = m L / M of a periodic grid,
+//   rho(n) = sum_m c_m e^{-2 pi i n.m/M} (one forward FFT), rho0 = sum_m c_m^2,
+//   S = |rho|^2 / rho0, L = sum_mask W (S - S0)^2,
+//   dL/dc_m = Re sum_mask [4 W (S - S0) rho / rho0] e^{+2 pi i n.m/M}
+//             - (4 c_m / rho0) sum_mask W S (S - S0).
+// The first gradient term is one real inverse FFT of a Hermitian half spectrum (the layout of the
+// kernel-derivative mode), the second a scalar times c. No NUFFT is involved: the grid is the
+// field. The mask folds onto half-space representatives as for points (S(n) = S(-n) for real
+// weights); both sums above fold the same way because only their real parts enter.
+// ============================================================================================
+
+namespace {
+
+constexpr int kUwuBlocks = 1024;
+
+__device__ __forceinline__ double uwu_block_sum(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double b = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += ws[w];
+    return b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_uwu_sumsq(const T *__restrict__ c, int64_t n,
+                                                   double *__restrict__ part) {
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc = fma((double)c[i], (double)c[i], acc);
+    const double b = uwu_block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+// out[k] = sum of part[k * nb .. (k + 1) * nb) (+ add[k]) for k < n_out; fixed order
+__global__ void __launch_bounds__(256) k_uwu_sum(const double *__restrict__ part, int nb,
+                                                 int n_out, double add0, double *__restrict__ out) {
+    for (int k = 0; k < n_out; ++k) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[(int64_t)k * nb + i];
+        const double s = uwu_block_sum(v);
+        if (threadIdx.x == 0) out[k] = s + (k == 0 ? add0 : 0.0);
+        __syncthreads();
+    }
+}
+
+// One pass over the folded representatives (n_x-major): S, the loss and F partials, and the
+// Hermitian half spectrum (E/2) rho at n (and its conjugate at -n on the n_x = 0 column),
+// E = 4 W' (S - S0') / rho0.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_uwu_mask(
+    int64_t n_rep, const int *__restrict__ rep_n, const T *__restrict__ rep_s0,
+    const T *__restrict__ rep_w, const typename std::conditional<sizeof(T) == 4, float2, double2>::type *__restrict__ spec,
+    int nf1, int nf2, int64_t plane, const double *__restrict__ rho0p,
+    typename std::conditional<sizeof(T) == 4, float2, double2>::type *__restrict__ hs,
+    double *__restrict__ part) {
+    using C = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const double rho0 = *rho0p;
+    const T inv = (T)(1.0 / rho0);
+    double lsum = 0.0, fsum = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_rep;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int nx = rep_n[e * D + 0], ny = rep_n[e * D + 1], nz = D == 3 ? rep_n[e * D + 2] : 0;
+        const int ry = ny < 0 ? ny + nf1 : ny, rz = nz < 0 ? nz + nf2 : nz;
+        const int64_t row = (int64_t)rz * nf1 + ry;
+        const C F = spec[(int64_t)nx * plane + row];
+        const T S = (F.x * F.x + F.y * F.y) * inv;
+        const double d = (double)S - (double)rep_s0[e];
+        const double wgt = (double)rep_w[e];
+        lsum = fma(wgt * d, d, lsum);
+        fsum = fma(wgt * (double)S, d, fsum);
+        const T h = (T)(2.0 * wgt * d / rho0);   // E / 2
+        hs[(int64_t)nx * plane + row] = C{h * F.x, h * F.y};
+        if (nx == 0) {
+            const int my = ny > 0 ? nf1 - ny : -ny, mz = nz > 0 ? nf2 - nz : -nz;
+            hs[(int64_t)mz * nf1 + my] = C{h * F.x, -h * F.y};
+        }
+    }
+    const double bl = uwu_block_sum(lsum);
+    const double bf = uwu_block_sum(fsum);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = bl;
+        part[gridDim.x + blockIdx.x] = bf;
+    }
+}
+
+// grad_m = h_m - (4 c_m / rho0) * fsum
+template <typename T>
+__global__ void __launch_bounds__(256) k_uwu_grad(const T *__restrict__ h, const T *__restrict__ c,
+                                                  int64_t n, const double *__restrict__ scal,
+                                                  const double *__restrict__ fsum,
+                                                  T *__restrict__ grad) {
+    const T coef = (T)(4.0 * (*fsum) / scal[0]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        grad[i] = h[i] - coef * c[i];
+}
+
+}  // namespace
+
+struct fresco_uwu_s {
+    int dim = 0, precision = FRESCO_F32;
+    size_t esize = 4;
+    int M[3] = {1, 1, 1};
+    int kx = 0;
+    int64_t cells = 0, plane = 0, half = 0, n_rep = 0, n_mask_blocks = 0;
+    double loss_const = 0.0;
+    cudaStream_t stream = nullptr;
+    std::vector<void *> allocs;
+    int *rep_n = nullptr;
+    void *rep_s0 = nullptr, *rep_w = nullptr;
+    void *spec = nullptr, *specT = nullptr, *hs = nullptr, *bt = nullptr, *r = nullptr, *h = nullptr;
+    double *part = nullptr, *scal = nullptr;   // scal[0] = rho0, scal[1] = F sum
+    void *work = nullptr;
+    cufftHandle fft[4] = {0, 0, 0, 0};        // rows R2C, cols fwd, cols inv, rows C2R
+    bool have[4] = {false, false, false, false};
+};
+
+namespace {
+
+bool ualloc(fresco_uwu_s *u, void **p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    u->allocs.push_back(*p);
+    return true;
+}
+
+void uwu_free(fresco_uwu_s *u) {
+    if (!u) return;
+    if (u->stream) cudaStreamSynchronize(u->stream);
+    else cudaDeviceSynchronize();
+    for (int i = 0; i < 4; ++i)
+        if (u->have[i]) cufftDestroy(u->fft[i]);
+    for (void *p : u->allocs) cudaFree(p);
+    delete u;
+}
+
+template <typename T>
+fresco_status uwu_build(fresco_uwu_s *u, const Folded &F) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    const int dim = u->dim;
+    u->plane = (int64_t)u->M[1] * u->M[2];
+    u->half = u->M[0] / 2 + 1;
+    u->cells = u->plane * u->M[0];
+    u->n_rep = (int64_t)F.s0.size();
+    u->n_mask_blocks = std::max<int64_t>(1, std::min<int64_t>((u->n_rep + 255) / 256, kUwuBlocks));
+    const size_t specT_n = (size_t)(u->kx + 1) * (size_t)u->plane;
+    bool ok = ualloc(u, (void **)&u->rep_n, sizeof(int) * F.n.size()) &&
+              ualloc(u, &u->rep_s0, sizeof(T) * (size_t)u->n_rep) &&
+              ualloc(u, &u->rep_w, sizeof(T) * (size_t)u->n_rep) &&
+              ualloc(u, &u->spec, sizeof(C2) * (size_t)(u->plane * u->half)) &&
+              ualloc(u, &u->specT, sizeof(C2) * specT_n) && ualloc(u, &u->hs, sizeof(C2) * specT_n) &&
+              ualloc(u, &u->bt, sizeof(C2) * specT_n) &&
+              ualloc(u, &u->r, sizeof(C2) * (size_t)(u->plane * u->half)) &&
+              ualloc(u, &u->h, sizeof(T) * (size_t)u->cells) &&
+              ualloc(u, (void **)&u->part, sizeof(double) * (size_t)std::max<int64_t>(2 * u->n_mask_blocks, kUwuBlocks)) &&
+              ualloc(u, (void **)&u->scal, sizeof(double) * 4);
+    if (!ok) return FRESCO_ERR_OOM;
+    std::vector<T> s0(F.s0.size()), w(F.w.size());
+    for (size_t i = 0; i < s0.size(); ++i) {
+        s0[i] = (T)F.s0[i];
+        w[i] = (T)F.w[i];
+    }
+    FR_CUDA(cudaMemcpy(u->rep_n, F.n.data(), sizeof(int) * F.n.size(), cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(u->rep_s0, s0.data(), sizeof(T) * s0.size(), cudaMemcpyHostToDevice));
+    FR_CUDA(cudaMemcpy(u->rep_w, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
+    // entries outside the mask stay zero from here on
+    FR_CUDA(cudaMemset(u->hs, 0, sizeof(C2) * specT_n));
+    FR_CUDA(cudaMemset(u->r, 0, sizeof(C2) * (size_t)(u->plane * u->half)));
+    // cuFFT: rows R2C, (z,)y columns forward over n_x = 0..kx, the same inverse, rows C2R
+    long long n0 = u->M[0], half = u->half, rows = u->plane, cn[2];
+    const int crank = dim - 1;
+    if (dim == 2) cn[0] = u->M[1];
+    else { cn[0] = u->M[2]; cn[1] = u->M[1]; }
+    size_t ws[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) {
+        FR_CUFFT(cufftCreate(&u->fft[i]));
+        u->have[i] = true;
+        FR_CUFFT(cufftSetAutoAllocation(u->fft[i], 0));
+    }
+    FR_CUFFT(cufftMakePlanMany64(u->fft[0], 1, &n0, nullptr, 1, n0, nullptr, 1, half,
+                                 r2c_type<T>(), rows, &ws[0]));
+    FR_CUFFT(cufftMakePlanMany64(u->fft[1], crank, cn, nullptr, 1, rows, nullptr, 1, rows,
+                                 c2c_type<T>(), u->kx + 1, &ws[1]));
+    FR_CUFFT(cufftMakePlanMany64(u->fft[2], crank, cn, nullptr, 1, rows, nullptr, 1, rows,
+                                 c2c_type<T>(), u->kx + 1, &ws[2]));
+    FR_CUFFT(cufftMakePlanMany64(u->fft[3], 1, &n0, nullptr, 1, half, nullptr, 1, n0,
+                                 c2r_type<T>(), rows, &ws[3]));
+    const size_t wmax = std::max(std::max(ws[0], ws[1]), std::max(ws[2], ws[3]));
+    if (!ualloc(u, &u->work, wmax)) return FRESCO_ERR_OOM;
+    for (int i = 0; i < 4; ++i) {
+        FR_CUFFT(cufftSetWorkArea(u->fft[i], u->work));
+        FR_CUFFT(cufftSetStream(u->fft[i], u->stream));
+    }
+    FR_CUDA(cudaDeviceSynchronize());
+    return FRESCO_OK;
+}
+
+template <typename T>
+fresco_status uwu_eval(fresco_uwu_s *u, const T *c, double *loss, T *grad) {
+    using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    cudaStream_t s = u->stream;
+    // rho0 = sum c^2
+    k_uwu_sumsq<T><<<kUwuBlocks, 256, 0, s>>>(c, u->cells, u->part);
+    k_uwu_sum<<<1, 256, 0, s>>>(u->part, kUwuBlocks, 1, 0.0, u->scal);
+    // forward transform, columns n_x = 0..kx transposed
+    if (sizeof(T) == 4)
+        FR_CUFFT(cufftExecR2C(u->fft[0], (cufftReal *)c, (cufftComplex *)u->spec));
+    else
+        FR_CUFFT(cufftExecD2Z(u->fft[0], (cufftDoubleReal *)c, (cufftDoubleComplex *)u->spec));
+    FR_CUDA(Launch<T>::cols_to_rows(u->spec, u->specT, u->plane, u->half, u->kx + 1, s));
+    if (sizeof(T) == 4)
+        FR_CUFFT(cufftExecC2C(u->fft[1], (cufftComplex *)u->specT, (cufftComplex *)u->specT,
+                              CUFFT_FORWARD));
+    else
+        FR_CUFFT(cufftExecZ2Z(u->fft[1], (cufftDoubleComplex *)u->specT,
+                              (cufftDoubleComplex *)u->specT, CUFFT_FORWARD));
+    // S, loss and F partials, Hermitian half spectrum of the gradient field
+    const unsigned nb = (unsigned)u->n_mask_blocks;
+    if (u->dim == 2)
+        k_uwu_mask<T, 2><<<nb, 256, 0, s>>>(u->n_rep, u->rep_n, (const T *)u->rep_s0,
+                                            (const T *)u->rep_w, (const C2 *)u->specT, u->M[1],
+                                            u->M[2], u->plane, u->scal, (C2 *)u->hs, u->part);
+    else
+        k_uwu_mask<T, 3><<<nb, 256, 0, s>>>(u->n_rep, u->rep_n, (const T *)u->rep_s0,
+                                            (const T *)u->rep_w, (const C2 *)u->specT, u->M[1],
+                                            u->M[2], u->plane, u->scal, (C2 *)u->hs, u->part);
+    k_uwu_sum<<<1, 256, 0, s>>>(u->part, (int)nb, 2, u->loss_const, u->scal + 2);
+    FR_CUDA(cudaMemcpyAsync(loss, u->scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (!grad) return cuda_status(cudaGetLastError());
+    if (sizeof(T) == 4)
+        FR_CUFFT(cufftExecC2C(u->fft[2], (cufftComplex *)u->hs, (cufftComplex *)u->bt,
+                              CUFFT_INVERSE));
+    else
+        FR_CUFFT(cufftExecZ2Z(u->fft[2], (cufftDoubleComplex *)u->hs, (cufftDoubleComplex *)u->bt,
+                              CUFFT_INVERSE));
+    FR_CUDA(Launch<T>::rows_to_half(u->bt, u->r, u->plane, u->half, u->kx, s));
+    if (sizeof(T) == 4)
+        FR_CUFFT(cufftExecC2R(u->fft[3], (cufftComplex *)u->r, (cufftReal *)u->h));
+    else
+        FR_CUFFT(cufftExecZ2D(u->fft[3], (cufftDoubleComplex *)u->r, (cufftDoubleReal *)u->h));
+    k_uwu_grad<T><<<(unsigned)std::min<int64_t>((u->cells + 255) / 256, 152 * 16), 256, 0, s>>>(
+        (const T *)u->h, c, u->cells, u->scal, u->scal + 3, grad);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, const int32_t *mask,
+                              int64_t n_k, const double *S0, const double *W, int precision,
+                              void *stream) {
+    if (!out) return FRESCO_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || !grid || !mask || !S0 || !W || n_k < 1) return FRESCO_ERR_ARG;
+    if (precision != FRESCO_F32 && precision != FRESCO_F64) return FRESCO_ERR_ARG;
+    Params P{};
+    P.dim = dim;
+    P.precision = precision;
+    for (int a = 0; a < 3; ++a) {
+        P.nf[a] = 1;
+        P.kmax[a] = 0;
+    }
+    for (int a = 0; a < dim; ++a) {
+        if (grid[a] < 4 || grid[a] > (1 << 26) || grid[a] % 2) return FRESCO_ERR_ARG;
+        P.nf[a] = (int)grid[a];
+    }
+    if ((double)P.nf[0] * P.nf[1] * P.nf[2] > 2147483647.0 * 8) return FRESCO_ERR_UNSUPPORTED;
+    for (int64_t q = 0; q < n_k; ++q) {
+        bool zero = true;
+        for (int a = 0; a < dim; ++a) {
+            const int32_t v = mask[q * dim + a];
+            if (v != 0) zero = false;
+            // each wavevector must be a distinct frequency of the grid: |n_a| < M_a / 2
+            if (2 * (int64_t)std::abs((int64_t)v) >= P.nf[a]) return FRESCO_ERR_ARG;
+            P.kmax[a] = std::max(P.kmax[a], std::abs(v));
+        }
+        if (zero) return FRESCO_ERR_ARG;
+        if (!std::isfinite(S0[q]) || !std::isfinite(W[q]) || W[q] < 0.0) return FRESCO_ERR_ARG;
+    }
+    Folded F;
+    fresco_status st = fold_mask(P, mask, n_k, S0, W, F);
+    if (st) return st;
+    if (F.s0.empty()) return FRESCO_ERR_ARG;
+    fresco_uwu_s *u = new (std::nothrow) fresco_uwu_s();
+    if (!u) return FRESCO_ERR_OOM;
+    u->dim = dim;
+    u->precision = precision;
+    u->esize = precision == FRESCO_F64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) u->M[a] = P.nf[a];
+    u->kx = P.kmax[0];
+    u->loss_const = F.loss_const;
+    u->stream = (cudaStream_t)stream;
+    st = precision == FRESCO_F64 ? uwu_build<double>(u, F) : uwu_build<float>(u, F);
+    if (st) {
+        uwu_free(u);
+        return st;
+    }
+    *out = u;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad) {
+    if (!u || !d_c || !d_loss) return FRESCO_ERR_ARG;
+    if (u->precision == FRESCO_F64)
+        return uwu_eval<double>(u, (const double *)d_c, d_loss, (double *)d_grad);
+    return uwu_eval<float>(u, (const float *)d_c, d_loss, (float *)d_grad);
+}
+
+fresco_status fresco_uwu_destroy(fresco_uwu_t u) {
+    uwu_free(u);
+    return FRESCO_OK;
+}
+
+}  // extern "C"

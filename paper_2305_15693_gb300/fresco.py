@@ -48,6 +48,7 @@ EXPORTS = (
     "fresco_batch_lbfgs_create", "fresco_batch_lbfgs_start", "fresco_batch_lbfgs_step",
     "fresco_batch_lbfgs_read", "fresco_batch_lbfgs_destroy", "fresco_batch_profile",
     "fresco_batch_profile_read", "fresco_batch_get_info",
+    "fresco_uwu_plan", "fresco_uwu_loss_grad", "fresco_uwu_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -157,6 +158,11 @@ def load(path: str = LIB_PATH):
             "fresco_batch_profile_read": (I, [P, P, P]),
             "fresco_batch_get_info": (I, [P, I, P]),
         }
+        sig.update({
+            "fresco_uwu_plan": (I, [P, I, P, P, I64, P, P, I, P]),
+            "fresco_uwu_loss_grad": (I, [P, P, P, P]),
+            "fresco_uwu_destroy": (I, [P]),
+        })
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
             f.restype = res
@@ -538,6 +544,74 @@ class BatchLBFGS:
     def close(self):
         if getattr(self, "handle", None):
             fresco_batch_lbfgs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fresco_uwu_plan(grid_shape, mask, S0, W, precision="f32", stream=None):
+    """Plan for real weights on a uniform grid (grid_shape = (M_0, M_1[, M_2]), x first)."""
+    lib = load()
+    mask = np.ascontiguousarray(np.asarray(mask, dtype=np.int32))
+    dim = mask.shape[1]
+    grid = np.ascontiguousarray(np.asarray(grid_shape, dtype=np.int64).reshape(-1))
+    if grid.size != dim:
+        raise ValueError("one grid size per axis")
+    S0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    h = ctypes.c_void_p()
+    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    _check(lib.fresco_uwu_plan(ctypes.byref(h), dim, grid.ctypes.data, mask.ctypes.data,
+                               mask.shape[0], S0.ctypes.data, W.ctypes.data, prec,
+                               _stream_handle(stream)), "fresco_uwu_plan")
+    return h.value
+
+
+def fresco_uwu_loss_grad(plan, c, loss, grad=None):
+    _check(load().fresco_uwu_loss_grad(plan, _addr(c), _addr(loss), _addr(grad)),
+           "fresco_uwu_loss_grad")
+
+
+def fresco_uwu_destroy(plan):
+    _check(load().fresco_uwu_destroy(plan), "fresco_uwu_destroy")
+
+
+class Uwu:
+    """Weights on a uniform grid (fresco_uwu_* in include/fresco.h). Weights and gradients are
+    CUDA tensors of shape grid_shape[::-1] (x the last, contiguous index) in the plan's dtype."""
+
+    def __init__(self, grid_shape, mask, S0, W, precision="f32", stream=None):
+        import torch
+        self._torch = torch
+        self.shape = tuple(int(x) for x in grid_shape)[::-1]
+        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = fresco_uwu_plan(grid_shape, mask, S0, W, precision, self.stream)
+
+    def loss_grad(self, c, want_grad=True):
+        t = self._torch
+        if (not c.is_cuda or c.dtype != self.dtype or not c.is_contiguous()
+                or tuple(c.shape) != self.shape):
+            raise ValueError("weights must be a contiguous CUDA %s tensor %s" % (self.dtype,
+                                                                                   self.shape))
+        loss = t.empty((), dtype=t.float64, device=c.device)
+        grad = t.empty_like(c) if want_grad else None
+        fresco_uwu_loss_grad(self.handle, c, loss, grad)
+        return loss, grad
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_uwu_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
