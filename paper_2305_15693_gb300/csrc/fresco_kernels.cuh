@@ -1075,8 +1075,12 @@ __device__ __forceinline__ void interp_tile(const Geom &g, const EsPoly<T> &ep,
     }
 }
 
+// At most 6 resident blocks per SM (the tile and its halo in shared memory allow no more at the
+// default tiles), so each thread may hold 40 registers: at the 32 that 8 blocks would impose the
+// window loop spills (measured: kernel-derivative interpolation 6.10 -> 5.47 ms in 3D and
+// 4.23 -> 4.13 ms in 2D at 1e8 points when the bound went from 8 to 6).
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp(Geom g, EsPoly<T> ep,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp(Geom g, EsPoly<T> ep,
                                                 const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ perm,
                                                 const int *__restrict__ off,
@@ -1216,7 +1220,7 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
 }
 
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_kd(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
     const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
     const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad) {
