@@ -215,8 +215,13 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
             // average (fewer points straddle tile borders than with small tiles; more than that
             // and the tile's shared memory limits residency), but enough tiles for about twelve
             // blocks per SM (one and a half waves of the interpolation kernel) where the grid
-            // allows it; 3D: 16 x 16 x 8
-            int deft = a < 2 ? 16 : 8;
+            // allows it. 3D: 24 x 24 x 12 (measured best of 18x18x8, 18^3, 24x24x12, 27x27x12, 24^3
+            // on the 2^24-point workload), scaled down likewise on small grids
+            int deft = a < 2 ? 24 : 12;
+            if (dim == 3) {
+                const double f = std::cbrt(cells_all / (12.0 * 152.0) / (24.0 * 24.0 * 12.0));
+                if (f < 1.0) deft = std::max(a < 2 ? 8 : 4, (int)(deft * f));
+            }
             if (dim == 2) {
                 deft = (int)std::lround(std::sqrt(kTileHits / std::max(density, 1e-9))) - w;
                 deft = std::min(deft, (int)std::sqrt(cells_all / (12.0 * 152.0)));
