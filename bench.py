@@ -202,7 +202,7 @@ def time_device(plan, pts, steps, warmup, dist_on, profile=True):
     st = plan.status()
     if st != 0:
         raise RuntimeError("device status after timing: %d" % st)
-    return ms, launches, stages, float(loss.item())
+    return ms, launches, stages, float(loss.item()), grad
 
 
 def time_e2e(plan, pts_np, steps, warmup):
@@ -237,17 +237,18 @@ def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2):
     t_probe = max(time.perf_counter() - t0, 1e-6)
     per_row = t_probe / 2
     n_s = int(max(2, min(256, budget_s / per_row)))
-    sample = mask[g.choice(n_k, n_s, replace=False)]
+    rows = np.sort(g.choice(n_k, n_s, replace=False))
+    sample = mask[rows]
     t0 = time.perf_counter()
-    oracle.rho(r64, sample, box)
+    rho = oracle.rho(r64, sample, box)
     t = time.perf_counter() - t0
     rate = N * n_s / t                                  # pair terms / s
     t_eval = 2.0 * N * n_k / rate
-    return {"value": N / t_eval, "unit": "points/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": "rho at %d of %d mask rows over all %d points (%.1f s); full evaluation "
-                      "extrapolated as 2*N*N_K pair terms at the measured %.3e terms/s"
-                      % (n_s, n_k, N, t, rate),
-            "seconds_per_eval_extrapolated": t_eval}
+    return ({"value": N / t_eval, "unit": "points/s", "cores": oracle.threads(), "kind": "oracle",
+             "sample": "rho at %d of %d mask rows over all %d points (%.1f s); full evaluation "
+                       "extrapolated as 2*N*N_K pair terms at the measured %.3e terms/s"
+                       % (n_s, n_k, N, t, rate),
+             "seconds_per_eval_extrapolated": t_eval}, rows, rho)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -613,10 +614,22 @@ def main():
         info["device_bytes"] / 1e9))
     clocks = ClockSampler(_device_selector(local_rank))
     clocks.start()
-    ms, launches, stages, loss_val = time_device(plan, pts, args.steps, args.warmup, dist_on)
+    ms, launches, stages, loss_val, grad32 = time_device(plan, pts, args.steps, args.warmup,
+                                                         dist_on)
     clk = clocks.stop()
     t_step = max_over_ranks(ms / args.steps / 1e3, dist_on, "cuda")
     value = replica_throughput(N, world, t_step)
+
+    # the oracle on the host cores (a bounded sample of mask rows), and the GPU's rho at the same
+    # rows for the accuracy report
+    cpu, rho_err = None, None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, rows, rho_oracle = cpu_baseline(pts_np, mask, wl.box)
+        rho_dev, _ = plan.rho_S()
+        got = rho_dev[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+        del rho_dev
+        got = got[:, 0] + 1j * got[:, 1]
+        rho_err = float(np.linalg.norm(got - rho_oracle) / np.linalg.norm(rho_oracle))
 
     # e2e through the host-buffer entry point
     dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
@@ -659,18 +672,26 @@ def main():
         pts64 = pts.double()
         plan64 = fresco.Plan(wl.box, mask, S0, W, N, precision="f64", tol=1e-12,
                              upsample=wl.upsample, grad_mode=wl.grad_mode)
-        ms64, _, st64, loss64 = time_device(plan64, pts64, args.f64_steps, 3, dist_on)
+        ms64, _, st64, loss64, grad64 = time_device(plan64, pts64, args.f64_steps, 3, dist_on)
         plan64.close()
         del pts64
+        grad_err = float(torch.linalg.vector_norm(grad32.double() - grad64) /
+                         torch.linalg.vector_norm(grad64))
+        del grad64
         t64 = ms64 / args.f64_steps / 1e3
         f64 = {"value": world * N / t64, "ms_per_step": 1e3 * t64, "width": None,
                "speedup_f32_over_f64": t64 / t_step,
                "loss_rel_diff_f32_vs_f64": abs(loss_val - loss64) / abs(loss64),
+               "grad_rel_l2_f32_vs_f64": grad_err,
                "stages_ms": {k: round(v[0] / max(v[1], 1), 3) for k, v in st64.items()}}
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pts_np, mask, wl.box)
+    accuracy = {
+        "fp32_vs_fp64_gpu": ({"loss_rel": f64["loss_rel_diff_f32_vs_f64"],
+                              "grad_rel_l2": f64["grad_rel_l2_f32_vs_f64"]} if f64 else None),
+        "rho_rel_l2_vs_oracle": rho_err,
+        "rho_rows_vs_oracle": (int(len(rows)) if rho_err is not None else 0),
+        "bars": {"rho": 1e-5, "loss": 1e-5, "grad": 1e-4},
+    }
 
     if rank == 0:
         line = {
@@ -690,6 +711,7 @@ def main():
             "roofline": roofline,
             "stages": per_stage,
             "fp64": f64,
+            "accuracy": accuracy,
             "cpu_baseline": cpu,
             "e2e": {"value": replica_throughput(N, world, dt_e2e), "unit": "points/s",
                     "h2d_bytes_per_step": h2d,
