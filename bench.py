@@ -348,10 +348,11 @@ def run_ensemble(args, ens, rank, world, local_rank, dist_on):
         best = {"upsample": args.upsample or ens.upsample, "tile": tuple(args.tile[:2])}
     else:
         best, table = tune.autotune_batch(ens.boxes, ens.n_points, masks, S0s, Ws, pts,
-                                          precision=ens.dtype, tol=ens.tol)
+                                          precision=ens.dtype, tol=ens.tol,
+                                          grad_mode=ens.grad_mode)
         log("autotune: %s" % json.dumps(table))
     b = fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision=ens.dtype, tol=ens.tol,
-                     upsample=best["upsample"], tile=best["tile"])
+                     upsample=best["upsample"], tile=best["tile"], grad_mode=ens.grad_mode)
     infos = [fresco.fresco_batch_get_info(b.handle, i) for i in range(n_inst)]
 
     # launches of one evaluation (eager), then per-stage device time
@@ -480,7 +481,8 @@ def run_ensemble(args, ens, rank, world, local_rank, dist_on):
             "config": {"workload": ens.name, "n_inst": n_inst, "total_points": n_tot,
                        "n_modes": int(sum(m.shape[0] for m in masks)), "tol": ens.tol,
                        "upsample": best["upsample"], "tile": list(best["tile"]),
-                       "width": infos[0]["width"], "autotune": table,
+                       "width": infos[0]["width"], "grad_mode": ens.grad_mode,
+                       "autotune": table,
                        "parallelism": "replicas" if world > 1 else "single",
                        "timing": "CUDA-graph replay per evaluation",
                        "l2": "inputs larger than L2 (points %.0f MB + grids, %d MB L2)"

@@ -78,7 +78,7 @@ typedef struct {
  *   single complex-to-real FFT), interpolated with the kernel's derivative psi' along each axis:
  *   the gradient of the type-2 interpolant. It needs one real FFT instead of d real FFTs' worth
  *   and reads one real grid, at an accuracy slightly below the direct mode's (the derivative
- *   amplifies the kernel's aliasing error). Batch plans use the direct mode only. */
+ *   amplifies the kernel's aliasing error). Batch plans support both modes. */
 #define FRESCO_GRAD_DIRECT 0
 #define FRESCO_GRAD_KDERIV 1
 

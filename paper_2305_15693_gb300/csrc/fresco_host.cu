@@ -1204,10 +1204,13 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
             go += cells;
             ao += plane * half;
             ato += plane * (K.kx + 1);
-            hco += plane * (2 * (int64_t)K.kx + 2);
-            ro += cells;
+            // kderiv: scalar half spectrum [kx+1][plane], half rows [plane][nf0/2+1]; direct:
+            // [2kx+2][plane] and full complex rows
+            hco += plane * (b->kderiv ? (int64_t)K.kx + 1 : 2 * (int64_t)K.kx + 2);
+            ro += b->kderiv ? plane * half : cells;
         }
     }
+    b->n_r = ro;
     b->cells = go;
     b->n_spec = ao;
     b->n_specT = ato;
@@ -1250,7 +1253,8 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         I.m.kx = K.kx;
         I.m.n_rep = (int64_t)F[i].s0.size();
         I.m.half_row = p.nf[0] / 2 + 1;
-        I.m.hc_row = 2 * (int64_t)K.kx + 2;
+        I.m.hc_row = b->kderiv ? (int64_t)K.kx + 1 : 2 * (int64_t)K.kx + 2;
+        I.m.kderiv = b->kderiv;
         I.m.plane = (int64_t)p.nf[1] * p.nf[2];
         I.m.inv_n = 1.0 / (double)n_points[i];
         for (int a = 0; a < dim; ++a) {
@@ -1280,7 +1284,8 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
               balloc(b, &b->spec, sizeof(C2) * b->n_spec) &&
               balloc(b, &b->specT, sizeof(C2) * b->n_specT) &&
               balloc(b, &b->hc, sizeof(C2) * b->n_hc) && balloc(b, &b->bt, sizeof(C2) * b->n_hc) &&
-              balloc(b, &b->r, sizeof(C2) * b->cells) && balloc(b, &b->g, sizeof(C2) * b->cells) &&
+              balloc(b, &b->r, sizeof(C2) * b->n_r) &&
+              (b->kderiv || balloc(b, &b->g, sizeof(C2) * b->cells)) &&
               balloc(b, (void **)&b->rep_n, sizeof(int) * b->n_rep * dim) &&
               balloc(b, &b->rep_s0, sizeof(T) * b->n_rep) &&
               balloc(b, &b->rep_w, sizeof(T) * b->n_rep) &&
@@ -1314,7 +1319,7 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         FR_CUDA(cudaMemcpy(b->d_mblk_first, b->mblk_first.data(), sizeof(int64_t) * (n + 1),
                            cudaMemcpyHostToDevice));
         FR_CUDA(cudaMemset(b->hc, 0, sizeof(C2) * b->n_hc));
-        FR_CUDA(cudaMemset(b->r, 0, sizeof(C2) * b->cells));
+        FR_CUDA(cudaMemset(b->r, 0, sizeof(C2) * b->n_r));
         FR_CUDA(cudaMemset(b->err, 0, sizeof(int)));
     }
     BTables &t = b->tab;
@@ -1339,7 +1344,9 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         tg.width = t.width;
         tg.list_cap = cap_max;
         for (int a = 0; a < 3; ++a) tg.tmax[a] = tmax[a];
-        if (Launch<T>::spread_smem(tg) > optin || Launch<T>::interp_smem(tg) > optin)
+        const int interp_bytes =
+            b->kderiv ? Launch<T>::interp_kd_smem(tg) : Launch<T>::interp_smem(tg);
+        if (Launch<T>::spread_smem(tg) > optin || interp_bytes > optin)
             return FRESCO_ERR_UNSUPPORTED;
     }
     // ---- cuFFT plans per class (all transforms of a class in one batch)
@@ -1359,10 +1366,15 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
                                      cnt * (K.kx + 1), &ws));
         wmax = std::max(wmax, ws);
         FR_CUFFT(cufftMakePlanMany64(K.h[2], 1, &n1, nullptr, 1, n1, nullptr, 1, n1, c2c_type<T>(),
-                                     cnt * (2 * (long long)K.kx + 2), &ws));
+                                     cnt * (b->kderiv ? (long long)K.kx + 1
+                                                      : 2 * (long long)K.kx + 2), &ws));
         wmax = std::max(wmax, ws);
-        FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, n0, nullptr, 1, n0, c2c_type<T>(),
-                                     cnt * n1, &ws));
+        if (b->kderiv)
+            FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, half, nullptr, 1, n0,
+                                         c2r_type<T>(), cnt * n1, &ws));
+        else
+            FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, n0, nullptr, 1, n0,
+                                         c2c_type<T>(), cnt * n1, &ws));
         wmax = std::max(wmax, ws);
     }
     if (!balloc(b, &b->work, wmax)) return FRESCO_ERR_OOM;
@@ -1435,6 +1447,34 @@ fresco_status batch_eval(fresco_batch_s *b, const T *pts, double *losses, T *gra
         b->launches += 1;
     }
     if (!grad) return FRESCO_OK;
+    if (b->kderiv) {
+        {
+            StageScope sc(b->prof, s, ST_FFT_INV);
+            for (auto &K : b->cls) {   // scalar spectrum -> real field (in the spread grid's place)
+                const int64_t plane = K.nf[1], half = K.nf[0] / 2 + 1;
+                C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0, *R = (C2 *)b->r + K.ro0;
+                T *Hr = (T *)b->grid + K.go0;
+                if (sizeof(T) == 4)
+                    FR_CUFFT(cufftExecC2C(K.h[2], (cufftComplex *)H, (cufftComplex *)BT,
+                                          CUFFT_INVERSE));
+                else
+                    FR_CUFFT(cufftExecZ2Z(K.h[2], (cufftDoubleComplex *)H,
+                                          (cufftDoubleComplex *)BT, CUFFT_INVERSE));
+                FR_CUDA(Launch<T>::rows_to_half(BT, R, plane, half, K.kx, s, K.count,
+                                                plane * ((int64_t)K.kx + 1), plane * half));
+                if (sizeof(T) == 4)
+                    FR_CUFFT(cufftExecC2R(K.h[3], (cufftComplex *)R, (cufftReal *)Hr));
+                else
+                    FR_CUFFT(cufftExecZ2D(K.h[3], (cufftDoubleComplex *)R, (cufftDoubleReal *)Hr));
+                b->launches += 1;
+            }
+        }
+        StageScope sc(b->prof, s, ST_INTERP);
+        FR_CUDA(Launch<T>::interp_kd_b(t, bpoly<T>(b), b->sorted, b->perm, b->off,
+                                       (const T *)b->grid, nullptr, grad, s));
+        b->launches += 1;
+        return FRESCO_OK;
+    }
     {
         StageScope sc(b->prof, s, ST_FFT_INV);
         for (auto &K : b->cls) {   // inverse FFT of each size class
@@ -1490,7 +1530,6 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     if (opts) o = *opts;
     for (int i = 0; i < n_inst; ++i) {
         if (n_modes[i] < 1) return FRESCO_ERR_ARG;
-        if (o.grad_mode != FRESCO_GRAD_DIRECT) return FRESCO_ERR_UNSUPPORTED;
         // one kernel serves every instance: the width rule at the requested oversampling
         fresco_status st = check_and_params(dim, boxes + (size_t)i * dim, n_points[i],
                                             masks + m0 * dim, n_modes[i], S0 + m0, W + m0, &o,
@@ -1507,6 +1546,7 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
     if (!b) return FRESCO_ERR_OOM;
     b->dim = dim;
     b->precision = o.precision;
+    b->kderiv = o.grad_mode == FRESCO_GRAD_KDERIV ? 1 : 0;
     b->esize = o.precision == FRESCO_F64 ? 8 : 4;
     b->n_inst = n_inst;
     b->stream = (cudaStream_t)stream;

@@ -175,7 +175,11 @@ struct Launch {
                                  cudaStream_t s);
     static int interp_kd_smem(const Geom &g);
     static cudaError_t rows_to_half(const void *bt, void *r, int64_t rows, int64_t half_row,
-                                    int kx, cudaStream_t s);
+                                    int kx, cudaStream_t s, int batch = 1, int64_t bt_stride = 0,
+                                    int64_t r_stride = 0);
+    static cudaError_t interp_kd_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                   const int *perm, const int *off, const T *h,
+                                   const double *grad_out, T *grad, cudaStream_t s);
     static cudaError_t cols_to_rows(const void *a, void *at, int64_t rows, int64_t lda,
                                     int ncols, cudaStream_t s, int batch = 1,
                                     int64_t a_stride = 0, int64_t at_stride = 0);
@@ -312,4 +316,6 @@ struct fresco_batch_s {
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     fresco::StageProfile prof;
+    int kderiv = 0;                  // gradient mode FRESCO_GRAD_KDERIV
+    int64_t n_r = 0;                 // complex elements of the row-order backward buffer
 };

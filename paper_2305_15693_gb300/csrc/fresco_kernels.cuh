@@ -1229,6 +1229,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd(
                             blockIdx.x);
 }
 
+// Batched kernel-derivative interpolation: a persistent grid walks the tiles of every instance;
+// instance i's real field sits at h + I.go and its scale is -2 n_f / L per axis.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd_b(
+    const BInst *__restrict__ inst, const int64_t *__restrict__ tile_first, int n_inst,
+    int64_t n_tiles, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
+    const double *__restrict__ grad_out, T *__restrict__ grad) {
+    const double sc = grad_out ? *grad_out : 1.0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int i = find_segment(tile_first, n_inst, t);
+        const BInst &I = inst[i];
+        const Geom &g = I.g;
+        interp_tile_kd<T, W, D>(g, ep, sorted, perm, off + I.bo, h + I.go,
+                                (T)(-2.0 * (g.s_hi[0] + g.s_lo[0]) * sc),
+                                (T)(-2.0 * (g.s_hi[1] + g.s_lo[1]) * sc),
+                                (T)(-2.0 * (g.s_hi[2] + g.s_lo[2]) * sc), grad,
+                                t - tile_first[i]);
+        __syncthreads();
+    }
+}
+
 // rho and S for the mask rows as given to the plan (diagnostic output).
 template <typename T, int D>
 __global__ void k_rho_s(MaskGeom m, const int *__restrict__ mask_n, int64_t n_k,
@@ -1308,8 +1330,11 @@ __global__ void __launch_bounds__(256) k_rows_to_cols(const C *__restrict__ bt, 
 // half spectrum [rows][half_row] (columns 0 .. kx; the others stay zero from plan time).
 template <typename C>
 __global__ void __launch_bounds__(256) k_rows_to_half(const C *__restrict__ bt, C *__restrict__ r,
-                                                      int64_t rows, int64_t half_row, int ncols) {
+                                                      int64_t rows, int64_t half_row, int ncols,
+                                                      int64_t bt_stride, int64_t r_stride) {
     __shared__ C tile[32][33];
+    bt += blockIdx.z * bt_stride;
+    r += blockIdx.z * r_stride;
     const int c0 = blockIdx.y * 32;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     for (int k = threadIdx.y; k < 32; k += 8) {
@@ -1383,10 +1408,12 @@ int Launch<T>::interp_kd_smem(const Geom &g) {
 
 template <typename T>
 cudaError_t Launch<T>::rows_to_half(const void *bt, void *r, int64_t rows, int64_t half_row,
-                                    int kx, cudaStream_t s) {
+                                    int kx, cudaStream_t s, int batch, int64_t bt_stride,
+                                    int64_t r_stride) {
     using C = typename PT<T>::C;
-    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((kx + 1 + 31) / 32));
-    k_rows_to_half<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, half_row, kx + 1);
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)((kx + 1 + 31) / 32), (unsigned)batch);
+    k_rows_to_half<C><<<grid, dim3(32, 8), 0, s>>>((const C *)bt, (C *)r, rows, half_row, kx + 1,
+                                                   bt_stride, r_stride);
     return cudaGetLastError();
 }
 
@@ -1624,6 +1651,34 @@ static cudaError_t launch_interp_bw(const BTables &b, const EsPoly<T> &ep, const
     kern<<<blocks, 256, smem, s>>>(b.inst, b.tile_first, b.n_inst, b.n_tiles, ep, (const U *)sorted,
                                    perm, off, (const C *)g0, (const C *)g1, grad_out, grad);
     return cudaGetLastError();
+}
+
+template <typename T, int W, int D>
+static cudaError_t launch_interp_kd_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                       const int *perm, const int *off, const T *h,
+                                       const double *grad_out, T *grad, cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int smem = Launch<T>::interp_kd_smem(tiles_geom(b));
+    auto kern = k_interp_kd_b<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<int64_t>(b.n_tiles, 152 * 6);
+    kern<<<blocks, 256, smem, s>>>(b.inst, b.tile_first, b.n_inst, b.n_tiles, ep, (const U *)sorted,
+                                   perm, off, h, grad_out, grad);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::interp_kd_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                   const int *perm, const int *off, const T *h,
+                                   const double *grad_out, T *grad, cudaStream_t s) {
+    if (b.dim == 2) {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_kd_bw<T, WW, 2>(b, ep, sorted, perm, off,
+                                                                           h, grad_out, grad, s)));
+    } else {
+        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_kd_bw<T, WW, 3>(b, ep, sorted, perm, off,
+                                                                           h, grad_out, grad, s)));
+    }
 }
 
 template <typename T>

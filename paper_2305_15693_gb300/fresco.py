@@ -634,10 +634,10 @@ class Batch:
     own (needed for graph capture), ordered after and before torch's current stream."""
 
     def __init__(self, boxes, n_points, masks, S0s, Ws, precision="f32", tol=0.0, upsample=2.0,
-                 width=0, tile=None, stream=None):
+                 width=0, tile=None, stream=None, grad_mode=FRESCO_GRAD_DIRECT):
         import torch
         self._torch = torch
-        self.opts = make_opts(precision, tol, upsample, width, tile)
+        self.opts = make_opts(precision, tol, upsample, width, tile, grad_mode)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.n_points = [int(n) for n in n_points]
         self.first = np.concatenate([[0], np.cumsum(self.n_points)]).astype(np.int64)

@@ -270,6 +270,7 @@ class Ensemble:
     seed: int = 7
     tol: float = 1e-6
     upsample: float = 2.0
+    grad_mode: str = "direct"
 
     @property
     def n_inst(self) -> int:
@@ -314,7 +315,9 @@ def ensemble_workload(name: str) -> Ensemble:
     """The named ensembles: 512 stealthy 2D configurations, N log-uniform in [1e3, 1e5] and chi
     uniform in [0.1, 0.5], seed 7, unit square boxes."""
     if name == "stealthy2d_ens512_n1e3to1e5_f32":
-        return ensemble(512, 1e3, 1e5, 0.1, 0.5, 7, "f32", tol=1e-6, name=name)
+        e = ensemble(512, 1e3, 1e5, 0.1, 0.5, 7, "f32", tol=1e-6, name=name)
+        e.grad_mode = "kderiv"
+        return e
     if name == "stealthy2d_ens512_n1e3to1e5_f64":
         return ensemble(512, 1e3, 1e5, 0.1, 0.5, 7, "f64", tol=1e-12, name=name)
     raise KeyError(name)

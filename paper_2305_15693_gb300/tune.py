@@ -43,7 +43,8 @@ def time_graph(batch, points, reps=10, warmup=3):
 
 
 def autotune_batch(boxes, n_points, masks, S0s, Ws, points, precision="f32", tol=0.0,
-                   upsamples=DEFAULT_UPSAMPLES, tiles=DEFAULT_TILES, reps=10, warmup=3):
+                   upsamples=DEFAULT_UPSAMPLES, tiles=DEFAULT_TILES, reps=10, warmup=3,
+                   grad_mode="direct"):
     """Time every (upsample, tile) candidate; returns (best, table). `best` holds the keyword
     arguments (upsample, tile) for fresco.Batch and its median time; `table` lists every
     candidate with its median ms (None where the plan is unsupported)."""
@@ -53,7 +54,7 @@ def autotune_batch(boxes, n_points, masks, S0s, Ws, points, precision="f32", tol
             row = {"upsample": float(sigma), "tile": int(t), "ms": None}
             try:
                 b = fresco.Batch(boxes, n_points, masks, S0s, Ws, precision=precision, tol=tol,
-                                 upsample=sigma, tile=(t, t))
+                                 upsample=sigma, tile=(t, t), grad_mode=grad_mode)
             except fresco.FrescoError as e:
                 row["error"] = fresco.status_string(e.status)
                 table.append(row)

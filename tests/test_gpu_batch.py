@@ -33,6 +33,7 @@ def _batch_eval(ens, masks, S0s, Ws, pts_np, **kw):
     from paper_2305_15693_gb300 import fresco
     dt = torch.float64 if ens.dtype == "f64" else torch.float32
     pts = torch.from_numpy(pts_np).to("cuda", dt)
+    kw.setdefault("grad_mode", ens.grad_mode)
     with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision=ens.dtype, tol=ens.tol,
                       upsample=ens.upsample, **kw) as b:
         losses, grad = b.loss_grad(pts)
@@ -50,12 +51,13 @@ def _mixed_ensemble(dtype):
     return ens
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_batch_matches_oracle_per_instance(dtype):
+@pytest.mark.parametrize("dtype,grad_mode", [("f64", "direct"), ("f32", "direct"),
+                                             ("f64", "kderiv"), ("f32", "kderiv")])
+def test_batch_matches_oracle_per_instance(dtype, grad_mode):
     ens = _mixed_ensemble(dtype)
     masks, S0s, Ws = _problem(ens)
     pts = ens.points()
-    losses, grad, first, info = _batch_eval(ens, masks, S0s, Ws, pts)
+    losses, grad, first, info = _batch_eval(ens, masks, S0s, Ws, pts, grad_mode=grad_mode)
     assert info["total_points"] == sum(ens.n_points)
     tol = TOL[dtype]
     for i in range(ens.n_inst):
@@ -86,14 +88,16 @@ def test_batch_matches_single_plans():
             assert rel_l2(grad[first[i]:first[i + 1]], g1.cpu().numpy()) <= 1e-9
 
 
-def test_graph_replay_equals_eager_and_follows_the_points():
+@pytest.mark.parametrize("grad_mode", ["direct", "kderiv"])
+def test_graph_replay_equals_eager_and_follows_the_points(grad_mode):
     import torch
     from paper_2305_15693_gb300 import fresco
     ens = inputs.ensemble(24, 300, 30000, 0.1, 0.5, 3, "f32")
     masks, S0s, Ws = _problem(ens)
     pts_np = ens.points()
     pts = torch.from_numpy(pts_np).cuda()
-    with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision="f32") as b:
+    with fresco.Batch(ens.boxes, ens.n_points, masks, S0s, Ws, precision="f32",
+                      grad_mode=grad_mode) as b:
         l_e, g_e = b.loss_grad(pts)
         l_e, g_e = l_e.clone(), g_e.clone()
         losses = torch.empty(ens.n_inst, dtype=torch.float64, device="cuda")
