@@ -52,7 +52,7 @@ typedef enum {
     FRESCO_ERR_NONFINITE = 5,    /* a coordinate was NaN or infinite (device-detected) */
     FRESCO_ERR_BOUNDS = 6,       /* an index check failed (device-detected) */
     FRESCO_ERR_TIMEOUT = 7,      /* a bounded device wait gave up */
-    FRESCO_ERR_UNSUPPORTED = 8   /* valid request this build does not handle */
+    FRESCO_ERR_UNSUPPORTED = 8   /* a valid request outside what the library implements */
 } fresco_status;
 
 enum { FRESCO_F32 = 0, FRESCO_F64 = 1 };
