@@ -124,3 +124,32 @@ def test_lbfgs_drives_1e6_points_below_1e_minus_10_N():
         print("1e6 L-BFGS:", rep)
         assert rep["status"] == 2, rep
         assert rep["loss"] < target
+
+
+def test_graph_solver_follows_the_host_driven_solver_exactly():
+    """The same L-BFGS iteration run two ways on one 2D problem: fresco_lbfgs (host decides the
+    line search from device scalars) and the per-instance device state machine of a one-instance
+    batch replayed as a CUDA graph. Evaluations are deterministic, so both take the same steps."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    N = 20000
+    pts0 = inputs.uniform_points(N, 2, 33, np.float32)
+    K = 95            # fine grid 384 = 3 * 2^7: already a batch size class, so both use one grid
+    mask = inputs.ball_mask(K, 2)
+    S0, W = inputs.stealthy_target(mask), inputs.unit_weights(mask)
+    pts = torch.from_numpy(pts0).cuda()
+    with fresco.Plan(1.0, mask, S0, W, N, grad_mode="kderiv") as plan:
+        assert plan.info["n_fine"][:2] == [384, 384]
+        opt = fresco.LBFGS(plan)
+        rep = opt.run(pts, 60)
+        opt.close()
+    x_host = pts.cpu().numpy()
+    pts = torch.from_numpy(pts0).cuda()
+    with fresco.Batch([1.0], [N], [mask], [S0], [W], grad_mode="kderiv") as b, \
+            fresco.BatchLBFGS(b, max_iter=60) as opt:
+        reps = opt.run(pts, 2000, check_every=50)
+    x_graph = pts.cpu().numpy()
+    assert reps[0]["iterations"] == rep["iterations"] == 60
+    assert reps[0]["evaluations"] == rep["evaluations"]
+    assert reps[0]["loss"] == pytest.approx(rep["loss"], rel=1e-12)
+    np.testing.assert_allclose(x_graph, x_host, rtol=0, atol=1e-6)
