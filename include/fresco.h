@@ -167,7 +167,10 @@ fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S);
 /* End-to-end variant on host buffers: copies h_points (host, [N][dim] plan type) to the device,
  * evaluates, and copies the loss (host double) and, if h_grad is not NULL, the gradient back.
  * Synchronises the plan's stream before returning. Uses staging buffers the plan allocates on
- * first use. */
+ * first use. Points of 64 MB or more are copied in up to 8 chunks on a second stream that the
+ * plan creates on first use, and each chunk is binned while the next is in flight; the result is
+ * the same as that of fresco_loss_grad on a device copy. Page-locked h_points and h_grad give
+ * the full copy rate. */
 fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, double *h_loss,
                                     void *h_grad);
 

@@ -502,6 +502,12 @@ void release(fresco_plan_s *p) {
                     p->d_stage_loss};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (cudaEvent_t e : p->copy_ev)
+        if (e) cudaEventDestroy(e);
+    if (p->copy_stream) {
+        cudaStreamSynchronize(p->copy_stream);
+        cudaStreamDestroy(p->copy_stream);
+    }
     cufftHandle hs[] = {p->fft_rows, p->fft_cols, p->ifft_cols, p->ifft_rows};
     for (int i = 0; i < 4; ++i)
         if (p->have_fft[i]) cufftDestroy(hs[i]);
@@ -722,8 +728,42 @@ const EsPoly<float> &poly_of<float>(const fresco_plan_s *p) { return p->poly32; 
 template <>
 const EsPoly<double> &poly_of<double>(const fresco_plan_s *p) { return p->poly64; }
 
+// Host points into the device staging buffer, overlapped with the binning: the copy runs in
+// chunks on a second stream and the plan's stream bins each chunk as soon as it has landed. The
+// ranks within a sub-bin come from atomics in any case and the fixed-point spread does not depend
+// on them, so the result is the same as binning all points at once.
 template <typename T>
-fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
+fresco_status stage_and_bin(fresco_plan_s *p, const T *h_pts, T *d_pts) {
+    const Geom &g = p->geom;
+    const int64_t n = g.n_points, d = g.dim;
+    const int64_t bytes = (int64_t)sizeof(T) * n * d;
+    const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(kHostChunks, bytes / kHostChunkBytes));
+    if (!p->copy_stream) FR_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : p->copy_ev)
+        if (!e) FR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    FR_CUDA(cudaEventRecord(p->copy_ev[kHostChunks], p->stream));
+    FR_CUDA(cudaStreamWaitEvent(p->copy_stream, p->copy_ev[kHostChunks], 0));
+    const int64_t per = (n + chunks - 1) / chunks;
+    for (int c = 0; c < chunks; ++c) {
+        const int64_t j0 = c * per, cnt = std::min(per, n - j0);
+        if (cnt <= 0) break;
+        FR_CUDA(cudaMemcpyAsync(d_pts + j0 * d, h_pts + j0 * d, sizeof(T) * (size_t)(cnt * d),
+                                cudaMemcpyHostToDevice, p->copy_stream));
+        FR_CUDA(cudaEventRecord(p->copy_ev[c], p->copy_stream));
+        FR_CUDA(cudaStreamWaitEvent(p->stream, p->copy_ev[c], 0));
+        Geom gc = g;
+        gc.n_points = cnt;
+        FR_CUDA(Launch<T>::bin(gc, d_pts + j0 * d, p->d_cnt, p->d_key + j0, p->d_slot + j0,
+                               p->d_err, p->stream));
+        p->launches += 1;
+    }
+    return FRESCO_OK;
+}
+
+// h_pts, when not null, is the host copy of the points that pts (the staging buffer) receives.
+template <typename T>
+fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss,
+                           const T *h_pts = nullptr) {
     using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
     const Geom &g = p->geom;
     const MaskGeom &m = p->mgeom;
@@ -731,13 +771,19 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss) {
     {
         StageScope sc(p->prof, p->stream, ST_SORT);
         FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_bins, s));
-        FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
+        if (h_pts) {
+            fresco_status st = stage_and_bin<T>(p, h_pts, const_cast<T *>(pts));
+            if (st) return st;
+        } else {
+            FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
+            p->launches += 1;
+        }
         int nl = 0;
         FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl));
         FR_CUDA(Launch<T>::scatter(g, pts, p->d_key, p->d_slot, p->d_off, p->d_sorted, p->d_perm,
                                    s));
         nl += 1;
-        p->launches += 1 + nl;
+        p->launches += nl;
     }
     {
         StageScope sc(p->prof, p->stream, ST_SPREAD);
@@ -1044,8 +1090,12 @@ fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, doubl
     if (!p->d_stage_pts && (st = dalloc(p, &p->d_stage_pts, bytes))) return st;
     if (!p->d_stage_grad && (st = dalloc(p, &p->d_stage_grad, bytes))) return st;
     if (!p->d_stage_loss && (st = dalloc(p, &p->d_stage_loss, sizeof(double)))) return st;
-    FR_CUDA(cudaMemcpyAsync(p->d_stage_pts, h_points, bytes, cudaMemcpyHostToDevice, p->stream));
-    st = fresco_loss_grad(p, p->d_stage_pts, p->d_stage_loss, h_grad ? p->d_stage_grad : nullptr);
+    st = p->precision == FRESCO_F64
+             ? forward_impl<double>(p, (const double *)p->d_stage_pts, p->d_stage_loss,
+                                    (const double *)h_points)
+             : forward_impl<float>(p, (const float *)p->d_stage_pts, p->d_stage_loss,
+                                   (const float *)h_points);
+    if (!st && h_grad) st = fresco_backward(p, nullptr, p->d_stage_grad);
     if (st) return st;
     FR_CUDA(cudaMemcpyAsync(h_loss, p->d_stage_loss, sizeof(double), cudaMemcpyDeviceToHost,
                             p->stream));

@@ -14,6 +14,10 @@ namespace fresco {
 constexpr int kMaxWidth = 16;     // largest ES kernel width instantiated
 constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
+// fresco_loss_grad_host copies the points in up to kHostChunks pieces of at least
+// kHostChunkBytes, binning each piece while the next one is in flight
+constexpr int kHostChunks = 8;
+constexpr int64_t kHostChunkBytes = 32ll << 20;
 
 // Geometry of the fine grid and its tiling, passed by value to kernels.
 // Axis 0 is x, the contiguous axis of every grid. With q = nf / nb and r = nf % nb, tile b on an
@@ -254,6 +258,8 @@ struct fresco_plan_s {
     void *d_stage_pts = nullptr;     // staging for fresco_loss_grad_host
     void *d_stage_grad = nullptr;
     double *d_stage_loss = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host-to-device chunks of fresco_loss_grad_host
+    cudaEvent_t copy_ev[fresco::kHostChunks + 1] = {};  // one per chunk, plus the start of the copy
     fresco::EsPoly<float> poly32{};
     fresco::EsPoly<double> poly64{};
     int n_mask_blocks = 0;
