@@ -494,7 +494,7 @@ void release(fresco_plan_s *p) {
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     void *bufs[] = {p->d_sorted, p->d_perm, p->d_key, p->d_slot, p->d_cnt, p->d_off,
-                    p->d_block_sums, p->d_grid, p->d_spec, p->d_specT, p->d_bt[0], p->d_bt[1],
+                    p->d_block_sums, p->d_grid, p->d_tw, p->d_specT, p->d_bt[0], p->d_bt[1],
                     p->d_hc[0], p->d_hc[1], p->d_r[0],
                     p->d_r[1], p->d_g[0], p->d_g[1], p->d_rep_n, p->d_rep_s0, p->d_rep_w,
                     p->d_ip[0], p->d_ip[1], p->d_ip[2], p->d_partial, p->d_err,
@@ -536,18 +536,21 @@ template <>
 cufftType c2c_type<double>() { return CUFFT_Z2Z; }
 
 // Four cuFFT plans implement the pruned d-dimensional transforms, every one a batch of
-// contiguous transforms (our transposes move the data in between):
-//   forward: R2C along x for every row; columns x = 0..kx transposed to [kx+1][plane]; C2C over
-//            the contiguous (z,)y plane of each, in place;
-//   inverse: C2C over (z,)y for the 2kx+2 transposed columns n_x = -kx-1..kx of the compact
-//            spectrum (out of place, so its zeros survive); transposed back into R, whose other
-//            columns were zeroed at plan time and are never written; C2C along x.
+// contiguous transforms (our kernels move the data in between):
+//   forward: each real row of length nf0 as a complex row of length nf0/2, in place on the grid;
+//            split into the half spectrum, whose columns x = 0..kx are written transposed to
+//            [kx+1][plane] (k_rfft_split_cols); C2C over the contiguous (z,)y plane of each, in
+//            place;
+//   inverse: C2C over (z,)y for the transposed columns of the compact spectrum (out of place, so
+//            its zeros survive); in the direct mode transposed back into R, whose other columns
+//            were zeroed at plan time and are never written, and C2C along x; in the kderiv mode
+//            merged into complex rows of length nf0/2 (k_rfft_merge_rows) and transformed in
+//            place, which leaves the real field in R.
 template <typename T>
 fresco_status make_ffts(fresco_plan_s *p) {
     const int dim = p->dim;
     const int nf0 = p->geom.nf[0], nf1 = p->geom.nf[1], nf2 = p->geom.nf[2];
     const long long rows = (long long)nf1 * nf2;
-    const long long half = nf0 / 2 + 1;
     const long long kx = p->mgeom.kx;
     const long long hcw = p->mgeom.hc_row;
     size_t ws[4] = {0, 0, 0, 0};
@@ -557,10 +560,11 @@ fresco_status make_ffts(fresco_plan_s *p) {
         p->have_fft[i] = true;
         FR_CUFFT(cufftSetAutoAllocation(*hs[i], 0));
     }
-    {   // rows, forward R2C
-        long long n[1] = {nf0};
-        FR_CUFFT(cufftMakePlanMany64(p->fft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, half,
-                                     r2c_type<T>(), rows, &ws[0]));
+    const long long mh = nf0 / 2;   // the real rows run as complex rows of half the length
+    {   // rows, forward, in place on the grid
+        long long n[1] = {mh};
+        FR_CUFFT(cufftMakePlanMany64(p->fft_rows, 1, n, nullptr, 1, mh, nullptr, 1, mh,
+                                     c2c_type<T>(), rows, &ws[0]));
     }
     long long cn[2];
     const int crank = dim - 1;
@@ -576,10 +580,10 @@ fresco_status make_ffts(fresco_plan_s *p) {
                                  c2c_type<T>(), kx + 1, &ws[1]));
     FR_CUFFT(cufftMakePlanMany64(p->ifft_cols, crank, cn, nullptr, 1, plane, nullptr, 1, plane,
                                  c2c_type<T>(), hcw, &ws[2]));
-    if (p->mgeom.kderiv) {   // rows, inverse complex-to-real from the half rows
-        long long n[1] = {nf0};
-        FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, half, nullptr, 1, nf0,
-                                     c2r_type<T>(), rows, &ws[3]));
+    if (p->mgeom.kderiv) {   // rows, inverse, in place on the merged half-length rows
+        long long n[1] = {mh};
+        FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, mh, nullptr, 1, mh,
+                                     c2c_type<T>(), rows, &ws[3]));
     } else {
         long long n[1] = {nf0};
         FR_CUFFT(cufftMakePlanMany64(p->ifft_rows, 1, n, nullptr, 1, nf0, nullptr, 1, nf0,
@@ -670,18 +674,29 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
         return st;
 
     if ((st = dalloc(p, &p->d_grid, sizeof(T) * (size_t)cells))) return st;
-    if ((st = dalloc(p, &p->d_spec, sizeof(C2) * (size_t)(rows * m.half_row)))) return st;
+    {   // tau_k = exp(-2 pi i k / nf0), k = 0..nf0/4, for the real-row split and merge
+        const int mh = g.nf[0] / 2;
+        std::vector<C2> tw(mh / 2 + 1);
+        for (int k = 0; k <= mh / 2; ++k) {
+            const double a = 2.0 * M_PI * (double)k / (double)g.nf[0];
+            tw[k].x = (T)std::cos(a);
+            tw[k].y = (T)-std::sin(a);
+        }
+        if ((st = dalloc(p, &p->d_tw, sizeof(C2) * tw.size()))) return st;
+        FR_CUDA(cudaMemcpy(p->d_tw, tw.data(), sizeof(C2) * tw.size(), cudaMemcpyHostToDevice));
+    }
     if ((st = dalloc(p, &p->d_specT, sizeof(C2) * (size_t)(rows * (m.kx + 1))))) return st;
     // backward spectra: compact transposed [hc_row][plane], after the (z,)y pass, back in row
     // order (a full complex row in the direct mode, the half row of the real transform in the
     // kderiv mode; columns outside the mask stay zero from here on), and the grid(s)
     const size_t r_elems = m.kderiv ? (size_t)(rows * m.half_row) : (size_t)cells;
-    const size_t g_bytes = m.kderiv ? sizeof(T) * (size_t)cells : sizeof(C2) * (size_t)cells;
+    // (the kderiv mode's inverse runs in place in R, whose rows then hold the real field)
+    const size_t g_bytes = m.kderiv ? 0 : sizeof(C2) * (size_t)cells;
     for (int q = 0; q < p->n_pipes; ++q) {
         if ((st = dalloc(p, &p->d_hc[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
         if ((st = dalloc(p, &p->d_bt[q], sizeof(C2) * (size_t)(rows * m.hc_row)))) return st;
         if ((st = dalloc(p, &p->d_r[q], sizeof(C2) * r_elems))) return st;
-        if ((st = dalloc(p, &p->d_g[q], g_bytes))) return st;
+        if (g_bytes && (st = dalloc(p, &p->d_g[q], g_bytes))) return st;
         FR_CUDA(cudaMemsetAsync(p->d_hc[q], 0, sizeof(C2) * (size_t)(rows * m.hc_row), p->stream));
         FR_CUDA(cudaMemsetAsync(p->d_r[q], 0, sizeof(C2) * r_elems, p->stream));
     }
@@ -794,11 +809,12 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss,
         StageScope sc(p->prof, p->stream, ST_FFT_FWD);
         const int64_t rows = m.plane;
         if (sizeof(T) == 4)
-            FR_CUFFT(cufftExecR2C(p->fft_rows, (cufftReal *)p->d_grid, (cufftComplex *)p->d_spec));
+            FR_CUFFT(cufftExecC2C(p->fft_rows, (cufftComplex *)p->d_grid,
+                                  (cufftComplex *)p->d_grid, CUFFT_FORWARD));
         else
-            FR_CUFFT(cufftExecD2Z(p->fft_rows, (cufftDoubleReal *)p->d_grid,
-                                  (cufftDoubleComplex *)p->d_spec));
-        FR_CUDA(Launch<T>::cols_to_rows(p->d_spec, p->d_specT, rows, m.half_row, m.kx + 1, s));
+            FR_CUFFT(cufftExecZ2Z(p->fft_rows, (cufftDoubleComplex *)p->d_grid,
+                                  (cufftDoubleComplex *)p->d_grid, CUFFT_FORWARD));
+        FR_CUDA(Launch<T>::rfft_split(p->d_grid, p->d_specT, p->d_tw, rows, g.nf[0] / 2, m.kx, s));
         p->launches += 1;
         if (sizeof(T) == 4)
             FR_CUFFT(cufftExecC2C(p->fft_cols, (cufftComplex *)p->d_specT,
@@ -839,18 +855,19 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
             else
                 FR_CUFFT(cufftExecZ2Z(p->ifft_cols, (cufftDoubleComplex *)p->d_hc[0],
                                       (cufftDoubleComplex *)p->d_bt[0], CUFFT_INVERSE));
-            FR_CUDA(Launch<T>::rows_to_half(p->d_bt[0], p->d_r[0], m.plane, m.half_row, m.kx, s));
+            FR_CUDA(Launch<T>::rfft_merge(p->d_bt[0], p->d_r[0], p->d_tw, m.plane, g.nf[0] / 2,
+                                          m.kx, s));
             p->launches += 1;
             if (sizeof(T) == 4)
-                FR_CUFFT(cufftExecC2R(p->ifft_rows, (cufftComplex *)p->d_r[0],
-                                      (cufftReal *)p->d_g[0]));
+                FR_CUFFT(cufftExecC2C(p->ifft_rows, (cufftComplex *)p->d_r[0],
+                                      (cufftComplex *)p->d_r[0], CUFFT_INVERSE));
             else
-                FR_CUFFT(cufftExecZ2D(p->ifft_rows, (cufftDoubleComplex *)p->d_r[0],
-                                      (cufftDoubleReal *)p->d_g[0]));
+                FR_CUFFT(cufftExecZ2Z(p->ifft_rows, (cufftDoubleComplex *)p->d_r[0],
+                                      (cufftDoubleComplex *)p->d_r[0], CUFFT_INVERSE));
         }
         StageScope sc(p->prof, p->stream, ST_INTERP);
         FR_CUDA(Launch<T>::interp_kd(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off,
-                                     (const T *)p->d_g[0], grad_out, p->dscale, grad, s));
+                                     (const T *)p->d_r[0], grad_out, p->dscale, grad, s));
         p->launches += 1;
         return FRESCO_OK;
     }
@@ -1241,29 +1258,28 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
     b->n_rep = reo;
     if (b->n_points > 2147483647LL || b->n_bins > 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
     // ---- class-order offsets (grids and spectra of a class are contiguous)
-    int64_t go = 0, ao = 0, ato = 0, hco = 0, ro = 0;
+    int64_t go = 0, ato = 0, hco = 0, ro = 0, two = 0;
     for (size_t c = 0; c < b->cls.size(); ++c) {
         auto &K = b->cls[c];
-        K.go0 = go; K.ao0 = ao; K.ato0 = ato; K.hco0 = hco; K.ro0 = ro;
+        K.go0 = go; K.ato0 = ato; K.hco0 = hco; K.ro0 = ro; K.two0 = two;
         const int64_t plane = K.nf[1], cells = (int64_t)K.nf[0] * K.nf[1];
-        const int64_t half = K.nf[0] / 2 + 1;
+        two += K.nf[0] / 4 + 1;
         for (int i = 0; i < n; ++i) {
             if (cls_of[i] != (int)c) continue;
             BInst &I = b->inst[i];
-            I.go = go; I.ao = ao; I.ato = ato; I.hco = hco; I.ro = ro;
+            I.go = go; I.ato = ato; I.hco = hco; I.ro = ro;
             go += cells;
-            ao += plane * half;
             ato += plane * (K.kx + 1);
-            // kderiv: scalar half spectrum [kx+1][plane], half rows [plane][nf0/2+1]; direct:
-            // [2kx+2][plane] and full complex rows
+            // kderiv: scalar half spectrum [kx+1][plane], merged and transformed in the grid's
+            // place; direct: [2kx+2][plane] and full complex rows
             hco += plane * (b->kderiv ? (int64_t)K.kx + 1 : 2 * (int64_t)K.kx + 2);
-            ro += b->kderiv ? plane * half : cells;
+            ro += b->kderiv ? 0 : cells;
         }
     }
     b->n_r = ro;
     b->cells = go;
-    b->n_spec = ao;
     b->n_specT = ato;
+    b->n_tw = two;
     b->n_hc = hco;
     // ---- per-instance geometry (one spread list size for all: the largest any instance needs)
     int cap_max = 1024;
@@ -1331,10 +1347,10 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
               balloc(b, (void **)&b->bsum, sizeof(int) * ((b->n_bins + 1023) / 1024 + 1)) &&
               balloc(b, (void **)&b->err, sizeof(int)) &&
               balloc(b, &b->grid, sizeof(T) * b->cells) &&
-              balloc(b, &b->spec, sizeof(C2) * b->n_spec) &&
+              balloc(b, &b->tw, sizeof(C2) * b->n_tw) &&
               balloc(b, &b->specT, sizeof(C2) * b->n_specT) &&
               balloc(b, &b->hc, sizeof(C2) * b->n_hc) && balloc(b, &b->bt, sizeof(C2) * b->n_hc) &&
-              balloc(b, &b->r, sizeof(C2) * b->n_r) &&
+              (b->kderiv || balloc(b, &b->r, sizeof(C2) * b->n_r)) &&
               (b->kderiv || balloc(b, &b->g, sizeof(C2) * b->cells)) &&
               balloc(b, (void **)&b->rep_n, sizeof(int) * b->n_rep * dim) &&
               balloc(b, &b->rep_s0, sizeof(T) * b->n_rep) &&
@@ -1369,7 +1385,15 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         FR_CUDA(cudaMemcpy(b->d_mblk_first, b->mblk_first.data(), sizeof(int64_t) * (n + 1),
                            cudaMemcpyHostToDevice));
         FR_CUDA(cudaMemset(b->hc, 0, sizeof(C2) * b->n_hc));
-        FR_CUDA(cudaMemset(b->r, 0, sizeof(C2) * b->n_r));
+        if (b->r) FR_CUDA(cudaMemset(b->r, 0, sizeof(C2) * b->n_r));
+        std::vector<C2> tw((size_t)b->n_tw);
+        for (auto &K : b->cls)
+            for (int k = 0; k <= K.nf[0] / 4; ++k) {
+                const double a = 2.0 * M_PI * (double)k / (double)K.nf[0];
+                tw[(size_t)(K.two0 + k)].x = (T)std::cos(a);
+                tw[(size_t)(K.two0 + k)].y = (T)-std::sin(a);
+            }
+        FR_CUDA(cudaMemcpy(b->tw, tw.data(), sizeof(C2) * tw.size(), cudaMemcpyHostToDevice));
         FR_CUDA(cudaMemset(b->err, 0, sizeof(int)));
     }
     BTables &t = b->tab;
@@ -1408,9 +1432,10 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
             K.have[i] = true;
             FR_CUFFT(cufftSetAutoAllocation(K.h[i], 0));
         }
-        long long n0 = K.nf[0], n1 = K.nf[1], half = K.nf[0] / 2 + 1, cnt = K.count;
-        FR_CUFFT(cufftMakePlanMany64(K.h[0], 1, &n0, nullptr, 1, n0, nullptr, 1, half,
-                                     r2c_type<T>(), cnt * n1, &ws));
+        // the real rows of length n0 run as complex rows of length n0 / 2, in place
+        long long n0 = K.nf[0], n1 = K.nf[1], mh = K.nf[0] / 2, cnt = K.count;
+        FR_CUFFT(cufftMakePlanMany64(K.h[0], 1, &mh, nullptr, 1, mh, nullptr, 1, mh,
+                                     c2c_type<T>(), cnt * n1, &ws));
         wmax = std::max(wmax, ws);
         FR_CUFFT(cufftMakePlanMany64(K.h[1], 1, &n1, nullptr, 1, n1, nullptr, 1, n1, c2c_type<T>(),
                                      cnt * (K.kx + 1), &ws));
@@ -1420,8 +1445,8 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
                                                       : 2 * (long long)K.kx + 2), &ws));
         wmax = std::max(wmax, ws);
         if (b->kderiv)
-            FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, half, nullptr, 1, n0,
-                                         c2r_type<T>(), cnt * n1, &ws));
+            FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &mh, nullptr, 1, mh, nullptr, 1, mh,
+                                         c2c_type<T>(), cnt * n1, &ws));
         else
             FR_CUFFT(cufftMakePlanMany64(K.h[3], 1, &n0, nullptr, 1, n0, nullptr, 1, n0,
                                          c2c_type<T>(), cnt * n1, &ws));
@@ -1466,16 +1491,17 @@ fresco_status batch_eval(fresco_batch_s *b, const T *pts, double *losses, T *gra
     {
         StageScope sc(b->prof, s, ST_FFT_FWD);
         for (auto &K : b->cls) {   // forward FFT of each size class
-            const int64_t half = K.nf[0] / 2 + 1, plane = K.nf[1];
-            C2 *A = (C2 *)b->spec + K.ao0, *AT = (C2 *)b->specT + K.ato0;
+            const int64_t plane = K.nf[1];
+            const int mh = K.nf[0] / 2;
+            C2 *A = (C2 *)((T *)b->grid + K.go0), *AT = (C2 *)b->specT + K.ato0;
             if (sizeof(T) == 4)
-                FR_CUFFT(cufftExecR2C(K.h[0], (cufftReal *)((T *)b->grid + K.go0),
-                                      (cufftComplex *)A));
+                FR_CUFFT(cufftExecC2C(K.h[0], (cufftComplex *)A, (cufftComplex *)A,
+                                      CUFFT_FORWARD));
             else
-                FR_CUFFT(cufftExecD2Z(K.h[0], (cufftDoubleReal *)((T *)b->grid + K.go0),
-                                      (cufftDoubleComplex *)A));
-            FR_CUDA(Launch<T>::cols_to_rows(A, AT, plane, half, K.kx + 1, s, K.count,
-                                            plane * half, plane * (K.kx + 1)));
+                FR_CUFFT(cufftExecZ2Z(K.h[0], (cufftDoubleComplex *)A, (cufftDoubleComplex *)A,
+                                      CUFFT_FORWARD));
+            FR_CUDA(Launch<T>::rfft_split(A, AT, (C2 *)b->tw + K.two0, plane, mh, K.kx, s,
+                                          K.count, plane * mh, plane * (K.kx + 1)));
             if (sizeof(T) == 4)
                 FR_CUFFT(cufftExecC2C(K.h[1], (cufftComplex *)AT, (cufftComplex *)AT,
                                       CUFFT_FORWARD));
@@ -1501,21 +1527,24 @@ fresco_status batch_eval(fresco_batch_s *b, const T *pts, double *losses, T *gra
         {
             StageScope sc(b->prof, s, ST_FFT_INV);
             for (auto &K : b->cls) {   // scalar spectrum -> real field (in the spread grid's place)
-                const int64_t plane = K.nf[1], half = K.nf[0] / 2 + 1;
-                C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0, *R = (C2 *)b->r + K.ro0;
-                T *Hr = (T *)b->grid + K.go0;
+                const int64_t plane = K.nf[1];
+                const int mh = K.nf[0] / 2;
+                C2 *H = (C2 *)b->hc + K.hco0, *BT = (C2 *)b->bt + K.hco0;
+                C2 *Z = (C2 *)((T *)b->grid + K.go0);
                 if (sizeof(T) == 4)
                     FR_CUFFT(cufftExecC2C(K.h[2], (cufftComplex *)H, (cufftComplex *)BT,
                                           CUFFT_INVERSE));
                 else
                     FR_CUFFT(cufftExecZ2Z(K.h[2], (cufftDoubleComplex *)H,
                                           (cufftDoubleComplex *)BT, CUFFT_INVERSE));
-                FR_CUDA(Launch<T>::rows_to_half(BT, R, plane, half, K.kx, s, K.count,
-                                                plane * ((int64_t)K.kx + 1), plane * half));
+                FR_CUDA(Launch<T>::rfft_merge(BT, Z, (C2 *)b->tw + K.two0, plane, mh, K.kx, s,
+                                              K.count, plane * ((int64_t)K.kx + 1), plane * mh));
                 if (sizeof(T) == 4)
-                    FR_CUFFT(cufftExecC2R(K.h[3], (cufftComplex *)R, (cufftReal *)Hr));
+                    FR_CUFFT(cufftExecC2C(K.h[3], (cufftComplex *)Z, (cufftComplex *)Z,
+                                          CUFFT_INVERSE));
                 else
-                    FR_CUFFT(cufftExecZ2D(K.h[3], (cufftDoubleComplex *)R, (cufftDoubleReal *)Hr));
+                    FR_CUFFT(cufftExecZ2Z(K.h[3], (cufftDoubleComplex *)Z,
+                                          (cufftDoubleComplex *)Z, CUFFT_INVERSE));
                 b->launches += 1;
             }
         }

@@ -88,10 +88,9 @@ struct BInst {
     int64_t po;        // first point
     int64_t bo;        // first sub-bin
     int64_t go;        // first fine-grid cell (real grid)
-    int64_t ao;        // forward half spectrum (complex elements)
     int64_t ato;       // transposed forward spectrum
     int64_t hco;       // transposed compact backward spectrum (and the buffer after its y pass)
-    int64_t ro;        // R and G (complex elements)
+    int64_t ro;        // R and G of the direct gradient mode (complex elements)
     int64_t reo;       // first representative
     int64_t ipo[3];    // 1 / Psi tables per axis
     double loss_const;
@@ -178,6 +177,15 @@ struct Launch {
                                  const double *grad_out, const double dscale[3], T *grad,
                                  cudaStream_t s);
     static int interp_kd_smem(const Geom &g);
+    // real transforms of even length 2M along x as complex transforms of length M: split the
+    // forward result into the half spectrum (columns 0..kx, transposed), and merge a transposed
+    // half spectrum into the complex rows of the inverse; tw[k] = exp(-2 pi i k / 2M), k <= M/2
+    static cudaError_t rfft_split(const void *z, void *xt, const void *tw, int64_t rows, int M,
+                                  int kx, cudaStream_t s, int batch = 1, int64_t z_stride = 0,
+                                  int64_t xt_stride = 0);
+    static cudaError_t rfft_merge(const void *xt, void *z, const void *tw, int64_t rows, int M,
+                                  int kx, cudaStream_t s, int batch = 1, int64_t xt_stride = 0,
+                                  int64_t z_stride = 0);
     static cudaError_t rows_to_half(const void *bt, void *r, int64_t rows, int64_t half_row,
                                     int kx, cudaStream_t s, int batch = 1, int64_t bt_stride = 0,
                                     int64_t r_stride = 0);
@@ -241,7 +249,7 @@ struct fresco_plan_s {
     int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of d_cnt
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
-    void *d_spec = nullptr;          // complex forward half spectrum after the x pass
+    void *d_tw = nullptr;            // exp(-2 pi i k / nf0), k = 0..nf0/4 (real-row split/merge)
     void *d_specT = nullptr;         // its columns x = 0..kx transposed: [kx+1][plane]
     void *d_hc[2] = {nullptr, nullptr};   // transposed compact backward spectra [2kx+2][plane]
     void *d_bt[2] = {nullptr, nullptr};   // after the (z,)y pass, still transposed
@@ -285,8 +293,8 @@ struct fresco_batch_s {
         int nf[2] = {0, 0};
         int kx = 0;
         int count = 0;
-        int64_t go0 = 0, ao0 = 0, ato0 = 0, hco0 = 0, ro0 = 0;
-        cufftHandle h[4] = {0, 0, 0, 0};   // rows R2C, cols fwd, cols inv, rows inv
+        int64_t go0 = 0, ato0 = 0, hco0 = 0, ro0 = 0, two0 = 0;
+        cufftHandle h[4] = {0, 0, 0, 0};   // rows fwd, cols fwd, cols inv, rows inv
         bool have[4] = {false, false, false, false};
     };
     int dim = 0;
@@ -303,15 +311,16 @@ struct fresco_batch_s {
     fresco::EsPoly<float> poly32{};
     fresco::EsPoly<double> poly64{};
     int64_t n_points = 0, n_bins = 0, n_rep = 0;
-    int64_t cells = 0, n_spec = 0, n_specT = 0, n_hc = 0;
+    int64_t cells = 0, n_specT = 0, n_hc = 0, n_tw = 0;
     // device
     fresco::BInst *d_inst = nullptr;
     int64_t *d_pt_first = nullptr, *d_tile_first = nullptr, *d_mblk_first = nullptr;
     void *sorted = nullptr;
     int *perm = nullptr, *key = nullptr, *slot = nullptr, *cnt = nullptr, *off = nullptr;
     int *bsum = nullptr, *err = nullptr;
-    void *grid = nullptr, *spec = nullptr, *specT = nullptr, *hc = nullptr, *bt = nullptr;
+    void *grid = nullptr, *specT = nullptr, *hc = nullptr, *bt = nullptr;
     void *r = nullptr, *g = nullptr;
+    void *tw = nullptr;              // per class: exp(-2 pi i k / nf0), k = 0..nf0/4
     int *rep_n = nullptr;
     void *rep_s0 = nullptr, *rep_w = nullptr, *ip = nullptr;
     double *partial = nullptr;

@@ -1350,6 +1350,123 @@ __global__ void __launch_bounds__(256) k_rows_to_half(const C *__restrict__ bt, 
     }
 }
 
+// A real row x of even length n_f = 2M is transformed as the complex row z[m] = x[2m] + i x[2m+1]
+// of length M (Z = FFT_M z); its half spectrum is then
+//   X[k] = E + tau_k O,  E = (Z[k] + conj Z[M-k]) / 2,  O = (Z[k] - conj Z[M-k]) / (2i),
+//   X[M-k] = conj(E - tau_k O),  tau_k = exp(-2 pi i k / n_f),  indices of Z taken modulo M.
+// One thread forms the pair (k, M-k) for 0 <= k <= M/2 from the same two values, so every Z is
+// read once. The columns k <= kx are written transposed: xt[k][row], rows contiguous. z is
+// [rows][M]; tw[k] = tau_k for k = 0..M/2. blockIdx.z selects one of a batch of such transforms
+// (z and xt advanced by their strides).
+template <typename C>
+__global__ void __launch_bounds__(256) k_rfft_split_cols(const C *__restrict__ z, C *__restrict__ xt,
+                                                         const C *__restrict__ tw, int64_t rows,
+                                                         int M, int kx, int64_t z_stride,
+                                                         int64_t xt_stride) {
+    using R = decltype(C{}.x);
+    __shared__ C ta[32][33];
+    __shared__ C tb[32][33];
+    z += blockIdx.z * z_stride;
+    xt += blockIdx.z * xt_stride;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    const int half = M / 2;
+    // nothing to write: every direct column beyond kx and every mirror column (M - k, for the
+    // block's k) beyond kx as well
+    if (k0 > kx && M - (k0 + 31) > kx) return;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        const int k = k0 + threadIdx.x;
+        if (r < rows && k <= half) {
+            const int km = (k == 0) ? 0 : M - k;
+            ta[i][threadIdx.x] = z[r * M + k];
+            tb[i][threadIdx.x] = z[r * M + km];
+        }
+    }
+    __syncthreads();
+    const int64_t r = r0 + threadIdx.x;
+    if (r >= rows) return;
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        const int k = k0 + t;
+        if (k > half) break;
+        const C a = ta[threadIdx.x][t], b = tb[threadIdx.x][t];
+        const C w = tw[k];
+        // E = (a + conj b) / 2, O = -i (a - conj b) / 2
+        const R ex = R(0.5) * (a.x + b.x), ey = R(0.5) * (a.y - b.y);
+        const R ox = R(0.5) * (a.y + b.y), oy = R(-0.5) * (a.x - b.x);
+        const R px = w.x * ox - w.y * oy, py = w.x * oy + w.y * ox;   // tau_k O
+        if (k <= kx) {
+            C v;
+            v.x = ex + px;
+            v.y = ey + py;
+            xt[(int64_t)k * rows + r] = v;
+        }
+        const int km = M - k;
+        if (km > half && km <= kx) {
+            C v;
+            v.x = ex - px;
+            v.y = -(ey - py);
+            xt[(int64_t)km * rows + r] = v;
+        }
+    }
+}
+
+// Inverse of the above for a Hermitian half spectrum X[k], k = 0..kx (zero beyond, and kx < M):
+//   Z[k] = P + i Q,  P = X[k] + conj X[M-k],  Q = (X[k] - conj X[M-k]) conj(tau_k),
+//   Z[M-k] = conj P + i conj Q,
+// so that the inverse FFT_M of Z is x[2m] + i x[2m+1] with x[n] = sum_k X[k] e^{+2 pi i k n / n_f}
+// (both halves of the Hermitian spectrum). xt is [kx+1][rows] (rows contiguous); z is
+// [rows][M], every entry written. blockIdx.z selects one of a batch, as above.
+template <typename C>
+__global__ void __launch_bounds__(256) k_rfft_merge_rows(const C *__restrict__ xt, C *__restrict__ z,
+                                                         const C *__restrict__ tw, int64_t rows,
+                                                         int M, int kx, int64_t xt_stride,
+                                                         int64_t z_stride) {
+    using R = decltype(C{}.x);
+    __shared__ C ta[32][33];
+    __shared__ C tb[32][33];
+    xt += blockIdx.z * xt_stride;
+    z += blockIdx.z * z_stride;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    const int half = M / 2;
+    for (int t = threadIdx.y; t < 32; t += 8) {
+        const int k = k0 + t;
+        const int64_t r = r0 + threadIdx.x;
+        if (k <= half && r < rows) {
+            const int km = M - k;   // M for k = 0: X[M] = 0 since kx < M
+            C zero;
+            zero.x = R(0);
+            zero.y = R(0);
+            ta[t][threadIdx.x] = k <= kx ? xt[(int64_t)k * rows + r] : zero;
+            tb[t][threadIdx.x] = km <= kx ? xt[(int64_t)km * rows + r] : zero;
+        }
+    }
+    __syncthreads();
+    const int k = k0 + threadIdx.x;
+    if (k > half) return;
+    const C w = tw[k];
+    const int km = M - k;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int64_t r = r0 + i;
+        if (r >= rows) break;
+        const C a = ta[threadIdx.x][i], b = tb[threadIdx.x][i];
+        const R px = a.x + b.x, py = a.y - b.y;           // P = a + conj b
+        const R dx = a.x - b.x, dy = a.y + b.y;           // a - conj b
+        const R qx = dx * w.x + dy * w.y, qy = dy * w.x - dx * w.y;   // (a - conj b) conj(tau_k)
+        C v;
+        v.x = px - qy;
+        v.y = py + qx;
+        z[r * M + k] = v;
+        if (km > half && km < M) {
+            C u;   // conj P + i conj Q
+            u.x = px + qy;
+            u.y = -py + qx;
+            z[r * M + km] = u;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Launchers
 
@@ -1404,6 +1521,28 @@ int Launch<T>::interp_kd_smem(const Geom &g) {
     const int w = g.width;
     size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
     return (int)(cells * sizeof(T));
+}
+
+template <typename T>
+cudaError_t Launch<T>::rfft_split(const void *z, void *xt, const void *tw, int64_t rows, int M,
+                                  int kx, cudaStream_t s, int batch, int64_t z_stride,
+                                  int64_t xt_stride) {
+    using C = typename PT<T>::C;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)(M / 2 / 32 + 1), (unsigned)batch);
+    k_rfft_split_cols<C><<<grid, dim3(32, 8), 0, s>>>((const C *)z, (C *)xt, (const C *)tw, rows,
+                                                      M, kx, z_stride, xt_stride);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::rfft_merge(const void *xt, void *z, const void *tw, int64_t rows, int M,
+                                  int kx, cudaStream_t s, int batch, int64_t xt_stride,
+                                  int64_t z_stride) {
+    using C = typename PT<T>::C;
+    dim3 grid((unsigned)((rows + 31) / 32), (unsigned)(M / 2 / 32 + 1), (unsigned)batch);
+    k_rfft_merge_rows<C><<<grid, dim3(32, 8), 0, s>>>((const C *)xt, (C *)z, (const C *)tw, rows,
+                                                      M, kx, xt_stride, z_stride);
+    return cudaGetLastError();
 }
 
 template <typename T>
