@@ -815,6 +815,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_b(
 //   H[n] = (a_x + i a_y) ip / 2 and H[-n] = (conj a_x + i conj a_y) ip / 2 (pipeline 0),
 //   H1[n] = a_z ip / 2, H1[-n] = conj(a_z) ip / 2 (pipeline 1, 3D).
 // The inverse FFT of H then gives d/dr_x + i d/dr_y on the grid (before interpolation).
+// Knuth's two-sum: s + e == a + b exactly (round to nearest, no overflow)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 template <typename T, int D>
 __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__restrict__ rep_n,
                                              const T *__restrict__ rep_s0,
@@ -826,7 +833,8 @@ __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__res
                                              typename PT<T>::C *__restrict__ hc1, int64_t e0,
                                              int64_t stride) {
     using C = typename PT<T>::C;
-    double lsum = 0.0;
+    double lsum = 0.0;          // FP64 plans
+    float ah = 0.f, al = 0.f;   // FP32 plans: the thread's sum as an unevaluated float pair
     const T inv_n = (T)m.inv_n;
     for (int64_t e = e0; e < m.n_rep; e += stride) {
         const int nx = rep_n[e * D + 0];
@@ -841,9 +849,29 @@ __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__res
         const T re = F.x * ip, im = F.y * ip;
         const T S = (re * re + im * im) * inv_n;
         const T wgt = rep_w[e];
-        const double d = (double)S - (double)rep_s0[e];   // exact difference of two T values
-        lsum = fma((double)wgt * d, d, lsum);
-        const T E = T(4) * wgt * (T)d * inv_n;
+        T dt;
+        if constexpr (sizeof(T) == 4) {
+            // W (S - S0)^2 by error-free transformations: S - S0 exactly as dh + dl, its square
+            // and the product with W to about 46 bits, added to the thread's pair; the loss
+            // keeps FP64-level accuracy while the narrow FP64 pipe sees one conversion per
+            // thread instead of several operations per representative
+            float dh, dl;
+            two_sum(S, -rep_s0[e], dh, dl);
+            const float p = dh * dh;
+            const float pl = fmaf(2.f * dh, dl, fmaf(dh, dh, -p));
+            const float th = wgt * p;
+            const float tl = fmaf(wgt, pl, fmaf(wgt, p, -th));
+            float sh, se;
+            two_sum(ah, th, sh, se);
+            ah = sh;
+            al += se + tl;
+            dt = dh;
+        } else {
+            const double d = S - rep_s0[e];
+            lsum = fma(wgt * d, d, lsum);
+            dt = d;
+        }
+        const T E = T(4) * wgt * dt * inv_n;
         const T h = T(0.5) * ip * E;
         const T er = re * h, ei = im * h;
         const int my = ny > 0 ? m.nf[1] - ny : -ny;
@@ -867,6 +895,7 @@ __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__res
             hc1[cm] = C{-kz * ei, -kz * er};
         }
     }
+    if constexpr (sizeof(T) == 4) lsum = (double)ah + (double)al;
     return lsum;
 }
 
