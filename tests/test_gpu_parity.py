@@ -258,6 +258,27 @@ def test_kernel_derivative_gradient_mode_matches_oracle(dim, precision):
     _assert_within(err, precision)
 
 
+@pytest.mark.parametrize("grad_mode", ["direct", "kderiv"])
+@pytest.mark.parametrize("dim,precision", [(2, "f32"), (2, "f64"), (3, "f32"), (3, "f64")])
+def test_odd_half_length_x_transform(dim, precision, grad_mode):
+    """Fine grids whose x length is twice an odd number (90 in 2D, 42 in 3D): the real transforms
+    along x run as complex transforms of odd length M = n_f / 2, where the pair (k, M - k) never
+    meets itself, and the half spectrum must still match the oracle."""
+    from paper_2305_15693_gb300 import fresco
+    g = inputs.rng(90 + dim)
+    dt = np.float64 if precision == "f64" else np.float32
+    n = 2000
+    pts = g.random((n, dim)).astype(dt)
+    mask = inputs.ball_mask(22 if dim == 2 else 10, dim)
+    S0 = g.random(mask.shape[0])
+    W = 0.5 + g.random(mask.shape[0])
+    mode = fresco.FRESCO_GRAD_KDERIV if grad_mode == "kderiv" else fresco.FRESCO_GRAD_DIRECT
+    err = compare(pts, mask, S0, W, precision=precision, grad_mode=mode)
+    nf = err["info"]["n_fine"][0]
+    assert nf == (90 if dim == 2 else 42) and (nf // 2) % 2 == 1
+    _assert_within(err, precision)
+
+
 def test_kernel_derivative_mode_follows_the_incoming_gradient():
     """backward(g_out) scales the kderiv gradient by g_out, as in the direct mode."""
     import torch
