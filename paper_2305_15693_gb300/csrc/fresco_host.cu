@@ -687,9 +687,10 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     }
     if ((st = dalloc(p, &p->d_specT, sizeof(C2) * (size_t)(rows * (m.kx + 1))))) return st;
     // backward spectra: compact transposed [hc_row][plane], after the (z,)y pass, back in row
-    // order (a full complex row in the direct mode, the half row of the real transform in the
-    // kderiv mode; columns outside the mask stay zero from here on), and the grid(s)
-    const size_t r_elems = m.kderiv ? (size_t)(rows * m.half_row) : (size_t)cells;
+    // order (the direct mode's full complex rows, whose columns outside the mask stay zero from
+    // here on; the kderiv mode's merged complex rows of nf0/2, every entry written per call), and
+    // the direct mode's gradient grid(s)
+    const size_t r_elems = m.kderiv ? (size_t)rows * (size_t)(g.nf[0] / 2) : (size_t)cells;
     // (the kderiv mode's inverse runs in place in R, whose rows then hold the real field)
     const size_t g_bytes = m.kderiv ? 0 : sizeof(C2) * (size_t)cells;
     for (int q = 0; q < p->n_pipes; ++q) {

@@ -276,10 +276,10 @@ struct fresco_plan_s {
     int64_t device_bytes = 0;
 
     // cuFFT plans
-    cufftHandle fft_rows = 0;        // R2C along x, all rows
+    cufftHandle fft_rows = 0;        // x pass: every real row as a complex row of nf0/2, in place
     cufftHandle fft_cols = 0;        // C2C forward over the other axes, columns x in [0, kx]
     cufftHandle ifft_cols = 0;       // C2C inverse over the other axes, kx + 1 columns
-    cufftHandle ifft_rows = 0;       // C2C inverse along x, all rows
+    cufftHandle ifft_rows = 0;       // C2C inverse along x, all rows (kderiv: nf0/2, in place)
     bool have_fft[4] = {false, false, false, false};
 
     fresco::StageProfile prof;

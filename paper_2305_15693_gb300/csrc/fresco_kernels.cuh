@@ -879,7 +879,7 @@ __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__res
         const int64_t rowm = (int64_t)mz * m.nf[1] + my;
         if (m.kderiv) {
             // the scalar half spectrum E / Psi at n (and, on the n_x = 0 column, its conjugate at
-            // -n, which the complex-to-real transform expects to find there)
+            // -n, which the real inverse transform along x reads there)
             hc0[(int64_t)nx * m.plane + row] = C{er, ei};
             if (nx == 0) hc0[rowm] = C{er, -ei};
             continue;
