@@ -15,7 +15,8 @@
 // takes a new direction.
 //
 // Vectors live in the plan's precision, packed like the points (instance after instance); inner
-// products accumulate in FP64. The packed vector is cut into chunks that never straddle two
+// products keep FP64 accuracy (fresco::DotAcc: float pairs per thread for FP32 vectors, FP64
+// from there on). The packed vector is cut into chunks that never straddle two
 // instances; a chunk kernel writes one partial per chunk, and whoever needs an instance's sum
 // adds that instance's partials in a fixed order (deterministic, and the same in every block).
 //
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(kThreads) k_accept(
     double *__restrict__ p_gg, double *__restrict__ p_gmax) {
     const int c = blockIdx.x;
     const BLState &s = st[chunk_inst[c]];
-    double sy = 0.0, yy = 0.0, gg = 0.0, gm = 0.0;
+    fresco::DotAcc<T> sy, yy, gg;
+    T gm = T(0);
     if (running(s.act)) {
         const bool pair = s.act == ACT_ACCEPT;
         T *S = Sv[s.head], *Y = Yv[s.head];
@@ -170,20 +172,20 @@ __global__ void __launch_bounds__(kThreads) k_accept(
                 const T se = xn - x[e], ye = gn - g[e];
                 S[e] = se;
                 Y[e] = ye;
-                sy = fma((double)se, (double)ye, sy);
-                yy = fma((double)ye, (double)ye, yy);
+                sy.add(se, ye);
+                yy.add(ye, ye);
             }
             x[e] = xn;
             g[e] = gn;
             q[e] = gn;
-            gg = fma((double)gn, (double)gn, gg);
-            gm = fmax(gm, fabs((double)gn));
+            gg.add(gn, gn);
+            gm = fmax(gm, fabs(gn));
         }
     }
-    block_store(sy, false, p_sy);
-    block_store(yy, false, p_yy);
-    block_store(gg, false, p_gg);
-    block_store(gm, true, p_gmax);
+    block_store(sy.value(), false, p_sy);
+    block_store(yy.value(), false, p_yy);
+    block_store(gg.value(), false, p_gg);
+    block_store((double)gm, true, p_gmax);
 }
 
 // One warp per instance: store the pair (or not), convergence tests.
@@ -246,10 +248,9 @@ __global__ void __launch_bounds__(kThreads) k_loop1(
     }
     if (k < s.count) {
         const T *S = Sv[ring(s.head, k, m)];
-        double v = 0.0;
-        for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads)
-            v = fma((double)S[e], (double)q[e], v);
-        block_store(v, false, p_a[k]);
+        fresco::DotAcc<T> v;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads) v.add(S[e], q[e]);
+        block_store(v.value(), false, p_a[k]);
     }
 }
 
@@ -284,10 +285,9 @@ __global__ void __launch_bounds__(kThreads) k_loop2(
     }
     if (j < s.count) {
         const T *Y = Yv[ring(s.head, s.count - 1 - j, m)];
-        double v = 0.0;
-        for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads)
-            v = fma((double)Y[e], (double)r[e], v);
-        block_store(v, false, p_b[j]);
+        fresco::DotAcc<T> v;
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kThreads) v.add(Y[e], r[e]);
+        block_store(v.value(), false, p_b[j]);
     }
 }
 
@@ -301,17 +301,18 @@ __global__ void __launch_bounds__(kThreads) k_dir(const BLState *__restrict__ st
                                                   double *__restrict__ p_dmax) {
     const int c = blockIdx.x;
     const BLState &s = st[chunk_inst[c]];
-    double gd = 0.0, dm = 0.0;
+    fresco::DotAcc<T> gd;
+    T dm = T(0);
     if (running(s.act)) {
         for (int64_t e = chunk_lo[c] + threadIdx.x; e < chunk_lo[c + 1]; e += kThreads) {
             const T de = -d[e];
             d[e] = de;
-            gd = fma((double)g[e], (double)de, gd);
-            dm = fmax(dm, fabs((double)de));
+            gd.add(g[e], de);
+            dm = fmax(dm, fabs(de));
         }
     }
-    block_store(gd, false, p_gd);
-    block_store(dm, true, p_dmax);
+    block_store(gd.value(), false, p_gd);
+    block_store((double)dm, true, p_dmax);
 }
 
 // One warp per instance: descent check, first step of the line search.

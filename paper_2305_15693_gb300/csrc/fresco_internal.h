@@ -221,6 +221,41 @@ struct Launch {
     static int interp_smem(const Geom &g);
 };
 
+#ifdef __CUDACC__
+// Knuth's two-sum: s + e == a + b exactly (round to nearest, no overflow)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// One thread's running sum of products a_i b_i. FP32 operands: each product exactly as a float
+// pair (fmaf), summed into an unevaluated float pair by two-sum, and converted to FP64 once, so
+// the sum keeps about 48 bits without the narrow FP64 pipe in the loop; FP64 operands: FMA in
+// FP64.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float pe = fmaf(a, b, -p);
+        float s, e;
+        two_sum(hi, p, s, e);
+        hi = s;
+        lo += e + pe;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct DotAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double value() const { return v; }
+};
+#endif
+
 }  // namespace fresco
 
 // The plan object behind fresco_plan_t.

@@ -810,18 +810,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_b(
 // ---------------------------------------------------------------------------------------------
 // K4: deconvolve and crop to the mask, S, the loss partial sums and the gradient coefficients.
 // For each half-space representative n (n_x >= 0), with ip = 1 / Psi(n):
-//   rho = F(n) ip, S = |rho|^2 / N, loss += W' (S - S0')^2 (FP64),
+//   rho = F(n) ip, S = |rho|^2 / N, loss += W' (S - S0')^2 (to FP64 accuracy),
 //   E = 4 W' (S - S0') / N, a_d = i k_d E rho (Eq. 4 coefficient, both members of the +-n pair),
 //   H[n] = (a_x + i a_y) ip / 2 and H[-n] = (conj a_x + i conj a_y) ip / 2 (pipeline 0),
 //   H1[n] = a_z ip / 2, H1[-n] = conj(a_z) ip / 2 (pipeline 1, 3D).
 // The inverse FFT of H then gives d/dr_x + i d/dr_y on the grid (before interpolation).
-// Knuth's two-sum: s + e == a + b exactly (round to nearest, no overflow)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
 template <typename T, int D>
 __device__ __forceinline__ double mask_range(const MaskGeom &m, const int *__restrict__ rep_n,
                                              const T *__restrict__ rep_s0,

@@ -2,8 +2,8 @@
 // Eq. 4: L-BFGS with a maximal step size and a backtracking line search).
 //
 // All vectors (positions, gradients, search direction, the m (s, y) history pairs) stay on the
-// device in the plan's precision; every inner product is accumulated in FP64 with a fixed-order
-// two-stage reduction. The two-loop recursion keeps its scalars (rho_i, alpha_i, beta, gamma) in
+// device in the plan's precision; every inner product keeps FP64 accuracy (per thread a float
+// pair for FP32 vectors, fresco::DotAcc) and is reduced in FP64 in a fixed two-stage order. The two-loop recursion keeps its scalars (rho_i, alpha_i, beta, gamma) in
 // device memory, so it runs without host round trips; the host reads back two scalars per
 // line-search trial (the trial loss and, once per iteration, the slope and the step bound).
 //
@@ -45,10 +45,11 @@ __global__ void __launch_bounds__(kRedThreads) k_dot_part(const T *__restrict__ 
                                                           const T *__restrict__ b, int64_t n,
                                                           double *__restrict__ part) {
     __shared__ double ws[kRedThreads / 32];
-    double acc = 0.0;
+    fresco::DotAcc<T> dot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        acc = fma((double)a[i], (double)b[i], acc);
+        dot.add(a[i], b[i]);
+    double acc = dot.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
@@ -64,10 +65,11 @@ template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_absmax_part(const T *__restrict__ a, int64_t n,
                                                              double *__restrict__ part) {
     __shared__ double ws[kRedThreads / 32];
-    double m = 0.0;
+    T mt = T(0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        m = fmax(m, fabs((double)a[i]));
+        mt = fmax(mt, fabs(a[i]));
+    double m = (double)mt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
