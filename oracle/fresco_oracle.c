@@ -229,6 +229,66 @@ int oracle_weight_loss_grad(int dim, int64_t n_points, const double *r, const do
     return 0;
 }
 
+/* Weighted points at arbitrary real wavevectors (the weight-gradient form of Methods
+ * "Analytical gradients" with non-uniform k constraints, UwNU): the same quantities as
+ * oracle_weight_loss_grad, but each constraint is a wavevector k_q given directly
+ * (kvec [n_k][dim], any real values, free boundaries: no periodicity is assumed),
+ *   rho(k_q) = sum_j c_j exp(-i k_q . r_j),  rho0 = sum_j c_j^2,  S_q = |rho(k_q)|^2 / rho0,
+ *   L_S = sum_q W_q (S_q - S0_q)^2,
+ *   dL/dc_j = sum_q 2 W_q (S_q - S0_q) [2 Re(rho(k_q) e^{+i k_q . r_j}) / rho0 - 2 c_j S_q / rho0].
+ * Arguments as oracle_weight_loss_grad with kvec in place of (mask, box). */
+int oracle_weight_loss_grad_k(int dim, int64_t n_points, const double *r, const double *c,
+                              int64_t n_k, const double *kvec, const double *S0, const double *W,
+                              double *loss, double *S_out, double *rho_re_out,
+                              double *rho_im_out, double *grad)
+{
+    if (dim < 1 || dim > 3 || n_points <= 0 || n_k < 0) return 1;
+    double *re = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *im = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *S = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    if (!re || !im || !S) { free(re); free(im); free(S); return 2; }
+    double rho0 = 0.0;
+    for (int64_t j = 0; j < n_points; ++j) rho0 += c[j] * c[j];
+    if (!(rho0 > 0.0)) { free(re); free(im); free(S); return 3; }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_k; ++q) {
+        double complex acc = 0.0;
+        for (int64_t j = 0; j < n_points; ++j) {
+            double kr = 0.0;
+            for (int a = 0; a < dim; ++a) kr += kvec[q * dim + a] * r[j * dim + a];
+            acc += c[j] * cexp(-I * kr);
+        }
+        re[q] = creal(acc);
+        im[q] = cimag(acc);
+    }
+    double total = 0.0;
+    for (int64_t q = 0; q < n_k; ++q) {
+        S[q] = (re[q] * re[q] + im[q] * im[q]) / rho0;
+        double d = S[q] - S0[q];
+        total += W[q] * d * d;
+    }
+    *loss = total;
+    if (grad) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t j = 0; j < n_points; ++j) {
+            double g = 0.0;
+            for (int64_t q = 0; q < n_k; ++q) {
+                double kr = 0.0;
+                for (int a = 0; a < dim; ++a) kr += kvec[q * dim + a] * r[j * dim + a];
+                double complex rho = re[q] + I * im[q];
+                double dS = 2.0 * creal(rho * cexp(I * kr)) / rho0 - 2.0 * c[j] * S[q] / rho0;
+                g += 2.0 * W[q] * (S[q] - S0[q]) * dS;
+            }
+            grad[j] = g;
+        }
+    }
+    if (S_out) for (int64_t q = 0; q < n_k; ++q) S_out[q] = S[q];
+    if (rho_re_out) for (int64_t q = 0; q < n_k; ++q) rho_re_out[q] = re[q];
+    if (rho_im_out) for (int64_t q = 0; q < n_k; ++q) rho_im_out[q] = im[q];
+    free(re); free(im); free(S);
+    return 0;
+}
+
 int oracle_threads(void)
 {
 #ifdef _OPENMP

@@ -13,7 +13,10 @@ sign or index, a transposed operand, a wrong factor in the gradient):
 * central finite differences of the oracle's own loss against its gradient;
 * translation invariance: sum_j dL/dr_j = 0;
 * lattice with spacing finer than the mask (m > K): L = 0 and dL/dr = 0 (stealthy ground
-  state).
+  state);
+* weighted points at real wavevectors (non-uniform constraints): integer wavevectors reproduce
+  the separately written mask form, one and two weights have closed forms off the lattice, and
+  central differences pin the weight gradient.
 """
 
 import math
@@ -277,3 +280,60 @@ def test_unit_weights_reproduce_the_point_oracle():
     l2, _, S2, r2 = oracle.loss_grad(pts, mask, S0, W, want_grad=False)
     assert l1 == pytest.approx(l2, rel=1e-13)
     np.testing.assert_allclose(S1, S2, rtol=1e-12)
+
+
+# ---- weighted points at arbitrary real wavevectors (UwNU, Methods "Analytical gradients") -------
+
+def test_integer_wavevectors_reproduce_the_mask_form():
+    """With k = 2 pi n / L for integer n, the wavevector form equals the separately written
+    mask form on the same weighted grid (loss, gradient, S and rho)."""
+    g = inputs.rng(41)
+    shape, box = (7, 6), np.array([1.3, 0.8])
+    pts = oracle.grid_points(shape, box)
+    c = g.standard_normal(pts.shape[0])
+    mask = np.array([[1, 0], [0, 2], [-3, 1], [2, -2], [3, 2]], dtype=np.int32)
+    S0 = g.random(mask.shape[0])
+    W = 0.5 + g.random(mask.shape[0])
+    l1, g1, S1, r1 = oracle.weight_loss_grad(pts, c, mask, S0, W, box=box)
+    kvec = 2.0 * np.pi * mask / box
+    l2, g2, S2, r2 = oracle.weight_loss_grad_k(pts, c, kvec, S0, W)
+    assert l2 == pytest.approx(l1, rel=1e-12)
+    np.testing.assert_allclose(g2, g1, rtol=1e-10, atol=1e-12 * np.abs(g1).max())
+    np.testing.assert_allclose(S2, S1, rtol=1e-12)
+    np.testing.assert_allclose(r2, r1, rtol=1e-12, atol=1e-12)
+
+
+def test_wavevector_form_closed_forms_off_the_lattice():
+    """One weight: S = 1 at every k and no force. Two weights c1, c2 at distance dr:
+    S(k) = (c1^2 + c2^2 + 2 c1 c2 cos(k . dr)) / (c1^2 + c2^2) at non-integer k."""
+    k = np.array([[0.37, -2.11], [5.5, 0.25], [-1.0, 3.3]])
+    S0 = np.array([0.3, 1.2, 0.8])
+    W = np.array([1.0, 0.5, 2.0])
+    loss, grad, S, _ = oracle.weight_loss_grad_k(np.array([[0.4, -0.7]]), [2.5], k, S0, W)
+    np.testing.assert_allclose(S, 1.0, rtol=1e-14)
+    assert loss == pytest.approx(float(np.sum(W * (1.0 - S0) ** 2)), rel=1e-14)
+    assert abs(grad[0]) < 1e-13
+    r = np.array([[0.1, 0.2], [0.9, -0.4]])
+    c = np.array([1.5, -0.7])
+    _, _, S, _ = oracle.weight_loss_grad_k(r, c, k, S0, W, want_grad=False)
+    dr = r[0] - r[1]
+    ref = (c[0] ** 2 + c[1] ** 2 + 2 * c[0] * c[1] * np.cos(k @ dr)) / (c @ c)
+    np.testing.assert_allclose(S, ref, rtol=1e-13)
+
+
+def test_wavevector_form_gradient_matches_central_differences():
+    g = inputs.rng(43)
+    pts = oracle.grid_points((5, 4, 3))
+    c = g.standard_normal(pts.shape[0])
+    k = g.uniform(-9.0, 9.0, (11, 3))
+    S0 = g.random(11)
+    W = 0.5 + g.random(11)
+    _, grad, _, _ = oracle.weight_loss_grad_k(pts, c, k, S0, W)
+    h = 1e-6
+    for j in (0, 7, 31, 59):
+        cp, cm = c.copy(), c.copy()
+        cp[j] += h
+        cm[j] -= h
+        lp = oracle.weight_loss_grad_k(pts, cp, k, S0, W, want_grad=False)[0]
+        lm = oracle.weight_loss_grad_k(pts, cm, k, S0, W, want_grad=False)[0]
+        assert grad[j] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-8)
