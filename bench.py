@@ -728,11 +728,16 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+# the sources that build (and size the launches of) the kernels the traffic entries describe
+TRAFFIC_SOURCES = ("fresco_host.cu", "fresco_internal.h", "fresco_kernels.cuh",
+                   "fresco_kernels_f32.cu", "fresco_kernels_f64.cu")
+
+
 def _kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in TRAFFIC_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

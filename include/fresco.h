@@ -375,6 +375,42 @@ fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, c
 fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad);
 fresco_status fresco_uwu_destroy(fresco_uwu_t u);
 
+/* ---- Weights on a uniform grid, constraints at real frequencies (UwNU, Methods "Analytical
+ * gradients") ---------------------------------------------------------------------------------
+ * The same weighted grid as fresco_uwu_plan with free boundaries: constraint q sits at a real
+ * frequency nu_q (cycles per grid length along each axis; any value, not only integers),
+ *   rho(nu) = sum_m c_m e^{-2 pi i sum_a nu_a m_a / M_a},  rho0 = sum_m c_m^2,  S = |rho|^2 / rho0,
+ *   L = sum_q W_q (S_q - S0_q)^2,
+ *   dL/dc_m = Re sum_q [4 W (S - S0) rho / rho0]_q e^{+2 pi i sum_a nu_qa m_a / M_a}
+ *             - (4 c_m / rho0) sum_q W S (S - S0).
+ * As Methods states for this variant, S comes from one type-2 NUFFT of the weights (deconvolve,
+ * inverse FFT on the oversampled grid, interpolate at the constraints) and the gradient from one
+ * type-1 NUFFT of the per-constraint coefficients (spread, forward FFT, deconvolve), both with the
+ * exponential-of-semicircle kernel: accurate to the tolerance, not exact. At integer nu the
+ * quantities are those of fresco_uwu_plan. Constraints are not folded: +nu and -nu are separate
+ * terms if both are given.
+ * grid: host [dim] cell counts, 2 .. 2^20 each (odd allowed); nu: host [n_k][dim] double, finite;
+ * S0, W: host [n_k] (W >= 0); opts: precision, tol (0: 1e-6 F32, 1e-12 F64) and upsample (0: 2.0,
+ * in [1.25, 3]) are used, the other fields are ignored; NULL = defaults. The fine grid per axis is
+ * the smallest even 2-3-5-7-smooth size >= max(sigma M_a, 2 w). FRESCO_ERR_ARG for invalid
+ * arguments, FRESCO_ERR_UNSUPPORTED when the fine grid exceeds 4e9 cells or w > 16. The plan owns
+ * copies of the constraints, its fine grid and its cuFFT plan; it computes asynchronously on
+ * `stream`. */
+typedef struct fresco_uwnu_s *fresco_uwnu_t;
+fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid, int64_t n_k,
+                               const double *nu, const double *S0, const double *W,
+                               const fresco_opts *opts, void *stream);
+/* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
+ * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. */
+fresco_status fresco_uwnu_loss_grad(fresco_uwnu_t u, const void *d_c, double *d_loss,
+                                    void *d_grad);
+/* After fresco_uwnu_loss_grad: S at the constraints into d_S (device [n_k], plan precision, in
+ * the order given to the plan). FRESCO_ERR_ARG before the first evaluation. */
+fresco_status fresco_uwnu_get_S(fresco_uwnu_t u, void *d_S);
+/* Kernel width, shape parameter beta and fine grid (n_fine[3], 1 beyond dim); any may be NULL. */
+fresco_status fresco_uwnu_get_info(fresco_uwnu_t u, int *width, double *beta, int *n_fine);
+fresco_status fresco_uwnu_destroy(fresco_uwnu_t u);
+
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);
 

@@ -49,6 +49,8 @@ EXPORTS = (
     "fresco_batch_lbfgs_read", "fresco_batch_lbfgs_destroy", "fresco_batch_profile",
     "fresco_batch_profile_read", "fresco_batch_get_info",
     "fresco_uwu_plan", "fresco_uwu_loss_grad", "fresco_uwu_destroy",
+    "fresco_uwnu_plan", "fresco_uwnu_loss_grad", "fresco_uwnu_get_S", "fresco_uwnu_get_info",
+    "fresco_uwnu_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -162,6 +164,11 @@ def load(path: str = LIB_PATH):
             "fresco_uwu_plan": (I, [P, I, P, P, I64, P, P, I, P]),
             "fresco_uwu_loss_grad": (I, [P, P, P, P]),
             "fresco_uwu_destroy": (I, [P]),
+            "fresco_uwnu_plan": (I, [P, I, P, I64, P, P, P, P, P]),
+            "fresco_uwnu_loss_grad": (I, [P, P, P, P]),
+            "fresco_uwnu_get_S": (I, [P, P]),
+            "fresco_uwnu_get_info": (I, [P, P, P, P]),
+            "fresco_uwnu_destroy": (I, [P]),
         })
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -612,6 +619,101 @@ class Uwu:
     def close(self):
         if getattr(self, "handle", None):
             fresco_uwu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fresco_uwnu_plan(grid_shape, nu, S0, W, opts=None, stream=None):
+    """Plan for real weights on a uniform grid with constraints at real frequencies nu [n_k, dim]
+    (cycles per grid length; grid_shape = (M_0, M_1[, M_2]), x first)."""
+    lib = load()
+    nu = np.ascontiguousarray(np.asarray(nu, dtype=np.float64))
+    dim = nu.shape[1]
+    grid = np.ascontiguousarray(np.asarray(grid_shape, dtype=np.int64).reshape(-1))
+    if grid.size != dim:
+        raise ValueError("one grid size per axis")
+    S0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    if S0.size != nu.shape[0] or W.size != nu.shape[0]:
+        raise ValueError("one S0 and one W per constraint")
+    h = ctypes.c_void_p()
+    _check(lib.fresco_uwnu_plan(ctypes.byref(h), dim, grid.ctypes.data, nu.shape[0],
+                                nu.ctypes.data, S0.ctypes.data, W.ctypes.data,
+                                ctypes.byref(opts) if opts is not None else None,
+                                _stream_handle(stream)), "fresco_uwnu_plan")
+    return h.value
+
+
+def fresco_uwnu_loss_grad(plan, c, loss, grad=None):
+    _check(load().fresco_uwnu_loss_grad(plan, _addr(c), _addr(loss), _addr(grad)),
+           "fresco_uwnu_loss_grad")
+
+
+def fresco_uwnu_get_S(plan, S):
+    _check(load().fresco_uwnu_get_S(plan, _addr(S)), "fresco_uwnu_get_S")
+
+
+def fresco_uwnu_get_info(plan) -> dict:
+    w = ctypes.c_int()
+    beta = ctypes.c_double()
+    nf = (ctypes.c_int * 3)()
+    _check(load().fresco_uwnu_get_info(plan, ctypes.byref(w), ctypes.byref(beta), nf),
+           "fresco_uwnu_get_info")
+    return {"width": w.value, "beta": beta.value, "n_fine": list(nf)}
+
+
+def fresco_uwnu_destroy(plan):
+    _check(load().fresco_uwnu_destroy(plan), "fresco_uwnu_destroy")
+
+
+class Uwnu:
+    """Weights on a uniform grid with constraints at real frequencies (fresco_uwnu_* in
+    include/fresco.h). Weights and gradients are CUDA tensors of shape grid_shape[::-1] (x the
+    last, contiguous index) in the plan's dtype."""
+
+    def __init__(self, grid_shape, nu, S0, W, precision="f32", tol=0.0, upsample=2.0,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.shape = tuple(int(x) for x in grid_shape)[::-1]
+        self.n_k = int(np.asarray(nu).shape[0])
+        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opts = make_opts(precision=precision, tol=tol, upsample=upsample)
+        self.handle = fresco_uwnu_plan(grid_shape, nu, S0, W, opts, self.stream)
+        self.info = fresco_uwnu_get_info(self.handle)
+
+    def loss_grad(self, c, want_grad=True):
+        t = self._torch
+        if (not c.is_cuda or c.dtype != self.dtype or not c.is_contiguous()
+                or tuple(c.shape) != self.shape):
+            raise ValueError("weights must be a contiguous CUDA %s tensor %s" % (self.dtype,
+                                                                                   self.shape))
+        loss = t.empty((), dtype=t.float64, device=c.device)
+        grad = t.empty_like(c) if want_grad else None
+        fresco_uwnu_loss_grad(self.handle, c, loss, grad)
+        return loss, grad
+
+    def S(self):
+        t = self._torch
+        out = t.empty(self.n_k, dtype=self.dtype, device="cuda")
+        fresco_uwnu_get_S(self.handle, out)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_uwnu_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
