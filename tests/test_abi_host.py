@@ -192,3 +192,49 @@ def test_argument_errors(fr, bad):
     with pytest.raises(fr.FrescoError) as e:
         fr.fresco_plan_query(1.0, mask, S0, W, n, fr.make_opts(**kw))
     assert e.value.status == fr.FRESCO_ERR_ARG
+
+
+@pytest.mark.parametrize("bad", ["grid_small", "grid_big", "dim4", "nan_nu", "huge_nu", "neg_w",
+                                 "nan_s0", "n0", "tol", "sigma"])
+def test_uwnu_argument_errors(fr, bad):
+    """fresco_uwnu_plan rejects invalid arguments before it touches the device."""
+    grid = (16, 12)
+    nu = np.array([[0.5, -1.25], [3.0, 2.5], [-7.5, 0.0]])
+    S0 = np.zeros(3)
+    W = np.ones(3)
+    kw = {}
+    if bad == "grid_small":
+        grid = (1, 12)
+    elif bad == "grid_big":
+        grid = (16, (1 << 20) + 2)
+    elif bad == "dim4":
+        grid = (4, 4, 4, 4)
+        nu = np.ones((3, 4))
+    elif bad == "nan_nu":
+        nu[1, 0] = np.nan
+    elif bad == "huge_nu":
+        nu[2, 1] = 3e9
+    elif bad == "neg_w":
+        W[2] = -1.0
+    elif bad == "nan_s0":
+        S0[0] = np.inf
+    elif bad == "n0":
+        nu = np.zeros((0, 2))
+        S0 = np.zeros(0)
+        W = np.zeros(0)
+    elif bad == "tol":
+        kw["tol"] = 1.5
+    elif bad == "sigma":
+        kw["upsample"] = 3.5
+    with pytest.raises(fr.FrescoError) as e:
+        fr.fresco_uwnu_plan(grid, nu, S0, W, fr.make_opts(**kw))
+    assert e.value.status == fr.FRESCO_ERR_ARG
+
+
+def test_uwnu_unsupported_sizes(fr):
+    nu = np.array([[0.5, 1.5]])
+    for grid, kw in (((1 << 20, 1 << 20), {}),                        # fine grid > 4e9 cells
+                     ((64, 64), {"precision": "f64", "tol": 1e-15, "upsample": 1.25})):   # w > 16
+        with pytest.raises(fr.FrescoError) as e:
+            fr.fresco_uwnu_plan(grid, nu, [0.0], [1.0], fr.make_opts(**kw))
+        assert e.value.status == fr.FRESCO_ERR_UNSUPPORTED
