@@ -58,6 +58,9 @@ def _load():
             lib.oracle_weight_loss_grad_k.argtypes = [ctypes.c_int, i64, p, p, i64, p, p, p, p,
                                                       p, p, p, p]
             lib.oracle_weight_loss_grad_k.restype = ctypes.c_int
+            lib.oracle_loss_grad_k.argtypes = [ctypes.c_int, i64, p, i64, p, p, p, p, p, p, p,
+                                               p]
+            lib.oracle_loss_grad_k.restype = ctypes.c_int
             lib.oracle_threads.argtypes = []
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
@@ -149,6 +152,28 @@ def weight_loss_grad(points, weights, mask, S0, W, box=1.0, want_grad=True):
                                          _ptr(im), _ptr(grad))
     if rc != 0:
         raise ValueError("oracle_weight_loss_grad failed (%d)" % rc)
+    return float(loss[0]), grad, S, re + 1j * im
+
+
+def loss_grad_k(points, kvec, S0, W, want_grad=True):
+    """Unit-weight points at arbitrary real wavevectors kvec [n_k, dim] (non-uniform constraints,
+    free boundaries): rho = sum_j e^{-ik.r_j}, S = |rho|^2 / N.
+    Returns (loss, dL/dr [N, dim] or None, S, rho)."""
+    r = np.ascontiguousarray(np.asarray(points).astype(np.float64))
+    dim = r.shape[1]
+    k = np.ascontiguousarray(np.asarray(kvec, dtype=np.float64).reshape(-1, dim))
+    s0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    w = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    n_k = k.shape[0]
+    loss = np.zeros(1)
+    S = np.empty(n_k)
+    re = np.empty(n_k)
+    im = np.empty(n_k)
+    grad = np.empty_like(r) if want_grad else None
+    rc = _load().oracle_loss_grad_k(dim, r.shape[0], _ptr(r), n_k, _ptr(k), _ptr(s0), _ptr(w),
+                                    _ptr(loss), _ptr(S), _ptr(re), _ptr(im), _ptr(grad))
+    if rc != 0:
+        raise ValueError("oracle_loss_grad_k failed (%d)" % rc)
     return float(loss[0]), grad, S, re + 1j * im
 
 

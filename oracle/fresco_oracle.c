@@ -171,6 +171,67 @@ int oracle_pair_energy_grad(int dim, int64_t n_points, const double *r, const do
     return 0;
 }
 
+/* Points at arbitrary real wavevectors (the position gradient with non-uniform k constraints and
+ * free boundaries, NUwNU, Methods "Analytical gradients"): unit weights, each constraint a
+ * wavevector k_q given directly (kvec [n_k][dim], any real values; nothing is periodic),
+ *   rho(k_q) = sum_j exp(-i k_q . r_j),  S_q = |rho(k_q)|^2 / N,  L = sum_q W_q (S_q - S0_q)^2,
+ * and the gradient by the chain rule per (point, wavevector) pair,
+ *   dS_q/dr_j = (2 / N) Re[conj(rho_q) d rho_q / dr_j],  d rho_q / dr_j = -i k_q e^{-i k_q . r_j},
+ *   dL/dr_j = sum_q 2 W_q (S_q - S0_q) dS_q/dr_j.
+ * grad: out [n_points][dim] or NULL; the other outputs as oracle_loss_grad. */
+int oracle_loss_grad_k(int dim, int64_t n_points, const double *r, int64_t n_k,
+                       const double *kvec, const double *S0, const double *W, double *loss,
+                       double *S_out, double *rho_re_out, double *rho_im_out, double *grad)
+{
+    if (dim < 1 || dim > 3 || n_points <= 0 || n_k < 0) return 1;
+    double *re = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *im = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    double *S = (double *)malloc(sizeof(double) * (size_t)(n_k > 0 ? n_k : 1));
+    if (!re || !im || !S) { free(re); free(im); free(S); return 2; }
+    const double N = (double)n_points;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t q = 0; q < n_k; ++q) {
+        double complex acc = 0.0;
+        for (int64_t j = 0; j < n_points; ++j) {
+            double kr = 0.0;
+            for (int a = 0; a < dim; ++a) kr += kvec[q * dim + a] * r[j * dim + a];
+            acc += cexp(-I * kr);
+        }
+        re[q] = creal(acc);
+        im[q] = cimag(acc);
+    }
+    double total = 0.0;
+    for (int64_t q = 0; q < n_k; ++q) {
+        S[q] = (re[q] * re[q] + im[q] * im[q]) / N;
+        double d = S[q] - S0[q];
+        total += W[q] * d * d;
+    }
+    *loss = total;
+    if (grad) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t j = 0; j < n_points; ++j) {
+            double g[3] = {0.0, 0.0, 0.0};
+            for (int64_t q = 0; q < n_k; ++q) {
+                double kr = 0.0;
+                for (int a = 0; a < dim; ++a) kr += kvec[q * dim + a] * r[j * dim + a];
+                const double complex conj_rho = re[q] - I * im[q];
+                const double complex e = cexp(-I * kr);
+                const double pre = 2.0 * W[q] * (S[q] - S0[q]) * 2.0 / N;
+                for (int a = 0; a < dim; ++a) {
+                    const double complex drho = -I * kvec[q * dim + a] * e;
+                    g[a] += pre * creal(conj_rho * drho);
+                }
+            }
+            for (int a = 0; a < dim; ++a) grad[j * dim + a] = g[a];
+        }
+    }
+    if (S_out) for (int64_t q = 0; q < n_k; ++q) S_out[q] = S[q];
+    if (rho_re_out) for (int64_t q = 0; q < n_k; ++q) rho_re_out[q] = re[q];
+    if (rho_im_out) for (int64_t q = 0; q < n_k; ++q) rho_im_out[q] = im[q];
+    free(re); free(im); free(S);
+    return 0;
+}
+
 /* Threads the OpenMP runtime will use (1 without OpenMP). */
 /* Weighted points (the "UwU" / "UwNU" weight-gradient forms of Methods "Analytical
  * gradients"): real weights c_j at fixed positions r_j,

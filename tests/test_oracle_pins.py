@@ -16,7 +16,10 @@ sign or index, a transposed operand, a wrong factor in the gradient):
   state);
 * weighted points at real wavevectors (non-uniform constraints): integer wavevectors reproduce
   the separately written mask form, one and two weights have closed forms off the lattice, and
-  central differences pin the weight gradient.
+  central differences pin the weight gradient;
+* unit-weight points at real wavevectors (free boundaries): the same reduction to the mask form,
+  N = 1 and N = 2 closed forms off the lattice (S and the forces), central differences in 3D and
+  invariance under a rigid shift.
 """
 
 import math
@@ -337,3 +340,61 @@ def test_wavevector_form_gradient_matches_central_differences():
         lp = oracle.weight_loss_grad_k(pts, cp, k, S0, W, want_grad=False)[0]
         lm = oracle.weight_loss_grad_k(pts, cm, k, S0, W, want_grad=False)[0]
         assert grad[j] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-8)
+
+
+# ---- points at arbitrary real wavevectors (NUwNU, free boundaries) ------------------------------
+
+def test_point_form_at_integer_wavevectors_reproduces_the_mask_form():
+    g = inputs.rng(51)
+    box = np.array([1.3, 0.7])
+    pts = g.random((40, 2)) * box
+    mask = np.array([[1, 0], [0, 3], [-2, 1], [4, -1], [2, 2]], dtype=np.int32)
+    S0 = g.random(5)
+    W = 0.5 + g.random(5)
+    l1, g1, S1, r1 = oracle.loss_grad(pts, mask, S0, W, box=box)
+    l2, g2, S2, r2 = oracle.loss_grad_k(pts, 2.0 * np.pi * mask / box, S0, W)
+    assert l2 == pytest.approx(l1, rel=1e-12)
+    np.testing.assert_allclose(g2, g1, rtol=1e-10, atol=1e-12 * np.abs(g1).max())
+    np.testing.assert_allclose(S2, S1, rtol=1e-12)
+    np.testing.assert_allclose(r2, r1, rtol=1e-12, atol=1e-12)
+
+
+def test_point_form_closed_forms_off_the_lattice():
+    """N = 1: S = 1, no force. N = 2 at non-integer k: S = 1 + cos(k . dr) and
+    dL/dr_1 = -sum_q 2 W (S - S0) sin(k . dr) k = -dL/dr_2."""
+    k = np.array([[0.37, -2.11], [5.5, 0.25], [-1.0, 3.3]])
+    S0 = np.array([0.3, 1.2, 0.8])
+    W = np.array([1.0, 0.5, 2.0])
+    loss, grad, S, _ = oracle.loss_grad_k(np.array([[0.4, -0.7]]), k, S0, W)
+    np.testing.assert_allclose(S, 1.0, rtol=1e-14)
+    assert loss == pytest.approx(float(np.sum(W * (1.0 - S0) ** 2)), rel=1e-14)
+    assert np.abs(grad).max() < 1e-13
+    r = np.array([[0.1, 0.2], [0.9, -0.4]])
+    loss, grad, S, _ = oracle.loss_grad_k(r, k, S0, W)
+    ph = k @ (r[0] - r[1])
+    np.testing.assert_allclose(S, 1.0 + np.cos(ph), rtol=1e-13)
+    assert loss == pytest.approx(float(np.sum(W * (1.0 + np.cos(ph) - S0) ** 2)), rel=1e-13)
+    g1 = -(2.0 * W * (1.0 + np.cos(ph) - S0) * np.sin(ph)) @ k
+    np.testing.assert_allclose(grad[0], g1, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(grad[1], -g1, rtol=1e-12, atol=1e-14)
+
+
+def test_point_form_central_differences_and_translation():
+    g = inputs.rng(53)
+    pts = g.random((30, 3)) * 2.0 - 0.5
+    k = g.uniform(-12.0, 12.0, (17, 3))
+    S0 = g.random(17)
+    W = 0.5 + g.random(17)
+    loss, grad, _, _ = oracle.loss_grad_k(pts, k, S0, W)
+    h = 1e-6
+    for j, a in ((0, 0), (7, 1), (29, 2)):
+        pp, pm = pts.copy(), pts.copy()
+        pp[j, a] += h
+        pm[j, a] -= h
+        lp = oracle.loss_grad_k(pp, k, S0, W, want_grad=False)[0]
+        lm = oracle.loss_grad_k(pm, k, S0, W, want_grad=False)[0]
+        assert grad[j, a] == pytest.approx((lp - lm) / (2 * h), rel=1e-6, abs=1e-8)
+    # a rigid shift multiplies every rho by a phase: L unchanged and the forces sum to zero
+    shifted = oracle.loss_grad_k(pts + np.array([0.3, -1.7, 2.9]), k, S0, W, want_grad=False)[0]
+    assert shifted == pytest.approx(loss, rel=1e-12)
+    np.testing.assert_allclose(grad.sum(axis=0), 0.0, atol=1e-10 * np.abs(grad).max())
