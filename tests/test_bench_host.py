@@ -1,0 +1,68 @@
+"""CPU checks of bench.py's host logic that shapes the reported numbers: the algorithmic bytes per
+stage (the roofline numerators) at the bench workload's sizes, and the clock record's reduction
+of nvidia-smi samples (median SM clock, throttle reasons seen)."""
+
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _info(grad_mode, dim=2, nf=20736, kx=6180, n_rep=59_992_318):
+    return {"dim": dim, "n_fine": [nf] * dim + [1] * (3 - dim), "k_max": [kx] * dim + [0] * (3 - dim),
+            "n_rep": n_rep, "grad_mode": grad_mode}
+
+
+def test_stage_bytes_per_unit_fp32_2d_kderiv():
+    N, nf = 100_000_000, 20736
+    cells = nf * nf
+    b = bench.stage_bytes(_info(1), N, 4)
+    assert b["sort"] == 20 * N                                   # 8 read + 8 packed + 4 index
+    assert b["spread"] == 8 * N + 4 * cells
+    assert b["mask"] == 32 * 59_992_318                          # n (8) + S0, W (8) + F (8) + E (8)
+    assert b["interp"] == 4 * cells + 20 * N
+    assert b["fft_fwd"] == 4 * cells + nf * (nf // 2 + 1) * 8    # real grid in, half spectrum out
+    assert b["fft_inv"] == nf * (6180 + 1) * 8 + 4 * cells
+    assert b["loss"] == 0
+
+
+def test_stage_bytes_direct_mode_and_3d():
+    N = 1 << 24
+    b2 = bench.stage_bytes(_info(0, nf=4096, kx=1000, n_rep=10), N, 4)
+    cells = 4096 * 4096
+    assert b2["interp"] == cells * 8 + 20 * N                    # one complex grid (x + iy)
+    assert b2["mask"] == 10 * (8 + 8 + 8 + 2 * 8)
+    b3 = bench.stage_bytes(_info(1, dim=3, nf=648, kx=193, n_rep=15_055_467), N, 4)
+    cells = 648 ** 3
+    assert b3["sort"] == N * (12 + 16 + 4)
+    assert b3["interp"] == 4 * cells + N * (16 + 4 + 12)
+    b3f64 = bench.stage_bytes(_info(1, dim=3, nf=648, kx=193, n_rep=15_055_467), N, 8)
+    assert b3f64["spread"] == 2 * b3["spread"]
+
+
+def test_clock_record_reduction():
+    c = bench.ClockSampler(None)
+    c.proc = None
+    assert c.stop() is None                                      # no sampler, no record
+
+    class _P:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler(None)
+    c.proc = _P()
+    c.rows = [["2070", "2070", "700", "0x0", "Not Active", "Not Active", "Not Active", "Active"],
+              ["2055", "2070", "710", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+              ["1980", "2070", "720", "0x8", "Active", "Not Active", "Not Active", "Not Active"],
+              ["[N/A]", "2070", "0", "0x0", "", "", "", ""]]
+    rec = c.stop()
+    assert rec["samples"] == 3
+    assert rec["sm_mhz"] == pytest.approx(2055.0)
+    assert rec["sm_max_mhz"] == 2070.0
+    assert rec["reasons"] == ["hw_slowdown", "sw_power_cap"]
