@@ -662,7 +662,11 @@ def main():
         with open(tfile) as f:
             tr = json.load(f)
         entry = tr.get(wl.name, {}).get(dom)
-        if entry and entry.get("source_hash") == _kernel_source_hash():
+        try:
+            current = _kernel_source_hash()
+        except OSError:   # a listed source is missing: the entry cannot be matched
+            current = None
+        if entry and current and entry.get("source_hash") == current:
             traffic = entry.get("bytes_per_launch")
     roofline = {"bound": "hbm", "achieved": per_stage[dom]["GB/s"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": per_stage[dom]["frac"], "traffic": traffic,

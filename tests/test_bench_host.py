@@ -66,3 +66,12 @@ def test_clock_record_reduction():
     assert rec["sm_mhz"] == pytest.approx(2055.0)
     assert rec["sm_max_mhz"] == 2070.0
     assert rec["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_traffic_sources_exist_and_hash_is_stable():
+    csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2305_15693_gb300", "csrc")
+    for name in bench.TRAFFIC_SOURCES:
+        assert os.path.isfile(os.path.join(csrc, name)), name
+    h = bench._kernel_source_hash()
+    assert len(h) == 16 and h == bench._kernel_source_hash()
