@@ -222,10 +222,11 @@ def time_e2e(plan, pts_np, steps, warmup):
     return dt, a_pts.nbytes, a_grad.nbytes + 8
 
 
-def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2):
+def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2, min_rows=16):
     """The oracle timed on the host cores on a bounded sample: rho at a seeded sample of mask rows
-    over all N points (direct sums). A full evaluation costs rho over all N_K rows plus the
-    gradient over all N points x N_K rows: about 2 N N_K pair terms at the same per-term cost."""
+    (at least min_rows, more while they fit the budget) over all N points (direct sums). A full
+    evaluation costs rho over all N_K rows plus the gradient over all N points x N_K rows: about
+    2 N N_K pair terms at the same per-term cost."""
     import oracle
     N = pts_np.shape[0]
     n_k = mask.shape[0]
@@ -236,7 +237,7 @@ def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2):
     oracle.rho(r64, probe, box)
     t_probe = max(time.perf_counter() - t0, 1e-6)
     per_row = t_probe / 2
-    n_s = int(max(2, min(256, budget_s / per_row)))
+    n_s = int(max(min(min_rows, n_k), min(256, n_k, budget_s / per_row)))
     rows = np.sort(g.choice(n_k, n_s, replace=False))
     sample = mask[rows]
     t0 = time.perf_counter()
@@ -249,6 +250,59 @@ def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2):
                        "extrapolated as 2*N*N_K pair terms at the measured %.3e terms/s"
                        % (n_s, n_k, N, t, rate),
              "seconds_per_eval_extrapolated": t_eval}, rows, rho)
+
+
+def rho_error_report(got, want, rows_n, K, n_bins=4):
+    """rho of the GPU against the oracle at sampled mask rows: relative L2 over the rows, the
+    largest per-row error |got - want| relative to the rows' RMS |want| (|rho| ~ sqrt(N) for
+    uniform points, so a single row's own |rho| can be near zero), and the relative L2 per bin of
+    |n| / K."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    err = np.abs(got - want)
+    rms = float(np.sqrt(np.mean(np.abs(want) ** 2)))
+    r = np.linalg.norm(np.asarray(rows_n, dtype=np.float64), axis=1) / float(K)
+    edges = np.linspace(0.0, 1.0, n_bins + 1)
+    bins = []
+    for b in range(n_bins):
+        sel = (r > edges[b]) & (r <= edges[b + 1]) if b else (r <= edges[b + 1])
+        if np.any(sel):
+            bins.append({"n_over_K": [float(edges[b]), float(edges[b + 1])],
+                         "rows": int(sel.sum()),
+                         "rel_l2": float(np.linalg.norm(got[sel] - want[sel]) /
+                                         np.linalg.norm(want[sel]))})
+    return {"rows": int(got.size),
+            "rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+            "max_row_err_over_rms": float(err.max() / rms) if rms > 0 else None,
+            "by_n_over_K": bins}
+
+
+def smem_peaks(device="cuda"):
+    """Conflict-free shared-memory 32-bit atomic adds and loads per second, measured now on this
+    GPU (fresco_smem_peak)."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    sink = torch.zeros(8 * torch.cuda.get_device_properties(device).multi_processor_count,
+                       dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+    return {"atomic_add": fresco.fresco_smem_peak(fresco.FRESCO_SMEM_ATOMIC_ADD, sink, stream),
+            "load": fresco.fresco_smem_peak(fresco.FRESCO_SMEM_LOAD, sink, stream)}
+
+
+def smem_rooflines(per_stage: dict, n_points: int, dim: int, width: int, peaks: dict) -> dict:
+    """Spread and interpolation against the shared-memory pipe that binds them: every point costs
+    w^d 32-bit atomic adds (spread) or w^d 32-bit loads (interpolation) of shared memory."""
+    ops = float(n_points) * width ** dim
+    out = {}
+    for stage, op in (("spread", "atomic_add"), ("interp", "load")):
+        if stage not in per_stage or op not in peaks:
+            continue
+        rate = ops / (per_stage[stage]["ms"] * 1e-3)
+        out[stage] = {"op": "shared 32-bit " + op.replace("_", " "), "ops_per_launch": ops,
+                      "achieved_ops_per_s": rate, "peak_ops_per_s": peaks[op],
+                      "frac": round(rate / peaks[op], 4),
+                      "peak_source": "fresco_smem_peak, measured in this run (conflict-free)"}
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -279,10 +333,13 @@ def run_reference(args, wl, rank, world):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_eval, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "n_points": N, "K": wl.K, "n_modes": n_k,
                    "parallelism": "replicas"},
+        # ms_per_step is the measured time of one step (the bounded sample); a full evaluation at
+        # the measured pair-term rate would take this long:
+        "ms_per_eval_extrapolated": 1e3 * t_eval,
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.threads(),
                          "kind": "oracle",
                          "sample": "per step: rho at %d seeded mask rows over all %d points by "
@@ -444,11 +501,12 @@ def run_ensemble(args, ens, rank, world, local_rank, dist_on):
         gbs = sb[name] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
         per_stage[name] = {"ms": round(avg, 4), "alg_bytes": int(sb[name]),
                            "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
-    ours = {k: v for k, v in per_stage.items() if k in ("spread", "interp", "mask")}
+    ours = {k: v for k, v in per_stage.items() if k in ("sort", "spread", "interp", "mask")}
     dom = max(ours, key=lambda k: ours[k]["ms"])
     roofline = {"bound": "hbm", "achieved": per_stage[dom]["GB/s"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": per_stage[dom]["frac"], "traffic": None, "kernel": dom,
                 "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+    smem_roof = smem_rooflines(per_stage, n_tot, 2, infos[0]["width"], smem_peaks())
     b.close()
 
     # ---- all-FP64 batch on the same ensemble ------------------------------------------------
@@ -495,6 +553,7 @@ def run_ensemble(args, ens, rank, world, local_rank, dist_on):
                             "iterations_median": float(np.median([r["iterations"]
                                                                   for r in reps]))},
             "roofline": roofline,
+            "smem_roofline": smem_roof,
             "stages": per_stage,
             "fp64": f64,
             "cpu_baseline": cpu,
@@ -515,16 +574,19 @@ def run_reference_ensemble(args, ens, rank):
     import oracle
     oracle.build()
     pts_np, masks, _, _ = ensemble_inputs(ens)
-    times = []
+    times, samples = [], []
     for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         rate, terms, _ = ensemble_cpu_rate(ens, pts_np, masks, budget_s=5.0, seed=10 + k)
         if k >= args.warmup:
             times.append(terms / rate)
+            samples.append(time.perf_counter() - t0)
     t = float(np.mean(times))
     value = ens.n_inst / t
     line = {
         "impl": "reference", "metric": ENS_METRIC, "value": value, "unit": "configurations/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(samples)), "ms_per_eval_extrapolated": 1e3 * t,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": ens.name, "n_inst": ens.n_inst,
@@ -538,6 +600,56 @@ def run_reference_ensemble(args, ens, rank):
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_accuracy(args, wl):
+    """Where the FP32 path's rho error comes from, on the same points: rho at seeded mask rows by
+    the oracle's direct sums against (a) the FP32 plan, (b) an FP64 plan with the same grid and
+    kernel width (FP64 arithmetic, the same truncation of the kernel), (c) the FP64 plan at
+    tolerance 1e-12. (b) - oracle is the truncation error of the kernel at the plan's tolerance,
+    (a) - (b) the FP32 arithmetic (fixed-point spread, FP32 transforms, deconvolution); both binned
+    by |n| / K, where 1 / Psi grows toward the mask edge."""
+    import torch
+    import oracle
+    from paper_2305_15693_gb300 import _build, fresco
+    _build.build()
+    oracle.build()
+    pts_np, mask, S0, W = make_inputs(wl)
+    N = wl.n_points
+    g = np.random.Generator(np.random.Philox(args.accuracy_seed))
+    rows = np.sort(g.choice(mask.shape[0], args.accuracy_rows, replace=False))
+    sel = torch.from_numpy(rows).cuda()
+    pts = torch.from_numpy(pts_np).cuda()
+    out = {"workload": wl.name, "rows": int(len(rows)), "seed": args.accuracy_seed}
+
+    def rho_at(precision, tol, upsample, width=0):
+        p = pts if precision == wl.dtype else pts.double()
+        with fresco.Plan(wl.box, mask, S0, W, N, precision=precision, tol=tol,
+                         upsample=upsample, width=width, grad_mode=wl.grad_mode) as plan:
+            plan.forward(p)
+            r, _ = plan.rho_S()
+            got = r[sel].double().cpu().numpy()
+            info = plan.info
+        return got[:, 0] + 1j * got[:, 1], info
+
+    rho32, info32 = rho_at(wl.dtype, wl.tol, wl.upsample)
+    rho64k, info64k = rho_at("f64", wl.tol, wl.upsample, width=info32["width"])
+    rho64, info64 = rho_at("f64", 1e-12, 2.0)
+    t0 = time.perf_counter()
+    want = oracle.rho(np.ascontiguousarray(pts_np, dtype=np.float64), mask[rows], wl.box)
+    out["oracle_seconds"] = time.perf_counter() - t0
+    out["oracle_cores"] = oracle.threads()
+    out["plans"] = {"f32": {"width": info32["width"], "n_fine": info32["n_fine"][:wl.dim]},
+                    "f64_same_kernel": {"width": info64k["width"],
+                                        "n_fine": info64k["n_fine"][:wl.dim]},
+                    "f64_tol_1e-12": {"width": info64["width"],
+                                      "n_fine": info64["n_fine"][:wl.dim]}}
+    out["f32_vs_oracle"] = rho_error_report(rho32, want, mask[rows], wl.K)
+    out["f64_same_kernel_vs_oracle"] = rho_error_report(rho64k, want, mask[rows], wl.K)
+    out["f32_vs_f64_same_kernel"] = rho_error_report(rho32, rho64k, mask[rows], wl.K)
+    out["f64_tol_1e-12_vs_oracle"] = rho_error_report(rho64, want, mask[rows], wl.K)
+    out["bar"] = 1e-5
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -557,6 +669,10 @@ def main():
                     help="override the spread/interp tile edge per axis")
     ap.add_argument("--grad-mode", default=None, choices=["direct", "kderiv"],
                     help="override the workload's gradient mode")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="instead of timing: attribute the FP32 rho error at sampled mask rows")
+    ap.add_argument("--accuracy-rows", type=int, default=64)
+    ap.add_argument("--accuracy-seed", type=int, default=2)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warmup raised to 3")
@@ -576,6 +692,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.accuracy:
+        run_accuracy(args, wl)
+        return
 
     if args.impl == "reference":
         if ens is not None:
@@ -631,7 +751,7 @@ def main():
         got = rho_dev[torch.from_numpy(rows).cuda()].double().cpu().numpy()
         del rho_dev
         got = got[:, 0] + 1j * got[:, 1]
-        rho_err = float(np.linalg.norm(got - rho_oracle) / np.linalg.norm(rho_oracle))
+        rho_err = rho_error_report(got, rho_oracle, mask[rows], wl.K)
 
     # e2e through the host-buffer entry point
     dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
@@ -652,9 +772,9 @@ def main():
         gbs = sb[name] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
         per_stage[name] = {"ms": round(avg, 4), "alg_bytes": int(sb[name]),
                            "GB/s": round(gbs, 1), "frac": round(gbs / hbm_peak, 4)}
-    # the roofline names the slowest single libfresco kernel (sort and the FFT stages are several
-    # launches each and keep their own lines in "stages")
-    ours = {k: v for k, v in per_stage.items() if k in ("spread", "interp", "mask")}
+    # the roofline names the slowest libfresco stage (the FFT stages, cuFFT's own kernels plus a
+    # transpose, keep their lines in "stages")
+    ours = {k: v for k, v in per_stage.items() if k in ("sort", "spread", "interp", "mask")}
     dom = max(ours, key=lambda k: ours[k]["ms"])
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
@@ -671,6 +791,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": per_stage[dom]["GB/s"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": per_stage[dom]["frac"], "traffic": traffic,
                 "kernel": dom, "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+    smem_roof = smem_rooflines(per_stage, N, wl.dim, info["width"], smem_peaks())
 
     # ---- all-FP64 GPU path on the same workload ----------------------------------------------
     f64 = None
@@ -694,8 +815,9 @@ def main():
     accuracy = {
         "fp32_vs_fp64_gpu": ({"loss_rel": f64["loss_rel_diff_f32_vs_f64"],
                               "grad_rel_l2": f64["grad_rel_l2_f32_vs_f64"]} if f64 else None),
-        "rho_rel_l2_vs_oracle": rho_err,
-        "rho_rows_vs_oracle": (int(len(rows)) if rho_err is not None else 0),
+        "rho_rel_l2_vs_oracle": rho_err["rel_l2"] if rho_err else None,
+        "rho_rows_vs_oracle": rho_err["rows"] if rho_err else 0,
+        "rho_vs_oracle": rho_err,
         "bars": {"rho": 1e-5, "loss": 1e-5, "grad": 1e-4},
     }
 
@@ -715,6 +837,7 @@ def main():
                              % (np.prod(info["n_fine"][:wl.dim]) * esize / 1e9,
                                 L2_BYTES // 2 ** 20)},
             "roofline": roofline,
+            "smem_roofline": smem_roof,
             "stages": per_stage,
             "fp64": f64,
             "accuracy": accuracy,
@@ -732,17 +855,22 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-# the sources that build (and size the launches of) the kernels the traffic entries describe
-TRAFFIC_SOURCES = ("fresco_host.cu", "fresco_internal.h", "fresco_kernels.cuh",
-                   "fresco_kernels_f32.cu", "fresco_kernels_f64.cu")
+def traffic_sources() -> list:
+    """The sources that build (and size the launches of) the kernels the traffic entries
+    describe: every CUDA source and header of the library."""
+    import glob
+    csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
+    return sorted(os.path.basename(f) for f in glob.glob(os.path.join(csrc, "*"))
+                  if f.endswith((".cu", ".cuh", ".h")))
 
 
 def _kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
-    for name in TRAFFIC_SOURCES:
+    for name in traffic_sources():
         with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 

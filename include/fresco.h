@@ -190,8 +190,22 @@ fresco_status fresco_profile_read(fresco_plan_t p, double *ms, int64_t *counts);
 /* Number of libfresco kernels launched through this plan so far (cuFFT's own not included). */
 int64_t fresco_launch_count(fresco_plan_t p);
 
-/* Allocation-free loss: *d_loss = sum_{q < n_k} W[q] (S[q] - S0[q])^2, summed in FP64 in a fixed
- * order (the same two-stage reduction a plan uses for Eq. 2, but without a plan).
+/* Measured shared-memory throughput of the current device, the denominator of the spread's and
+ * the interpolation's roofline (both are bound by shared memory, not by HBM; the paper has no
+ * counterpart, it is measurement support). op FRESCO_SMEM_ATOMIC_ADD: 32-bit integer atomic adds
+ * (the spread's fixed-point accumulation); FRESCO_SMEM_LOAD: 32-bit loads (the interpolation's
+ * window reads). Every warp instruction of the probe addresses 32 distinct banks, the pipe's best
+ * case. d_sink: device int array of at least 8 x (multiprocessor count) entries (never read back);
+ * stream: cudaStream_t (as void*), NULL = default stream. Launches a few untimed and ten timed
+ * kernels (about a millisecond in all) and synchronises; *ops_per_s = lane operations per
+ * second. FRESCO_ERR_ARG for a bad op or pointer, FRESCO_ERR_CUDA if a launch fails. */
+#define FRESCO_SMEM_ATOMIC_ADD 0
+#define FRESCO_SMEM_LOAD 1
+fresco_status fresco_smem_peak(int op, void *d_sink, void *stream, double *ops_per_s);
+
+/* Allocation-free loss: *d_loss = sum_{q < n_k} W[q] (S[q] - S0[q])^2, FP64 per-block partial
+ * sums plus a fixed-order final stage: bitwise repeatable, and equal to a plan's loss for the same
+ * S within the precision's tolerance.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate device
  * memory at call time -- code running under a device-memory budget fixed at start-up, or inside
  * a framework whose allocator already owns the device memory, where a cudaMalloc would fail or
@@ -203,13 +217,17 @@ int64_t fresco_launch_count(fresco_plan_t p);
  *   d_S0, d_W : device double [n_k] target and weight
  *   d_loss    : device double, receives the loss
  *   stream    : cudaStream_t (as void*), NULL = default stream
- * Its scratch (512 KiB of per-block partial sums) is one array compiled into the library, held
- * by every GPU that loads the library until the process exits. The first call on each device
- * looks up that array's device address (cudaGetSymbolAddress, with the device current); make
- * that first call before any stream capture. All calls on a device share the array: calls that
- * overlap on the GPU (different streams, no ordering between them) race and give wrong results;
- * calls ordered on one stream are safe. Asynchronous; returns FRESCO_ERR_ARG for bad arguments,
- * FRESCO_ERR_CUDA if the address lookup or a launch fails. */
+ * Its scratch (512 KiB of per-block partial sums) is one array compiled into the library. CUDA
+ * loads modules lazily by default, so that array takes its device memory on a device at the
+ * first call there (the call loads the module while it looks up the array's device address with
+ * cudaGetSymbolAddress, the device current); from then on the GPU holds it until the process
+ * exits. Make one warm-up call per device at start-up, before the memory budget is fixed and
+ * before any stream capture (or run with CUDA_MODULE_LOADING=EAGER, which loads it with the
+ * context). All calls on a device share the array: calls that overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong results; calls ordered on one stream are
+ * safe. A pending launch error of earlier work on the thread is cleared on entry. Asynchronous;
+ * returns FRESCO_ERR_ARG for bad arguments, FRESCO_ERR_CUDA if the address lookup or a launch
+ * fails. */
 #define FRESCO_LOSS_NOALLOC_MAX_ROWS ((int64_t)65536 * 4096)
 fresco_status fresco_loss_noalloc(int precision, int64_t n_k, const void *d_S, const double *d_S0,
                                   const double *d_W, double *d_loss, void *stream);
@@ -371,7 +389,9 @@ fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, c
                               int64_t n_k, const double *S0, const double *W, int precision,
                               void *stream);
 /* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
- * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. */
+ * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. The loss
+ * is summed in a fixed order and repeats bitwise; the gradient's type-1 spread adds with floating-
+ * point atomics, so repeated calls agree only to rounding (not bitwise). */
 fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad);
 fresco_status fresco_uwu_destroy(fresco_uwu_t u);
 
@@ -401,7 +421,9 @@ fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid,
                                const double *nu, const double *S0, const double *W,
                                const fresco_opts *opts, void *stream);
 /* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
- * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. */
+ * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. The loss
+ * is summed in a fixed order and repeats bitwise; the gradient's type-1 spread adds with floating-
+ * point atomics, so repeated calls agree only to rounding (not bitwise). */
 fresco_status fresco_uwnu_loss_grad(fresco_uwnu_t u, const void *d_c, double *d_loss,
                                     void *d_grad);
 /* After fresco_uwnu_loss_grad: S at the constraints into d_S (device [n_k], plan precision, in
@@ -410,6 +432,47 @@ fresco_status fresco_uwnu_get_S(fresco_uwnu_t u, void *d_S);
 /* Kernel width, shape parameter beta and fine grid (n_fine[3], 1 beyond dim); any may be NULL. */
 fresco_status fresco_uwnu_get_info(fresco_uwnu_t u, int *width, double *beta, int *n_fine);
 fresco_status fresco_uwnu_destroy(fresco_uwnu_t u);
+
+/* ---- Points at free positions, constraints at real wavevectors (NUwNU, Methods "Analytical
+ * gradients": type-3 transforms of the positions; the main text's quasicrystal targets have
+ * Bragg peaks at non-integer k) -------------------------------------------------------------
+ * rho(k_q) = sum_j exp(-i k_q . r_j), S_q = |rho_q|^2 / N, L = sum_q W_q (S_q - S0_q)^2,
+ * dL/dr_j = Re sum_q (4 i k_q W_q (S_q - S0_q) rho_q / N) exp(+i k_q . r_j) (Eq. 4 without a
+ * periodic box). Points lie in [-L_a/2, L_a/2] per axis (free boundaries, no wrapping); k_q are
+ * real wavevectors (radians per unit length), none folded.
+ * The type-3 transform runs as a spread of the points onto a grid of spacing h_a = pi / (sigma
+ * K_a) (K_a = max_q |k_q,a|) and n1_a > L_a / h_a + w + 2 cells, followed by the type-2 transform
+ * of that grid at theta_q = k_q h (a grid upsampled by sigma, the weights-on-a-grid machinery
+ * above) and a division by the spreading kernel's Fourier transform at theta_q; the gradient by
+ * the adjoint type-1 transform and the derivative of the spreading kernel at the points.
+ *   dim 2 or 3; box host [dim] (L_a > 0); n_points N >= 1; kvec host [n_k][dim]; S0, W host
+ *   [n_k] (W >= 0); opts: precision, tol (0: 1e-6 F32, 1e-12 F64), upsample (0: 2.0, in
+ *   [1.25, 3]); other fields ignored; NULL = defaults. FRESCO_ERR_ARG for invalid arguments,
+ *   FRESCO_ERR_UNSUPPORTED when a grid exceeds 4e9 cells or w > 16. The plan owns copies of the
+ *   constraints, both grids, the points' sort buffers and a cuFFT plan; asynchronous on `stream`. */
+typedef struct fresco_nuwnu_s *fresco_nuwnu_t;
+fresco_status fresco_nuwnu_plan(fresco_nuwnu_t *out, int dim, const double *box, int64_t n_points,
+                                int64_t n_k, const double *kvec, const double *S0, const double *W,
+                                const fresco_opts *opts, void *stream);
+/* d_points: device [N][dim] of the plan's precision, caller order; d_loss: device double;
+ * d_grad: device [N][dim], caller order, or NULL. A point farther than L_a/2 + h_a/2 from the
+ * origin on some axis is latched in the device error word (FRESCO_ERR_BOUNDS from
+ * fresco_nuwnu_status_check), a NaN or infinite coordinate as
+ * FRESCO_ERR_NONFINITE; the results are then undefined. Asynchronous on the plan's stream. The
+ * loss repeats bitwise; the type-1 spread of the gradient adds with floating-point atomics, so
+ * repeated gradients agree to rounding. */
+fresco_status fresco_nuwnu_loss_grad(fresco_nuwnu_t p, const void *d_points, double *d_loss,
+                                     void *d_grad);
+/* After fresco_nuwnu_loss_grad: S at the constraints into d_S (device [n_k], plan precision, in
+ * the order given). */
+fresco_status fresco_nuwnu_get_S(fresco_nuwnu_t p, void *d_S);
+/* Synchronise and return the first device-detected error (clearing it) or a pending CUDA error. */
+fresco_status fresco_nuwnu_status_check(fresco_nuwnu_t p);
+/* Kernel width, cells per axis of the points' grid (n_grid[3]) and of the type-2 grid
+ * (n_fine[3]), libfresco kernels launched so far; any pointer may be NULL. */
+fresco_status fresco_nuwnu_get_info(fresco_nuwnu_t p, int *width, int *n_grid, int *n_fine,
+                                    int64_t *launches);
+fresco_status fresco_nuwnu_destroy(fresco_nuwnu_t p);
 
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);

@@ -180,8 +180,7 @@ bool canonical(const int32_t *n, int dim) {
     return dim == 3 && n[2] > 0;
 }
 
-int choose_tiles(int nf, int target, int w) {
-    int minw = (w + 1) / 2;
+int choose_tiles(int nf, int target, int minw) {
     if (target < minw) target = minw;
     int best = std::max(1, (int)std::lround((double)nf / target));
     // prefer an exact divisor of nf near the target edge
@@ -200,10 +199,13 @@ int choose_tiles(int nf, int target, int w) {
 // halo, or the spread tile plus its point list, would not fit the shared-memory budget (2 blocks
 // per SM by default, the opt-in maximum when the caller fixed the tiles). Needs P.nf, P.width,
 // P.dim, P.precision.
-fresco_status choose_tiling(Params &P, const int tile_req[3]) {
+fresco_status choose_tiling(Params &P, const int tile_req[3], bool own_tiles = false) {
     const int dim = P.dim, w = P.width;
     const size_t es = P.precision == FRESCO_F64 ? 8 : 4;
     const bool user_tiles = tile_req[0] > 0 || tile_req[1] > 0 || tile_req[2] > 0;
+    // a tile is at least ceil(w / 2) cells wide: a point's window then reaches only the adjacent
+    // tiles (the halo fold and the gathering spread rely on it)
+    const int minw = (w + 1) / 2;
     size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
     double cells_all = 1.0;
     for (int a = 0; a < dim; ++a) cells_all *= (double)P.nf[a];
@@ -235,7 +237,7 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
         if (target[a] > kMaxTileEdge) return FRESCO_ERR_ARG;
     for (int iter = 0;; ++iter) {
         for (int a = 0; a < dim; ++a) {
-            P.nb[a] = choose_tiles(P.nf[a], target[a], w);
+            P.nb[a] = choose_tiles(P.nf[a], target[a], minw);
             P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
         }
         // spread list: the expected points reaching a tile plus five standard deviations
@@ -255,13 +257,14 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
         const size_t interp =
             es == 8 ? (kd ? Launch<double>::interp_kd_smem(tg) : Launch<double>::interp_smem(tg))
                     : (kd ? Launch<float>::interp_kd_smem(tg) : Launch<float>::interp_smem(tg));
-        const size_t spread = es == 8 ? Launch<double>::spread_smem(tg)
-                                      : Launch<float>::spread_smem(tg);
+        const size_t spread =
+            own_tiles ? (es == 8 ? Launch<double>::spread_own_smem(tg)
+                                 : Launch<float>::spread_own_smem(tg))
+                      : (es == 8 ? Launch<double>::spread_smem(tg) : Launch<float>::spread_smem(tg));
         if (interp <= budget && spread <= budget) break;
         int amax = 0;
         for (int a = 1; a < dim; ++a)
             if (P.tmax[a] > P.tmax[amax]) amax = a;
-        const int minw = (w + 1) / 2;
         if (target[amax] <= minw || iter > 256) {
             if (budget >= kSmemOptin) return FRESCO_ERR_UNSUPPORTED;
             budget = kSmemOptin;   // one block per SM rather than no plan
@@ -281,7 +284,7 @@ fresco_status choose_tiling(Params &P, const int tile_req[3]) {
 fresco_status check_and_params(int dim, const double *box, int64_t n_points, const int32_t *mask,
                                int64_t n_k, const double *S0, const double *W,
                                const fresco_opts *opts_in, Params &P,
-                               bool width_from_reached = true) {
+                               bool width_from_reached = true, bool own_tiles = true) {
     if (dim != 2 && dim != 3) return FRESCO_ERR_ARG;
     if (!box || !mask || !S0 || !W) return FRESCO_ERR_ARG;
     if (n_points < 1 || n_points > 2147483647LL) return FRESCO_ERR_ARG;
@@ -352,7 +355,7 @@ fresco_status check_and_params(int dim, const double *box, int64_t n_points, con
             P.beta = es_beta(w, sig_eff);
         }
     }
-    fresco_status st = choose_tiling(P, o.tile);
+    fresco_status st = choose_tiling(P, o.tile, own_tiles);
     if (st) return st;
     int64_t cells = (int64_t)P.nf[0] * P.nf[1] * P.nf[2];
     if (cells > (int64_t)1 << 36) return FRESCO_ERR_UNSUPPORTED;
@@ -493,7 +496,7 @@ void release(fresco_plan_s *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
-    void *bufs[] = {p->d_sorted, p->d_perm, p->d_key, p->d_slot, p->d_cnt, p->d_off,
+    void *bufs[] = {p->d_sorted, p->d_perm, p->d_ring, p->d_cnt, p->d_off,
                     p->d_block_sums, p->d_grid, p->d_tw, p->d_specT, p->d_bt[0], p->d_bt[1],
                     p->d_hc[0], p->d_hc[1], p->d_r[0],
                     p->d_r[1], p->d_g[0], p->d_g[1], p->d_rep_n, p->d_rep_s0, p->d_rep_w,
@@ -623,8 +626,8 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     es_poly<double>(P.width, P.beta, p->poly64);
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
     g.list_cap = P.list_cap;
-    g.sub = dim == 3 ? 27 : 9;
-    for (int a = 0; a < 3; ++a) g.strips[a] = a < dim && P.nf[a] / P.nb[a] >= P.width ? 1 : 0;
+    g.sub = kTileCursors;   // own-points spread: no border strips; sub-cursors per tile
+    for (int a = 0; a < 3; ++a) g.strips[a] = 0;
     g.n_bins = g.n_tiles * g.sub;
     if (g.n_bins >= 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
     g.n_points = p->n_points;
@@ -655,7 +658,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     FR_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int interp_bytes =
         m.kderiv ? Launch<T>::interp_kd_smem(g) : Launch<T>::interp_smem(g);
-    if (Launch<T>::spread_smem(g) > smem_optin || interp_bytes > smem_optin)
+    if (Launch<T>::spread_own_smem(g) > smem_optin || interp_bytes > smem_optin)
         return FRESCO_ERR_UNSUPPORTED;
 
     const int64_t N = p->n_points;
@@ -666,8 +669,8 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     fresco_status st;
     if ((st = dalloc(p, &p->d_sorted, sizeof(T) * (size_t)N * pw))) return st;
     if (sizeof(T) == 8 && (st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)N))) return st;
-    if ((st = dalloc(p, &p->d_key, sizeof(int) * (size_t)N))) return st;
-    if ((st = dalloc(p, &p->d_slot, sizeof(int) * (size_t)N))) return st;
+    p->ring_slot = Launch<T>::ring_slot(g);
+    if ((st = dalloc(p, &p->d_ring, sizeof(T) * (size_t)(g.n_tiles * p->ring_slot)))) return st;
     if ((st = dalloc(p, &p->d_cnt, sizeof(int) * (size_t)g.n_bins))) return st;
     if ((st = dalloc(p, &p->d_off, sizeof(int) * (size_t)(g.n_bins + 1)))) return st;
     if ((st = dalloc(p, &p->d_block_sums, sizeof(int) * (size_t)((g.n_bins + 1023) / 1024 + 1))))
@@ -759,7 +762,9 @@ fresco_status stage_and_bin(fresco_plan_s *p, const T *h_pts, T *d_pts) {
         if (!e) FR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     FR_CUDA(cudaEventRecord(p->copy_ev[kHostChunks], p->stream));
     FR_CUDA(cudaStreamWaitEvent(p->copy_stream, p->copy_ev[kHostChunks], 0));
-    const int64_t per = (n + chunks - 1) / chunks;
+    // chunks start at multiples of the cursors per tile, so a point's bin (which depends on its
+    // caller index modulo g.sub) is the same whether it is counted in its chunk or placed later
+    const int64_t per = ((n + chunks - 1) / chunks + g.sub - 1) / g.sub * g.sub;
     for (int c = 0; c < chunks; ++c) {
         const int64_t j0 = c * per, cnt = std::min(per, n - j0);
         if (cnt <= 0) break;
@@ -769,8 +774,7 @@ fresco_status stage_and_bin(fresco_plan_s *p, const T *h_pts, T *d_pts) {
         FR_CUDA(cudaStreamWaitEvent(p->stream, p->copy_ev[c], 0));
         Geom gc = g;
         gc.n_points = cnt;
-        FR_CUDA(Launch<T>::bin(gc, d_pts + j0 * d, p->d_cnt, p->d_key + j0, p->d_slot + j0,
-                               p->d_err, p->stream));
+        FR_CUDA(Launch<T>::count(gc, d_pts + j0 * d, p->d_cnt, p->d_err, p->stream));
         p->launches += 1;
     }
     return FRESCO_OK;
@@ -791,20 +795,22 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss,
             fresco_status st = stage_and_bin<T>(p, h_pts, const_cast<T *>(pts));
             if (st) return st;
         } else {
-            FR_CUDA(Launch<T>::bin(g, pts, p->d_cnt, p->d_key, p->d_slot, p->d_err, s));
+            FR_CUDA(Launch<T>::count(g, pts, p->d_cnt, p->d_err, s));
             p->launches += 1;
         }
         int nl = 0;
-        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl));
-        FR_CUDA(Launch<T>::scatter(g, pts, p->d_key, p->d_slot, p->d_off, p->d_sorted, p->d_perm,
-                                   s));
+        // the counts become the placement cursors (a copy of the tile offsets)
+        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl, p->d_cnt));
+        FR_CUDA(Launch<T>::place(g, pts, p->d_cnt, p->d_sorted, p->d_perm, s));
         nl += 1;
         p->launches += nl;
     }
     {
         StageScope sc(p->prof, p->stream, ST_SPREAD);
-        FR_CUDA(Launch<T>::spread(g, poly_of<T>(p), p->d_sorted, p->d_off, (T *)p->d_grid, s));
-        p->launches += 1;
+        int nl = 0;
+        FR_CUDA(Launch<T>::spread_own(g, poly_of<T>(p), p->d_sorted, p->d_off, (T *)p->d_grid,
+                                      (T *)p->d_ring, p->ring_slot, s, &nl));
+        p->launches += nl;
     }
     {
         StageScope sc(p->prof, p->stream, ST_FFT_FWD);
@@ -911,6 +917,130 @@ fresco_status check_point_ptr(fresco_plan_s *p, const void *ptr) {
 }  // namespace
 
 // ---- profiling event pool --------------------------------------------------------------------
+// ---- point sets spread for other transforms (type-3 plans) -------------------------------------
+
+void fresco::kernel_ft_at(int w, double beta, const double *theta, int64_t n, double *out) {
+    const int nq = 200;
+    std::vector<double> x, wq;
+    gauss_legendre(nq, x, wq);
+    const double h = 0.25 * kPi;
+    std::vector<double> u(nq), f(nq);
+    for (int q = 0; q < nq; ++q) {
+        const double th = h * (1.0 + x[q]);
+        u[q] = 0.5 * w * std::sin(th);
+        f[q] = 2.0 * h * wq[q] * std::exp(beta * (std::cos(th) - 1.0)) * 0.5 * w * std::cos(th);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int q = 0; q < nq; ++q) s += f[q] * std::cos(theta[i] * u[q]);
+        out[i] = s;
+    }
+}
+
+namespace {
+bool ps_alloc(fresco::PointSide &ps, void **p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    ps.allocs.push_back(*p);
+    ps.device_bytes += (int64_t)bytes;
+    return true;
+}
+}  // namespace
+
+void fresco::point_side_free(PointSide &ps) {
+    for (void *p : ps.allocs) cudaFree(p);
+    ps.allocs.clear();
+}
+
+fresco_status fresco::point_side_build(PointSide &ps, int dim, const int nf[3], const double box[3],
+                                       int64_t n_points, int width, double beta, int precision,
+                                       cudaStream_t s) {
+    Params P{};
+    P.dim = dim;
+    P.precision = precision;
+    P.width = width;
+    P.beta = beta;
+    P.n_points = n_points;
+    P.grad_mode = FRESCO_GRAD_KDERIV;
+    for (int a = 0; a < 3; ++a) {
+        P.nf[a] = a < dim ? nf[a] : 1;
+        P.kmax[a] = 0;
+    }
+    const int no_req[3] = {0, 0, 0};
+    fresco_status st = choose_tiling(P, no_req, true);
+    if (st) return st;
+    Geom &g = ps.g;
+    g = Geom{};
+    g.dim = dim;
+    const size_t es = precision == FRESCO_F64 ? 8 : 4;
+    for (int a = 0; a < 3; ++a) {
+        g.nf[a] = P.nf[a];
+        g.nb[a] = P.nb[a];
+        g.tmax[a] = P.tmax[a];
+        g.tq[a] = P.nf[a] / P.nb[a];
+        g.tr[a] = P.nf[a] % P.nb[a];
+        g.tinv[a] = (float)P.nb[a] / (float)P.nf[a];
+        const double sc = a < dim ? (double)P.nf[a] / box[a] : 0.0;
+        const double shi = es == 4 ? (double)(float)sc : sc;
+        const long double slo = a < dim ? (long double)P.nf[a] / (long double)box[a] - shi : 0.0L;
+        g.s_hi[a] = shi;
+        g.s_lo[a] = es == 4 ? (double)(float)(double)slo : (double)slo;
+    }
+    es_poly<float>(width, beta, ps.p32);
+    es_poly<double>(width, beta, ps.p64);
+    g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
+    g.list_cap = P.list_cap;
+    g.sub = kTileCursors;
+    g.n_bins = g.n_tiles * g.sub;
+    g.n_points = n_points;
+    g.width = width;
+    g.beta = beta;
+    ps.precision = precision;
+    const int64_t cells = (int64_t)g.nf[0] * g.nf[1] * g.nf[2];
+    const int pw = es == 4 ? 4 : (dim == 3 ? 4 : 2);
+    ps.ring_slot = es == 8 ? Launch<double>::ring_slot(g) : Launch<float>::ring_slot(g);
+    bool ok = ps_alloc(ps, &ps.sorted, es * (size_t)n_points * pw) &&
+              (es == 4 || ps_alloc(ps, (void **)&ps.perm, sizeof(int) * (size_t)n_points)) &&
+              ps_alloc(ps, (void **)&ps.cnt, sizeof(int) * (size_t)g.n_bins) &&
+              ps_alloc(ps, (void **)&ps.off, sizeof(int) * (size_t)(g.n_bins + 1)) &&
+              ps_alloc(ps, (void **)&ps.bsum, sizeof(int) * (size_t)((g.n_bins + 1023) / 1024 + 1)) &&
+              ps_alloc(ps, (void **)&ps.err, sizeof(int)) &&
+              ps_alloc(ps, &ps.grid, es * (size_t)cells) &&
+              ps_alloc(ps, &ps.ring, es * (size_t)(g.n_tiles * ps.ring_slot));
+    if (!ok) {
+        point_side_free(ps);
+        return FRESCO_ERR_OOM;
+    }
+    if (cudaMemsetAsync(ps.err, 0, sizeof(int), s) != cudaSuccess) return FRESCO_ERR_CUDA;
+    return FRESCO_OK;
+}
+
+template <typename T>
+fresco_status fresco::point_side_spread(PointSide &ps, const T *pts, cudaStream_t s,
+                                        int64_t *launches) {
+    const Geom &g = ps.g;
+    FR_CUDA(cudaMemsetAsync(ps.cnt, 0, sizeof(int) * (size_t)g.n_bins, s));
+    FR_CUDA(Launch<T>::count(g, pts, ps.cnt, ps.err, s));
+    int nl = 1;
+    FR_CUDA(Launch<T>::scan(ps.cnt, ps.off, ps.bsum, g.n_bins, s, &nl, ps.cnt));
+    FR_CUDA(Launch<T>::place(g, pts, ps.cnt, ps.sorted, ps.perm, s));
+    nl += 1;
+    const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(sizeof(T) == 4 ? (const void *)&ps.p32
+                                                                              : (const void *)&ps.p64);
+    FR_CUDA(Launch<T>::spread_own(g, ep, ps.sorted, ps.off, (T *)ps.grid, (T *)ps.ring,
+                                  ps.ring_slot, s, &nl));
+    if (launches) *launches += nl;
+    return FRESCO_OK;
+}
+
+template fresco_status fresco::point_side_spread<float>(PointSide &, const float *, cudaStream_t,
+                                                        int64_t *);
+template fresco_status fresco::point_side_spread<double>(PointSide &, const double *, cudaStream_t,
+                                                         int64_t *);
+
 cudaEvent_t fresco::StageProfile::take() {
     if (!spare.empty()) {
         cudaEvent_t e = spare.back();
@@ -1613,7 +1743,7 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
         // one kernel serves every instance: the width rule at the requested oversampling
         fresco_status st = check_and_params(dim, boxes + (size_t)i * dim, n_points[i],
                                             masks + m0 * dim, n_modes[i], S0 + m0, W + m0, &o,
-                                            P[i], false);
+                                            P[i], false, false);
         if (st) return st;
         if (i > 0 && P[i].width != P[0].width) return FRESCO_ERR_UNSUPPORTED;
         for (int a = 0; a < dim; ++a) P[i].nf[a] = class_size(P[i].nf[a]);

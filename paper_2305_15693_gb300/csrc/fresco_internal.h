@@ -14,6 +14,7 @@ namespace fresco {
 constexpr int kMaxWidth = 16;     // largest ES kernel width instantiated
 constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
+constexpr int kTileCursors = 4;   // placement cursors per tile of a single plan (Geom.sub)
 // fresco_loss_grad_host copies the points in up to kHostChunks pieces of at least
 // kHostChunkBytes, binning each piece while the next one is in flight
 constexpr int kHostChunks = 8;
@@ -32,8 +33,10 @@ struct Geom {
     float tinv[3];      // nb / nf (estimate of the tile of a cell, corrected exactly)
     int64_t n_tiles;
     int list_cap;       // entries of the spread kernel's compacted point list (shared memory)
-    int sub;            // sub-bins per tile, 3^dim: per axis the low border strip (cells that can
-                        // reach the previous tile), the interior, the high border strip
+    int sub;            // bins per tile. Ensemble plans: 3^dim, per axis the low border strip
+                        // (cells that can reach the previous tile), the interior, the high border
+                        // strip. Single plans: kTileCursors placement cursors (bin = tile * sub +
+                        // caller index mod sub)
     int strips[3];      // 1 if every tile on the axis is at least w cells wide (strips disjoint)
     int64_t n_bins;     // n_tiles * sub: the sort key space
     int64_t n_points;
@@ -154,15 +157,21 @@ struct StageScope {
 // return the cudaError_t of the launch. Element layouts are documented in fresco_kernels.cuh.
 template <typename T>
 struct Launch {
-    static cudaError_t bin(const Geom &g, const T *points, int *cnt, int *key, int *slot,
-                           int *err, cudaStream_t s);
+    // exclusive prefix sum of cnt into off[0..n] (off[n] = total); when cur is not null it
+    // receives a copy of off[0..n) (the placement cursors of k_place)
     static cudaError_t scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
-                            int *launches);
-    static cudaError_t scatter(const Geom &g, const T *points, const int *key, const int *slot,
-                               const int *off, void *sorted, int *perm, cudaStream_t s);
+                            int *launches, int *cur = nullptr);
+    // single plans (tiles without border sub-bins): points per tile, then placement by cursor
+    static cudaError_t count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s);
+    static cudaError_t place(const Geom &g, const T *points, int *cur, void *sorted, int *perm,
+                             cudaStream_t s);
+    // own-points spread into the grid plus per-tile rings, then the ring sums into the grid
+    static cudaError_t spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  cudaStream_t s, int *launches);
+    static int spread_own_smem(const Geom &g);
+    static int64_t ring_slot(const Geom &g);
 
-    static cudaError_t spread(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                              const int *off, T *grid, cudaStream_t s);
     static cudaError_t mask(const MaskGeom &m, const int *rep_n, const T *rep_s0, const T *rep_w,
                             const void *spec, const T *ip0, const T *ip1, const T *ip2,
                             void *hc0, void *hc1, double *partial, int n_blocks, cudaStream_t s);
@@ -221,6 +230,32 @@ struct Launch {
     static int interp_smem(const Geom &g);
 };
 
+// A point set spread onto a periodic fine grid by the plan machinery (own-points tiles, sorted
+// records), for transforms other than fresco_plan's: its geometry, kernel polynomials and
+// buffers. point_side_build chooses the tiles and allocates; point_side_spread bins the points and
+// spreads them (unit strengths) into `grid`; Launch<T>::interp_kd interpolates a field at them.
+struct PointSide {
+    Geom g{};
+    EsPoly<float> p32{};
+    EsPoly<double> p64{};
+    int precision = FRESCO_F32;
+    void *sorted = nullptr;
+    int *perm = nullptr, *cnt = nullptr, *off = nullptr, *bsum = nullptr, *err = nullptr;
+    void *grid = nullptr, *ring = nullptr;
+    int64_t ring_slot = 0;
+    int64_t device_bytes = 0;
+    std::vector<void *> allocs;
+};
+fresco_status point_side_build(PointSide &ps, int dim, const int nf[3], const double box[3],
+                               int64_t n_points, int width, double beta, int precision,
+                               cudaStream_t s);
+void point_side_free(PointSide &ps);
+template <typename T>
+fresco_status point_side_spread(PointSide &ps, const T *pts, cudaStream_t s, int64_t *launches);
+// Psi(theta) = integral psi(u) cos(theta u) du of the kernel of width w (u in cells), at n real
+// frequencies theta (radians per cell).
+void kernel_ft_at(int w, double beta, const double *theta, int64_t n, double *out);
+
 #ifdef __CUDACC__
 // Knuth's two-sum: s + e == a + b exactly (round to nearest, no overflow)
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -278,10 +313,10 @@ struct fresco_plan_s {
     void *d_sorted = nullptr;        // sorted records: packed tile-relative coordinates (and, for
                                      // float plans, the caller index)
     int *d_perm = nullptr;           // double plans: sorted position -> caller index
-    int *d_key = nullptr;            // caller index -> tile id
-    int *d_slot = nullptr;           // caller index -> rank within its tile
-    int *d_cnt = nullptr;            // [n_bins] points per sub-bin
-    int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of d_cnt
+    void *d_ring = nullptr;          // [n_tiles][ring_slot] spread rings (own-points spread)
+    int64_t ring_slot = 0;
+    int *d_cnt = nullptr;            // [n_bins] points per tile, then the placement cursors
+    int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of the counts
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
     void *d_tw = nullptr;            // exp(-2 pi i k / nf0), k = 0..nf0/4 (real-row split/merge)

@@ -190,59 +190,6 @@ __device__ __forceinline__ int strip_part(int rel, int wd, int w, int strips) {
     return 1;
 }
 
-// K1a: wrap, fine cell, sub-bin (tile x 3^D border parts) and the rank of each point within it.
-// Each thread handles 4 points per iteration (independent loads and atomics in flight).
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_bin(Geom g, const T *__restrict__ pts,
-                                             int *__restrict__ cnt, int *__restrict__ key,
-                                             int *__restrict__ slot, int *__restrict__ err) {
-    constexpr int IL = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
-         j0 += stride) {
-        T r[IL][3];
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            const int64_t j = j0 + (int64_t)k * blockDim.x;
-#pragma unroll
-            for (int a = 0; a < D; ++a) r[k][a] = j < g.n_points ? pts[j * D + a] : T(0);
-        }
-        int bin[IL];
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            int t[3] = {0, 0, 0}, part[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                int cell;
-                T frac;
-                ok &= fine_coord<T>(r[k][a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
-                t[a] = tile_of_cell(cell, g.tq[a], g.tr[a], g.tinv[a]);
-                const int st = tile_start(t[a], g.tq[a], g.tr[a]);
-                const int wd = tile_start(t[a] + 1, g.tq[a], g.tr[a]) - st;
-                part[a] = strip_part(cell - st, wd, g.width, g.strips[a]);
-            }
-            const int lin = t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
-            bin[k] = lin * g.sub + (part[0] + 3 * part[1] + 9 * part[2]);
-        }
-        if (!ok) atomicOr(err, 1);
-        int sl[IL];
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            const int64_t j = j0 + (int64_t)k * blockDim.x;
-            sl[k] = j < g.n_points ? atomicAdd(&cnt[bin[k]], 1) : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            const int64_t j = j0 + (int64_t)k * blockDim.x;
-            if (j < g.n_points) {
-                key[j] = bin[k];
-                slot[j] = sl[k];
-            }
-        }
-    }
-}
-
 // K1b: exclusive prefix sum of the tile counts, in three passes over blocks of 1024.
 static __global__ void __launch_bounds__(1024) k_scan_blocks(const int *__restrict__ cnt,
                                                       int *__restrict__ off,
@@ -312,56 +259,13 @@ static __global__ void __launch_bounds__(1024) k_scan_sums(int *__restrict__ bsu
 }
 
 static __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ off,
-                                                   const int *__restrict__ bsum, int64_t n) {
+                                                   const int *__restrict__ bsum, int64_t n,
+                                                   int *__restrict__ cur) {
     int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    if (i < n) off[i] += bsum[blockIdx.x];
-}
-
-// K1c: scatter every point to its sub-bin's slice of the sorted arrays (4 points per thread per
-// iteration, loads issued before the dependent offset lookups and stores).
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_scatter(Geom g, const T *__restrict__ pts,
-                                                 const int *__restrict__ key,
-                                                 const int *__restrict__ slot,
-                                                 const int *__restrict__ off,
-                                                 typename PT<T>::U *__restrict__ sorted,
-                                                 int *__restrict__ perm) {
-    using U = typename PT<T>::U;
-    constexpr int IL = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
-         j0 += stride) {
-        int bin[IL], sl[IL];
-        T r[IL][3];
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            const int64_t j = j0 + (int64_t)k * blockDim.x;
-            const bool in = j < g.n_points;
-            bin[k] = in ? key[j] : 0;
-            sl[k] = in ? slot[j] : 0;
-#pragma unroll
-            for (int a = 0; a < D; ++a) r[k][a] = in ? pts[j * D + a] : T(0);
-        }
-        int64_t pos[IL];
-#pragma unroll
-        for (int k = 0; k < IL; ++k) pos[k] = (int64_t)off[bin[k]] + sl[k];
-#pragma unroll
-        for (int k = 0; k < IL; ++k) {
-            const int64_t j = j0 + (int64_t)k * blockDim.x;
-            if (j >= g.n_points) continue;
-            const int lin = bin[k] / g.sub;
-            const int tc[3] = {lin % g.nb[0], (lin / g.nb[0]) % g.nb[1],
-                               lin / (g.nb[0] * g.nb[1])};
-            U u[3] = {0, 0, 0};
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                int cell;
-                T frac;
-                fine_coord<T>(r[k][a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac);
-                u[a] = pack_coord<T>(cell - tile_start(tc[a], g.tq[a], g.tr[a]), frac);
-            }
-            store_record<T, D>(sorted, perm, pos[k], u, (int)j);
-        }
+    if (i < n) {
+        const int v = off[i] + bsum[blockIdx.x];
+        off[i] = v;
+        if (cur) cur[i] = v;
     }
 }
 
@@ -786,13 +690,6 @@ __device__ __forceinline__ void spread_tile(const Geom &g, const EsPoly<T> &ep,
     }
 }
 
-template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread(Geom g, EsPoly<T> ep,
-                                                const typename PT<T>::U *__restrict__ sorted,
-                                                const int *__restrict__ off, T *__restrict__ grid) {
-    spread_tile<T, W, D>(g, ep, sorted, off, grid, blockIdx.x);
-}
-
 // Batched spread: a persistent grid walks the tiles of every instance of the ensemble.
 template <typename T, int W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_b(
@@ -806,6 +703,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_b(
         __syncthreads();
     }
 }
+
+}  // namespace fresco
+
+#include "fresco_tiles.cuh"
+
+namespace fresco {
 
 // ---------------------------------------------------------------------------------------------
 // K4: deconvolve and crop to the mask, S, the loss partial sums and the gradient coefficients.
@@ -1135,6 +1038,123 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_b(
 //   dL/dr_a = -(2 n_f[a] / L[a]) sum_m h(m) (d psi / d tau along a) (psi along the other axes),
 // scaled by the incoming gradient; dscale holds -2 n_f[a] / L[a].
 template <typename T, int W, int D>
+__device__ __forceinline__ void interp_window_kd(const EsPoly<T> &ep, const int (&i0)[3],
+                                                 const T (&x1)[3], int64_t j, const T *sh, int rx,
+                                                 int rxy, T dsx, T dsy, T dsz,
+                                                 T *__restrict__ grad);
+
+template <typename T, int W, int D>
+__device__ __forceinline__ void interp_point_kd(const EsPoly<T> &ep,
+                                                const typename PT<T>::U (&u)[3], int64_t j,
+                                                const T *sh, int rx, int rxy, T dsx, T dsy, T dsz,
+                                                T *__restrict__ grad) {
+    int i0[3];
+    T x1[3];
+    window_of<T, W, D>(u, rx, rxy, i0, x1);
+    interp_window_kd<T, W, D>(ep, i0, x1, j, sh, rx, rxy, dsx, dsy, dsz, grad);
+}
+
+// The window of one point (start i0 in the staged region, kernel offsets x1): the gradient of the
+// interpolant, scaled per axis, written at the caller index j.
+template <typename T, int W, int D>
+__device__ __forceinline__ void interp_window_kd(const EsPoly<T> &ep, const int (&i0)[3],
+                                                 const T (&x1)[3], int64_t j, const T *sh, int rx,
+                                                 int rxy, T dsx, T dsy, T dsz,
+                                                 T *__restrict__ grad) {
+    T wx[W], dwx[W], wy[W], dwy[W];
+    es_weights_d<T, W>(ep, x1[0], wx, dwx);
+    es_weights_d<T, W>(ep, x1[1], wy, dwy);
+    if constexpr (D == 2) {
+        T gx = T(0), gy = T(0);
+        if constexpr (sizeof(T) == 4) {
+            const unsigned step = 4u * (unsigned)rx;
+            unsigned row = smem_addr(sh) + 4u * (unsigned)(i0[1] * rx + i0[0]);
+#pragma unroll
+            for (int b = 0; b < W; ++b, row += step) {
+                float r0 = 0.f, r1 = 0.f;
+                dot_row_kd<W>(row, wx, dwx, r0, r1, std::make_integer_sequence<int, W>{});
+                gx = fmaf(wy[b], r1, gx);
+                gy = fmaf(dwy[b], r0, gy);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const T *row = sh + (i0[1] + b) * rx + i0[0];
+                T r0 = T(0), r1 = T(0);
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    const T v = row[a];
+                    r0 = fma(wx[a], v, r0);
+                    r1 = fma(dwx[a], v, r1);
+                }
+                gx = fma(wy[b], r1, gx);
+                gy = fma(dwy[b], r0, gy);
+            }
+        }
+        using T2 = typename PT<T>::C;
+        reinterpret_cast<T2 *>(grad)[j] = T2{dsx * gx, dsy * gy};
+    } else {
+        T wz[W], dwz[W];
+        es_weights_d<T, W>(ep, x1[2], wz, dwz);
+        T gx = T(0), gy = T(0), gz = T(0);
+        if constexpr (sizeof(T) == 4) {
+            const unsigned step = 4u * (unsigned)rx, pstep = 4u * (unsigned)rxy;
+            unsigned plane = smem_addr(sh) + 4u * (unsigned)(i0[2] * rxy + i0[1] * rx + i0[0]);
+#pragma unroll (W <= 8 ? W : 1)
+            for (int c = 0; c < W; ++c, plane += pstep) {
+                float px = 0.f, py = 0.f, pz = 0.f;
+                unsigned row = plane;
+#pragma unroll
+                for (int b = 0; b < W; ++b, row += step) {
+                    float r0 = 0.f, r1 = 0.f;
+                    dot_row_kd<W>(row, wx, dwx, r0, r1, std::make_integer_sequence<int, W>{});
+                    px = fmaf(wy[b], r1, px);
+                    py = fmaf(dwy[b], r0, py);
+                    pz = fmaf(wy[b], r0, pz);
+                }
+                gx = fmaf(wz[c], px, gx);
+                gy = fmaf(wz[c], py, gy);
+                gz = fmaf(dwz[c], pz, gz);
+            }
+        } else {
+#pragma unroll 1
+            for (int c = 0; c < W; ++c) {
+                T px = T(0), py = T(0), pz = T(0);
+#pragma unroll
+                for (int b = 0; b < W; ++b) {
+                    const T *row = sh + (i0[2] + c) * rxy + (i0[1] + b) * rx + i0[0];
+                    T r0 = T(0), r1 = T(0);
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        const T v = row[a];
+                        r0 = fma(wx[a], v, r0);
+                        r1 = fma(dwx[a], v, r1);
+                    }
+                    px = fma(wy[b], r1, px);
+                    py = fma(dwy[b], r0, py);
+                    pz = fma(wy[b], r0, pz);
+                }
+                gx = fma(wz[c], px, gx);
+                gy = fma(wz[c], py, gy);
+                gz = fma(dwz[c], pz, gz);
+            }
+        }
+        grad[j * 3 + 0] = dsx * gx;
+        grad[j * 3 + 1] = dsy * gy;
+        grad[j * 3 + 2] = dsz * gz;
+    }
+}
+
+// bytes of the staged real field of a kernel-derivative interpolation tile (rounded up to 16)
+__host__ __device__ inline size_t interp_kd_tile_bytes(const Geom &g, size_t esize) {
+    const int w = g.width;
+    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
+    return (cells * esize + 15) & ~(size_t)15;
+}
+
+// FP32 tiles of at most g.list_cap points run in the bank-residue schedule of the spread (every
+// window load of a warp hits 32 distinct banks); others one point per thread in sorted order.
+template <typename T, int W, int D>
 __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &ep,
                                                const typename PT<T>::U *__restrict__ sorted,
                                                const int *__restrict__ perm,
@@ -1143,6 +1163,7 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
                                                T *__restrict__ grad, const int64_t t) {
     using U = typename PT<T>::U;
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ int s_cnt[32], s_start[65];
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
     constexpr int HL = W / 2;
@@ -1159,90 +1180,76 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
     }
     const int rxy = rw[0] * rw[1];
     T *sh = reinterpret_cast<T *>(sm_raw);
-    {
-        const int lane = threadIdx.x & 31;
-        const int nrows = rw[1] * rw[2];
-        for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
-            const int z = D == 3 ? row / rw[1] : 0, y = D == 3 ? row - z * rw[1] : row;
-            int gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
-            gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
-            if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
-            const int64_t rbase = ((int64_t)gz * g.nf[1] + gy) * g.nf[0];
-            for (int x = lane; x < rw[0]; x += 32) {
-                int gx = s[0] - HL + x;
-                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
-                sh[row * rw[0] + x] = h[rbase + gx];
+    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+    {   // stage the tile and its halo, four loads per thread in flight; the staged region is
+        // narrower than the grid, so it wraps at most once per axis
+        constexpr int IL = 4;
+        const int cells = rxy * rw[2];
+        for (int i0 = threadIdx.x; i0 < cells; i0 += IL * blockDim.x) {
+            T v[IL];
+#pragma unroll
+            for (int k = 0; k < IL; ++k) {
+                const int i = i0 + k * blockDim.x;
+                if (i < cells) {
+                    const int row = i / rw[0], x = i - row * rw[0];
+                    const int z = D == 3 ? row / rw[1] : 0, y = D == 3 ? row - z * rw[1] : row;
+                    int gx = s[0] - HL + x, gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
+                    gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+                    gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+                    if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
+                    v[k] = h[((int64_t)gz * g.nf[1] + gy) * g.nf[0] + gx];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < IL; ++k) {
+                const int i = i0 + k * blockDim.x;
+                if (i < cells) sh[i] = v[k];
             }
         }
     }
     __syncthreads();
     const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+    if (sizeof(T) == 4 && p1 - p0 <= g.list_cap) {
+        // residue-grouped entries: packed window start, D kernel offsets, caller index
+        const int cap = g.list_cap;
+        int *l_i0 = reinterpret_cast<int *>(sm_raw + interp_kd_tile_bytes(g, sizeof(T)));
+        float *l_x1 = reinterpret_cast<float *>(l_i0 + cap);
+        int *l_j = l_i0 + (1 + D) * cap;
+        const int rounds = residue_lists<T, W, D>(
+            sorted, p0, p1, rw[0], rxy, s_cnt, s_start,
+            [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned j) {
+                l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
+#pragma unroll
+                for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
+                l_j[slot] = (int)j;
+            });
+        const int lane = threadIdx.x & 31;
+        const int mine = s_cnt[lane], first = s_start[lane];
+        for (int q = threadIdx.x >> 5; q < rounds; q += blockDim.x >> 5) {
+            if (q < mine) {
+                const int h = first + q;
+                const int pk = l_i0[h];
+                const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+                T x1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + h];
+                interp_window_kd<T, W, D>(ep, i0, x1, (int64_t)l_j[h], sh, rw[0], rxy, dsx, dsy,
+                                          dsz, grad);
+            }
+        }
+        return;
+    }
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
         const int64_t j = load_record<T, D>(sorted, perm, p, u);
-        int i0[3] = {0, 0, 0};
-        T x1[3] = {T(0), T(0), T(0)};
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-            int rel;
-            T f;
-            unpack_coord<T>(u[a], rel, f);
-            i0[a] = rel + support_start<T, W>(f, x1[a]) + HL;
-        }
-        T wx[W], dwx[W], wy[W], dwy[W];
-        es_weights_d<T, W>(ep, x1[0], wx, dwx);
-        es_weights_d<T, W>(ep, x1[1], wy, dwy);
-        if constexpr (D == 2) {
-            T gx = T(0), gy = T(0);
-#pragma unroll
-            for (int b = 0; b < W; ++b) {
-                const T *row = sh + (i0[1] + b) * rw[0] + i0[0];
-                T r0 = T(0), r1 = T(0);
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const T v = row[a];
-                    r0 = fma(wx[a], v, r0);
-                    r1 = fma(dwx[a], v, r1);
-                }
-                gx = fma(wy[b], r1, gx);
-                gy = fma(dwy[b], r0, gy);
-            }
-            using T2 = typename PT<T>::C;
-            reinterpret_cast<T2 *>(grad)[j] = T2{dsx * gx, dsy * gy};
-        } else {
-            T wz[W], dwz[W];
-            es_weights_d<T, W>(ep, x1[2], wz, dwz);
-            T gx = T(0), gy = T(0), gz = T(0);
-#pragma unroll 1
-            for (int c = 0; c < W; ++c) {
-                T px = T(0), py = T(0), pz = T(0);
-#pragma unroll
-                for (int b = 0; b < W; ++b) {
-                    const T *row = sh + (i0[2] + c) * rxy + (i0[1] + b) * rw[0] + i0[0];
-                    T r0 = T(0), r1 = T(0);
-#pragma unroll
-                    for (int a = 0; a < W; ++a) {
-                        const T v = row[a];
-                        r0 = fma(wx[a], v, r0);
-                        r1 = fma(dwx[a], v, r1);
-                    }
-                    px = fma(wy[b], r1, px);
-                    py = fma(dwy[b], r0, py);
-                    pz = fma(wy[b], r0, pz);
-                }
-                gx = fma(wz[c], px, gx);
-                gy = fma(wz[c], py, gy);
-                gz = fma(dwz[c], pz, gz);
-            }
-            grad[j * 3 + 0] = dsx * gx;
-            grad[j * 3 + 1] = dsy * gy;
-            grad[j * 3 + 2] = dsz * gz;
-        }
+        interp_point_kd<T, W, D>(ep, u, j, sh, rw[0], rxy, dsx, dsy, dsz, grad);
     }
 }
 
+// FP32 tiles with their entry lists take 60-110 KB of shared memory, so at most three (2D) or
+// two (3D) blocks are resident.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (D == 3 ? 2 : 3) : 2) k_interp_kd(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
     const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
     const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad) {
@@ -1254,7 +1261,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd(
 // Batched kernel-derivative interpolation: a persistent grid walks the tiles of every instance;
 // instance i's real field sits at h + I.go and its scale is -2 n_f / L per axis.
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp_kd_b(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_interp_kd_b(
     const BInst *__restrict__ inst, const int64_t *__restrict__ tile_first, int n_inst,
     int64_t n_tiles, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
     const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
@@ -1489,8 +1496,53 @@ __global__ void __launch_bounds__(256) k_rfft_merge_rows(const C *__restrict__ x
     }
 }
 
+
 // ---------------------------------------------------------------------------------------------
 // Launchers
+
+// Width-specialised launchers (one kernel instantiation per ES kernel width). Their definitions
+// below are instantiated in the fresco_w_*.cu units, a few widths per unit so that the units
+// compile in parallel; the units that instantiate Launch<T> see them through the extern
+// declarations of FRESCO_EXTERN_WIDTH_OPS.
+template <typename T, int W, int D>
+struct WOps {
+    static cudaError_t spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  cudaStream_t s);
+    static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const double *grad_out, T *grad, cudaStream_t s);
+    static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                 const int *perm, const int *off, const T *h,
+                                 const double *grad_out, const double dscale[3], T *grad,
+                                 cudaStream_t s);
+};
+
+// the same for the (2D) ensemble kernels
+template <typename T, int W>
+struct WOpsB {
+    static cudaError_t spread_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *off, T *grid, cudaStream_t s);
+    static cudaError_t interp_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                const int *perm, const int *off, const void *g0, const void *g1,
+                                const double *grad_out, T *grad, cudaStream_t s);
+    static cudaError_t interp_kd_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                   const int *perm, const int *off, const T *h,
+                                   const double *grad_out, T *grad, cudaStream_t s);
+};
+
+#define FRESCO_WIDTHS_LO(M, ...) M(2, __VA_ARGS__) M(3, __VA_ARGS__) M(4, __VA_ARGS__) \
+    M(5, __VA_ARGS__) M(6, __VA_ARGS__) M(7, __VA_ARGS__) M(8, __VA_ARGS__)
+#define FRESCO_WIDTHS_HI(M, ...) M(9, __VA_ARGS__) M(10, __VA_ARGS__) M(11, __VA_ARGS__) \
+    M(12, __VA_ARGS__) M(13, __VA_ARGS__) M(14, __VA_ARGS__) M(15, __VA_ARGS__) M(16, __VA_ARGS__)
+#define FRESCO_EXTERN_WOPS(W, T, D) extern template struct WOps<T, W, D>;
+#define FRESCO_EXTERN_WOPSB(W, T) extern template struct WOpsB<T, W>;
+#define FRESCO_INST_WOPS(W, T, D) template struct WOps<T, W, D>;
+#define FRESCO_INST_WOPSB(W, T) template struct WOpsB<T, W>;
+#define FRESCO_EXTERN_WIDTH_OPS(T)                                                             \
+    FRESCO_WIDTHS_LO(FRESCO_EXTERN_WOPS, T, 2) FRESCO_WIDTHS_HI(FRESCO_EXTERN_WOPS, T, 2)      \
+    FRESCO_WIDTHS_LO(FRESCO_EXTERN_WOPS, T, 3) FRESCO_WIDTHS_HI(FRESCO_EXTERN_WOPS, T, 3)      \
+    FRESCO_WIDTHS_LO(FRESCO_EXTERN_WOPSB, T) FRESCO_WIDTHS_HI(FRESCO_EXTERN_WOPSB, T)
 
 inline int grid_for(int64_t n, int threads, int cap) {
     int64_t b = (n + threads - 1) / threads;
@@ -1500,34 +1552,89 @@ inline int grid_for(int64_t n, int threads, int cap) {
 }
 
 template <typename T>
-cudaError_t Launch<T>::bin(const Geom &g, const T *points, int *cnt, int *key, int *slot,
-                           int *err, cudaStream_t s) {
-    const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
-    if (g.dim == 2) k_bin<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
-    else k_bin<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, key, slot, err);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t Launch<T>::scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
-                            int *launches) {
+                            int *launches, int *cur) {
     const int64_t nb = (n + 1023) / 1024;
     k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(cnt, off, block_sums, n);
     k_scan_sums<<<1, 1024, 0, s>>>(block_sums, nb, off + n);
-    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(off, block_sums, n);
+    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(off, block_sums, n, cur);
     *launches += 3;
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::scatter(const Geom &g, const T *points, const int *key, const int *slot,
-                               const int *off, void *sorted, int *perm, cudaStream_t s) {
+cudaError_t Launch<T>::count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s) {
+    const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
+    if (g.dim == 2) k_count<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, err);
+    else k_count<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::place(const Geom &g, const T *points, int *cur, void *sorted, int *perm,
+                             cudaStream_t s) {
     using U = typename PT<T>::U;
     const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
-    if (g.dim == 2)
-        k_scatter<T, 2><<<grid, 256, 0, s>>>(g, points, key, slot, off, (U *)sorted, perm);
-    else
-        k_scatter<T, 3><<<grid, 256, 0, s>>>(g, points, key, slot, off, (U *)sorted, perm);
+    if (g.dim == 2) k_place<T, 2><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm);
+    else k_place<T, 3><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm);
+    return cudaGetLastError();
+}
+
+template <typename T>
+int Launch<T>::spread_own_smem(const Geom &g) {
+    // the extended region, then (FP32) the residue-grouped entries: packed window start and D
+    // kernel offsets
+    return (int)(spread_own_tile_bytes(g, sizeof(T)) +
+                 (sizeof(T) == 4 ? (size_t)(1 + g.dim) * 4 * (size_t)g.list_cap : 0));
+}
+
+template <typename T>
+int64_t Launch<T>::ring_slot(const Geom &g) {
+    const int w = g.width;
+    int64_t e = (int64_t)(g.tmax[0] + w) * (g.tmax[1] + w);
+    int64_t i = (int64_t)g.tmax[0] * g.tmax[1];
+    if (g.dim == 3) {
+        e *= g.tmax[2] + w;
+        i *= g.tmax[2];
+    }
+    return e - i;
+}
+
+template <typename T, int W, int D>
+cudaError_t WOps<T, W, D>::spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                      const int *off, T *grid, T *ring, int64_t ring_slot,
+                                      cudaStream_t s) {
+    using U = typename PT<T>::U;
+    const int smem = Launch<T>::spread_own_smem(g);
+    auto kern = k_spread_own<T, W, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid, ring,
+                                                ring_slot);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // one launch per axis when every tile along it is at least W wide, else two (low, high)
+    const unsigned nt = (unsigned)g.n_tiles;
+    if (g.tq[0] >= W) {
+        k_halo_fold<T, W, D, 0, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+    } else {
+        k_halo_fold<T, W, D, 0, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 0, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+    }
+    if (g.tq[1] >= W) {
+        k_halo_fold<T, W, D, 1, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+    } else {
+        k_halo_fold<T, W, D, 1, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 1, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+    }
+    if constexpr (D == 3) {
+        if (g.tq[2] >= W) {
+            k_halo_fold<T, W, D, 2, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        } else {
+            k_halo_fold<T, W, D, 2, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 2, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -1540,9 +1647,10 @@ int Launch<T>::spread_smem(const Geom &g) {
 
 template <typename T>
 int Launch<T>::interp_kd_smem(const Geom &g) {
-    const int w = g.width;
-    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
-    return (int)(cells * sizeof(T));
+    // the staged field, then (FP32) the residue-grouped entries: packed window start, D kernel
+    // offsets and the caller index
+    return (int)(interp_kd_tile_bytes(g, sizeof(T)) +
+                 (sizeof(T) == 4 ? (size_t)(2 + g.dim) * 4 * (size_t)g.list_cap : 0));
 }
 
 template <typename T>
@@ -1587,22 +1695,9 @@ int Launch<T>::interp_smem(const Geom &g) {
 }
 
 template <typename T, int W, int D>
-static cudaError_t launch_spread_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                   const int *off, T *grid, cudaStream_t s) {
-    using U = typename PT<T>::U;
-    const int smem = Launch<T>::spread_smem(g);
-    auto kern = k_spread<T, W, D>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid);
-    return cudaGetLastError();
-}
-
-template <typename T, int W, int D>
-static cudaError_t launch_interp_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                   const int *perm, const int *off, const void *g0,
-                                   const void *g1, const double *grad_out, T *grad,
-                                   cudaStream_t s) {
+cudaError_t WOps<T, W, D>::interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                  const int *perm, const int *off, const void *g0, const void *g1,
+                                  const double *grad_out, T *grad, cudaStream_t s) {
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
     const int smem = Launch<T>::interp_smem(g);
@@ -1615,10 +1710,10 @@ static cudaError_t launch_interp_w(const Geom &g, const EsPoly<T> &ep, const voi
 }
 
 template <typename T, int W, int D>
-static cudaError_t launch_interp_kd_w(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                      const int *perm, const int *off, const T *h,
-                                      const double *grad_out, const double dscale[3], T *grad,
-                                      cudaStream_t s) {
+cudaError_t WOps<T, W, D>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                     const int *perm, const int *off, const T *h,
+                                     const double *grad_out, const double dscale[3], T *grad,
+                                     cudaStream_t s) {
     using U = typename PT<T>::U;
     const int smem = Launch<T>::interp_kd_smem(g);
     auto kern = k_interp_kd<T, W, D>;
@@ -1650,14 +1745,17 @@ static cudaError_t launch_interp_kd_w(const Geom &g, const EsPoly<T> &ep, const 
     }
 
 template <typename T>
-cudaError_t Launch<T>::spread(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                              const int *off, T *grid, cudaStream_t s) {
+cudaError_t Launch<T>::spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
+                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  cudaStream_t s, int *launches) {
+    *launches += 1;
+    for (int a = 0; a < g.dim; ++a) *launches += g.tq[a] >= g.width ? 1 : 2;
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width,
-                            return (launch_spread_w<T, WW, 2>(g, ep, sorted, off, grid, s)));
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::spread_own(g, ep, sorted, off, grid,
+                                                                          ring, ring_slot, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width,
-                            return (launch_spread_w<T, WW, 3>(g, ep, sorted, off, grid, s)));
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::spread_own(g, ep, sorted, off, grid,
+                                                                          ring, ring_slot, s)));
     }
 }
 
@@ -1666,10 +1764,10 @@ cudaError_t Launch<T>::interp(const Geom &g, const EsPoly<T> &ep, const void *so
                               const int *perm, const int *off, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s) {
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 2>(g, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp(g, ep, sorted, perm, off,
                                                                       g0, g1, grad_out, grad, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_w<T, WW, 3>(g, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp(g, ep, sorted, perm, off,
                                                                       g0, g1, grad_out, grad, s)));
     }
 }
@@ -1680,10 +1778,10 @@ cudaError_t Launch<T>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void 
                                  const double *grad_out, const double dscale[3], T *grad,
                                  cudaStream_t s) {
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_kd_w<T, WW, 2>(
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp_kd(
                                          g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (launch_interp_kd_w<T, WW, 3>(
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp_kd(
                                          g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
     }
 }
@@ -1783,9 +1881,10 @@ cudaError_t Launch<T>::scatter_b(const BTables &b, const T *points, const int *k
     return cudaGetLastError();
 }
 
-template <typename T, int W, int D>
-static cudaError_t launch_spread_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
-                                    const int *off, T *grid, cudaStream_t s) {
+template <typename T, int W>
+cudaError_t WOpsB<T, W>::spread_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                  const int *off, T *grid, cudaStream_t s) {
+    constexpr int D = 2;
     using U = typename PT<T>::U;
     const int smem = Launch<T>::spread_smem(tiles_geom(b));
     auto kern = k_spread_b<T, W, D>;
@@ -1797,11 +1896,11 @@ static cudaError_t launch_spread_bw(const BTables &b, const EsPoly<T> &ep, const
     return cudaGetLastError();
 }
 
-template <typename T, int W, int D>
-static cudaError_t launch_interp_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
-                                    const int *perm, const int *off, const void *g0,
-                                    const void *g1, const double *grad_out, T *grad,
-                                    cudaStream_t s) {
+template <typename T, int W>
+cudaError_t WOpsB<T, W>::interp_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                  const int *perm, const int *off, const void *g0, const void *g1,
+                                  const double *grad_out, T *grad, cudaStream_t s) {
+    constexpr int D = 2;
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
     const int smem = Launch<T>::interp_smem(tiles_geom(b));
@@ -1814,16 +1913,17 @@ static cudaError_t launch_interp_bw(const BTables &b, const EsPoly<T> &ep, const
     return cudaGetLastError();
 }
 
-template <typename T, int W, int D>
-static cudaError_t launch_interp_kd_bw(const BTables &b, const EsPoly<T> &ep, const void *sorted,
-                                       const int *perm, const int *off, const T *h,
-                                       const double *grad_out, T *grad, cudaStream_t s) {
+template <typename T, int W>
+cudaError_t WOpsB<T, W>::interp_kd_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
+                                     const int *perm, const int *off, const T *h,
+                                     const double *grad_out, T *grad, cudaStream_t s) {
+    constexpr int D = 2;
     using U = typename PT<T>::U;
     const int smem = Launch<T>::interp_kd_smem(tiles_geom(b));
     auto kern = k_interp_kd_b<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int blocks = (int)std::min<int64_t>(b.n_tiles, 152 * 6);
+    const int blocks = (int)std::min<int64_t>(b.n_tiles, 152 * 3);
     kern<<<blocks, 256, smem, s>>>(b.inst, b.tile_first, b.n_inst, b.n_tiles, ep, (const U *)sorted,
                                    perm, off, h, grad_out, grad);
     return cudaGetLastError();
@@ -1834,22 +1934,19 @@ cudaError_t Launch<T>::interp_kd_b(const BTables &b, const EsPoly<T> &ep, const 
                                    const int *perm, const int *off, const T *h,
                                    const double *grad_out, T *grad, cudaStream_t s) {
     if (b.dim == 2) {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_kd_bw<T, WW, 2>(b, ep, sorted, perm, off,
-                                                                           h, grad_out, grad, s)));
-    } else {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_kd_bw<T, WW, 3>(b, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(b.width, return (WOpsB<T, WW>::interp_kd_b(b, ep, sorted, perm, off,
                                                                            h, grad_out, grad, s)));
     }
+    return cudaErrorInvalidValue;   // ensembles are 2D
 }
 
 template <typename T>
 cudaError_t Launch<T>::spread_b(const BTables &b, const EsPoly<T> &ep, const void *sorted,
                                 const int *off, T *grid, cudaStream_t s) {
     if (b.dim == 2) {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_spread_bw<T, WW, 2>(b, ep, sorted, off, grid, s)));
-    } else {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_spread_bw<T, WW, 3>(b, ep, sorted, off, grid, s)));
+        FRESCO_WIDTH_SWITCH(b.width, return (WOpsB<T, WW>::spread_b(b, ep, sorted, off, grid, s)));
     }
+    return cudaErrorInvalidValue;   // ensembles are 2D
 }
 
 template <typename T>
@@ -1857,12 +1954,10 @@ cudaError_t Launch<T>::interp_b(const BTables &b, const EsPoly<T> &ep, const voi
                                 const int *perm, const int *off, const void *g0, const void *g1,
                                 const double *grad_out, T *grad, cudaStream_t s) {
     if (b.dim == 2) {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_bw<T, WW, 2>(b, ep, sorted, perm, off,
-                                                                        g0, g1, grad_out, grad, s)));
-    } else {
-        FRESCO_WIDTH_SWITCH(b.width, return (launch_interp_bw<T, WW, 3>(b, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(b.width, return (WOpsB<T, WW>::interp_b(b, ep, sorted, perm, off,
                                                                         g0, g1, grad_out, grad, s)));
     }
+    return cudaErrorInvalidValue;   // ensembles are 2D
 }
 
 template <typename T>

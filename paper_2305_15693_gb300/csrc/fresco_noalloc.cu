@@ -1,19 +1,25 @@
 // fresco_loss_noalloc: the structure-factor loss sum_q W_q (S_q - S0_q)^2 over caller-provided
 // device arrays, computed without allocating any memory.
 //
-// It is a variant of the plan's loss reduction (per-block FP64 partial sums, then a fixed-order
-// second stage). The plan keeps its partial sums in memory it allocated at plan time; this entry
-// point keeps them instead in one file-scope device array, g_loss_partials, that the library
-// image brings with it. Every GPU that loads the library holds that array (512 KiB) until the
-// process exits.
+// It sums like the plan's loss reduction (per-block FP64 partial sums, then a fixed-order second
+// stage). A plan keeps its partial sums in memory it allocated at plan time; this entry point
+// keeps them instead in one file-scope device array, g_loss_partials, that the library image
+// brings with it (512 KiB, held by every GPU on which the library's module is loaded, until the
+// process exits).
+//
+// CUDA loads a library's modules lazily by default (CUDA_MODULE_LOADING=LAZY): the module holding
+// the array, and with it the array's device memory, is loaded on a device by the first
+// cudaGetSymbolAddress made with that device current, that is, by the first call of this entry
+// point there. Callers under a fixed memory budget make one warm-up call per device at start-up.
 //
 // The array's name, used in host code, is only a host-side stand-in for the device symbol, never
-// a device address. The device address is obtained once per device with cudaGetSymbolAddress
-// while that device is current, checked, cached, and passed to the kernels as a pointer.
+// a device address. Every call looks the device address up with cudaGetSymbolAddress while the
+// caller's device is current (no allocation once the module is loaded), checks the result, and
+// passes the pointer to the kernels; nothing is cached, so a context that was torn down and
+// created again (cudaDeviceReset) gets the address of its own copy.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "fresco.h"
 
@@ -23,7 +29,6 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;                                  // rows per thread
 constexpr int64_t kRowsPerBlock = (int64_t)kThreads * kItems;
 constexpr int kMaxPartials = 65536;                         // 65536 doubles = 512 KiB
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_loss_partials[kMaxPartials];
 
@@ -70,27 +75,16 @@ __global__ void __launch_bounds__(512) k_loss_final(const double *__restrict__ p
     if (threadIdx.x == 0) *loss = sm[0];
 }
 
-std::mutex g_mutex;
-double *g_scratch[kMaxDevices] = {};
-
-// Device address of g_loss_partials on the current device, looked up on first use per device.
+// Device address of g_loss_partials on the current device (loading the module on the first use
+// per context).
 fresco_status scratch_on_current_device(double **out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_loss_partials);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
         return FRESCO_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_loss_partials);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return FRESCO_ERR_CUDA;
-        }
-        g_scratch[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch[dev];
+    *out = static_cast<double *>(p);
     return FRESCO_OK;
 }
 
@@ -103,6 +97,7 @@ extern "C" fresco_status fresco_loss_noalloc(int precision, int64_t n_k, const v
     if (n_k < 1 || !d_S || !d_S0 || !d_W || !d_loss) return FRESCO_ERR_ARG;
     const int64_t nb = (n_k + kRowsPerBlock - 1) / kRowsPerBlock;
     if (nb > kMaxPartials) return FRESCO_ERR_UNSUPPORTED;   // n_k above FRESCO_LOSS_NOALLOC_MAX_ROWS
+    cudaGetLastError();   // a pending launch error of earlier, unrelated work is not this call's
     double *partial = nullptr;
     fresco_status st = scratch_on_current_device(&partial);
     if (st != FRESCO_OK) return st;

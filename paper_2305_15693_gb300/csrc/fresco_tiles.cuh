@@ -1,0 +1,548 @@
+// Single-plan binning and type-1 spreading over tiles without border sub-bins.
+//
+// Binning (K1) in two passes over the caller's points, with no per-point key or rank arrays:
+//   k_count  counts the points of every bin (global atomics whose result is unused);
+//   (exclusive scan of the counts into off[], and a copy of off[] into the cursor array cur[])
+//   k_place  recomputes each point's bin and record and takes its sorted position from the
+//            bin's cursor, pos = atomicAdd(&cur[bin], 1).
+// A tile owns Geom.sub consecutive bins, bin = tile * sub + (caller index mod sub): the points of
+// a tile stay contiguous (off[t sub] .. off[(t + 1) sub]), and each cursor takes 1/sub of the
+// tile's atomics, which keeps the returning atomics from queueing on few addresses.
+// The order of the points inside a tile depends on the order the atomics run in. Nothing
+// downstream depends on it: the fixed-point spread sums integers (order independent), the
+// interpolation writes each point's gradient through its caller index.
+//
+// Spreading (K2) with own points only: the block of tile t accumulates the full kernel windows of
+// the points of tile t into the tile's extended region (the tile plus W/2 cells below and
+// W - W/2 above on each axis, where a window of a point of the tile can reach) in shared memory,
+// with no bounds checks. It writes the tile's own cells to the grid and the rest of the region
+// (its ring) to a per-tile ring buffer; k_halo_add then adds to every cell near a tile border the
+// ring values that the neighbouring tiles' points put there, in a fixed order.
+//
+// Ring layout of one tile (extents E_a = w_a + W, HL = W/2): the extended region is walked plane
+// by plane (z) and row by row (y); rows that lie outside the tile (in y or z) are stored whole
+// (E_x cells), rows through the tile store only their W halo cells (HL below the tile in x, then
+// W - HL above). ring_index maps an extended-region cell outside the tile to its position.
+#pragma once
+
+#include <utility>
+
+namespace fresco {
+
+template <int W, int D>
+__host__ __device__ __forceinline__ int ring_index(int ex, int ey, int ez, int wx, int wy, int wz) {
+    constexpr int HL = W / 2;
+    const int Ex = wx + W, Ey = wy + W;
+    const int full_plane = Ex * Ey;
+    const int mid_plane = W * Ex + wy * W;
+    int base = 0;
+    bool mid = true;
+    if (D == 3) {
+        if (ez < HL) {
+            base = ez * full_plane;
+            mid = false;
+        } else if (ez < HL + wz) {
+            base = HL * full_plane + (ez - HL) * mid_plane;
+        } else {
+            base = HL * full_plane + wz * mid_plane + (ez - HL - wz) * full_plane;
+            mid = false;
+        }
+    }
+    if (!mid || ey < HL) return base + ey * Ex + ex;
+    if (ey < HL + wy) return base + HL * Ex + (ey - HL) * W + (ex < HL ? ex : ex - wx);
+    return base + HL * Ex + wy * W + (ey - HL - wy) * Ex + ex;
+}
+
+// ring cells of a tile of widths w (unused axes 1)
+template <int W, int D>
+__host__ __device__ inline int64_t ring_cells(int wx, int wy, int wz) {
+    int64_t e = (int64_t)(wx + W) * (wy + W), i = (int64_t)wx * wy;
+    if (D == 3) {
+        e *= wz + W;
+        i *= wz;
+    }
+    return e - i;
+}
+
+// tile of a point along every axis, its cell relative to the tile and the fraction
+template <typename T, int D>
+__device__ __forceinline__ int tile_cell(const Geom &g, const T (&r)[3], int (&rel)[3],
+                                         T (&frac)[3], bool &ok) {
+    int t[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int cell;
+        ok &= fine_coord<T>(r[a], (T)g.s_hi[a], (T)g.s_lo[a], g.nf[a], cell, frac[a]);
+        t[a] = tile_of_cell(cell, g.tq[a], g.tr[a], g.tinv[a]);
+        rel[a] = cell - tile_start(t[a], g.tq[a], g.tr[a]);
+    }
+    return t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_count(Geom g, const T *__restrict__ pts,
+                                               int *__restrict__ cnt, int *__restrict__ err) {
+    constexpr int IL = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
+    bool ok = true;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
+         j0 += stride) {
+        T r[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                r[k][a] = (a < D && j < g.n_points) ? pts[j * D + a] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            int rel[3];
+            T frac[3];
+            const int t = tile_cell<T, D>(g, r[k], rel, frac, ok);
+            if (j < g.n_points) atomicAdd(&cnt[t * g.sub + (int)(j % g.sub)], 1);
+        }
+    }
+    if (!ok) atomicOr(err, 1);
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_place(Geom g, const T *__restrict__ pts,
+                                               int *__restrict__ cur,
+                                               typename PT<T>::U *__restrict__ sorted,
+                                               int *__restrict__ perm) {
+    using U = typename PT<T>::U;
+    constexpr int IL = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
+         j0 += stride) {
+        T r[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                r[k][a] = (a < D && j < g.n_points) ? pts[j * D + a] : T(0);
+        }
+        int pos[IL];
+        U u[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            int rel[3] = {0, 0, 0};
+            T frac[3] = {T(0), T(0), T(0)};
+            bool ok = true;
+            const int t = tile_cell<T, D>(g, r[k], rel, frac, ok);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u[k][a] = a < D ? pack_coord<T>(rel[a], frac[a]) : U(0);
+            pos[k] = j < g.n_points ? atomicAdd(&cur[t * g.sub + (int)(j % g.sub)], 1) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = j0 + (int64_t)k * blockDim.x;
+            if (j < g.n_points) store_record<T, D>(sorted, perm, pos[k], u[k], (int)j);
+        }
+    }
+}
+
+// Shared-memory accesses of the window loops, written as PTX on 32-bit shared-space addresses
+// with the offset inside the window row as an immediate, so that each cell of a window costs one
+// memory instruction (plus the arithmetic of its value) and no address arithmetic. They carry no
+// memory clobber (that would make the compiler reload every value around each access); their
+// order against the block's other shared-memory traffic comes from the __syncthreads() that
+// separate the phases of the kernels (staging / accumulation / write-out).
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+template <int OFF>
+__device__ __forceinline__ void red_add_shared(unsigned addr, int v) {
+    asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF));
+}
+
+template <int OFF>
+__device__ __forceinline__ float ld_shared_f32(unsigned addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+// row[a] += round(ws * wx[a] * 2^s) for a < W (ws carries the scale), as fixed-point integers:
+// adding 1.5 * 2^23 rounds the product to an integer held in the low mantissa bits.
+template <int W, int... A>
+__device__ __forceinline__ void red_row_fixed(unsigned row, float ws, const float (&wx)[W],
+                                              std::integer_sequence<int, A...>) {
+    (red_add_shared<4 * A>(row, __float_as_int(fmaf(ws, wx[A], 12582912.0f)) - 0x4B400000), ...);
+}
+
+template <int A, int W>
+__device__ __forceinline__ void dot_cell_kd(unsigned row, const float (&wx)[W],
+                                            const float (&dwx)[W], float &r0, float &r1) {
+    const float v = ld_shared_f32<4 * A>(row);
+    r0 = fmaf(wx[A], v, r0);
+    r1 = fmaf(dwx[A], v, r1);
+}
+
+// (sum_a wx[a] row[a], sum_a dwx[a] row[a]) for a < W, one load per cell
+template <int W, int... A>
+__device__ __forceinline__ void dot_row_kd(unsigned row, const float (&wx)[W],
+                                           const float (&dwx)[W], float &r0, float &r1,
+                                           std::integer_sequence<int, A...>) {
+    (dot_cell_kd<A, W>(row, wx, dwx, r0, r1), ...);
+}
+
+// Bytes of a tile's extended region in shared memory (rounded up to 16), before the index list.
+__host__ __device__ inline size_t spread_own_tile_bytes(const Geom &g, size_t esize) {
+    const int w = g.width;
+    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
+    return (cells * (esize > 4 ? esize : 4) + 15) & ~(size_t)15;
+}
+
+// One point's full window into the extended region (i0: window start in extended-region
+// coordinates, which keeps the whole window inside the region), no bounds checks.
+template <typename T, int W, int D>
+__device__ __forceinline__ void spread_point_own(const EsPoly<T> &ep, const int (&i0)[3],
+                                                 const T (&x1)[3], int Ex, int Exy, T *ftile,
+                                                 int *itile, bool fixed, float fscale) {
+    T wx[W], wy[W];
+    es_weights<T, W>(ep, x1[0], wx);
+    es_weights<T, W>(ep, x1[1], wy);
+    if constexpr (D == 2) {
+        if constexpr (sizeof(T) == 4) {
+            if (fixed) {
+                const unsigned step = 4u * (unsigned)Ex;
+                unsigned row = smem_addr(itile) + 4u * (unsigned)(i0[1] * Ex + i0[0]);
+#pragma unroll
+                for (int b = 0; b < W; ++b, row += step)
+                    red_row_fixed<W>(row, wy[b] * fscale, wx, std::make_integer_sequence<int, W>{});
+                return;
+            }
+        }
+        T *base = ftile + i0[1] * Ex + i0[0];
+#pragma unroll
+        for (int b = 0; b < W; ++b)
+#pragma unroll
+            for (int a = 0; a < W; ++a) atomicAdd(base + b * Ex + a, wy[b] * wx[a]);
+    } else {
+        T wz[W];
+        es_weights<T, W>(ep, x1[2], wz);
+        const int o = (i0[2] * Exy) + i0[1] * Ex + i0[0];
+        if constexpr (sizeof(T) == 4) {
+            if (fixed) {
+                const unsigned step = 4u * (unsigned)Ex, pstep = 4u * (unsigned)Exy;
+                unsigned plane = smem_addr(itile) + 4u * (unsigned)o;
+#pragma unroll (W <= 8 ? W : 1)
+                for (int c = 0; c < W; ++c, plane += pstep) {
+                    const float wzs = wz[c] * fscale;
+                    unsigned row = plane;
+#pragma unroll
+                    for (int b = 0; b < W; ++b, row += step)
+                        red_row_fixed<W>(row, wzs * wy[b], wx, std::make_integer_sequence<int, W>{});
+                }
+                return;
+            }
+        }
+#pragma unroll 1
+        for (int c = 0; c < W; ++c) {
+            T *plane = ftile + o + c * Exy;
+#pragma unroll
+            for (int b = 0; b < W; ++b) {
+                const T wzy = wz[c] * wy[b];
+#pragma unroll
+                for (int a = 0; a < W; ++a) atomicAdd(plane + b * Ex + a, wzy * wx[a]);
+            }
+        }
+    }
+}
+
+// Extended-region extents (and tile start / widths) of tile t.
+__device__ __forceinline__ void tile_extent(const Geom &g, int64_t t, int W, int (&s)[3],
+                                            int (&w)[3], int (&tc)[3]) {
+    tc[0] = (int)(t % g.nb[0]);
+    tc[1] = (int)((t / g.nb[0]) % g.nb[1]);
+    tc[2] = (int)(t / ((int64_t)g.nb[0] * g.nb[1]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a < g.dim) {
+            s[a] = tile_start(tc[a], g.tq[a], g.tr[a]);
+            w[a] = tile_start(tc[a] + 1, g.tq[a], g.tr[a]) - s[a];
+        } else {
+            s[a] = 0;
+            w[a] = 1;
+        }
+    }
+}
+
+// Points of tile t are spread in FP32 plans in 32-bit fixed point with scale 2^s, s = min(21,
+// clz(P) - 1) for P points, when P < kFixedMaxPoints (s >= 17: every contribution rounded to at
+// most 2^-18, and no cell sum can reach 2^31 because every weight is at most 1); a more crowded
+// tile accumulates float atomics. Double plans accumulate double atomics.
+constexpr int kFixedMaxPoints = 1 << 14;
+
+// Bank-residue schedule. A point's window starts at word b = i0_z E_xy + i0_y E_x + i0_x of the
+// extended region, and every step of the window loop adds the same offset to the start of all
+// lanes; so a warp whose 32 points have 32 distinct residues b mod 32 touches 32 distinct
+// shared-memory banks at every step (no bank conflicts). The block counts its points per residue,
+// lists their indices grouped by residue, and lane j of a warp always takes a point of residue j
+// (warp k takes the k-th, (k + n_warps)-th, ... point of every residue).
+template <typename T, int W, int D>
+__device__ __forceinline__ int window_of(const typename PT<T>::U (&u)[3], int Ex, int Exy,
+                                         int (&i0)[3], T (&x1)[3]) {
+    constexpr int HL = W / 2;
+    i0[0] = i0[1] = i0[2] = 0;
+    x1[0] = x1[1] = x1[2] = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        int rel;
+        T f;
+        unpack_coord<T>(u[a], rel, f);
+        i0[a] = rel + support_start<T, W>(f, x1[a]) + HL;
+    }
+    return (i0[2] * Exy + i0[1] * Ex + i0[0]) & 31;
+}
+
+// Groups the block's points [p0, p1) by window residue: cnt[j] points of residue j, placed at
+// slots start[j] ... (start[j] + cnt[j] - 1) by put(slot, p - p0, i0, x1, w3) (w3: the caller
+// index a float record carries, 0 for double records); returns the largest count. Needs
+// P <= list_cap.
+template <typename T, int W, int D, typename Put>
+__device__ __forceinline__ int residue_lists(const typename PT<T>::U *__restrict__ sorted, int p0,
+                                             int p1, int Ex, int Exy, int *cnt, int *start,
+                                             Put put) {
+    using U = typename PT<T>::U;
+    constexpr int IL = 4;   // records per thread in flight
+    int *cur = start + 32;
+    const int bs = blockDim.x;
+    for (int p = p0 + threadIdx.x; p < p1; p += IL * bs) {
+        U u[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k)
+            if (p + k * bs < p1) load_packed<T, D>(sorted, p + k * bs, u[k]);
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            if (p + k * bs >= p1) break;
+            int i0[3];
+            T x1[3];
+            atomicAdd(&cnt[window_of<T, W, D>(u[k], Ex, Exy, i0, x1)], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int v = cnt[threadIdx.x];
+        int x = v, m = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((int)threadIdx.x >= o) x += y;
+            m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        }
+        start[threadIdx.x] = x - v;
+        cur[threadIdx.x] = x - v;
+        if (threadIdx.x == 0) start[64] = m;
+    }
+    __syncthreads();
+    for (int p = p0 + threadIdx.x; p < p1; p += IL * bs) {
+        U u[IL][3];
+        unsigned w3[IL];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            w3[k] = 0;
+            if (p + k * bs < p1) {
+                if constexpr (sizeof(T) == 4) {
+                    const uint4 v = reinterpret_cast<const uint4 *>(sorted)[p + k * bs];
+                    u[k][0] = v.x;
+                    u[k][1] = v.y;
+                    u[k][2] = v.z;
+                    w3[k] = v.w;
+                } else {
+                    load_packed<T, D>(sorted, p + k * bs, u[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            if (p + k * bs >= p1) break;
+            int i0[3];
+            T x1[3];
+            const int slot = atomicAdd(&cur[window_of<T, W, D>(u[k], Ex, Exy, i0, x1)], 1);
+            put(slot, p + k * bs - p0, i0, x1, w3[k]);
+        }
+    }
+    __syncthreads();
+    return start[64];
+}
+
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
+    Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ off, T *__restrict__ grid, T *__restrict__ ring,
+    int64_t ring_slot) {
+    using U = typename PT<T>::U;
+    constexpr int HL = W / 2;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ int s_cnt[32], s_start[65];
+    T *ftile = reinterpret_cast<T *>(sm_raw);
+    int *itile = reinterpret_cast<int *>(sm_raw);
+    // residue-grouped entries: packed window start (10 bits per axis) and kernel offsets
+    int *l_i0 = reinterpret_cast<int *>(sm_raw + spread_own_tile_bytes(g, sizeof(T)));
+    float *l_x1 = reinterpret_cast<float *>(l_i0 + g.list_cap);
+    const int64_t t = blockIdx.x;
+    int s[3], w[3], tc[3];
+    tile_extent(g, t, W, s, w, tc);
+    const int Ex = w[0] + W, Ey = w[1] + W, Ez = D == 3 ? w[2] + W : 1;
+    const int Exy = Ex * Ey, cells = Exy * Ez;
+    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+    const int P = p1 - p0;
+    bool fixed = false;
+    int sc = 0;
+    if constexpr (sizeof(T) == 4) {
+        fixed = P < kFixedMaxPoints;
+        sc = fixed ? min(21, __clz(max(P, 1)) - 1) : 0;
+    }
+    {   // zero the region, 16 bytes per store (the region starts 16-byte aligned)
+        const int words = cells * (int)(sizeof(T) / 4);
+        uint4 *z4 = reinterpret_cast<uint4 *>(sm_raw);
+        for (int i = threadIdx.x; i < words / 4; i += blockDim.x) z4[i] = make_uint4(0, 0, 0, 0);
+        for (int i = (words & ~3) + threadIdx.x; i < words; i += blockDim.x) itile[i] = 0;
+    }
+    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
+    const bool listed = sizeof(T) == 4 && fixed && P <= g.list_cap;
+    if (listed) {
+        const int cap = g.list_cap;
+        const int rounds = residue_lists<T, W, D>(
+            sorted, p0, p1, Ex, Exy, s_cnt, s_start,
+            [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned) {
+                l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
+#pragma unroll
+                for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
+            });
+        const int lane = threadIdx.x & 31;
+        const int nw = blockDim.x >> 5;
+        const int mine = s_cnt[lane], first = s_start[lane];
+        for (int q = threadIdx.x >> 5; q < rounds; q += nw) {
+            if (q < mine) {
+                const int h = first + q;
+                const int pk = l_i0[h];
+                const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+                T x1[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + h];
+                spread_point_own<T, W, D>(ep, i0, x1, Ex, Exy, ftile, itile, true, fscale);
+            }
+        }
+    } else {
+        for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            U u[3];
+            load_packed<T, D>(sorted, p, u);
+            int i0[3];
+            T x1[3];
+            window_of<T, W, D>(u, Ex, Exy, i0, x1);
+            spread_point_own<T, W, D>(ep, i0, x1, Ex, Exy, ftile, itile, fixed, fscale);
+        }
+    }
+    __syncthreads();
+    const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
+    const int lane = threadIdx.x & 31;
+    T *myring = ring + t * ring_slot;
+    // one warp per row of the region: the cells inside the tile go to the grid, the others to the
+    // ring, whose cells of one row are contiguous
+    for (int row = threadIdx.x >> 5; row < Ey * Ez; row += blockDim.x >> 5) {
+        const int ez = D == 3 ? row / Ey : 0, ey = row - ez * Ey;
+        const bool through =
+            (D < 3 || (ez >= HL && ez < HL + w[2])) && (ey >= HL && ey < HL + w[1]);
+        const int64_t gbase =
+            ((int64_t)(D == 3 ? s[2] + ez - HL : 0) * g.nf[1] + (s[1] + ey - HL)) * g.nf[0] +
+            s[0] - HL;
+        T *rrow = myring + ring_index<W, D>(0, ey, ez, w[0], w[1], w[2]);
+        for (int ex = lane; ex < Ex; ex += 32) {
+            const int i = row * Ex + ex;
+            T v;
+            if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i] * finv : ftile[i];
+            else v = ftile[i];
+            if (!through) rrow[ex] = v;
+            else if (ex < HL) rrow[ex] = v;
+            else if (ex >= HL + w[0]) rrow[ex - w[0]] = v;
+            else grid[gbase + ex] = v;
+        }
+    }
+}
+
+// Folds the rings into the grid, one axis A at a time (x, then y, then z). In the pass along A
+// every tile adds the cells of its extended region that lie in its halo bands along A (the W/2
+// cells below the tile and the W - W/2 above it) and inside the tile along the axes already
+// folded (b < A) to the cells of its neighbour along A that they overlap; those lie in the
+// neighbour's own band along A, either inside the neighbour along every axis (a grid cell) or in
+// its halo along a later axis (one of its ring cells, folded in a later pass). A corner of the
+// region thus reaches its tile in up to D hops. Within one pass the cells read (halo bands along
+// A) and written (own bands along A) are disjoint; SIDES = 1 moves the low bands only, 2 the high
+// bands only, 3 both in one launch, which needs tiles at least W wide along A (the cells a tile
+// receives from below and from above are then disjoint). So no cell is written twice in a
+// launch: the passes are race-free and the sums are in a fixed order.
+template <typename T, int W, int D, int A, int SIDES>
+__global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
+                                                   int64_t ring_slot, T *__restrict__ grid) {
+    constexpr int HL = W / 2;
+    const int64_t t = blockIdx.x;
+    int s[3], w[3], tc[3];
+    tile_extent(g, t, W, s, w, tc);
+    // extents of the cells moved: NA along A, the tile along folded axes, the region after A
+    constexpr int HR = W - HL;
+    constexpr int NA = SIDES == 3 ? W : (SIDES == 1 ? HL : HR);   // cells moved along A
+    int ext[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        ext[b] = b >= D ? 1 : (b == A ? NA : (b < A ? w[b] : w[b] + W));
+    // neighbours along A
+    const int lo_t = tc[A] == 0 ? g.nb[A] - 1 : tc[A] - 1;
+    const int hi_t = tc[A] == g.nb[A] - 1 ? 0 : tc[A] + 1;
+    const int lo_s = tile_start(lo_t, g.tq[A], g.tr[A]);
+    const int lo_w = tile_start(lo_t + 1, g.tq[A], g.tr[A]) - lo_s;
+    const int hi_s = tile_start(hi_t, g.tq[A], g.tr[A]);
+    const int hi_w = tile_start(hi_t + 1, g.tq[A], g.tr[A]) - hi_s;
+    int64_t stride_t[3] = {1, g.nb[0], (int64_t)g.nb[0] * g.nb[1]};
+    const int64_t t_lo = t + (int64_t)(lo_t - tc[A]) * stride_t[A];
+    const int64_t t_hi = t + (int64_t)(hi_t - tc[A]) * stride_t[A];
+    const T *src_ring = ring + t * ring_slot;
+    const int count = ext[0] * ext[1] * ext[2];
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        int e[3];
+        e[0] = i % ext[0];
+        e[1] = (i / ext[0]) % ext[1];
+        e[2] = i / (ext[0] * ext[1]);
+        // e along folded axes counts from the tile's first cell
+#pragma unroll
+        for (int b = 0; b < A; ++b) e[b] += HL;
+        if (SIDES == 2) e[A] += HL;   // high band only
+        const bool low = e[A] < HL;
+        if (!low) e[A] += w[A];      // high band: HL + w .. w + W - 1
+        const T v = src_ring[ring_index<W, D>(e[0], e[1], e[2], w[0], w[1], w[2])];
+        // the same cell in the neighbour's extended region
+        int f[3] = {e[0], e[1], e[2]}, fw[3] = {w[0], w[1], w[2]};
+        int64_t u;
+        if (low) {
+            f[A] = e[A] + lo_w;
+            fw[A] = lo_w;
+            u = t_lo;
+        } else {
+            f[A] = e[A] - w[A];
+            fw[A] = hi_w;
+            u = t_hi;
+        }
+        bool inside = true;
+#pragma unroll
+        for (int b = A + 1; b < D; ++b) inside = inside && f[b] >= HL && f[b] < HL + fw[b];
+        if (inside) {
+            int gc[3] = {0, 0, 0};
+#pragma unroll
+            for (int b = 0; b < D; ++b) gc[b] = (b == A ? (low ? lo_s : hi_s) : s[b]) + f[b] - HL;
+            grid[((int64_t)gc[2] * g.nf[1] + gc[1]) * g.nf[0] + gc[0]] += v;
+        } else {
+            ring[u * ring_slot + ring_index<W, D>(f[0], f[1], f[2], fw[0], fw[1], fw[2])] += v;
+        }
+    }
+}
+
+}  // namespace fresco

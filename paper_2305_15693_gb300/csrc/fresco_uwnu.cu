@@ -31,6 +31,13 @@
 
 using namespace fresco;
 
+namespace fresco {
+FRESCO_EXTERN_WIDTH_OPS(float)
+FRESCO_EXTERN_WIDTH_OPS(double)
+extern template struct Launch<float>;
+extern template struct Launch<double>;
+}  // namespace fresco
+
 namespace {
 
 constexpr double kPiU = 3.141592653589793238462643383279502884;
@@ -151,6 +158,9 @@ __global__ void __launch_bounds__(256) k_un_fill(UGrid g, int64_t cells, const T
 
 // type 2, step 3, and the loss: rho~_q by interpolation, S_q, the loss and F partials, and the
 // type-1 strengths C_q = 4 W (S - S0) rho~ / rho0
+// dq (optional, point plans with constraints at real wavevectors): a per-constraint factor that
+// multiplies the interpolated sum before S is formed (the deconvolution of the points' own
+// spreading kernel); then C_q = 4 W (S - S0) dq rho_q / norm. norm = scal[0] (rho0, or N).
 template <typename T, int W, int D>
 __global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
                                                    const int *__restrict__ tcell,
@@ -159,6 +169,7 @@ __global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
                                                    const T *__restrict__ s0,
                                                    const T *__restrict__ wq,
                                                    const double *__restrict__ scal,
+                                                   const T *__restrict__ dq,
                                                    CxT<T> *__restrict__ coef, T *__restrict__ S_out,
                                                    double *__restrict__ part) {
     const double rho0 = scal[0];
@@ -204,12 +215,18 @@ __global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
                 im = fma(wt[2][k2], pm, im);
             }
         }
+        T dk = T(1);
+        if (dq) {
+            dk = dq[q];
+            re *= dk;
+            im *= dk;
+        }
         const T S = (re * re + im * im) * inv_rho0;
         const double d = (double)S - (double)s0[q];
         const double w = (double)wq[q];
         lsum = fma(w * d, d, lsum);
         fsum = fma(w * (double)S, d, fsum);
-        const T h = (T)(4.0 * w * d / rho0);
+        const T h = (T)(4.0 * w * d / rho0) * dk;
         coef[q] = CxT<T>{h * re, h * im};
         S_out[q] = S;
     }
@@ -275,13 +292,13 @@ __global__ void __launch_bounds__(256) k_un_grad(UGrid g, int64_t cells, const T
 template <typename T, int W>
 cudaError_t launch_un_interp(const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
                              T beta, const void *U, const T *s0, const T *wq, const double *scal,
-                             void *coef, T *S, double *part, int nb, cudaStream_t s) {
+                             const T *dq, void *coef, T *S, double *part, int nb, cudaStream_t s) {
     if (g.dim == 2)
         k_un_interp<T, W, 2><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta, (const CxT<T> *)U,
-                                                s0, wq, scal, (CxT<T> *)coef, S, part);
+                                                s0, wq, scal, dq, (CxT<T> *)coef, S, part);
     else
         k_un_interp<T, W, 3><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta, (const CxT<T> *)U,
-                                                s0, wq, scal, (CxT<T> *)coef, S, part);
+                                                s0, wq, scal, dq, (CxT<T> *)coef, S, part);
     return cudaGetLastError();
 }
 
@@ -300,9 +317,10 @@ cudaError_t launch_un_spread(const UGrid &g, int64_t n_k, const int *tcell, cons
 template <typename T>
 cudaError_t un_interp(int width, const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
                       T beta, const void *U, const T *s0, const T *wq, const double *scal,
-                      void *coef, T *S, double *part, int nb, cudaStream_t s) {
+                      const T *dq, void *coef, T *S, double *part, int nb, cudaStream_t s) {
     FRESCO_WIDTH_SWITCH(width, return (launch_un_interp<T, WW>(g, n_k, tcell, tfrac, beta, U, s0,
-                                                               wq, scal, coef, S, part, nb, s)));
+                                                               wq, scal, dq, coef, S, part, nb,
+                                                               s)));
 }
 
 template <typename T>
@@ -455,8 +473,8 @@ fresco_status un_eval(fresco_uwnu_s *u, const T *c, double *loss, T *grad) {
     fresco_status st = un_fft<T>(u, CUFFT_INVERSE);
     if (st) return st;
     UN_CUDA(un_interp<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, beta, u->U,
-                         (const T *)u->s0, (const T *)u->wq, u->scal, u->coef, (T *)u->S, u->part,
-                         u->nb, s));
+                         (const T *)u->s0, (const T *)u->wq, u->scal, (const T *)nullptr, u->coef,
+                         (T *)u->S, u->part, u->nb, s));
     k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 2, u->scal + 1);
     UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
     u->evaluated = true;
@@ -561,6 +579,345 @@ fresco_status fresco_uwnu_get_info(fresco_uwnu_t u, int *width, double *beta, in
 
 fresco_status fresco_uwnu_destroy(fresco_uwnu_t u) {
     un_free(u);
+    return FRESCO_OK;
+}
+
+}  // extern "C"
+
+// =============================================================================================
+// Points at free positions with constraints at real wavevectors (NUwNU, Methods "Analytical
+// gradients"): rho(k_q) = sum_j exp(-i k_q . r_j) for points r_j in [-L_a / 2, L_a / 2] (no
+// periodicity) and wavevectors k_q anywhere, S_q = |rho_q|^2 / N, L = sum_q W_q (S_q - S0_q)^2,
+// dL/dr_j = Re sum_q (4 i k_q W_q (S_q - S0_q) rho_q / N) exp(+i k_q . r_j).
+//
+// The type-3 transform is a spread followed by a type-2 transform. With a grid spacing h_a =
+// pi / (sigma K_a) (K_a = max_q |k_q,a|) the points spread with the ES kernel psi onto a periodic
+// grid of n1_a > L_a / h_a + w + 2 cells, cell c at position l h (l = c, or c - n1 past the middle,
+// so the windows never meet across the seam), give b_l = sum_j psi(l - r_j / h), and by Poisson
+// summation sum_l b_l exp(-i theta l) = Psi(theta) rho(k) at theta_a = k_a h_a (|theta_a| <= pi /
+// sigma, where the kernel's aliases are below the tolerance): rho_q = [sum_l b_l exp(-i theta_q
+// l)] / Psi(theta_q). The bracket is the type-2 sum of the weights-on-a-grid plan above, at nu_q =
+// theta_q n1 / (2 pi) cycles per grid length; Psi(theta) = prod_a integral psi(u) cos(theta_a u)
+// du, tabulated per constraint at plan time. The gradient is the chain rule through the same
+// steps: G_l = Re sum_q C_q exp(+i theta_q l), C_q = 4 W_q (S_q - S0_q) rho_q / (N Psi(theta_q)),
+// is the type-1 sum of that plan, and dL/dr_j,a = sum_l G_l d b_l / d r_j,a, the derivative of the
+// points' spreading kernel: the kernel-derivative interpolation at the points with scale -2 / h_a.
+// =============================================================================================
+
+namespace {
+
+// grid cell c of the points' grid (n1 per axis) -> centred index l, its cell on the fine grid of
+// the type-2 transform (n2 per axis), and 1 / Psi2(l)
+template <typename T>
+__device__ __forceinline__ T grid_site(const UGrid &g, int64_t c, const T *__restrict__ ip0,
+                                       const T *__restrict__ ip1, const T *__restrict__ ip2,
+                                       int64_t &fine) {
+    int l[3], f[3];
+    const int64_t cc[3] = {c % g.M[0], (c / g.M[0]) % g.M[1], c / ((int64_t)g.M[0] * g.M[1])};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        l[a] = (int)cc[a] < g.M[a] / 2 ? (int)cc[a] : (int)cc[a] - g.M[a];
+        f[a] = l[a] < 0 ? l[a] + g.nf[a] : l[a];
+    }
+    fine = ((int64_t)f[2] * g.nf[1] + f[1]) * g.nf[0] + f[0];
+    T ip = ip0[l[0] < 0 ? -l[0] : l[0]] * ip1[l[1] < 0 ? -l[1] : l[1]];
+    if (g.dim == 3) ip *= ip2[l[2] < 0 ? -l[2] : l[2]];
+    return ip;
+}
+
+// type 2, step 1: U[l mod n2] = b_c / Psi2(l)
+template <typename T>
+__global__ void __launch_bounds__(256) k_nu_fill(UGrid g, int64_t cells, const T *__restrict__ b,
+                                                 const T *__restrict__ ip0,
+                                                 const T *__restrict__ ip1,
+                                                 const T *__restrict__ ip2, CxT<T> *__restrict__ U) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t f;
+        const T ip = grid_site<T>(g, c, ip0, ip1, ip2, f);
+        U[f] = CxT<T>{b[c] * ip, T(0)};
+    }
+}
+
+// type 1, step 3: G_c = Re U[l mod n2] / Psi2(l) on the points' grid
+template <typename T>
+__global__ void __launch_bounds__(256) k_nu_field(UGrid g, int64_t cells,
+                                                  const T *__restrict__ ip0,
+                                                  const T *__restrict__ ip1,
+                                                  const T *__restrict__ ip2,
+                                                  const CxT<T> *__restrict__ U, T *__restrict__ G) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cells;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t f;
+        const T ip = grid_site<T>(g, c, ip0, ip1, ip2, f);
+        G[c] = U[f].x * ip;
+    }
+}
+
+// flags (bit 2 of err) a point outside [-half_a, half_a] on some axis
+template <typename T>
+__global__ void __launch_bounds__(256) k_nu_bounds(const T *__restrict__ pts, int64_t n, int dim,
+                                                   double hx, double hy, double hz,
+                                                   int *__restrict__ err) {
+    const double half[3] = {hx, hy, hz};
+    bool out = false;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x)
+        for (int a = 0; a < dim; ++a) {
+            const double r = (double)pts[j * dim + a];
+            out |= r < -half[a] || r > half[a];   // NaN passes here: k_count flags it
+        }
+    if (out) atomicOr(err, 2);
+}
+
+}  // namespace
+
+struct fresco_nuwnu_s {
+    fresco_uwnu_s *c = nullptr;   // the constraint side: grid <-> wavevectors (type 2 / type 1)
+    fresco::PointSide ps;         // the point side: the points spread onto the n1 grid
+    int dim = 0, precision = FRESCO_F32;
+    double box[3] = {1, 1, 1};
+    double h[3] = {1, 1, 1};
+    int64_t n_points = 0, cells = 0;
+    void *dq = nullptr;           // [n_k] 1 / Psi1(theta_q)
+    cudaStream_t stream = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void nu_free(fresco_nuwnu_s *p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    if (p->c) un_free(p->c);
+    fresco::point_side_free(p->ps);
+    if (p->dq) cudaFree(p->dq);
+    delete p;
+}
+
+template <typename T>
+fresco_status nu_build(fresco_nuwnu_s *p, const double *kvec, const double *S0, const double *W,
+                       int64_t n_k) {
+    fresco_uwnu_s *u = p->c;
+    const int dim = p->dim;
+    // constraint side: nu_q = k_q h n1 / (2 pi)
+    std::vector<double> nu((size_t)(n_k * dim));
+    std::vector<double> theta((size_t)n_k);
+    std::vector<double> psi((size_t)n_k);
+    std::vector<T> dq((size_t)n_k, T(1));
+    for (int a = 0; a < dim; ++a) {
+        for (int64_t q = 0; q < n_k; ++q) {
+            theta[(size_t)q] = kvec[q * dim + a] * p->h[a];
+            nu[(size_t)(q * dim + a)] = theta[(size_t)q] * (double)u->g.M[a] / (2.0 * kPiU);
+        }
+        fresco::kernel_ft_at(u->width, u->beta, theta.data(), n_k, psi.data());
+        for (int64_t q = 0; q < n_k; ++q) dq[(size_t)q] = (T)((double)dq[(size_t)q] / psi[(size_t)q]);
+    }
+    fresco_status st = un_build<T>(u, nu.data(), S0, W);
+    if (st) return st;
+    if (cudaMalloc(&p->dq, sizeof(T) * (size_t)n_k) != cudaSuccess) {
+        cudaGetLastError();
+        p->dq = nullptr;
+        return FRESCO_ERR_OOM;
+    }
+    UN_CUDA(cudaMemcpy(p->dq, dq.data(), sizeof(T) * (size_t)n_k, cudaMemcpyHostToDevice));
+    const double norm = (double)p->n_points;   // S = |rho|^2 / N
+    UN_CUDA(cudaMemcpy(u->scal, &norm, sizeof(double), cudaMemcpyHostToDevice));
+    // point side: the n1 grid over the periodic box n1 h
+    int n1[3] = {1, 1, 1};
+    double pbox[3] = {1, 1, 1};
+    for (int a = 0; a < dim; ++a) {
+        n1[a] = u->g.M[a];
+        pbox[a] = (double)n1[a] * p->h[a];
+    }
+    st = fresco::point_side_build(p->ps, dim, n1, pbox, p->n_points, u->width, u->beta,
+                                  p->precision, p->stream);
+    if (st) return st;
+    UN_CUDA(cudaDeviceSynchronize());
+    return FRESCO_OK;
+}
+
+template <typename T>
+fresco_status nu_eval(fresco_nuwnu_s *p, const T *pts, double *loss, T *grad) {
+    using C2 = CxT<T>;
+    fresco_uwnu_s *u = p->c;
+    const UGrid &g = u->g;
+    cudaStream_t s = p->stream;
+    const unsigned pb = (unsigned)std::min<int64_t>((p->cells + 255) / 256, 152 * 16);
+    const T *ip0 = (const T *)u->ip[0], *ip1 = (const T *)u->ip[1], *ip2 = (const T *)u->ip[2];
+    // the grid keeps spare cells beyond the box, so half a cell of slack (FP32 coordinates of
+    // points on a face may round just outside it) changes nothing
+    k_nu_bounds<T><<<(unsigned)std::min<int64_t>((p->n_points + 255) / 256, 152 * 8), 256, 0, s>>>(
+        pts, p->n_points, p->dim, 0.5 * (p->box[0] + p->h[0]), 0.5 * (p->box[1] + p->h[1]),
+        0.5 * (p->box[2] + p->h[2]), p->ps.err);
+    fresco_status st = fresco::point_side_spread<T>(p->ps, pts, s, &p->launches);
+    if (st) return st;
+    // type 2 of the spread grid at the wavevectors, S, the loss and the type-1 strengths
+    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
+    k_nu_fill<T><<<pb, 256, 0, s>>>(g, p->cells, (const T *)p->ps.grid, ip0, ip1, ip2, (C2 *)u->U);
+    st = un_fft<T>(u, CUFFT_INVERSE);
+    if (st) return st;
+    UN_CUDA(un_interp<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, (T)u->beta, u->U,
+                         (const T *)u->s0, (const T *)u->wq, u->scal, (const T *)p->dq, u->coef,
+                         (T *)u->S, u->part, u->nb, s));
+    k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 1, u->scal + 1);
+    UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    p->launches += 4;
+    u->evaluated = true;
+    if (!grad) return un_status(cudaGetLastError());
+    // type 1 of the strengths onto the grid, then the kernel-derivative interpolation
+    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
+    UN_CUDA(un_spread<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, (T)u->beta, u->coef,
+                         u->U, u->nb, s));
+    st = un_fft<T>(u, CUFFT_FORWARD);
+    if (st) return st;
+    k_nu_field<T><<<pb, 256, 0, s>>>(g, p->cells, ip0, ip1, ip2, (const C2 *)u->U, (T *)p->ps.grid);
+    const double dscale[3] = {-2.0 / p->h[0], -2.0 / p->h[1], -2.0 / p->h[2]};
+    const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(
+        sizeof(T) == 4 ? (const void *)&p->ps.p32 : (const void *)&p->ps.p64);
+    UN_CUDA(Launch<T>::interp_kd(p->ps.g, ep, p->ps.sorted, p->ps.perm, p->ps.off,
+                                 (const T *)p->ps.grid, nullptr, dscale, grad, s));
+    p->launches += 3;
+    return un_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+fresco_status fresco_nuwnu_plan(fresco_nuwnu_t *out, int dim, const double *box,
+                                int64_t n_points, int64_t n_k, const double *kvec,
+                                const double *S0, const double *W, const fresco_opts *opts,
+                                void *stream) {
+    if (!out) return FRESCO_ERR_ARG;
+    *out = nullptr;
+    if ((dim != 2 && dim != 3) || !box || !kvec || !S0 || !W || n_k < 1 || n_k > (1ll << 30) ||
+        n_points < 1 || n_points > 2147483647LL)
+        return FRESCO_ERR_ARG;
+    fresco_opts o;
+    fresco_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.precision != FRESCO_F32 && o.precision != FRESCO_F64) return FRESCO_ERR_ARG;
+    const double sigma = o.upsample == 0.0 ? 2.0 : o.upsample;
+    if (!(sigma >= 1.25 && sigma <= 3.0)) return FRESCO_ERR_ARG;
+    const double tol = o.tol == 0.0 ? (o.precision == FRESCO_F64 ? 1e-12 : 1e-6) : o.tol;
+    if (!(tol > 0.0 && tol < 1.0)) return FRESCO_ERR_ARG;
+    const int w = uwnu_width(tol, sigma);
+    if (w > kMaxWidth) return FRESCO_ERR_UNSUPPORTED;
+    for (int a = 0; a < dim; ++a)
+        if (!(box[a] > 0.0) || !std::isfinite(box[a])) return FRESCO_ERR_ARG;
+    for (int64_t q = 0; q < n_k * dim; ++q)
+        if (!std::isfinite(kvec[q])) return FRESCO_ERR_ARG;
+    for (int64_t q = 0; q < n_k; ++q)
+        if (!std::isfinite(S0[q]) || !std::isfinite(W[q]) || W[q] < 0.0) return FRESCO_ERR_ARG;
+    fresco_nuwnu_s *p = new (std::nothrow) fresco_nuwnu_s();
+    if (!p) return FRESCO_ERR_OOM;
+    p->dim = dim;
+    p->precision = o.precision;
+    p->n_points = n_points;
+    p->stream = (cudaStream_t)stream;
+    UGrid g{};
+    g.dim = dim;
+    double fine = 1.0, cells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        g.M[a] = 1;
+        g.nf[a] = 1;
+    }
+    for (int a = 0; a < dim; ++a) {
+        p->box[a] = box[a];
+        double kmax = 0.0;
+        for (int64_t q = 0; q < n_k; ++q) kmax = std::max(kmax, std::fabs(kvec[q * dim + a]));
+        kmax = std::max(kmax, kPiU / box[a]);   // at least one cycle per box: any spacing works
+        p->h[a] = kPiU / (sigma * kmax);
+        // the points span box / h cells; their windows w more; two cells to spare at the seam
+        const double need = std::ceil(box[a] / p->h[a]) + w + 2;
+        if (need > (double)(1 << 24)) {
+            delete p;
+            return FRESCO_ERR_UNSUPPORTED;
+        }
+        const int64_t n1 = uwnu_smooth_even(std::max<int64_t>((int64_t)need, 2 * w));
+        const int64_t n2 = uwnu_smooth_even(std::max<int64_t>((int64_t)std::ceil(sigma * (double)n1), 2 * w));
+        if (n1 > 255 * 65535 || n2 > (1 << 26)) {
+            delete p;
+            return FRESCO_ERR_UNSUPPORTED;
+        }
+        g.M[a] = (int)n1;
+        g.nf[a] = (int)n2;
+        fine *= (double)n2;
+        cells *= (double)n1;
+    }
+    if (fine > 4.0e9 || cells > 4.0e9) {
+        delete p;
+        return FRESCO_ERR_UNSUPPORTED;
+    }
+    fresco_uwnu_s *u = new (std::nothrow) fresco_uwnu_s();
+    if (!u) {
+        delete p;
+        return FRESCO_ERR_OOM;
+    }
+    p->c = u;
+    u->g = g;
+    u->precision = o.precision;
+    u->width = w;
+    u->beta = uwnu_beta(w, sigma);
+    u->cells = (int64_t)cells;
+    u->fine = (int64_t)fine;
+    u->n_k = n_k;
+    u->nb = (int)std::max<int64_t>(1, std::min<int64_t>((n_k + 255) / 256, kUBlocks));
+    u->stream = p->stream;
+    p->cells = (int64_t)cells;
+    const fresco_status st = o.precision == FRESCO_F64 ? nu_build<double>(p, kvec, S0, W, n_k)
+                                                       : nu_build<float>(p, kvec, S0, W, n_k);
+    if (st) {
+        nu_free(p);
+        return st;
+    }
+    *out = p;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_nuwnu_loss_grad(fresco_nuwnu_t p, const void *d_points, double *d_loss,
+                                     void *d_grad) {
+    if (!p || !d_points || !d_loss) return FRESCO_ERR_ARG;
+    cudaGetLastError();
+    if (p->precision == FRESCO_F64)
+        return nu_eval<double>(p, (const double *)d_points, d_loss, (double *)d_grad);
+    return nu_eval<float>(p, (const float *)d_points, d_loss, (float *)d_grad);
+}
+
+fresco_status fresco_nuwnu_get_S(fresco_nuwnu_t p, void *d_S) {
+    if (!p) return FRESCO_ERR_ARG;
+    return fresco_uwnu_get_S(p->c, d_S);
+}
+
+fresco_status fresco_nuwnu_status_check(fresco_nuwnu_t p) {
+    if (!p) return FRESCO_ERR_ARG;
+    UN_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    int err = 0;
+    UN_CUDA(cudaMemcpy(&err, p->ps.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        const int zero = 0;
+        UN_CUDA(cudaMemcpy(p->ps.err, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        return (err & 1) ? FRESCO_ERR_NONFINITE : FRESCO_ERR_BOUNDS;
+    }
+    return un_status(cudaGetLastError());
+}
+
+fresco_status fresco_nuwnu_get_info(fresco_nuwnu_t p, int *width, int *n_grid, int *n_fine,
+                                    int64_t *launches) {
+    if (!p) return FRESCO_ERR_ARG;
+    if (width) *width = p->c->width;
+    for (int a = 0; a < 3; ++a) {
+        if (n_grid) n_grid[a] = p->c->g.M[a];
+        if (n_fine) n_fine[a] = p->c->g.nf[a];
+    }
+    if (launches) *launches = p->launches;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_nuwnu_destroy(fresco_nuwnu_t p) {
+    nu_free(p);
     return FRESCO_OK;
 }
 

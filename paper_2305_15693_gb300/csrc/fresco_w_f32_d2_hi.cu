@@ -1,0 +1,7 @@
+// float, 2D, ES kernel widths 9-16: the width-specialised launchers and their kernels.
+#include "fresco_kernels.cuh"
+
+namespace fresco {
+FRESCO_WIDTHS_HI(FRESCO_INST_WOPS, float, 2)
+FRESCO_WIDTHS_HI(FRESCO_INST_WOPSB, float)
+}

@@ -1,0 +1,6 @@
+// double, 3D, ES kernel widths 2-8: the width-specialised launchers and their kernels.
+#include "fresco_kernels.cuh"
+
+namespace fresco {
+FRESCO_WIDTHS_LO(FRESCO_INST_WOPS, double, 3)
+}

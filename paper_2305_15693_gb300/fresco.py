@@ -50,7 +50,9 @@ EXPORTS = (
     "fresco_batch_profile_read", "fresco_batch_get_info",
     "fresco_uwu_plan", "fresco_uwu_loss_grad", "fresco_uwu_destroy",
     "fresco_uwnu_plan", "fresco_uwnu_loss_grad", "fresco_uwnu_get_S", "fresco_uwnu_get_info",
-    "fresco_uwnu_destroy",
+    "fresco_uwnu_destroy", "fresco_smem_peak",
+    "fresco_nuwnu_plan", "fresco_nuwnu_loss_grad", "fresco_nuwnu_get_S",
+    "fresco_nuwnu_status_check", "fresco_nuwnu_get_info", "fresco_nuwnu_destroy",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -169,6 +171,13 @@ def load(path: str = LIB_PATH):
             "fresco_uwnu_get_S": (I, [P, P]),
             "fresco_uwnu_get_info": (I, [P, P, P, P]),
             "fresco_uwnu_destroy": (I, [P]),
+            "fresco_smem_peak": (I, [I, P, P, P]),
+            "fresco_nuwnu_plan": (I, [P, I, P, I64, I64, P, P, P, P, P]),
+            "fresco_nuwnu_loss_grad": (I, [P, P, P, P]),
+            "fresco_nuwnu_get_S": (I, [P, P]),
+            "fresco_nuwnu_status_check": (I, [P]),
+            "fresco_nuwnu_get_info": (I, [P, P, P, P, P]),
+            "fresco_nuwnu_destroy": (I, [P]),
         })
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -221,11 +230,37 @@ def _host_arrays(box, mask, S0, W):
     return dim, box, mask, S0, W
 
 
+def parse_precision(precision) -> int:
+    """FRESCO_F32 or FRESCO_F64 from any accepted spelling ("f32", "float32", np.float32,
+    torch.float32, FRESCO_F32, and the same for 64 bits); anything else raises ValueError."""
+    if precision in (FRESCO_F32, FRESCO_F64) and not isinstance(precision, bool):
+        return int(precision)
+    name = getattr(precision, "__name__", None) or str(precision)
+    name = name.replace("torch.", "").lower()
+    if name in ("f32", "float32", "fp32", "single"):
+        return FRESCO_F32
+    if name in ("f64", "float64", "fp64", "double"):
+        return FRESCO_F64
+    raise ValueError("unknown precision %r (expected 'f32' or 'f64')" % (precision,))
+
+
+def _torch_dtype(prec: int):
+    import torch
+    return torch.float64 if prec == FRESCO_F64 else torch.float32
+
+
+def _check_dtype(name, x, dtype):
+    """Raise if x is a torch tensor whose dtype is not `dtype` (raw addresses are not checked)."""
+    dt = getattr(x, "dtype", None)
+    if dt is not None and dt != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, dt))
+
+
 def make_opts(precision="f32", tol=0.0, upsample=2.0, width=0, tile=None,
               grad_mode=FRESCO_GRAD_DIRECT) -> fresco_opts:
     o = fresco_opts()
     load().fresco_opts_default(ctypes.byref(o))
-    o.precision = FRESCO_F64 if precision in ("f64", FRESCO_F64, "float64") else FRESCO_F32
+    o.precision = parse_precision(precision)
     o.tol = float(tol)
     o.upsample = float(upsample)
     o.width_override = int(width)
@@ -322,6 +357,20 @@ def fresco_profile_read(plan):
     return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(STAGES)}
 
 
+FRESCO_SMEM_ATOMIC_ADD = 0
+FRESCO_SMEM_LOAD = 1
+
+
+def fresco_smem_peak(op, sink, stream=None) -> float:
+    """Shared-memory 32-bit atomic adds (op FRESCO_SMEM_ATOMIC_ADD) or loads (FRESCO_SMEM_LOAD)
+    per second on the current device, conflict-free (the pipe's best case). sink: a device int
+    tensor of at least 8 x the multiprocessor count entries."""
+    v = ctypes.c_double()
+    _check(load().fresco_smem_peak(int(op), _addr(sink), _stream_handle(stream), ctypes.byref(v)),
+           "fresco_smem_peak")
+    return v.value
+
+
 def fresco_launch_count(plan) -> int:
     return int(load().fresco_launch_count(plan))
 
@@ -339,7 +388,11 @@ def fresco_loss_noalloc(precision, n_k, S, S0, W, loss, stream=None):
     """sum W (S - S0)^2 into the device double `loss`, allocating nothing (see include/fresco.h:
     for callers that cannot allocate device memory at call time). S is float (precision "f32")
     or double ("f64"); S0 and W are device doubles."""
-    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    import torch
+    prec = parse_precision(precision)
+    _check_dtype("S", S, _torch_dtype(prec))
+    for name, x in (("S0", S0), ("W", W), ("loss", loss)):
+        _check_dtype(name, x, torch.float64)
     _check(load().fresco_loss_noalloc(prec, int(n_k), _addr(S), _addr(S0), _addr(W), _addr(loss),
                                       _stream_handle(stream)), "fresco_loss_noalloc")
 
@@ -378,7 +431,7 @@ def fresco_pair_plan(box, dim, n_points, sigma, eps=1.0, alpha=2.0, precision="f
                      stream=None):
     b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)))
     h = ctypes.c_void_p()
-    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    prec = parse_precision(precision)
     _check(load().fresco_pair_plan(ctypes.byref(h), int(dim), b.ctypes.data, int(n_points),
                                    float(sigma), float(eps), float(alpha), prec,
                                    _stream_handle(stream)), "fresco_pair_plan")
@@ -577,7 +630,7 @@ def fresco_uwu_plan(grid_shape, mask, S0, W, precision="f32", stream=None):
     S0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
     W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
     h = ctypes.c_void_p()
-    prec = FRESCO_F64 if precision in ("f64", FRESCO_F64) else FRESCO_F32
+    prec = parse_precision(precision)
     _check(lib.fresco_uwu_plan(ctypes.byref(h), dim, grid.ctypes.data, mask.ctypes.data,
                                mask.shape[0], S0.ctypes.data, W.ctypes.data, prec,
                                _stream_handle(stream)), "fresco_uwu_plan")
@@ -601,7 +654,7 @@ class Uwu:
         import torch
         self._torch = torch
         self.shape = tuple(int(x) for x in grid_shape)[::-1]
-        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.dtype = _torch_dtype(parse_precision(precision))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = fresco_uwu_plan(grid_shape, mask, S0, W, precision, self.stream)
 
@@ -688,7 +741,7 @@ class Uwnu:
         self._torch = torch
         self.shape = tuple(int(x) for x in grid_shape)[::-1]
         self.n_k = int(np.asarray(nu).shape[0])
-        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.dtype = _torch_dtype(parse_precision(precision))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         opts = make_opts(precision=precision, tol=tol, upsample=upsample)
         self.handle = fresco_uwnu_plan(grid_shape, nu, S0, W, opts, self.stream)
@@ -714,6 +767,109 @@ class Uwnu:
     def close(self):
         if getattr(self, "handle", None):
             fresco_uwnu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def fresco_nuwnu_plan(box, kvec, S0, W, n_points, opts=None, stream=None):
+    """Plan for points in [-L/2, L/2]^d with constraints at real wavevectors kvec [n_k, dim]
+    (radians per unit length)."""
+    lib = load()
+    k = np.ascontiguousarray(np.asarray(kvec, dtype=np.float64))
+    if k.ndim != 2:
+        raise ValueError("kvec must be [n_k, dim]")
+    dim = k.shape[1]
+    b = np.ascontiguousarray(np.broadcast_to(np.asarray(box, dtype=np.float64), (dim,)))
+    S0 = np.ascontiguousarray(np.asarray(S0, dtype=np.float64).reshape(-1))
+    W = np.ascontiguousarray(np.asarray(W, dtype=np.float64).reshape(-1))
+    if S0.size != k.shape[0] or W.size != k.shape[0]:
+        raise ValueError("one S0 and one W per constraint")
+    h = ctypes.c_void_p()
+    _check(lib.fresco_nuwnu_plan(ctypes.byref(h), dim, b.ctypes.data, int(n_points), k.shape[0],
+                                 k.ctypes.data, S0.ctypes.data, W.ctypes.data,
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 _stream_handle(stream)), "fresco_nuwnu_plan")
+    return h.value
+
+
+def fresco_nuwnu_loss_grad(plan, points, loss, grad=None):
+    _check(load().fresco_nuwnu_loss_grad(plan, _addr(points), _addr(loss), _addr(grad)),
+           "fresco_nuwnu_loss_grad")
+
+
+def fresco_nuwnu_get_S(plan, S):
+    _check(load().fresco_nuwnu_get_S(plan, _addr(S)), "fresco_nuwnu_get_S")
+
+
+def fresco_nuwnu_status_check(plan) -> int:
+    return int(load().fresco_nuwnu_status_check(plan))
+
+
+def fresco_nuwnu_get_info(plan) -> dict:
+    w = ctypes.c_int()
+    ng = (ctypes.c_int * 3)()
+    nf = (ctypes.c_int * 3)()
+    nl = ctypes.c_int64()
+    _check(load().fresco_nuwnu_get_info(plan, ctypes.byref(w), ng, nf, ctypes.byref(nl)),
+           "fresco_nuwnu_get_info")
+    return {"width": w.value, "n_grid": list(ng), "n_fine": list(nf), "launches": nl.value}
+
+
+def fresco_nuwnu_destroy(plan):
+    _check(load().fresco_nuwnu_destroy(plan), "fresco_nuwnu_destroy")
+
+
+class Nuwnu:
+    """Points at free positions in [-L/2, L/2]^d with constraints at real wavevectors
+    (fresco_nuwnu_* in include/fresco.h). Points and gradients are contiguous CUDA tensors
+    [N, dim] in the plan's dtype, caller order."""
+
+    def __init__(self, box, kvec, S0, W, n_points, precision="f32", tol=0.0, upsample=2.0,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.n_points = int(n_points)
+        self.n_k = int(np.asarray(kvec).shape[0])
+        self.dim = int(np.asarray(kvec).shape[1])
+        self.dtype = _torch_dtype(parse_precision(precision))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        opts = make_opts(precision=precision, tol=tol, upsample=upsample)
+        self.handle = fresco_nuwnu_plan(box, kvec, S0, W, n_points, opts, self.stream)
+        self.info = fresco_nuwnu_get_info(self.handle)
+
+    def loss_grad(self, points, want_grad=True):
+        t = self._torch
+        if (not points.is_cuda or points.dtype != self.dtype or not points.is_contiguous()
+                or tuple(points.shape) != (self.n_points, self.dim)):
+            raise ValueError("points must be a contiguous CUDA %s tensor [%d, %d]"
+                             % (self.dtype, self.n_points, self.dim))
+        loss = t.empty((), dtype=t.float64, device=points.device)
+        grad = t.empty_like(points) if want_grad else None
+        fresco_nuwnu_loss_grad(self.handle, points, loss, grad)
+        return loss, grad
+
+    def S(self):
+        out = self._torch.empty(self.n_k, dtype=self.dtype, device="cuda")
+        fresco_nuwnu_get_S(self.handle, out)
+        return out
+
+    def status(self) -> int:
+        return fresco_nuwnu_status_check(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            fresco_nuwnu_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -826,7 +982,7 @@ class PairTerm:
         if stream is None:
             stream = torch.cuda.current_stream()
         self.dim, self.n_points = int(dim), int(n_points)
-        self.dtype = torch.float64 if precision in ("f64", FRESCO_F64) else torch.float32
+        self.dtype = _torch_dtype(parse_precision(precision))
         self.handle = fresco_pair_plan(box, dim, n_points, sigma, eps, alpha, precision, stream)
 
     def energy_grad(self, points, energy=None, grad=None, accumulate=False):

@@ -250,6 +250,11 @@ def workload(name: str) -> Workload:
     if name == "peaked2d_n1e7_chi03_f32":
         return Workload(name, 2, 10**7, radius_for_chi(10**7, 2, 0.3), "peaked", "f32",
                         seed=0, tol=1e-6, upsample=1.6577, grad_mode="kderiv")
+    # 3D profiling stand-in: the same kernel width and point density per fine cell at 1/8 of the
+    # points (n_f = 324 = 2^2 3^4, K = 97, oversampling 1.6615; fine grid 136 MB > L2)
+    if name == "powerlaw3d_n2p21_chi03_f32":
+        return Workload(name, 3, 2**21, radius_for_chi(2**21, 3, 0.3), "power_law", "f32",
+                        seed=0, tol=1e-6, upsample=1.6615, grad_mode="kderiv")
     if name == "peaked2d_n1e8_chi03_f64":
         return Workload(name, 2, 10**8, radius_for_chi(10**8, 2, 0.3), "peaked", "f64",
                         seed=0, tol=1e-12, upsample=1.6775)

@@ -71,7 +71,37 @@ def test_clock_record_reduction():
 def test_traffic_sources_exist_and_hash_is_stable():
     csrc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                         "paper_2305_15693_gb300", "csrc")
-    for name in bench.TRAFFIC_SOURCES:
+    names = bench.traffic_sources()
+    assert "fresco_kernels.cuh" in names and "fresco_tiles.cuh" in names
+    for name in names:
         assert os.path.isfile(os.path.join(csrc, name)), name
     h = bench._kernel_source_hash()
     assert len(h) == 16 and h == bench._kernel_source_hash()
+
+
+def test_rho_error_report_bins_and_row_maximum():
+    import numpy as np
+    K = 100
+    rows = np.array([[10, 0], [0, 30], [60, 0], [0, 90], [70, 70]])   # |n|/K: .1 .3 .6 .9 .99
+    want = np.array([3 + 4j, 5.0, 1j * 5, -5.0, 4 - 3j])              # every |rho| = 5
+    got = want.copy()
+    got[3] += 0.5                                                     # one row off by 0.1 |rho|
+    rep = bench.rho_error_report(got, want, rows, K)
+    assert rep["rows"] == 5
+    assert rep["rel_l2"] == pytest.approx(0.5 / np.sqrt(5 * 25))
+    assert rep["max_row_err_over_rms"] == pytest.approx(0.1)
+    bins = {tuple(b["n_over_K"]): b for b in rep["by_n_over_K"]}
+    assert bins[(0.0, 0.25)]["rows"] == 1 and bins[(0.0, 0.25)]["rel_l2"] == 0.0
+    assert bins[(0.75, 1.0)]["rows"] == 2
+    assert bins[(0.75, 1.0)]["rel_l2"] == pytest.approx(0.5 / np.sqrt(50))
+
+
+def test_smem_roofline_counts_w_to_the_d_operations_per_point():
+    stages = {"spread": {"ms": 2.0}, "interp": {"ms": 4.0}}
+    out = bench.smem_rooflines(stages, 10**8, 2, 7, {"atomic_add": 9.8e12, "load": 9.8e12})
+    assert out["spread"]["ops_per_launch"] == 49e8
+    assert out["spread"]["achieved_ops_per_s"] == pytest.approx(49e8 / 2e-3)
+    assert out["spread"]["frac"] == pytest.approx(49e8 / 2e-3 / 9.8e12, abs=1e-4)
+    assert out["interp"]["frac"] == pytest.approx(49e8 / 4e-3 / 9.8e12, abs=1e-4)
+    out3 = bench.smem_rooflines(stages, 1 << 24, 3, 7, {"atomic_add": 1.0, "load": 1.0})
+    assert out3["spread"]["ops_per_launch"] == float((1 << 24) * 343)

@@ -21,8 +21,10 @@ from _parity import TOL, rel_l2
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 WORKLOADS = ["stealthy2d_n1e6_chi045_f32", "powerlaw3d_n2p24_chi03_f32", "peaked2d_n1e8_chi03_f32"]
-N_SAMPLE_ROWS = {"stealthy2d_n1e6_chi045_f32": 128, "powerlaw3d_n2p24_chi03_f32": 24,
-                 "peaked2d_n1e8_chi03_f32": 12}
+# rho rows checked against the oracle's direct sums (each an O(N) sum: ~2.7 s on 16 host cores at
+# 1e8 points, so the 1e8 workload's 64 rows take about three minutes)
+N_SAMPLE_ROWS = {"stealthy2d_n1e6_chi045_f32": 128, "powerlaw3d_n2p24_chi03_f32": 64,
+                 "peaked2d_n1e8_chi03_f32": 64}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,10 +60,13 @@ def test_full_size_workload(name):
     del rho32
     torch.cuda.empty_cache()
 
-    # rho at sampled rows against the oracle's direct sums
+    # rho at sampled rows against the oracle's direct sums: relative L2 over the rows, and no
+    # single row off by more than 1e-4 of the rows' RMS |rho| (|rho| ~ sqrt(N) for these points)
     want = oracle.rho(pts_np, mask[rows], box=wl.box)
     got = rho32_s[:, 0] + 1j * rho32_s[:, 1]
     assert rel_l2(got, want) <= TOL["f32"]["rho"], rel_l2(got, want)
+    rms = np.sqrt(np.mean(np.abs(want) ** 2))
+    assert np.max(np.abs(got - want)) <= 1e-4 * rms, np.max(np.abs(got - want)) / rms
 
     # FP32 against the plain all-FP64 GPU path (direct gradient, oversampling 2) on the same points
     pts64 = pts.double()

@@ -66,3 +66,44 @@ def test_noalloc_loss_matches_the_plan_loss_on_two_calls(fr, precision):
         assert np.isfinite(got)
         assert abs(got - want) <= tol * abs(want), (got, want)
     assert results[0] == results[1]          # fixed-order reduction: bitwise repeatable
+
+
+_WARMUP_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2305_15693_gb300 import fresco
+torch.cuda.set_device(0)
+g = np.random.default_rng(5)
+n = 50000
+S_h, S0_h, W_h = g.random(n) * 3.0, g.random(n) * 2.0, 0.5 + g.random(n)
+want = float(np.sum(W_h * (S_h - S0_h) ** 2))
+for precision, dt in (("f64", torch.float64), ("f32", torch.float32)):
+    S = torch.from_numpy(S_h).to(dt).cuda()
+    S0, W = torch.from_numpy(S0_h).cuda(), torch.from_numpy(W_h).cuda()
+    ref = float(np.sum(W_h * (S.double().cpu().numpy() - S0_h) ** 2))
+    outs = []
+    for _ in range(2):
+        out = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+        fresco.fresco_loss_noalloc(precision, n, S, S0, W, out, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        outs.append(out.item())
+    assert outs[0] == outs[1], outs
+    assert abs(outs[0] - ref) <= 1e-12 * abs(ref), (precision, outs[0], ref)
+print("WARMUP_OK", want)
+"""
+
+
+@pytest.mark.gpu
+def test_warm_up_call_before_any_plan_in_a_fresh_process(fr):
+    """A caller under a fixed memory budget makes its first (warm-up) call at start-up, before it
+    has made any plan: in a fresh process that first call loads the library's scratch array and
+    must already give the loss, on two calls in a row."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _WARMUP_SCRIPT, root], capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0 and "WARMUP_OK" in r.stdout, r.stdout + r.stderr
