@@ -222,22 +222,31 @@ def time_e2e(plan, pts_np, steps, warmup):
     return dt, a_pts.nbytes, a_grad.nbytes + 8
 
 
-def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2, min_rows=16):
+def oracle_sample_rows(threads: int) -> int:
+    """Mask rows per timed oracle sample: the oracle hands rows to its threads four at a time, so
+    four rows per host thread keep every core busy."""
+    return 4 * max(1, threads)
+
+
+def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2, min_rows=None):
     """The oracle timed on the host cores on a bounded sample: rho at a seeded sample of mask rows
-    (at least min_rows, more while they fit the budget) over all N points (direct sums). A full
-    evaluation costs rho over all N_K rows plus the gradient over all N points x N_K rows: about
-    2 N N_K pair terms at the same per-term cost."""
+    (at least four per host thread, more while they fit the budget) over all N points (direct
+    sums). A full evaluation costs rho over all N_K rows plus the gradient over all N points x N_K
+    rows: about 2 N N_K pair terms at the same per-term cost."""
     import oracle
     N = pts_np.shape[0]
     n_k = mask.shape[0]
+    threads = oracle.threads()
+    if min_rows is None:
+        min_rows = oracle_sample_rows(threads)
     g = np.random.Generator(np.random.Philox(seed))
     r64 = np.ascontiguousarray(pts_np, dtype=np.float64)
-    probe = mask[g.choice(n_k, 2, replace=False)]
+    probe = mask[g.choice(n_k, min(n_k, min_rows), replace=False)]
     t0 = time.perf_counter()
     oracle.rho(r64, probe, box)
     t_probe = max(time.perf_counter() - t0, 1e-6)
-    per_row = t_probe / 2
-    n_s = int(max(min(min_rows, n_k), min(256, n_k, budget_s / per_row)))
+    per_row = t_probe / probe.shape[0]
+    n_s = int(max(min(min_rows, n_k), min(4 * min_rows, n_k, budget_s / per_row)))
     rows = np.sort(g.choice(n_k, n_s, replace=False))
     sample = mask[rows]
     t0 = time.perf_counter()
@@ -245,7 +254,8 @@ def cpu_baseline(pts_np, mask, box, budget_s=12.0, seed=2, min_rows=16):
     t = time.perf_counter() - t0
     rate = N * n_s / t                                  # pair terms / s
     t_eval = 2.0 * N * n_k / rate
-    return ({"value": N / t_eval, "unit": "points/s", "cores": oracle.threads(), "kind": "oracle",
+    used = min(threads, (n_s + 3) // 4)
+    return ({"value": N / t_eval, "unit": "points/s", "cores": used, "kind": "oracle",
              "sample": "rho at %d of %d mask rows over all %d points (%.1f s); full evaluation "
                        "extrapolated as 2*N*N_K pair terms at the measured %.3e terms/s"
                        % (n_s, n_k, N, t, rate),
@@ -316,8 +326,8 @@ def run_reference(args, wl, rank, world):
     pts, mask, S0, W = make_inputs(wl)
     r64 = np.ascontiguousarray(pts, dtype=np.float64)
     g = np.random.Generator(np.random.Philox(3))
-    n_s = max(1, int(args.ref_rows))
     N, n_k = pts.shape[0], mask.shape[0]
+    n_s = min(n_k, max(int(args.ref_rows), oracle_sample_rows(oracle.threads())))
     for _ in range(args.warmup):
         oracle.rho(r64, mask[g.choice(n_k, n_s, replace=False)], wl.box)
     times = []
@@ -340,11 +350,11 @@ def run_reference(args, wl, rank, world):
         # ms_per_step is the measured time of one step (the bounded sample); a full evaluation at
         # the measured pair-term rate would take this long:
         "ms_per_eval_extrapolated": 1e3 * t_eval,
-        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.threads(),
-                         "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "points/s",
+                         "cores": min(oracle.threads(), (n_s + 3) // 4), "kind": "oracle",
                          "sample": "per step: rho at %d seeded mask rows over all %d points by "
-                                   "direct sums; evaluation extrapolated as 2*N*N_K pair terms"
-                                   % (n_s, N)},
+                                   "direct sums (four rows per host thread); evaluation "
+                                   "extrapolated as 2*N*N_K pair terms" % (n_s, N)},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -652,6 +662,140 @@ def run_accuracy(args, wl):
     print(json.dumps(out), flush=True)
 
 
+NUWNU_METRIC = "points/s per NUwNU loss+grad eval (free boundaries, real wavevectors)"
+
+
+def run_reference_free(args, fw, rank):
+    """The oracle as the reference arm of a NUwNU workload: each step is the loss and gradient of
+    a bounded sample of points (four per host thread x 64) at every wavevector."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    pts_np = fw.points()
+    k = fw.wavevectors()
+    S0, W = fw.targets(k)
+    n_s = min(fw.n_points, 256 * oracle_sample_rows(oracle.threads()))
+    times = []
+    for step in range(args.warmup + args.steps):
+        sub = pts_np[(step * n_s) % fw.n_points:][:n_s]
+        t0 = time.perf_counter()
+        oracle.loss_grad_k(sub, k, S0, W)
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    rate = 2.0 * n_s * k.shape[0] / t
+    t_eval = 2.0 * fw.n_points * k.shape[0] / rate
+    value = fw.n_points / t_eval
+    line = {
+        "impl": "reference", "metric": NUWNU_METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "ms_per_eval_extrapolated": 1e3 * t_eval, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": fw.name, "n_points": fw.n_points, "n_modes": fw.n_k,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": "per step: loss and gradient of %d points at all %d "
+                                   "wavevectors by direct sums; evaluation extrapolated as "
+                                   "2 N N_K pair terms" % (n_s, k.shape[0])},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_nuwnu(args, fw, rank, world, local_rank, dist_on):
+    """Points at free positions with constraints at real wavevectors (fresco_nuwnu_*)."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    pts_np = fw.points()
+    k = fw.wavevectors()
+    S0, W = fw.targets(k)
+    pts = torch.from_numpy(pts_np).cuda()
+    plan = fresco.Nuwnu(fw.box, k, S0, W, fw.n_points, fw.dtype, tol=fw.tol,
+                        upsample=fw.upsample)
+    s = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        loss, grad = plan.loss_grad(pts)
+    torch.cuda.synchronize()
+    l0 = fresco.fresco_nuwnu_get_info(plan.handle)["launches"]
+    clocks = ClockSampler(_device_selector(local_rank))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        loss, grad = plan.loss_grad(pts)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, dist_on, "cuda")
+    launches = fresco.fresco_nuwnu_get_info(plan.handle)["launches"] - l0
+    if plan.status() != 0:
+        raise RuntimeError("device status after timing")
+    # e2e: pinned host points in, loss and gradient out, every step
+    h_pts = torch.from_numpy(pts_np).pin_memory()
+    h_grad = torch.empty(pts_np.shape, dtype=h_pts.dtype).pin_memory()
+    h_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pts.copy_(h_pts, non_blocking=True)
+        loss, grad = plan.loss_grad(pts)
+        h_grad.copy_(grad, non_blocking=True)
+        h_loss.copy_(loss, non_blocking=True)
+        s.synchronize()
+    dt_e2e = max_over_ranks((time.perf_counter() - t0) / max(args.e2e_steps, 1), dist_on, "cuda")
+    info = plan.info
+    # accuracy on a subsample the oracle finishes in seconds: 4096 points, all wavevectors
+    acc = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        sub = pts_np[:4096]
+        with fresco.Nuwnu(fw.box, k, S0, W, sub.shape[0], fw.dtype, tol=fw.tol,
+                          upsample=fw.upsample) as p2:
+            l_g, g_g = p2.loss_grad(torch.from_numpy(sub).cuda())
+            S_g = p2.S().double().cpu().numpy()
+            l_g, g_g = l_g.item(), g_g.double().cpu().numpy()
+        t0 = time.perf_counter()
+        l_o, g_o, S_o, _ = oracle.loss_grad_k(sub, k, S0, W)
+        t_or = time.perf_counter() - t0
+        acc = {"points": int(sub.shape[0]), "S_rel_l2": float(np.linalg.norm(S_g - S_o) /
+                                                            np.linalg.norm(S_o)),
+               "loss_rel": abs(l_g - l_o) / abs(l_o),
+               "grad_rel_l2": float(np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o))}
+        rate = 2.0 * sub.shape[0] * k.shape[0] / t_or      # pair terms / s (rho and gradient)
+        cpu = {"value": fw.n_points / (2.0 * fw.n_points * k.shape[0] / rate), "unit": "points/s",
+               "cores": oracle.threads(), "kind": "oracle",
+               "sample": "loss and gradient of the first 4096 points at all %d wavevectors "
+                         "(%.1f s); full evaluation extrapolated as 2 N N_K pair terms"
+                         % (k.shape[0], t_or)}
+    plan.close()
+    if rank == 0:
+        line = {
+            "metric": NUWNU_METRIC, "value": world * fw.n_points / t_step, "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": fw.dtype, "data": "synthetic",
+            "config": {"workload": fw.name, "n_points": fw.n_points, "dim": fw.dim,
+                       "n_modes": fw.n_k, "kmax": fw.kmax, "tol": fw.tol,
+                       "upsample": fw.upsample, "width": info["width"],
+                       "n_grid": info["n_grid"][:fw.dim], "n_fine": info["n_fine"][:fw.dim],
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy_vs_oracle": acc,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * fw.n_points / dt_e2e, "unit": "points/s",
+                    "h2d_bytes_per_step": int(pts_np.nbytes),
+                    "d2h_bytes_per_step": int(pts_np.nbytes + 8), "ms_per_step": 1e3 * dt_e2e},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -661,7 +805,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--f64-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--ref-rows", type=int, default=4)
+    ap.add_argument("--ref-rows", type=int, default=0,
+                    help="mask rows per reference step (at least four per host thread)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--upsample", type=float, default=0.0,
                     help="override the workload's fine-grid oversampling sigma")
@@ -669,6 +814,8 @@ def main():
                     help="override the spread/interp tile edge per axis")
     ap.add_argument("--grad-mode", default=None, choices=["direct", "kderiv"],
                     help="override the workload's gradient mode")
+    ap.add_argument("--lbfgs-steps", type=int, default=0,
+                    help="also time this many L-BFGS iterations (caller order and tile order)")
     ap.add_argument("--accuracy", action="store_true",
                     help="instead of timing: attribute the FP32 rho error at sampled mask rows")
     ap.add_argument("--accuracy-rows", type=int, default=64)
@@ -680,26 +827,34 @@ def main():
 
     from paper_2305_15693_gb300 import inputs
     ens = None
+    fw = None
     try:
         ens = inputs.ensemble_workload(args.workload)
     except KeyError:
-        wl = inputs.workload(args.workload)
-        if args.upsample:
-            wl.upsample = args.upsample
-        if args.grad_mode:
-            wl.grad_mode = args.grad_mode
+        try:
+            fw = inputs.free_workload(args.workload)
+        except KeyError:
+            wl = inputs.workload(args.workload)
+            if args.upsample:
+                wl.upsample = args.upsample
+            if args.grad_mode:
+                wl.grad_mode = args.grad_mode
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.accuracy:
+        if fw is not None or ens is not None:
+            raise SystemExit("--accuracy takes a periodic single-problem workload")
         run_accuracy(args, wl)
         return
 
     if args.impl == "reference":
         if ens is not None:
             run_reference_ensemble(args, ens, rank)
+        elif fw is not None:
+            run_reference_free(args, fw, rank)
         else:
             run_reference(args, wl, rank, world)
         return
@@ -716,6 +871,12 @@ def main():
     from paper_2305_15693_gb300 import fresco
     fresco.load()
 
+    if fw is not None:
+        run_nuwnu(args, fw, rank, world, local_rank, dist_on)
+        if dist_on:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
     if ens is not None:
         run_ensemble(args, ens, rank, world, local_rank, dist_on)
         if dist_on:
@@ -752,6 +913,33 @@ def main():
         del rho_dev
         got = got[:, 0] + 1j * got[:, 1]
         rho_err = rho_error_report(got, rho_oracle, mask[rows], wl.K)
+
+    # L-BFGS iterations on the same plan, the solver's vectors in caller order and in tile order
+    lbfgs = None
+    if args.lbfgs_steps > 0:
+        lbfgs = {}
+        for tile_order in (False, True):
+            x = pts.clone()
+            solver = fresco.LBFGS(plan, tile_order=tile_order)
+            solver.run(x, 2)                              # warm-up (history, tile order)
+            torch.cuda.synchronize()
+            plan.profile_read()
+            plan.profile(True)
+            t0 = time.perf_counter()
+            rep0 = solver.run(x, 0)
+            rep = solver.run(x, args.lbfgs_steps)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = plan.profile_read()
+            plan.profile(False)
+            solver.close()
+            evals = rep["evaluations"] - rep0["evaluations"]
+            lbfgs["tile_order" if tile_order else "caller_order"] = {
+                "iterations": args.lbfgs_steps, "evaluations": evals,
+                "ms_per_iteration": 1e3 * dt / args.lbfgs_steps,
+                "ms_per_evaluation": 1e3 * dt / max(evals, 1), "loss": rep["loss"],
+                "stages_ms": {k: round(v[0] / max(v[1], 1), 3) for k, v in st.items()}}
+            del x
 
     # e2e through the host-buffer entry point
     dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
@@ -849,6 +1037,8 @@ def main():
             "gpu_launches": launches,
             "loss": loss_val,
         }
+        if lbfgs is not None:
+            line["lbfgs"] = lbfgs
         print(json.dumps(line), flush=True)
     if dist_on:
         torch.distributed.barrier()

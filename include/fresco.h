@@ -272,7 +272,16 @@ typedef struct {
     int max_backtrack;    /* halvings per line search, 0..60 (default 20) */
     double gtol;          /* stop when the RMS gradient sqrt(g.g / (N d)) < gtol (0: off) */
     double ftol;          /* stop when the loss < ftol (0: off) */
-    int reserved[4];      /* must be zero */
+    int tile_order;       /* 1: keep the solver's vectors in the plan's tile order. The first run
+                             after create / reset evaluates the start points, takes the tile order
+                             of that evaluation as a fixed permutation, and every run gathers the
+                             caller's points into it, iterates there, and scatters the result back
+                             (the returned points are in caller order). The points move little per
+                             iteration, so every evaluation then sees nearly sorted points: the
+                             binning's and the gradient's writes become nearly sequential instead
+                             of random. The steps equal those of tile_order 0 up to the order of
+                             the floating-point sums. Costs 4 bytes per point and one vector. */
+    int reserved[3];      /* must be zero */
 } fresco_lbfgs_opts;
 
 typedef struct {
@@ -301,7 +310,8 @@ fresco_status fresco_lbfgs_run(fresco_lbfgs_t s, void *d_points, int64_t max_ite
  * points, precision and stream as the plan) to the structure-factor loss. NULL removes it. */
 fresco_status fresco_lbfgs_set_pair(fresco_lbfgs_t s, fresco_pair_t p);
 
-/* Drop the stored pairs and zero the counters. */
+/* Drop the stored pairs, zero the counters and forget the tile order (tile_order: the next run
+ * takes a new one). */
 fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s);
 
 fresco_status fresco_lbfgs_destroy(fresco_lbfgs_t s);
@@ -355,8 +365,9 @@ fresco_status fresco_batch_destroy(fresco_batch_t b);
  * halve the step, or give up after max_backtrack halvings), the new (s, y) pair and the next
  * direction by the two-loop recursion over that instance's own history. From the second step
  * on, a step is one replay of a CUDA graph when the batch plan has a non-default stream.
- * opts: as for fresco_lbfgs_create (NULL = defaults; max_step 0 = a tenth of each instance's
- * mean spacing L N^(-1/d)); max_iter: accepted iterations per instance (0 = no limit).
+ * opts: as for fresco_lbfgs_create, with tile_order 0 (NULL = defaults; max_step 0 = a tenth of
+ * each instance's mean spacing L N^(-1/d)); max_iter: accepted iterations per instance (0 = no
+ * limit).
  * The solver owns its trial and history buffers ((5 + 2 history) x sum N x dim values). */
 typedef struct fresco_batch_lbfgs_s *fresco_batch_lbfgs_t;
 fresco_status fresco_batch_lbfgs_create(fresco_batch_lbfgs_t *out, fresco_batch_t b,

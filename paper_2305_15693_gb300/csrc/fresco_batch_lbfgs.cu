@@ -473,8 +473,10 @@ fresco_status fresco_batch_lbfgs_create(fresco_batch_lbfgs_t *out, fresco_batch_
     fresco_lbfgs_opts o;
     fresco_lbfgs_opts_default(&o);
     if (opts) o = *opts;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i]) return FRESCO_ERR_ARG;
+    // the ensemble solver keeps its instances' vectors in caller order (tile_order is 0)
+    if (o.tile_order != 0) return FRESCO_ERR_ARG;
     if (o.history < 1 || o.history > 64 || o.max_backtrack < 0 || o.max_backtrack > 60 ||
         !(o.c1 > 0.0 && o.c1 < 1.0) || o.max_step < 0.0 || o.gtol < 0.0 || o.ftol < 0.0)
         return FRESCO_ERR_ARG;

@@ -15,6 +15,7 @@ constexpr int kMaxWidth = 16;     // largest ES kernel width instantiated
 constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
 constexpr int kTileCursors = 4;   // placement cursors per tile of a single plan (Geom.sub)
+constexpr int kZSegment = 6;      // 3D single plans: tiles per z-column segment (Geom.zseg)
 // fresco_loss_grad_host copies the points in up to kHostChunks pieces of at least
 // kHostChunkBytes, binning each piece while the next one is in flight
 constexpr int kHostChunks = 8;
@@ -38,6 +39,8 @@ struct Geom {
                         // strip. Single plans: kTileCursors placement cursors (bin = tile * sub +
                         // caller index mod sub)
     int strips[3];      // 1 if every tile on the axis is at least w cells wide (strips disjoint)
+    int zseg;           // 3D single plans: tiles per z-column segment of the column spread (0:
+                        // tiles spread one by one)
     int64_t n_bins;     // n_tiles * sub: the sort key space
     int64_t n_points;
     int width;          // ES kernel width w

@@ -1582,10 +1582,11 @@ cudaError_t Launch<T>::place(const Geom &g, const T *points, int *cur, void *sor
 
 template <typename T>
 int Launch<T>::spread_own_smem(const Geom &g) {
-    // the extended region, then (FP32) the residue-grouped entries: packed window start and D
-    // kernel offsets
-    return (int)(spread_own_tile_bytes(g, sizeof(T)) +
-                 (sizeof(T) == 4 ? (size_t)(1 + g.dim) * 4 * (size_t)g.list_cap : 0));
+    // the extended region (3D columns: the plane buffer), then (FP32) the residue-grouped
+    // entries: packed window start and D kernel offsets
+    const size_t region = g.dim == 3 && g.zseg > 0 ? spread_col_tile_bytes(g, sizeof(T))
+                                                   : spread_own_tile_bytes(g, sizeof(T));
+    return (int)(region + (sizeof(T) == 4 ? (size_t)(1 + g.dim) * 4 * (size_t)g.list_cap : 0));
 }
 
 template <typename T>
@@ -1606,33 +1607,63 @@ cudaError_t WOps<T, W, D>::spread_own(const Geom &g, const EsPoly<T> &ep, const 
                                       cudaStream_t s) {
     using U = typename PT<T>::U;
     const int smem = Launch<T>::spread_own_smem(g);
+    const unsigned nt = (unsigned)g.n_tiles;
+    cudaError_t e;
+    if (D == 3 && g.zseg > 0) {
+        // z-columns: fold z (segment ends) first, then x, then y
+        auto kern = k_spread_col<T, W>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const unsigned nseg = (unsigned)((g.nb[2] + g.zseg - 1) / g.zseg);
+        kern<<<(unsigned)(g.nb[0] * g.nb[1]) * nseg, 256, smem, s>>>(g, ep, (const U *)sorted,
+                                                                     off, grid, ring, ring_slot);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (g.tq[2] >= W) {
+            k_halo_fold<T, W, D, 2, 3, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        } else {
+            k_halo_fold<T, W, D, 2, 1, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 2, 2, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        }
+        if (g.tq[0] >= W) {
+            k_halo_fold<T, W, D, 0, 3, 4><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        } else {
+            k_halo_fold<T, W, D, 0, 1, 4><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 0, 2, 4><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        }
+        if (g.tq[1] >= W) {
+            k_halo_fold<T, W, D, 1, 3, 5><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        } else {
+            k_halo_fold<T, W, D, 1, 1, 5><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 1, 2, 5><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        }
+        return cudaGetLastError();
+    }
     auto kern = k_spread_own<T, W, D>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid, ring,
-                                                ring_slot);
+    kern<<<nt, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid, ring, ring_slot);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one launch per axis when every tile along it is at least W wide, else two (low, high)
-    const unsigned nt = (unsigned)g.n_tiles;
     if (g.tq[0] >= W) {
-        k_halo_fold<T, W, D, 0, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 0, 3, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
     } else {
-        k_halo_fold<T, W, D, 0, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
-        k_halo_fold<T, W, D, 0, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 0, 1, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 0, 2, 0><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
     }
     if (g.tq[1] >= W) {
-        k_halo_fold<T, W, D, 1, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 1, 3, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
     } else {
-        k_halo_fold<T, W, D, 1, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
-        k_halo_fold<T, W, D, 1, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 1, 1, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+        k_halo_fold<T, W, D, 1, 2, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
     }
     if constexpr (D == 3) {
         if (g.tq[2] >= W) {
-            k_halo_fold<T, W, D, 2, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 2, 3, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
         } else {
-            k_halo_fold<T, W, D, 2, 1><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
-            k_halo_fold<T, W, D, 2, 2><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 2, 1, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
+            k_halo_fold<T, W, D, 2, 2, 3><<<nt, 256, 0, s>>>(g, ring, ring_slot, grid);
         }
     }
     return cudaGetLastError();
@@ -1748,7 +1779,7 @@ template <typename T>
 cudaError_t Launch<T>::spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                                   const int *off, T *grid, T *ring, int64_t ring_slot,
                                   cudaStream_t s, int *launches) {
-    *launches += 1;
+    *launches += 1;   // (the column spread's folds: the same count, z first)
     for (int a = 0; a < g.dim; ++a) *launches += g.tq[a] >= g.width ? 1 : 2;
     if (g.dim == 2) {
         FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::spread_own(g, ep, sorted, off, grid,

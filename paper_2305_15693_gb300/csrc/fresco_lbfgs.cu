@@ -144,6 +144,9 @@ struct fresco_lbfgs_s {
     int64_t n = 0;          // N * dim
     size_t es = 4;
     cudaStream_t stream = nullptr;
+    int *order = nullptr;   // tile_order: solver position i holds caller point order[i]
+    void *xs = nullptr;     // tile_order: the points in solver order
+    bool have_order = false;
     void *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
     std::vector<void *> S, Y;
     double *scal = nullptr;   // device scalars
@@ -185,6 +188,32 @@ struct Ops {
     }
 };
 
+// order[i] = caller index of the i-th point in tile order: the caller index that a float record
+// carries, or the double plans' separate permutation
+template <typename T>
+__global__ void __launch_bounds__(256) k_order_from_plan(const void *__restrict__ sorted,
+                                                         const int *__restrict__ perm, int64_t n,
+                                                         int *__restrict__ order) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        order[i] = sizeof(T) == 4 ? (int)reinterpret_cast<const uint4 *>(sorted)[i].w : perm[i];
+}
+
+// to_solver: y[i] = x[order[i]]; else x[order[i]] = y[i] (points of dim coordinates)
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(const int *__restrict__ order, int64_t n,
+                                                 int dim, T *__restrict__ x, T *__restrict__ y,
+                                                 int to_solver) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = order[i];
+        for (int a = 0; a < dim; ++a) {
+            if (to_solver) y[i * dim + a] = x[j * dim + a];
+            else x[j * dim + a] = y[i * dim + a];
+        }
+    }
+}
+
 fresco_status cerr(cudaError_t e) {
     if (e == cudaSuccess) return FRESCO_OK;
     return e == cudaErrorMemoryAllocation ? FRESCO_ERR_OOM : FRESCO_ERR_CUDA;
@@ -205,13 +234,33 @@ fresco_status evaluate(fresco_lbfgs_s *s, const void *x, double *loss, void *gra
 }
 
 template <typename T>
-fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfgs_report *rep) {
+fresco_status run_impl(fresco_lbfgs_s *s, void *x_caller, int64_t max_iter,
+                       fresco_lbfgs_report *rep) {
     Ops<T> op{s};
     const int m = s->opts.history;
     double *sc = s->scal;
     fresco_status st;
+    const int dim = s->plan->dim;
+    const int64_t np = s->n / dim;
+    const unsigned pb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((np + 255) / 256, 152 * 8));
+    void *x = x_caller;
     // loss and gradient at the start point
-    if ((st = evaluate(s, x, s->loss_x, s->g))) return st;
+    if (s->opts.tile_order && !s->have_order) {
+        // evaluate in caller order once; its tile order becomes the solver's order
+        if ((st = evaluate(s, x_caller, s->loss_x, s->gt))) return st;
+        k_order_from_plan<T><<<pb, 256, 0, s->stream>>>(s->plan->d_sorted, s->plan->d_perm, np,
+                                                         s->order);
+        k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)x_caller, (T *)s->xs, 1);
+        k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)s->gt, (T *)s->g, 1);
+        s->have_order = true;
+        x = s->xs;
+    } else if (s->opts.tile_order) {
+        k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)x_caller, (T *)s->xs, 1);
+        x = s->xs;
+        if ((st = evaluate(s, x, s->loss_x, s->g))) return st;
+    } else {
+        if ((st = evaluate(s, x, s->loss_x, s->g))) return st;
+    }
     ++s->evals;
     double fx = host_read(s, s->loss_x);
     int status = 0;
@@ -293,6 +342,8 @@ fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfg
         ++s->iters;
         if (it + 1 == max_iter) status = 3;
     }
+    if (s->opts.tile_order)   // the result back in caller order
+        k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)x_caller, (T *)x, 0);
     if (rep) {
         op.dot(s->g, s->g, sc + SL_GG);
         const double gg = host_read(s, sc + SL_GG);
@@ -308,7 +359,8 @@ fresco_status run_impl(fresco_lbfgs_s *s, void *x, int64_t max_iter, fresco_lbfg
 void lbfgs_free(fresco_lbfgs_s *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    void *bufs[] = {s->g, s->d, s->xt, s->gt, s->scal, s->part, s->loss_x, s->loss_t};
+    void *bufs[] = {s->g, s->d, s->xt, s->gt, s->scal, s->part, s->loss_x, s->loss_t,
+                    s->order, s->xs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (void *b : s->S)
@@ -338,8 +390,9 @@ fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
     fresco_lbfgs_opts o;
     fresco_lbfgs_opts_default(&o);
     if (opts) o = *opts;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
         if (o.reserved[i]) return FRESCO_ERR_ARG;
+    if (o.tile_order != 0 && o.tile_order != 1) return FRESCO_ERR_ARG;
     if (o.history < 1 || o.history > 64 || o.max_backtrack < 0 || o.max_backtrack > 60 ||
         !(o.c1 > 0.0 && o.c1 < 1.0) || o.max_step < 0.0 || o.gtol < 0.0 || o.ftol < 0.0)
         return FRESCO_ERR_ARG;
@@ -375,6 +428,8 @@ fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
     s->S.assign(o.history, nullptr);
     s->Y.assign(o.history, nullptr);
     for (int i = 0; ok && i < o.history; ++i) ok = alloc(&s->S[i], vb) && alloc(&s->Y[i], vb);
+    if (ok && o.tile_order)
+        ok = alloc((void **)&s->order, sizeof(int) * (size_t)info.n_points) && alloc(&s->xs, vb);
     if (!ok) {
         lbfgs_free(s);
         return FRESCO_ERR_OOM;
@@ -400,6 +455,7 @@ fresco_status fresco_lbfgs_set_pair(fresco_lbfgs_t s, fresco_pair_t p) {
 
 fresco_status fresco_lbfgs_reset(fresco_lbfgs_t s) {
     if (!s) return FRESCO_ERR_ARG;
+    s->have_order = false;
     s->count = 0;
     s->head = 0;
     s->iters = 0;

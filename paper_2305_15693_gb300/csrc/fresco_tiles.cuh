@@ -79,14 +79,24 @@ __device__ __forceinline__ int tile_cell(const Geom &g, const T (&r)[3], int (&r
     return t[0] + g.nb[0] * (t[1] + g.nb[1] * t[2]);
 }
 
+// Whether some lane of the warp has the same bin as the lane before it: points that arrive in
+// tile order (a solver that keeps them so) form runs, and the warp then combines its atomics per
+// bin; points in random order almost never do, and skip the (costlier) matching.
+__device__ __forceinline__ bool warp_has_runs(int bin, bool in) {
+    const int prev = __shfl_up_sync(0xffffffffu, bin, 1);
+    return __any_sync(0xffffffffu, in && (threadIdx.x & 31) > 0 && prev == bin);
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_count(Geom g, const T *__restrict__ pts,
                                                int *__restrict__ cnt, int *__restrict__ err) {
     constexpr int IL = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
     bool ok = true;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
-         j0 += stride) {
+    // the loop runs warp-uniformly (whole warps take part in the warp-level matching below)
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x * IL + (threadIdx.x & ~31u);
+         w0 < g.n_points; w0 += stride) {
+        const int64_t j0 = w0 + (threadIdx.x & 31);
         T r[IL][3];
 #pragma unroll
         for (int k = 0; k < IL; ++k) {
@@ -101,7 +111,15 @@ __global__ void __launch_bounds__(256) k_count(Geom g, const T *__restrict__ pts
             int rel[3];
             T frac[3];
             const int t = tile_cell<T, D>(g, r[k], rel, frac, ok);
-            if (j < g.n_points) atomicAdd(&cnt[t * g.sub + (int)(j % g.sub)], 1);
+            const bool in = j < g.n_points;
+            const int bin = in ? t * g.sub + (int)(j % g.sub) : -1;
+            if (warp_has_runs(bin, in)) {
+                // lanes that hit the same bin (points in tile order) add once together
+                const unsigned grp = __match_any_sync(0xffffffffu, bin);
+                if (in && (threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cnt[bin], __popc(grp));
+            } else if (in) {
+                atomicAdd(&cnt[bin], 1);
+            }
         }
     }
     if (!ok) atomicOr(err, 1);
@@ -115,8 +133,9 @@ __global__ void __launch_bounds__(256) k_place(Geom g, const T *__restrict__ pts
     using U = typename PT<T>::U;
     constexpr int IL = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
-    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x * IL + threadIdx.x; j0 < g.n_points;
-         j0 += stride) {
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x * IL + (threadIdx.x & ~31u);
+         w0 < g.n_points; w0 += stride) {
+        const int64_t j0 = w0 + (threadIdx.x & 31);
         T r[IL][3];
 #pragma unroll
         for (int k = 0; k < IL; ++k) {
@@ -136,7 +155,19 @@ __global__ void __launch_bounds__(256) k_place(Geom g, const T *__restrict__ pts
             const int t = tile_cell<T, D>(g, r[k], rel, frac, ok);
 #pragma unroll
             for (int a = 0; a < 3; ++a) u[k][a] = a < D ? pack_coord<T>(rel[a], frac[a]) : U(0);
-            pos[k] = j < g.n_points ? atomicAdd(&cur[t * g.sub + (int)(j % g.sub)], 1) : 0;
+            const bool in = j < g.n_points;
+            const int bin = in ? t * g.sub + (int)(j % g.sub) : -1;
+            if (warp_has_runs(bin, in)) {
+                // one cursor atomic per bin and warp; lanes take consecutive slots in lane order
+                const unsigned grp = __match_any_sync(0xffffffffu, bin);
+                const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+                int base = 0;
+                if (in && lane == leader) base = atomicAdd(&cur[bin], __popc(grp));
+                base = __shfl_sync(grp, base, leader);
+                pos[k] = base + __popc(grp & ((1u << lane) - 1u));
+            } else {
+                pos[k] = in ? atomicAdd(&cur[bin], 1) : 0;
+            }
         }
 #pragma unroll
         for (int k = 0; k < IL; ++k) {
@@ -470,6 +501,208 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// 3D column spread: one block walks a segment of g.zseg tiles of one (x, y) column along z and
+// keeps the planes of the current tile's extended region in a circular buffer of NP = tmax_z + W
+// planes in shared memory. The w planes a tile shares with the next (its top halo and the next
+// tile's bottom halo) stay in the buffer, so the z halo between the tiles of a segment is summed
+// on chip; a plane is written out once no later point of the segment can reach it: its cells
+// inside the column go to the grid, its x/y halo cells to the ring of the tile that owns the
+// plane, and the planes beyond the segment's ends to the z halo planes of the first / last tile's
+// ring. The rings are then folded z first (segment ends only), then x, then y. The plane stride
+// is a multiple of 32 words, so a window's bank residue does not depend on its plane and the
+// residue schedule stays conflict free across the wrap of the buffer. All tiles of a segment use
+// one fixed-point scale, set by the three most crowded consecutive tiles that can reach a plane.
+__host__ __device__ inline int col_plane_stride(const Geom &g) {
+    return ((g.tmax[0] + g.width) * (g.tmax[1] + g.width) + 31) & ~31;
+}
+__host__ __device__ inline size_t spread_col_tile_bytes(const Geom &g, size_t esize) {
+    const size_t words = (size_t)(g.tmax[2] + g.width) * col_plane_stride(g);
+    return (words * (esize > 4 ? esize : 4) + 15) & ~(size_t)15;
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void spread_point_col(const EsPoly<T> &ep, const int (&i0)[3],
+                                                 const T (&x1)[3], int Ex, int Sxy, int NP,
+                                                 int plane0, T *ftile, int *itile, bool fixed,
+                                                 float fscale) {
+    T wx[W], wy[W], wz[W];
+    es_weights<T, W>(ep, x1[0], wx);
+    es_weights<T, W>(ep, x1[1], wy);
+    es_weights<T, W>(ep, x1[2], wz);
+    const int oxy = i0[1] * Ex + i0[0];
+    if constexpr (sizeof(T) == 4) {
+        if (fixed) {
+            const unsigned base = smem_addr(itile) + 4u * (unsigned)oxy;
+            const unsigned step = 4u * (unsigned)Ex;
+#pragma unroll (W <= 8 ? W : 1)
+            for (int c = 0; c < W; ++c) {
+                int pl = plane0 + c;
+                pl -= pl >= NP ? NP : 0;
+                unsigned row = base + 4u * (unsigned)(pl * Sxy);
+                const float wzs = wz[c] * fscale;
+#pragma unroll
+                for (int b = 0; b < W; ++b, row += step)
+                    red_row_fixed<W>(row, wzs * wy[b], wx, std::make_integer_sequence<int, W>{});
+            }
+            return;
+        }
+    }
+#pragma unroll 1
+    for (int c = 0; c < W; ++c) {
+        int pl = plane0 + c;
+        pl -= pl >= NP ? NP : 0;
+        T *plane = ftile + (int64_t)pl * Sxy + oxy;
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            const T wzy = wz[c] * wy[b];
+#pragma unroll
+            for (int a = 0; a < W; ++a) atomicAdd(plane + b * Ex + a, wzy * wx[a]);
+        }
+    }
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
+    Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
+    const int *__restrict__ off, T *__restrict__ grid, T *__restrict__ ring,
+    int64_t ring_slot) {
+    using U = typename PT<T>::U;
+    constexpr int D = 3, HL = W / 2, HR = W - HL;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    __shared__ int s_cnt[32], s_start[65], s_pmax;
+    T *ftile = reinterpret_cast<T *>(sm_raw);
+    int *itile = reinterpret_cast<int *>(sm_raw);
+    const int cap = g.list_cap;
+    int *l_i0 = reinterpret_cast<int *>(sm_raw + spread_col_tile_bytes(g, sizeof(T)));
+    float *l_x1 = reinterpret_cast<float *>(l_i0 + cap);
+    const int bid = blockIdx.x;
+    const int tx = bid % g.nb[0], ty = (bid / g.nb[0]) % g.nb[1];
+    const int tz0 = (bid / (g.nb[0] * g.nb[1])) * g.zseg;
+    const int nz = min(g.zseg, g.nb[2] - tz0);
+    const int sx = tile_start(tx, g.tq[0], g.tr[0]);
+    const int wx = tile_start(tx + 1, g.tq[0], g.tr[0]) - sx;
+    const int sy = tile_start(ty, g.tq[1], g.tr[1]);
+    const int wy = tile_start(ty + 1, g.tq[1], g.tr[1]) - sy;
+    const int Ex = wx + W, Ey = wy + W;
+    const int Sxy = col_plane_stride(g), NP = g.tmax[2] + W;
+    const int zfirst = tile_start(tz0, g.tq[2], g.tr[2]);
+    const int zend = tile_start(tz0 + nz, g.tq[2], g.tr[2]);
+    const int zlast = tile_start(tz0 + nz - 1, g.tq[2], g.tr[2]);
+    const int zbase = zfirst - HL;   // plane zbase is slot 0
+    auto tile_id = [&](int tz) -> int64_t {
+        return ((int64_t)tz * g.nb[1] + ty) * g.nb[0] + tx;
+    };
+    if (threadIdx.x == 0) s_pmax = 0;
+    __syncthreads();
+    if ((int)threadIdx.x < nz) {
+        const int64_t t = tile_id(tz0 + threadIdx.x);
+        atomicMax(&s_pmax, off[(t + 1) * g.sub] - off[t * g.sub]);
+    }
+    {   // zero the buffer, 16 bytes per store
+        const int words = NP * Sxy * (int)(sizeof(T) / 4);
+        uint4 *z4 = reinterpret_cast<uint4 *>(sm_raw);
+        for (int i = threadIdx.x; i < words / 4; i += blockDim.x) z4[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+    const int P3 = 3 * s_pmax;
+    bool fixed = false;
+    int sc = 0;
+    if constexpr (sizeof(T) == 4) {
+        fixed = P3 < kFixedMaxPoints;
+        sc = fixed ? min(21, __clz(max(P3, 1)) - 1) : 0;
+    }
+    const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
+    const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < nz; ++k) {
+        const int tz = tz0 + k;
+        const int64_t t = tile_id(tz);
+        const int zk = tile_start(tz, g.tq[2], g.tr[2]);
+        const int wz = tile_start(tz + 1, g.tq[2], g.tr[2]) - zk;
+        const int r0 = zk - HL - zbase;            // buffer plane of the region's first plane
+        const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+        if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+        __syncthreads();
+        if (fixed && p1 - p0 <= cap) {
+            const int rounds = residue_lists<T, W, D>(
+                sorted, p0, p1, Ex, Sxy, s_cnt, s_start,
+                [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned) {
+                    l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
+                });
+            const int mine = s_cnt[lane], first = s_start[lane];
+            for (int q = threadIdx.x >> 5; q < rounds; q += blockDim.x >> 5) {
+                if (q < mine) {
+                    const int h = first + q;
+                    const int pk = l_i0[h];
+                    const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+                    const T x1[3] = {(T)l_x1[h], (T)l_x1[cap + h], (T)l_x1[2 * cap + h]};
+                    spread_point_col<T, W>(ep, i0, x1, Ex, Sxy, NP, (r0 + i0[2]) % NP, ftile,
+                                           itile, true, fscale);
+                }
+            }
+        } else {
+            for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                U u[3];
+                load_packed<T, D>(sorted, p, u);
+                int i0[3];
+                T x1[3];
+                window_of<T, W, D>(u, Ex, Sxy, i0, x1);
+                spread_point_col<T, W>(ep, i0, x1, Ex, Sxy, NP, (r0 + i0[2]) % NP, ftile, itile,
+                                       fixed, fscale);
+            }
+        }
+        __syncthreads();
+        // planes no later point of the segment reaches: [zk - HL, zk + wz - HL), or to the end
+        const int pz0 = zk - HL;
+        const int pz1 = k + 1 < nz ? zk + wz - HL : zk + wz + HR;
+        const int nrows = (pz1 - pz0) * Ey;
+        for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
+            const int pz = pz0 + row / Ey, ey = row % Ey;
+            const int slot = (pz - zbase) % NP;
+            // the tile whose ring or cells take this plane, and the plane's place in its region
+            int owner, ez, wo;
+            if (pz < zfirst) {
+                owner = tz0;
+                ez = pz - (zfirst - HL);
+                wo = tile_start(tz0 + 1, g.tq[2], g.tr[2]) - zfirst;
+            } else if (pz >= zend) {
+                owner = tz0 + nz - 1;
+                ez = pz - (zlast - HL);
+                wo = zend - zlast;
+            } else {
+                owner = pz < zk ? tz - 1 : tz;
+                const int zo = owner == tz ? zk : tile_start(owner, g.tq[2], g.tr[2]);
+                ez = pz - zo + HL;
+                wo = (owner == tz ? zk + wz : zk) - zo;
+            }
+            const bool zin = ez >= HL && ez < HL + wo;
+            const bool through = zin && ey >= HL && ey < HL + wy;
+            T *rrow = ring + tile_id(owner) * ring_slot + ring_index<W, D>(0, ey, ez, wx, wy, wo);
+            const int64_t gz = (int64_t)(pz < 0 ? pz + g.nf[2] : (pz >= g.nf[2] ? pz - g.nf[2] : pz));
+            const int64_t gbase = (gz * g.nf[1] + (sy + ey - HL)) * g.nf[0] + sx - HL;
+            const int base = slot * Sxy + ey * Ex;
+            for (int ex = lane; ex < Ex; ex += 32) {
+                T v;
+                if constexpr (sizeof(T) == 4) {
+                    v = fixed ? (float)itile[base + ex] * finv : ftile[base + ex];
+                    itile[base + ex] = 0;
+                } else {
+                    v = ftile[base + ex];
+                    ftile[base + ex] = T(0);
+                }
+                if (!through) rrow[ex] = v;
+                else if (ex < HL) rrow[ex] = v;
+                else if (ex >= HL + wx) rrow[ex - wx] = v;
+                else grid[gbase + ex] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Folds the rings into the grid, one axis A at a time (x, then y, then z). In the pass along A
 // every tile adds the cells of its extended region that lie in its halo bands along A (the W/2
 // cells below the tile and the W - W/2 above it) and inside the tile along the axes already
@@ -481,20 +714,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
 // bands only, 3 both in one launch, which needs tiles at least W wide along A (the cells a tile
 // receives from below and from above are then disjoint). So no cell is written twice in a
 // launch: the passes are race-free and the sums are in a fixed order.
-template <typename T, int W, int D, int A, int SIDES>
+//
+// FM is the set of axes folded before A (bit b: axis b); the default order x, y, z has FM = the
+// axes below A. Tiles spread by z-columns (k_spread_col) fold z first (FM = 0), then x ({z}),
+// then y ({x, z}), and along z only the ends of a column segment have rings: with zseg > 0 the z
+// pass moves the low band of a tile only if it starts a segment (tz % zseg == 0) and the high
+// band only if it ends one.
+template <typename T, int W, int D, int A, int SIDES, int FM>
 __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
                                                    int64_t ring_slot, T *__restrict__ grid) {
     constexpr int HL = W / 2;
     const int64_t t = blockIdx.x;
     int s[3], w[3], tc[3];
     tile_extent(g, t, W, s, w, tc);
-    // extents of the cells moved: NA along A, the tile along folded axes, the region after A
+    bool do_low = SIDES != 2, do_high = SIDES != 1;
+    if (A == 2 && g.zseg > 0) {
+        do_low = do_low && tc[2] % g.zseg == 0;
+        do_high = do_high && (tc[2] % g.zseg == g.zseg - 1 || tc[2] == g.nb[2] - 1);
+        if (!do_low && !do_high) return;
+    }
+    // extents of the cells moved: NA along A, the tile along folded axes, the region otherwise
     constexpr int HR = W - HL;
     constexpr int NA = SIDES == 3 ? W : (SIDES == 1 ? HL : HR);   // cells moved along A
     int ext[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
-        ext[b] = b >= D ? 1 : (b == A ? NA : (b < A ? w[b] : w[b] + W));
+        ext[b] = b >= D ? 1 : (b == A ? NA : ((FM >> b) & 1 ? w[b] : w[b] + W));
     // neighbours along A
     const int lo_t = tc[A] == 0 ? g.nb[A] - 1 : tc[A] - 1;
     const int hi_t = tc[A] == g.nb[A] - 1 ? 0 : tc[A] + 1;
@@ -514,9 +759,11 @@ __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
         e[2] = i / (ext[0] * ext[1]);
         // e along folded axes counts from the tile's first cell
 #pragma unroll
-        for (int b = 0; b < A; ++b) e[b] += HL;
+        for (int b = 0; b < 3; ++b)
+            if ((FM >> b) & 1) e[b] += HL;
         if (SIDES == 2) e[A] += HL;   // high band only
         const bool low = e[A] < HL;
+        if (low ? !do_low : !do_high) continue;
         if (!low) e[A] += w[A];      // high band: HL + w .. w + W - 1
         const T v = src_ring[ring_index<W, D>(e[0], e[1], e[2], w[0], w[1], w[2])];
         // the same cell in the neighbour's extended region
@@ -533,7 +780,8 @@ __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
         }
         bool inside = true;
 #pragma unroll
-        for (int b = A + 1; b < D; ++b) inside = inside && f[b] >= HL && f[b] < HL + fw[b];
+        for (int b = 0; b < D; ++b)
+            if (b != A && !((FM >> b) & 1)) inside = inside && f[b] >= HL && f[b] < HL + fw[b];
         if (inside) {
             int gc[3] = {0, 0, 0};
 #pragma unroll

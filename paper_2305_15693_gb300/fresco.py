@@ -73,7 +73,8 @@ class fresco_opts(ctypes.Structure):
 class fresco_lbfgs_opts(ctypes.Structure):
     _fields_ = [("history", ctypes.c_int), ("max_step", ctypes.c_double), ("c1", ctypes.c_double),
                 ("max_backtrack", ctypes.c_int), ("gtol", ctypes.c_double),
-                ("ftol", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+                ("ftol", ctypes.c_double), ("tile_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class fresco_lbfgs_report(ctypes.Structure):
@@ -1016,10 +1017,11 @@ class LBFGS:
     """Device-resident L-BFGS over a Plan (see fresco_lbfgs_* in include/fresco.h)."""
 
     def __init__(self, plan, history=10, max_step=0.0, c1=1e-4, max_backtrack=20, gtol=0.0,
-                 ftol=0.0):
+                 ftol=0.0, tile_order=False):
         o = fresco_lbfgs_opts_default()
         o.history, o.max_step, o.c1 = int(history), float(max_step), float(c1)
         o.max_backtrack, o.gtol, o.ftol = int(max_backtrack), float(gtol), float(ftol)
+        o.tile_order = 1 if tile_order else 0
         self.plan = plan
         self.handle = fresco_lbfgs_create(plan.handle, o)
 

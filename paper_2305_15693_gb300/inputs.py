@@ -262,6 +262,55 @@ def workload(name: str) -> Workload:
 
 
 @dataclass
+class FreeWorkload:
+    """Points at free positions in [-L/2, L/2]^d with constraints at real wavevectors (the
+    NUwNU form): a quasicrystal-like target, a ring of n_peaks Gaussian Bragg peaks at a radius
+    incommensurate with the box's reciprocal lattice."""
+    name: str
+    dim: int
+    n_points: int
+    n_k: int
+    kmax: float            # wavevectors uniform in the ball |k| <= kmax (radians per length)
+    dtype: str
+    seed: int = 0
+    box: float = 1.0
+    tol: float = 1e-6
+    upsample: float = 2.0
+    n_peaks: int = 10
+
+    def points(self) -> np.ndarray:
+        dt = np.float64 if self.dtype == "f64" else np.float32
+        g = rng(self.seed)
+        return ((g.random((self.n_points, self.dim)) - 0.5) * self.box).astype(dt)
+
+    def wavevectors(self) -> np.ndarray:
+        g = rng(self.seed + 1)
+        k = g.standard_normal((self.n_k, self.dim))
+        k *= (self.kmax * g.random(self.n_k) ** (1.0 / self.dim)
+              / np.linalg.norm(k, axis=1))[:, None]
+        return k
+
+    def targets(self, k: np.ndarray):
+        r = self.kmax / (1.0 + np.sqrt(5.0))
+        ang = 2 * np.pi * np.arange(self.n_peaks) / self.n_peaks
+        c = np.zeros((self.n_peaks, self.dim))
+        c[:, 0], c[:, 1] = r * np.cos(ang), r * np.sin(ang)
+        width = 2 * np.pi / self.box
+        S0 = np.zeros(k.shape[0])
+        for p in range(self.n_peaks):
+            S0 += (self.n_points / self.n_peaks) * np.exp(
+                -((k - c[p]) ** 2).sum(1) / (2 * width ** 2))
+        return S0, np.ones(k.shape[0])
+
+
+def free_workload(name: str) -> FreeWorkload:
+    """The named NUwNU workloads."""
+    if name == "quasicrystal2d_n1e6_k1e6_f32":
+        return FreeWorkload(name, 2, 10**6, 10**6, 2 * np.pi * 400, "f32", seed=11)
+    raise KeyError(name)
+
+
+@dataclass
 class Ensemble:
     """Many independent 2D problems: instance i has n_points[i] uniform points in a periodic box
     boxes[i] (a square of that side) and the ball mask of radius K[i] (from chi[i]), with a

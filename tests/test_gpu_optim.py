@@ -153,3 +153,56 @@ def test_graph_solver_follows_the_host_driven_solver_exactly():
     assert reps[0]["evaluations"] == rep["evaluations"]
     assert reps[0]["loss"] == pytest.approx(rep["loss"], rel=1e-12)
     np.testing.assert_allclose(x_graph, x_host, rtol=0, atol=1e-6)
+
+
+def test_tile_ordered_solver_follows_the_reference_and_returns_caller_order():
+    """tile_order = 1 (the solver's vectors kept in the plan's tile order): the same 20-iteration
+    trace of the 1024-point FP64 workload as the numpy reference on oracle gradients, run as
+    twenty continued calls (each gathers the caller's points and scatters them back), and the
+    returned points are the caller's points: their loss recomputed by the oracle agrees."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    wl = inputs.workload("stealthy2d_n1024_k20_f64")
+    pts_np = wl.points()
+    mask = wl.mask()
+    S0, W = wl.targets(mask)
+    max_step = 0.1 * wl.box * wl.n_points ** -0.5
+
+    def fg(x):
+        l, gr, _, _ = oracle.loss_grad(x, mask, S0, W, box=wl.box)
+        return l, gr
+
+    _, ref = lbfgs_ref(fg, pts_np, 20, m=10, max_step=max_step)
+    pts = torch.from_numpy(pts_np).cuda()
+    with fresco.Plan(wl.box, mask, S0, W, wl.n_points, precision="f64") as plan:
+        solver = fresco.LBFGS(plan, history=10, max_step=max_step, tile_order=True)
+        trace = [solver.run(pts, 1)["loss"] for _ in range(20)]
+        solver.close()
+    np.testing.assert_allclose(trace, ref[1:21], rtol=1e-6)
+    l_or, _, _, _ = oracle.loss_grad(pts.cpu().numpy(), mask, S0, W, box=wl.box)
+    assert abs(l_or - trace[-1]) <= 1e-9 * abs(l_or)
+
+
+def test_tile_ordered_solver_matches_the_caller_ordered_one_fp32():
+    """FP32, 2e5 points, kernel-derivative gradient: 40 iterations with and without tile order
+    give the same losses up to the order of the floating-point sums."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    N = 200000
+    pts0 = inputs.uniform_points(N, 2, 5, np.float32)
+    mask = inputs.ball_mask(inputs.radius_for_chi(N, 2, 0.3), 2)
+    S0, W = inputs.stealthy_target(mask), inputs.unit_weights(mask)
+    losses = []
+    for tile_order in (False, True):
+        pts = torch.from_numpy(pts0).cuda()
+        with fresco.Plan(1.0, mask, S0, W, N, grad_mode="kderiv") as plan:
+            opt = fresco.LBFGS(plan, tile_order=tile_order)
+            rep = opt.run(pts, 40)
+            opt.close()
+            l_check, _ = plan.loss_grad(pts, want_grad=False)
+            torch.cuda.synchronize()
+        assert rep["iterations"] == 40
+        losses.append((rep["loss"], l_check.item()))
+    (plain, plain_check), (tiled, tiled_check) = losses
+    assert tiled == pytest.approx(tiled_check, rel=1e-6)     # returned points are caller order
+    assert tiled == pytest.approx(plain, rel=1e-3)
