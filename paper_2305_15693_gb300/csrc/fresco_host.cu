@@ -19,7 +19,11 @@ using namespace fresco;
 namespace {
 
 constexpr double kPi = 3.141592653589793238462643383279502884;
-constexpr size_t kSmemOptin = 227 * 1024;   // opt-in shared memory per block on sm_100 / sm_103
+// Dynamic shared memory a tile kernel may take: an SM holds 228 KB, a block reserves 1 KB and the
+// kernels' static shared state (the residue schedule) takes up to 4 KB; one block may opt in to
+// at most 227 KB in all.
+constexpr size_t kSmemOptin = 223 * 1024;        // one block per SM
+constexpr size_t kSmemTwoBlocks = 109 * 1024;    // two blocks per SM
 constexpr double kTileHits = 2000.0;         // points per 2D tile (with halo) the default aims at
 
 // ---- fine grid and kernel parameters --------------------------------------------------------
@@ -206,7 +210,7 @@ fresco_status choose_tiling(Params &P, const int tile_req[3], bool own_tiles = f
     // a tile is at least ceil(w / 2) cells wide: a point's window then reaches only the adjacent
     // tiles (the halo fold and the gathering spread rely on it)
     const int minw = (w + 1) / 2;
-    size_t budget = user_tiles ? kSmemOptin : kSmemOptin / 2;
+    size_t budget = user_tiles ? kSmemOptin : kSmemTwoBlocks;
     double cells_all = 1.0;
     for (int a = 0; a < dim; ++a) cells_all *= (double)P.nf[a];
     const double density = (double)P.n_points / cells_all;   // points per fine cell

@@ -57,11 +57,15 @@ __device__ __forceinline__ bool fine_coord(T r, T s_hi, T s_lo, int nf, int &cel
     T f = (p - c) + lo;
     if (f < T(0)) { c -= T(1); f += T(1); }
     if (f >= T(1)) { c += T(1); f -= T(1); }
+    frac = f;
+    if (c >= T(0) && c < T(nf)) {   // a point inside the box: no wrap (the common case)
+        cell = (int)c;
+        return ok;
+    }
     long long ci = (long long)c;
     ci %= nf;
     if (ci < 0) ci += nf;
     cell = (int)ci;
-    frac = f;
     return ok;
 }
 
@@ -136,37 +140,71 @@ __host__ __device__ constexpr int record_words() {
     return sizeof(T) == 4 ? 4 : (D == 3 ? 4 : 2);
 }
 
-// ES kernel weights psi(x1 + k), k = 0..W-1, from the plan's piecewise polynomials (Horner in
-// tau = 2 (x1 + W/2) - 1 in [-1, 1)); coefficients come from the kernel parameter bank.
+// ES kernel weights psi(x1 + k), k = 0..W-1, from the plan's piecewise polynomials in
+// tau = 2 (x1 + W/2) - 1 in [-1, 1); coefficients come from the kernel parameter bank.
+// psi is even, so the polynomial of interval W-1-k is that of interval k at -tau. With
+// p_k(tau) = E_k(s) + tau O_k(s), s = tau^2 (E_k, O_k: the even and odd coefficients of p_k),
+// the pair is w[k] = E_k + tau O_k and w[W-1-k] = E_k - tau O_k: one Horner pass in s per pair.
+// The middle interval of an odd width is symmetric about tau = 0 (odd part zero to the fit's
+// rounding) and takes E only.
 template <typename T, int W>
 __device__ __forceinline__ void es_weights(const EsPoly<T> &ep, T x1, T (&w)[W]) {
     constexpr int P = PolyDeg<T>::value;
+    constexpr int PE = P & ~1, PO = (P & 1) ? P : P - 1;   // highest even / odd power
     const T tau = T(2) * x1 + T(W - 1);
+    const T s = tau * tau;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        T acc = ep.c[k][P];
+    for (int k = 0; k < (W + 1) / 2; ++k) {
+        T e = ep.c[k][PE];
 #pragma unroll
-        for (int j = P - 1; j >= 0; --j) acc = fma(acc, tau, ep.c[k][j]);
-        w[k] = acc;
+        for (int j = PE - 2; j >= 0; j -= 2) e = fma(e, s, ep.c[k][j]);
+        if (2 * k + 1 == W) {
+            w[k] = e;
+        } else {
+            T o = ep.c[k][PO];
+#pragma unroll
+            for (int j = PO - 2; j >= 1; j -= 2) o = fma(o, s, ep.c[k][j]);
+            w[k] = fma(tau, o, e);
+            w[W - 1 - k] = fma(-tau, o, e);
+        }
     }
 }
 
-// The weights and their derivatives d psi(x1 + k) / d tau (Horner for the value and the
-// derivative together); d psi / d x1 = 2 d psi / d tau.
+// The weights and their derivatives d psi(x1 + k) / d tau; d psi / d x1 = 2 d psi / d tau.
+// In the even/odd form above, d/dtau (E + tau O) = 2 tau E'(s) + (O(s) + 2 s O'(s)) and
+// d/dtau (E - tau O) = 2 tau E'(s) - (O(s) + 2 s O'(s)) (Horner for each value and its
+// s-derivative together).
 template <typename T, int W>
 __device__ __forceinline__ void es_weights_d(const EsPoly<T> &ep, T x1, T (&w)[W], T (&dw)[W]) {
     constexpr int P = PolyDeg<T>::value;
+    constexpr int PE = P & ~1, PO = (P & 1) ? P : P - 1;
     const T tau = T(2) * x1 + T(W - 1);
+    const T s = tau * tau, s2 = s + s, tau2 = tau + tau;
 #pragma unroll
-    for (int k = 0; k < W; ++k) {
-        T acc = ep.c[k][P], dacc = T(0);
+    for (int k = 0; k < (W + 1) / 2; ++k) {
+        T e = ep.c[k][PE], de = T(0);
 #pragma unroll
-        for (int j = P - 1; j >= 0; --j) {
-            dacc = fma(dacc, tau, acc);
-            acc = fma(acc, tau, ep.c[k][j]);
+        for (int j = PE - 2; j >= 0; j -= 2) {
+            de = fma(de, s, e);
+            e = fma(e, s, ep.c[k][j]);
         }
-        w[k] = acc;
-        dw[k] = dacc;
+        const T a = tau2 * de;
+        if (2 * k + 1 == W) {
+            w[k] = e;
+            dw[k] = a;
+        } else {
+            T o = ep.c[k][PO], dO = T(0);
+#pragma unroll
+            for (int j = PO - 2; j >= 1; j -= 2) {
+                dO = fma(dO, s, o);
+                o = fma(o, s, ep.c[k][j]);
+            }
+            const T b = fma(s2, dO, o);
+            w[k] = fma(tau, o, e);
+            w[W - 1 - k] = fma(-tau, o, e);
+            dw[k] = a + b;
+            dw[W - 1 - k] = a - b;
+        }
     }
 }
 
@@ -1152,8 +1190,24 @@ __host__ __device__ inline size_t interp_kd_tile_bytes(const Geom &g, size_t esi
     return (cells * esize + 15) & ~(size_t)15;
 }
 
-// FP32 tiles of at most g.list_cap points run in the bank-residue schedule of the spread (every
-// window load of a warp hits 32 distinct banks); others one point per thread in sorted order.
+// One element from global to shared memory without passing through registers (cp.async, 4 or 8
+// bytes, cached in L1): the copies of a thread stay in flight until cp_async_wait_all().
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *dst, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "n"(sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// FP32 tiles of at most g.list_cap points run in the level-ordered bank-residue schedule of the
+// spread (window loads of a warp hit distinct banks but where a run of 32 entries spans two
+// levels); others one point per thread in sorted order. The tile and its halo are staged with
+// asynchronous copies, row by row (warps take rows, lanes cells), while the block builds the
+// point list from the sorted records.
 template <typename T, int W, int D>
 __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &ep,
                                                const typename PT<T>::U *__restrict__ sorted,
@@ -1163,7 +1217,7 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
                                                T *__restrict__ grad, const int64_t t) {
     using U = typename PT<T>::U;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ int s_cnt[32], s_start[65];
+    __shared__ ResidueShared s_rl;
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
     constexpr int HL = W / 2;
@@ -1180,65 +1234,65 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
     }
     const int rxy = rw[0] * rw[1];
     T *sh = reinterpret_cast<T *>(sm_raw);
-    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
-    {   // stage the tile and its halo, four loads per thread in flight; the staged region is
-        // narrower than the grid, so it wraps at most once per axis
-        constexpr int IL = 4;
-        const int cells = rxy * rw[2];
-        for (int i0 = threadIdx.x; i0 < cells; i0 += IL * blockDim.x) {
-            T v[IL];
-#pragma unroll
-            for (int k = 0; k < IL; ++k) {
-                const int i = i0 + k * blockDim.x;
-                if (i < cells) {
-                    const int row = i / rw[0], x = i - row * rw[0];
-                    const int z = D == 3 ? row / rw[1] : 0, y = D == 3 ? row - z * rw[1] : row;
-                    int gx = s[0] - HL + x, gy = s[1] - HL + y, gz = (D == 3) ? s[2] - HL + z : 0;
-                    gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
-                    gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
-                    if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
-                    v[k] = h[((int64_t)gz * g.nf[1] + gy) * g.nf[0] + gx];
-                }
+    if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
+    {   // stage the tile and its halo; the staged region is narrower than the grid, so it wraps
+        // at most once per axis
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int rows = rw[1] * rw[2];
+        int y = threadIdx.x >> 5, z = 0;
+        if (D == 3) {
+            z = y / rw[1];
+            y -= z * rw[1];
+        }
+        for (int row = threadIdx.x >> 5; row < rows; row += nw) {
+            int gy = s[1] - HL + y, gz = D == 3 ? s[2] - HL + z : 0;
+            gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+            if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
+            const T *src = h + ((int64_t)gz * g.nf[1] + gy) * g.nf[0];
+            T *dst = sh + row * rw[0];
+            for (int x = lane; x < rw[0]; x += 32) {
+                int gx = s[0] - HL + x;
+                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+                cp_async_elem(dst + x, src + gx);
             }
-#pragma unroll
-            for (int k = 0; k < IL; ++k) {
-                const int i = i0 + k * blockDim.x;
-                if (i < cells) sh[i] = v[k];
+            y += nw;
+            while (y >= rw[1]) {   // next row of this warp (nw rows on)
+                y -= rw[1];
+                ++z;
             }
         }
     }
     __syncthreads();
     const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
     if (sizeof(T) == 4 && p1 - p0 <= g.list_cap) {
-        // residue-grouped entries: packed window start, D kernel offsets, caller index
+        // level-ordered entries: packed window start, D kernel offsets, caller index
         const int cap = g.list_cap;
         int *l_i0 = reinterpret_cast<int *>(sm_raw + interp_kd_tile_bytes(g, sizeof(T)));
         float *l_x1 = reinterpret_cast<float *>(l_i0 + cap);
         int *l_j = l_i0 + (1 + D) * cap;
-        const int rounds = residue_lists<T, W, D>(
-            sorted, p0, p1, rw[0], rxy, s_cnt, s_start,
-            [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned j) {
+        const int n = residue_lists<T, W, D>(
+            sorted, p0, p1, rw[0], rxy, s_rl,
+            [&](int slot, const int (&i0)[3], const T (&x1)[3], unsigned j) {
                 l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
 #pragma unroll
                 for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
                 l_j[slot] = (int)j;
             });
-        const int lane = threadIdx.x & 31;
-        const int mine = s_cnt[lane], first = s_start[lane];
-        for (int q = threadIdx.x >> 5; q < rounds; q += blockDim.x >> 5) {
-            if (q < mine) {
-                const int h = first + q;
-                const int pk = l_i0[h];
-                const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
-                T x1[3] = {T(0), T(0), T(0)};
+        cp_async_wait_all();
+        __syncthreads();
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const int pk = l_i0[q];
+            const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+            T x1[3] = {T(0), T(0), T(0)};
 #pragma unroll
-                for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + h];
-                interp_window_kd<T, W, D>(ep, i0, x1, (int64_t)l_j[h], sh, rw[0], rxy, dsx, dsy,
-                                          dsz, grad);
-            }
+            for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + q];
+            interp_window_kd<T, W, D>(ep, i0, x1, (int64_t)l_j[q], sh, rw[0], rxy, dsx, dsy,
+                                      dsz, grad);
         }
         return;
     }
+    cp_async_wait_all();
+    __syncthreads();
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
         const int64_t j = load_record<T, D>(sorted, perm, p, u);

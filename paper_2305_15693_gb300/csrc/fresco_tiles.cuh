@@ -314,9 +314,15 @@ constexpr int kFixedMaxPoints = 1 << 14;
 // Bank-residue schedule. A point's window starts at word b = i0_z E_xy + i0_y E_x + i0_x of the
 // extended region, and every step of the window loop adds the same offset to the start of all
 // lanes; so a warp whose 32 points have 32 distinct residues b mod 32 touches 32 distinct
-// shared-memory banks at every step (no bank conflicts). The block counts its points per residue,
-// lists their indices grouped by residue, and lane j of a warp always takes a point of residue j
-// (warp k takes the k-th, (k + n_warps)-th, ... point of every residue).
+// shared-memory banks at every step (no bank conflicts). The block counts its points per residue
+// (cnt[j] points of residue j) and lists them level by level: level q holds the (q+1)-th point
+// of every residue with more than q points, in residue order, and the levels follow each other
+// without gaps. Consecutive runs of 32 list entries then hold 32 distinct residues where they lie
+// inside one level and at most two points of a residue where they span two (the few short levels
+// at the end, where only the most crowded residues are left, conflict more), and every lane of
+// every warp round has a point but in the last round: lanes are not left idle for the residues
+// with fewer points, as a residue-per-lane schedule would (the largest of 32 Poisson counts is
+// ~1.3 times their mean at 50 points a tile, ~1.6 times at 13).
 template <typename T, int W, int D>
 __device__ __forceinline__ int window_of(const typename PT<T>::U (&u)[3], int Ex, int Exy,
                                          int (&i0)[3], T (&x1)[3]) {
@@ -333,17 +339,29 @@ __device__ __forceinline__ int window_of(const typename PT<T>::U (&u)[3], int Ex
     return (i0[2] * Exy + i0[1] * Ex + i0[0]) & 31;
 }
 
-// Groups the block's points [p0, p1) by window residue: cnt[j] points of residue j, placed at
-// slots start[j] ... (start[j] + cnt[j] - 1) by put(slot, p - p0, i0, x1, w3) (w3: the caller
-// index a float record carries, 0 for double records); returns the largest count. Needs
-// P <= list_cap.
+// Levels the schedule tabulates; a tile with a residue of more points (clustered input) lists its
+// points in arrival order instead (correct, with bank conflicts).
+constexpr int kResidueLevels = 256;
+
+// Shared state of the schedule. cnt must be zero (and visible to the block) before the call.
+struct ResidueShared {
+    int cnt[32];
+    int cur[32];
+    unsigned mask[kResidueLevels];   // residues with more than q points
+    int pre[kResidueLevels];         // entries in the levels before q
+    int levels;                      // largest count, or -1 beyond kResidueLevels
+};
+
+// Lists the block's points [p0, p1) in the level order above: put(slot, i0, x1, w3) stores the
+// entry of one point at list position slot (w3: the caller index a float record carries, 0 for
+// double records). Returns the number of entries, P = p1 - p0 (needs P <= list_cap); on return
+// the entries are visible to the block.
 template <typename T, int W, int D, typename Put>
 __device__ __forceinline__ int residue_lists(const typename PT<T>::U *__restrict__ sorted, int p0,
-                                             int p1, int Ex, int Exy, int *cnt, int *start,
+                                             int p1, int Ex, int Exy, ResidueShared &rs,
                                              Put put) {
     using U = typename PT<T>::U;
     constexpr int IL = 4;   // records per thread in flight
-    int *cur = start + 32;
     const int bs = blockDim.x;
     for (int p = p0 + threadIdx.x; p < p1; p += IL * bs) {
         U u[IL][3];
@@ -355,24 +373,43 @@ __device__ __forceinline__ int residue_lists(const typename PT<T>::U *__restrict
             if (p + k * bs >= p1) break;
             int i0[3];
             T x1[3];
-            atomicAdd(&cnt[window_of<T, W, D>(u[k], Ex, Exy, i0, x1)], 1);
+            atomicAdd(&rs.cnt[window_of<T, W, D>(u[k], Ex, Exy, i0, x1)], 1);
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int v = cnt[threadIdx.x];
-        int x = v, m = v;
+    {   // level masks (every warp takes every nw-th level), then their prefix sums (warp 0)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = bs >> 5;
+        const int c = rs.cnt[lane];
+        int m = c;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if ((int)threadIdx.x >= o) x += y;
-            m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int o = 1; o < 32; o <<= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (m <= kResidueLevels) {
+            for (int q = wid; q < m; q += nw) {
+                const unsigned msk = __ballot_sync(0xffffffffu, c > q);
+                if (lane == 0) rs.mask[q] = msk;
+            }
         }
-        start[threadIdx.x] = x - v;
-        cur[threadIdx.x] = x - v;
-        if (threadIdx.x == 0) start[64] = m;
+        if (threadIdx.x < 32) rs.cur[threadIdx.x] = 0;
+        __syncthreads();
+        if (wid == 0 && m <= kResidueLevels) {
+            int run = 0;
+            for (int q0 = 0; q0 < m; q0 += 32) {
+                const int q = q0 + lane;
+                const int v = q < m ? __popc(rs.mask[q]) : 0;
+                int x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (q < m) rs.pre[q] = run + x - v;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        if (threadIdx.x == 0) rs.levels = m <= kResidueLevels ? m : -1;
+        __syncthreads();
     }
-    __syncthreads();
+    const bool leveled = rs.levels >= 0;
     for (int p = p0 + threadIdx.x; p < p1; p += IL * bs) {
         U u[IL][3];
         unsigned w3[IL];
@@ -396,12 +433,19 @@ __device__ __forceinline__ int residue_lists(const typename PT<T>::U *__restrict
             if (p + k * bs >= p1) break;
             int i0[3];
             T x1[3];
-            const int slot = atomicAdd(&cur[window_of<T, W, D>(u[k], Ex, Exy, i0, x1)], 1);
-            put(slot, p + k * bs - p0, i0, x1, w3[k]);
+            const int r = window_of<T, W, D>(u[k], Ex, Exy, i0, x1);
+            int slot;
+            if (leveled) {
+                const int q = atomicAdd(&rs.cur[r], 1);
+                slot = rs.pre[q] + __popc(rs.mask[q] & ((1u << r) - 1u));
+            } else {
+                slot = atomicAdd(&rs.cur[0], 1);
+            }
+            put(slot, i0, x1, w3[k]);
         }
     }
     __syncthreads();
-    return start[64];
+    return p1 - p0;
 }
 
 template <typename T, int W, int D>
@@ -412,10 +456,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     using U = typename PT<T>::U;
     constexpr int HL = W / 2;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ int s_cnt[32], s_start[65];
+    __shared__ ResidueShared s_rl;
     T *ftile = reinterpret_cast<T *>(sm_raw);
     int *itile = reinterpret_cast<int *>(sm_raw);
-    // residue-grouped entries: packed window start (10 bits per axis) and kernel offsets
+    // level-ordered entries: packed window start (10 bits per axis) and kernel offsets
     int *l_i0 = reinterpret_cast<int *>(sm_raw + spread_own_tile_bytes(g, sizeof(T)));
     float *l_x1 = reinterpret_cast<float *>(l_i0 + g.list_cap);
     const int64_t t = blockIdx.x;
@@ -437,32 +481,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
         for (int i = threadIdx.x; i < words / 4; i += blockDim.x) z4[i] = make_uint4(0, 0, 0, 0);
         for (int i = (words & ~3) + threadIdx.x; i < words; i += blockDim.x) itile[i] = 0;
     }
-    if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
     __syncthreads();
     const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
     const bool listed = sizeof(T) == 4 && fixed && P <= g.list_cap;
     if (listed) {
         const int cap = g.list_cap;
-        const int rounds = residue_lists<T, W, D>(
-            sorted, p0, p1, Ex, Exy, s_cnt, s_start,
-            [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned) {
+        const int n = residue_lists<T, W, D>(
+            sorted, p0, p1, Ex, Exy, s_rl,
+            [&](int slot, const int (&i0)[3], const T (&x1)[3], unsigned) {
                 l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
 #pragma unroll
                 for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
             });
-        const int lane = threadIdx.x & 31;
-        const int nw = blockDim.x >> 5;
-        const int mine = s_cnt[lane], first = s_start[lane];
-        for (int q = threadIdx.x >> 5; q < rounds; q += nw) {
-            if (q < mine) {
-                const int h = first + q;
-                const int pk = l_i0[h];
-                const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
-                T x1[3] = {T(0), T(0), T(0)};
+        for (int h = threadIdx.x; h < n; h += blockDim.x) {
+            const int pk = l_i0[h];
+            const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+            T x1[3] = {T(0), T(0), T(0)};
 #pragma unroll
-                for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + h];
-                spread_point_own<T, W, D>(ep, i0, x1, Ex, Exy, ftile, itile, true, fscale);
-            }
+            for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + h];
+            spread_point_own<T, W, D>(ep, i0, x1, Ex, Exy, ftile, itile, true, fscale);
         }
     } else {
         for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -570,7 +608,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
     using U = typename PT<T>::U;
     constexpr int D = 3, HL = W / 2, HR = W - HL;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    __shared__ int s_cnt[32], s_start[65], s_pmax;
+    __shared__ ResidueShared s_rl;
+    __shared__ int s_pmax;
     T *ftile = reinterpret_cast<T *>(sm_raw);
     int *itile = reinterpret_cast<int *>(sm_raw);
     const int cap = g.list_cap;
@@ -620,28 +659,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
         const int64_t t = tile_id(tz);
         const int zk = tile_start(tz, g.tq[2], g.tr[2]);
         const int wz = tile_start(tz + 1, g.tq[2], g.tr[2]) - zk;
-        const int r0 = zk - HL - zbase;            // buffer plane of the region's first plane
+        const int r0 = (zk - HL - zbase) % NP;     // buffer plane of the region's first plane
         const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
-        if (threadIdx.x < 32) s_cnt[threadIdx.x] = 0;
+        if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
         __syncthreads();
         if (fixed && p1 - p0 <= cap) {
-            const int rounds = residue_lists<T, W, D>(
-                sorted, p0, p1, Ex, Sxy, s_cnt, s_start,
-                [&](int slot, int, const int (&i0)[3], const T (&x1)[3], unsigned) {
+            const int n = residue_lists<T, W, D>(
+                sorted, p0, p1, Ex, Sxy, s_rl,
+                [&](int slot, const int (&i0)[3], const T (&x1)[3], unsigned) {
                     l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
 #pragma unroll
                     for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
                 });
-            const int mine = s_cnt[lane], first = s_start[lane];
-            for (int q = threadIdx.x >> 5; q < rounds; q += blockDim.x >> 5) {
-                if (q < mine) {
-                    const int h = first + q;
-                    const int pk = l_i0[h];
-                    const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
-                    const T x1[3] = {(T)l_x1[h], (T)l_x1[cap + h], (T)l_x1[2 * cap + h]};
-                    spread_point_col<T, W>(ep, i0, x1, Ex, Sxy, NP, (r0 + i0[2]) % NP, ftile,
-                                           itile, true, fscale);
-                }
+            for (int h = threadIdx.x; h < n; h += blockDim.x) {
+                const int pk = l_i0[h];
+                const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
+                const T x1[3] = {(T)l_x1[h], (T)l_x1[cap + h], (T)l_x1[2 * cap + h]};
+                int pl = r0 + i0[2];
+                pl -= pl >= NP ? NP : 0;
+                spread_point_col<T, W>(ep, i0, x1, Ex, Sxy, NP, pl, ftile, itile, true, fscale);
             }
         } else {
             for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
@@ -655,13 +691,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
             }
         }
         __syncthreads();
-        // planes no later point of the segment reaches: [zk - HL, zk + wz - HL), or to the end
+        // planes no later point of the segment reaches: [zk - HL, zk + wz - HL), or to the end.
+        // A plane's destinations (its owner tile, ring plane and grid plane) are worked out once
+        // per plane; warps then take its rows and lanes its cells.
         const int pz0 = zk - HL;
         const int pz1 = k + 1 < nz ? zk + wz - HL : zk + wz + HR;
-        const int nrows = (pz1 - pz0) * Ey;
-        for (int row = threadIdx.x >> 5; row < nrows; row += blockDim.x >> 5) {
-            const int pz = pz0 + row / Ey, ey = row % Ey;
-            const int slot = (pz - zbase) % NP;
+        int slot = (pz0 - zbase) % NP;
+        for (int pz = pz0; pz < pz1; ++pz, slot = slot + 1 == NP ? 0 : slot + 1) {
             // the tile whose ring or cells take this plane, and the plane's place in its region
             int owner, ez, wo;
             if (pz < zfirst) {
@@ -679,24 +715,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
                 wo = (owner == tz ? zk + wz : zk) - zo;
             }
             const bool zin = ez >= HL && ez < HL + wo;
-            const bool through = zin && ey >= HL && ey < HL + wy;
-            T *rrow = ring + tile_id(owner) * ring_slot + ring_index<W, D>(0, ey, ez, wx, wy, wo);
-            const int64_t gz = (int64_t)(pz < 0 ? pz + g.nf[2] : (pz >= g.nf[2] ? pz - g.nf[2] : pz));
-            const int64_t gbase = (gz * g.nf[1] + (sy + ey - HL)) * g.nf[0] + sx - HL;
-            const int base = slot * Sxy + ey * Ex;
-            for (int ex = lane; ex < Ex; ex += 32) {
-                T v;
-                if constexpr (sizeof(T) == 4) {
-                    v = fixed ? (float)itile[base + ex] * finv : ftile[base + ex];
-                    itile[base + ex] = 0;
-                } else {
-                    v = ftile[base + ex];
-                    ftile[base + ex] = T(0);
+            T *rplane = ring + tile_id(owner) * ring_slot + ring_index<W, D>(0, 0, ez, wx, wy, wo);
+            const int64_t gz = pz < 0 ? pz + g.nf[2] : (pz >= g.nf[2] ? pz - g.nf[2] : pz);
+            const int64_t gplane = (gz * g.nf[1] + sy - HL) * g.nf[0] + sx - HL;
+            for (int ey = threadIdx.x >> 5; ey < Ey; ey += blockDim.x >> 5) {
+                const bool through = zin && ey >= HL && ey < HL + wy;
+                // rows outside the tile are stored whole, rows through it only their W halo cells
+                T *rrow = !zin || ey < HL ? rplane + ey * Ex
+                          : (ey < HL + wy ? rplane + HL * Ex + (ey - HL) * W
+                                          : rplane + HL * Ex + wy * W + (ey - HL - wy) * Ex);
+                T *grow = grid + gplane + (int64_t)ey * g.nf[0];
+                const int base = slot * Sxy + ey * Ex;
+                for (int ex = lane; ex < Ex; ex += 32) {
+                    T v;
+                    if constexpr (sizeof(T) == 4) {
+                        v = fixed ? (float)itile[base + ex] * finv : ftile[base + ex];
+                        itile[base + ex] = 0;
+                    } else {
+                        v = ftile[base + ex];
+                        ftile[base + ex] = T(0);
+                    }
+                    if (!through) rrow[ex] = v;
+                    else if (ex < HL) rrow[ex] = v;
+                    else if (ex >= HL + wx) rrow[ex - wx] = v;
+                    else grow[ex] = v;
                 }
-                if (!through) rrow[ex] = v;
-                else if (ex < HL) rrow[ex] = v;
-                else if (ex >= HL + wx) rrow[ex - wx] = v;
-                else grid[gbase + ex] = v;
             }
         }
         __syncthreads();
