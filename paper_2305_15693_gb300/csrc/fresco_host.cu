@@ -501,7 +501,7 @@ void release(fresco_plan_s *p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
-    void *bufs[] = {p->d_sorted, p->d_perm, p->d_ring, p->d_cnt, p->d_off,
+    void *bufs[] = {p->d_sorted, p->d_perm, p->d_ring, p->d_cnt, p->d_off, p->d_tcur, p->d_tr,
                     p->d_block_sums, p->d_grid, p->d_tw, p->d_specT, p->d_bt[0], p->d_bt[1],
                     p->d_hc[0], p->d_hc[1], p->d_r[0],
                     p->d_r[1], p->d_g[0], p->d_g[1], p->d_rep_n, p->d_rep_s0, p->d_rep_w,
@@ -607,6 +607,23 @@ fresco_status make_ffts(fresco_plan_s *p) {
     return FRESCO_OK;
 }
 
+// Records per tile of the direct binning form: the expected points of the widest tile (uniform
+// density) plus eight Poisson standard deviations and 32, so that uniform and near-uniform inputs
+// never overflow a tile. 0 (compact form only) where the slots would not be indexable in 32 bits
+// or would take more than four times the points' records.
+int direct_tile_capacity(const Geom &g) {
+    double cells = 1.0, tile = 1.0;
+    for (int a = 0; a < g.dim; ++a) {
+        cells *= (double)g.nf[a];
+        tile *= (double)g.tmax[a];
+    }
+    const double mu = (double)g.n_points / cells * tile;
+    const double cap = std::ceil(mu + 8.0 * std::sqrt(mu) + 32.0);
+    const double slots = cap * (double)g.n_tiles;
+    if (slots >= 2147483647.0 || slots > 4.0 * (double)g.n_points + 1048576.0) return 0;
+    return (int)cap;
+}
+
 template <typename T>
 fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     using C2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
@@ -639,6 +656,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     g.n_points = p->n_points;
     g.width = P.width;
     g.beta = P.beta;
+    g.tcap = direct_tile_capacity(g);
 
     MaskGeom &m = p->mgeom;
     m.dim = dim;
@@ -672,9 +690,13 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     const int64_t rows = (int64_t)P.nf[1] * P.nf[2];
     // sorted records: float plans keep the caller index inside each 16-byte record
     const int pw = sizeof(T) == 4 ? 4 : (dim == 3 ? 4 : 2);
+    // record slots: the compact form's N, or the direct form's tcap per tile if more
+    const int64_t slots = std::max<int64_t>(N, (int64_t)g.tcap * g.n_tiles);
     fresco_status st;
-    if ((st = dalloc(p, &p->d_sorted, sizeof(T) * (size_t)N * pw))) return st;
-    if (sizeof(T) == 8 && (st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)N))) return st;
+    if ((st = dalloc(p, &p->d_sorted, sizeof(T) * (size_t)slots * pw))) return st;
+    if (sizeof(T) == 8 && (st = dalloc(p, &p->d_perm, sizeof(int) * (size_t)slots))) return st;
+    if ((st = dalloc(p, &p->d_tcur, sizeof(int) * (size_t)(g.n_tiles + 1)))) return st;
+    if ((st = dalloc(p, &p->d_tr, sizeof(int2) * (size_t)g.n_tiles))) return st;
     p->ring_slot = Launch<T>::ring_slot(g);
     if ((st = dalloc(p, &p->d_ring, sizeof(T) * (size_t)(g.n_tiles * p->ring_slot)))) return st;
     if ((st = dalloc(p, &p->d_cnt, sizeof(int) * (size_t)g.n_bins))) return st;
@@ -754,9 +776,10 @@ template <>
 const EsPoly<double> &poly_of<double>(const fresco_plan_s *p) { return p->poly64; }
 
 // Host points into the device staging buffer, overlapped with the binning: the copy runs in
-// chunks on a second stream and the plan's stream bins each chunk as soon as it has landed. The
-// ranks within a sub-bin come from atomics in any case and the fixed-point spread does not depend
-// on them, so the result is the same as binning all points at once.
+// chunks on a second stream and the plan's stream bins each chunk as soon as it has landed (the
+// direct form places it, the compact form counts it). The slots within a tile come from atomics
+// in any case and the fixed-point spread does not depend on them, so the result is the same as
+// binning all points at once. The caller zeroes the counts (compact) or cursors (direct).
 template <typename T>
 fresco_status stage_and_bin(fresco_plan_s *p, const T *h_pts, T *d_pts) {
     const Geom &g = p->geom;
@@ -780,7 +803,11 @@ fresco_status stage_and_bin(fresco_plan_s *p, const T *h_pts, T *d_pts) {
         FR_CUDA(cudaStreamWaitEvent(p->stream, p->copy_ev[c], 0));
         Geom gc = g;
         gc.n_points = cnt;
-        FR_CUDA(Launch<T>::count(gc, d_pts + j0 * d, p->d_cnt, p->d_err, p->stream));
+        if (g.tcap)
+            FR_CUDA(Launch<T>::place_direct(gc, d_pts + j0 * d, j0, p->d_tcur, p->d_sorted,
+                                            p->d_perm, p->d_err, p->stream));
+        else
+            FR_CUDA(Launch<T>::count(gc, d_pts + j0 * d, p->d_cnt, p->d_err, p->stream));
         p->launches += 1;
     }
     return FRESCO_OK;
@@ -796,25 +823,39 @@ fresco_status forward_impl(fresco_plan_s *p, const T *pts, double *loss,
     cudaStream_t s = p->stream;
     {
         StageScope sc(p->prof, p->stream, ST_SORT);
+        int nl = 0;
+        // the direct form (one pass), then the compact form: always in a plan without the direct
+        // form, else only if a tile overflowed (its kernels read the overflow word as a guard)
+        const int *guard = nullptr;
+        if (g.tcap) {
+            FR_CUDA(cudaMemsetAsync(p->d_tcur, 0, sizeof(int) * (size_t)(g.n_tiles + 1), s));
+            guard = p->d_tcur + g.n_tiles;
+        }
         FR_CUDA(cudaMemsetAsync(p->d_cnt, 0, sizeof(int) * (size_t)g.n_bins, s));
         if (h_pts) {
             fresco_status st = stage_and_bin<T>(p, h_pts, const_cast<T *>(pts));
             if (st) return st;
-        } else {
-            FR_CUDA(Launch<T>::count(g, pts, p->d_cnt, p->d_err, s));
-            p->launches += 1;
+        } else if (g.tcap) {
+            FR_CUDA(Launch<T>::place_direct(g, pts, 0, p->d_tcur, p->d_sorted, p->d_perm, p->d_err,
+                                            s));
+            nl += 1;
         }
-        int nl = 0;
+        if (!h_pts || g.tcap) {
+            FR_CUDA(Launch<T>::count(g, pts, p->d_cnt, p->d_err, s, guard));
+            nl += 1;
+        }
         // the counts become the placement cursors (a copy of the tile offsets)
-        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl, p->d_cnt));
-        FR_CUDA(Launch<T>::place(g, pts, p->d_cnt, p->d_sorted, p->d_perm, s));
-        nl += 1;
+        FR_CUDA(Launch<T>::scan(p->d_cnt, p->d_off, p->d_block_sums, g.n_bins, s, &nl, p->d_cnt,
+                                guard));
+        FR_CUDA(Launch<T>::place(g, pts, p->d_cnt, p->d_sorted, p->d_perm, s, guard));
+        FR_CUDA(Launch<T>::tile_ranges(g, g.tcap ? p->d_tcur : nullptr, p->d_off, p->d_tr, s));
+        nl += 2;
         p->launches += nl;
     }
     {
         StageScope sc(p->prof, p->stream, ST_SPREAD);
         int nl = 0;
-        FR_CUDA(Launch<T>::spread_own(g, poly_of<T>(p), p->d_sorted, p->d_off, (T *)p->d_grid,
+        FR_CUDA(Launch<T>::spread_own(g, poly_of<T>(p), p->d_sorted, p->d_tr, (T *)p->d_grid,
                                       (T *)p->d_ring, p->ring_slot, s, &nl));
         p->launches += nl;
     }
@@ -879,7 +920,7 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
                                       (cufftDoubleComplex *)p->d_r[0], CUFFT_INVERSE));
         }
         StageScope sc(p->prof, p->stream, ST_INTERP);
-        FR_CUDA(Launch<T>::interp_kd(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off,
+        FR_CUDA(Launch<T>::interp_kd(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_tr,
                                      (const T *)p->d_r[0], grad_out, p->dscale, grad, s));
         p->launches += 1;
         return FRESCO_OK;
@@ -905,7 +946,7 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
     }
     {
         StageScope sc(p->prof, p->stream, ST_INTERP);
-        FR_CUDA(Launch<T>::interp(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_off, p->d_g[0],
+        FR_CUDA(Launch<T>::interp(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_tr, p->d_g[0],
                                   p->d_g[1], grad_out, grad, s));
         p->launches += 1;
     }
@@ -1013,6 +1054,7 @@ fresco_status fresco::point_side_build(PointSide &ps, int dim, const int nf[3], 
               (es == 4 || ps_alloc(ps, (void **)&ps.perm, sizeof(int) * (size_t)n_points)) &&
               ps_alloc(ps, (void **)&ps.cnt, sizeof(int) * (size_t)g.n_bins) &&
               ps_alloc(ps, (void **)&ps.off, sizeof(int) * (size_t)(g.n_bins + 1)) &&
+              ps_alloc(ps, (void **)&ps.tr, sizeof(int2) * (size_t)g.n_tiles) &&
               ps_alloc(ps, (void **)&ps.bsum, sizeof(int) * (size_t)((g.n_bins + 1023) / 1024 + 1)) &&
               ps_alloc(ps, (void **)&ps.err, sizeof(int)) &&
               ps_alloc(ps, &ps.grid, es * (size_t)cells) &&
@@ -1034,10 +1076,11 @@ fresco_status fresco::point_side_spread(PointSide &ps, const T *pts, cudaStream_
     int nl = 1;
     FR_CUDA(Launch<T>::scan(ps.cnt, ps.off, ps.bsum, g.n_bins, s, &nl, ps.cnt));
     FR_CUDA(Launch<T>::place(g, pts, ps.cnt, ps.sorted, ps.perm, s));
-    nl += 1;
+    FR_CUDA(Launch<T>::tile_ranges(g, nullptr, ps.off, ps.tr, s));
+    nl += 2;
     const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(sizeof(T) == 4 ? (const void *)&ps.p32
                                                                               : (const void *)&ps.p64);
-    FR_CUDA(Launch<T>::spread_own(g, ep, ps.sorted, ps.off, (T *)ps.grid, (T *)ps.ring,
+    FR_CUDA(Launch<T>::spread_own(g, ep, ps.sorted, ps.tr, (T *)ps.grid, (T *)ps.ring,
                                   ps.ring_slot, s, &nl));
     if (launches) *launches += nl;
     return FRESCO_OK;

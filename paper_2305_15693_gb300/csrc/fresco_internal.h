@@ -16,6 +16,7 @@ constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
 constexpr int kTileCursors = 4;   // placement cursors per tile of a single plan (Geom.sub)
 constexpr int kZSegment = 6;      // 3D single plans: tiles per z-column segment (Geom.zseg)
+constexpr int kDirectPointsPerThread = 8;   // points in flight per thread of k_place_direct
 // fresco_loss_grad_host copies the points in up to kHostChunks pieces of at least
 // kHostChunkBytes, binning each piece while the next one is in flight
 constexpr int kHostChunks = 8;
@@ -42,6 +43,8 @@ struct Geom {
     int zseg;           // 3D single plans: tiles per z-column segment of the column spread (0:
                         // tiles spread one by one)
     int64_t n_bins;     // n_tiles * sub: the sort key space
+    int tcap;           // single plans: records per tile of the direct binning form (0: the plan
+                        // bins in the compact form only)
     int64_t n_points;
     int width;          // ES kernel width w
     double beta;        // ES kernel shape
@@ -162,15 +165,27 @@ template <typename T>
 struct Launch {
     // exclusive prefix sum of cnt into off[0..n] (off[n] = total); when cur is not null it
     // receives a copy of off[0..n) (the placement cursors of k_place)
+    // (with a guard, not null: the passes do nothing unless *guard != 0)
     static cudaError_t scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
-                            int *launches, int *cur = nullptr);
-    // single plans (tiles without border sub-bins): points per tile, then placement by cursor
-    static cudaError_t count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s);
+                            int *launches, int *cur = nullptr, const int *guard = nullptr);
+    // single plans (tiles without border sub-bins), compact form: points per bin, then placement
+    // by cursor (guard as for scan)
+    static cudaError_t count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s,
+                             const int *guard = nullptr);
     static cudaError_t place(const Geom &g, const T *points, int *cur, void *sorted, int *perm,
-                             cudaStream_t s);
+                             cudaStream_t s, const int *guard = nullptr);
+    // direct form: g.n_points points starting at caller index j0 (points points at that point)
+    // into tile slots of capacity g.tcap; tcur [n_tiles + 1] zero before the first chunk, its
+    // last entry the overflow word
+    static cudaError_t place_direct(const Geom &g, const T *points, int64_t j0, int *tcur,
+                                    void *sorted, int *perm, int *err, cudaStream_t s);
+    // tr[t] = record range of tile t from the direct form (tcur) unless it overflowed or tcur is
+    // null, else from the compact offsets off
+    static cudaError_t tile_ranges(const Geom &g, const int *tcur, const int *off, int2 *tr,
+                                   cudaStream_t s);
     // own-points spread into the grid plus per-tile rings, then the ring sums into the grid
     static cudaError_t spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  const int2 *tr, T *grid, T *ring, int64_t ring_slot,
                                   cudaStream_t s, int *launches);
     static int spread_own_smem(const Geom &g);
     static int64_t ring_slot(const Geom &g);
@@ -181,11 +196,11 @@ struct Launch {
     static cudaError_t finalize(const double *partial, int n_blocks, double loss_const,
                                 double *loss, cudaStream_t s);
     static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const int *perm, const int2 *tr, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s);
     // kernel-derivative mode: h is the real field, dscale[a] = -2 n_f[a] / L[a]
     static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                 const int *perm, const int *off, const T *h,
+                                 const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
                                  cudaStream_t s);
     static int interp_kd_smem(const Geom &g);
@@ -244,6 +259,7 @@ struct PointSide {
     int precision = FRESCO_F32;
     void *sorted = nullptr;
     int *perm = nullptr, *cnt = nullptr, *off = nullptr, *bsum = nullptr, *err = nullptr;
+    int2 *tr = nullptr;   // record range of every tile (compact binning only: Geom.tcap = 0)
     void *grid = nullptr, *ring = nullptr;
     int64_t ring_slot = 0;
     int64_t device_bytes = 0;
@@ -318,8 +334,10 @@ struct fresco_plan_s {
     int *d_perm = nullptr;           // double plans: sorted position -> caller index
     void *d_ring = nullptr;          // [n_tiles][ring_slot] spread rings (own-points spread)
     int64_t ring_slot = 0;
-    int *d_cnt = nullptr;            // [n_bins] points per tile, then the placement cursors
+    int *d_cnt = nullptr;            // [n_bins] points per bin, then the placement cursors
     int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of the counts
+    int *d_tcur = nullptr;           // [n_tiles + 1] direct-form cursors, then the overflow word
+    int2 *d_tr = nullptr;            // [n_tiles] record range of every tile
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
     void *d_tw = nullptr;            // exp(-2 pi i k / nf0), k = 0..nf0/4 (real-row split/merge)

@@ -228,10 +228,13 @@ __device__ __forceinline__ int strip_part(int rel, int wd, int w, int strips) {
     return 1;
 }
 
-// K1b: exclusive prefix sum of the tile counts, in three passes over blocks of 1024.
+// K1b: exclusive prefix sum of the tile counts, in three passes over blocks of 1024. With a guard
+// (not null) the passes do nothing unless *guard != 0.
 static __global__ void __launch_bounds__(1024) k_scan_blocks(const int *__restrict__ cnt,
                                                       int *__restrict__ off,
-                                                      int *__restrict__ bsum, int64_t n) {
+                                                      int *__restrict__ bsum, int64_t n,
+                                                      const int *__restrict__ guard) {
+    if (guard && !*guard) return;
     __shared__ int warp_tot[32];
     int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
     int v = (i < n) ? cnt[i] : 0;
@@ -260,7 +263,9 @@ static __global__ void __launch_bounds__(1024) k_scan_blocks(const int *__restri
 }
 
 static __global__ void __launch_bounds__(1024) k_scan_sums(int *__restrict__ bsum, int64_t nb,
-                                                    int *__restrict__ off_end) {
+                                                    int *__restrict__ off_end,
+                                                    const int *__restrict__ guard) {
+    if (guard && !*guard) return;
     __shared__ int warp_tot[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -298,7 +303,9 @@ static __global__ void __launch_bounds__(1024) k_scan_sums(int *__restrict__ bsu
 
 static __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ off,
                                                    const int *__restrict__ bsum, int64_t n,
-                                                   int *__restrict__ cur) {
+                                                   int *__restrict__ cur,
+                                                   const int *__restrict__ guard) {
+    if (guard && !*guard) return;
     int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
     if (i < n) {
         const int v = off[i] + bsum[blockIdx.x];
@@ -924,8 +931,8 @@ static __global__ void __launch_bounds__(512) k_finalize(const double *__restric
 template <typename T, int W, int D>
 __device__ __forceinline__ void interp_tile(const Geom &g, const EsPoly<T> &ep,
                                             const typename PT<T>::U *__restrict__ sorted,
-                                            const int *__restrict__ perm,
-                                            const int *__restrict__ off,
+                                            const int *__restrict__ perm, const int p0,
+                                            const int p1,
                                             const typename PT<T>::C *__restrict__ g0,
                                             const typename PT<T>::C *__restrict__ g1,
                                             const double *__restrict__ grad_out,
@@ -973,7 +980,6 @@ __device__ __forceinline__ void interp_tile(const Geom &g, const EsPoly<T> &ep,
     __syncthreads();
 
     const T scale = grad_out ? (T)(*grad_out) : T(1);
-    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
         const int64_t j = load_record<T, D>(sorted, perm, p, u);
@@ -1046,12 +1052,13 @@ template <typename T, int W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 6 : 2) k_interp(Geom g, EsPoly<T> ep,
                                                 const typename PT<T>::U *__restrict__ sorted,
                                                 const int *__restrict__ perm,
-                                                const int *__restrict__ off,
+                                                const int2 *__restrict__ tr,
                                                 const typename PT<T>::C *__restrict__ g0,
                                                 const typename PT<T>::C *__restrict__ g1,
                                                 const double *__restrict__ grad_out,
                                                 T *__restrict__ grad) {
-    interp_tile<T, W, D>(g, ep, sorted, perm, off, g0, g1, grad_out, grad, blockIdx.x);
+    const int2 r = tr[blockIdx.x];
+    interp_tile<T, W, D>(g, ep, sorted, perm, r.x, r.y, g0, g1, grad_out, grad, blockIdx.x);
 }
 
 // Batched interpolation: a persistent grid walks the tiles of every instance.
@@ -1065,8 +1072,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 8 : 2) k_interp_b(
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int i = find_segment(tile_first, n_inst, t);
         const BInst &I = inst[i];
-        interp_tile<T, W, D>(I.g, ep, sorted, perm, off + I.bo, g0 + I.ro,
-                             D == 3 ? g1 + I.ro : g1, grad_out, grad, t - tile_first[i]);
+        const int64_t lt = t - tile_first[i];
+        const int *o = off + I.bo;
+        interp_tile<T, W, D>(I.g, ep, sorted, perm, o[lt * I.g.sub], o[(lt + 1) * I.g.sub],
+                             g0 + I.ro, D == 3 ? g1 + I.ro : g1, grad_out, grad, lt);
         __syncthreads();
     }
 }
@@ -1211,10 +1220,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 template <typename T, int W, int D>
 __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &ep,
                                                const typename PT<T>::U *__restrict__ sorted,
-                                               const int *__restrict__ perm,
-                                               const int *__restrict__ off,
-                                               const T *__restrict__ h, T dsx, T dsy, T dsz,
-                                               T *__restrict__ grad, const int64_t t) {
+                                               const int *__restrict__ perm, const int p0,
+                                               const int p1, const T *__restrict__ h, T dsx,
+                                               T dsy, T dsz, T *__restrict__ grad,
+                                               const int64_t t) {
     using U = typename PT<T>::U;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ ResidueShared s_rl;
@@ -1263,7 +1272,6 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
         }
     }
     __syncthreads();
-    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
     if (sizeof(T) == 4 && p1 - p0 <= g.list_cap) {
         // level-ordered entries: packed window start, D kernel offsets, caller index
         const int cap = g.list_cap;
@@ -1305,10 +1313,11 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
 template <typename T, int W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (D == 3 ? 2 : 3) : 2) k_interp_kd(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
-    const int *__restrict__ perm, const int *__restrict__ off, const T *__restrict__ h,
+    const int *__restrict__ perm, const int2 *__restrict__ tr, const T *__restrict__ h,
     const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad) {
     const T sc = grad_out ? (T)(*grad_out) : T(1);
-    interp_tile_kd<T, W, D>(g, ep, sorted, perm, off, h, sc * dsx, sc * dsy, sc * dsz, grad,
+    const int2 r = tr[blockIdx.x];
+    interp_tile_kd<T, W, D>(g, ep, sorted, perm, r.x, r.y, h, sc * dsx, sc * dsy, sc * dsz, grad,
                             blockIdx.x);
 }
 
@@ -1325,7 +1334,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_interp_kd_b(
         const int i = find_segment(tile_first, n_inst, t);
         const BInst &I = inst[i];
         const Geom &g = I.g;
-        interp_tile_kd<T, W, D>(g, ep, sorted, perm, off + I.bo, h + I.go,
+        const int64_t lt = t - tile_first[i];
+        const int *o = off + I.bo;
+        interp_tile_kd<T, W, D>(g, ep, sorted, perm, o[lt * g.sub], o[(lt + 1) * g.sub], h + I.go,
                                 (T)(-2.0 * (g.s_hi[0] + g.s_lo[0]) * sc),
                                 (T)(-2.0 * (g.s_hi[1] + g.s_lo[1]) * sc),
                                 (T)(-2.0 * (g.s_hi[2] + g.s_lo[2]) * sc), grad,
@@ -1561,13 +1572,13 @@ __global__ void __launch_bounds__(256) k_rfft_merge_rows(const C *__restrict__ x
 template <typename T, int W, int D>
 struct WOps {
     static cudaError_t spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  const int2 *tr, T *grid, T *ring, int64_t ring_slot,
                                   cudaStream_t s);
     static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const int *perm, const int2 *tr, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s);
     static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                 const int *perm, const int *off, const T *h,
+                                 const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
                                  cudaStream_t s);
 };
@@ -1607,30 +1618,51 @@ inline int grid_for(int64_t n, int threads, int cap) {
 
 template <typename T>
 cudaError_t Launch<T>::scan(const int *cnt, int *off, int *block_sums, int64_t n, cudaStream_t s,
-                            int *launches, int *cur) {
+                            int *launches, int *cur, const int *guard) {
     const int64_t nb = (n + 1023) / 1024;
-    k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(cnt, off, block_sums, n);
-    k_scan_sums<<<1, 1024, 0, s>>>(block_sums, nb, off + n);
-    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(off, block_sums, n, cur);
+    k_scan_blocks<<<(unsigned)nb, 1024, 0, s>>>(cnt, off, block_sums, n, guard);
+    k_scan_sums<<<1, 1024, 0, s>>>(block_sums, nb, off + n, guard);
+    k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(off, block_sums, n, cur, guard);
     *launches += 3;
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Launch<T>::count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s) {
+cudaError_t Launch<T>::count(const Geom &g, const T *points, int *cnt, int *err, cudaStream_t s,
+                             const int *guard) {
     const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
-    if (g.dim == 2) k_count<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, err);
-    else k_count<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, err);
+    if (g.dim == 2) k_count<T, 2><<<grid, 256, 0, s>>>(g, points, cnt, err, guard);
+    else k_count<T, 3><<<grid, 256, 0, s>>>(g, points, cnt, err, guard);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t Launch<T>::place(const Geom &g, const T *points, int *cur, void *sorted, int *perm,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int *guard) {
     using U = typename PT<T>::U;
     const int grid = grid_for((g.n_points + 3) / 4, 256, 152 * 16);
-    if (g.dim == 2) k_place<T, 2><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm);
-    else k_place<T, 3><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm);
+    if (g.dim == 2) k_place<T, 2><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm, guard);
+    else k_place<T, 3><<<grid, 256, 0, s>>>(g, points, cur, (U *)sorted, perm, guard);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::place_direct(const Geom &g, const T *points, int64_t j0, int *tcur,
+                                    void *sorted, int *perm, int *err, cudaStream_t s) {
+    using U = typename PT<T>::U;
+    constexpr int IL = kDirectPointsPerThread;
+    const int grid = grid_for((g.n_points + IL - 1) / IL, 256, 152 * 16);
+    if (g.dim == 2)
+        k_place_direct<T, 2><<<grid, 256, 0, s>>>(g, points, j0, tcur, (U *)sorted, perm, err);
+    else
+        k_place_direct<T, 3><<<grid, 256, 0, s>>>(g, points, j0, tcur, (U *)sorted, perm, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::tile_ranges(const Geom &g, const int *tcur, const int *off, int2 *tr,
+                                   cudaStream_t s) {
+    k_tile_ranges<<<grid_for(g.n_tiles, 256, 152 * 16), 256, 0, s>>>(g, tcur, off, tr);
     return cudaGetLastError();
 }
 
@@ -1657,7 +1689,7 @@ int64_t Launch<T>::ring_slot(const Geom &g) {
 
 template <typename T, int W, int D>
 cudaError_t WOps<T, W, D>::spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                      const int *off, T *grid, T *ring, int64_t ring_slot,
+                                      const int2 *tr, T *grid, T *ring, int64_t ring_slot,
                                       cudaStream_t s) {
     using U = typename PT<T>::U;
     const int smem = Launch<T>::spread_own_smem(g);
@@ -1670,7 +1702,7 @@ cudaError_t WOps<T, W, D>::spread_own(const Geom &g, const EsPoly<T> &ep, const 
         if (e != cudaSuccess) return e;
         const unsigned nseg = (unsigned)((g.nb[2] + g.zseg - 1) / g.zseg);
         kern<<<(unsigned)(g.nb[0] * g.nb[1]) * nseg, 256, smem, s>>>(g, ep, (const U *)sorted,
-                                                                     off, grid, ring, ring_slot);
+                                                                     tr, grid, ring, ring_slot);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (g.tq[2] >= W) {
@@ -1696,7 +1728,7 @@ cudaError_t WOps<T, W, D>::spread_own(const Geom &g, const EsPoly<T> &ep, const 
     auto kern = k_spread_own<T, W, D>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<nt, 256, smem, s>>>(g, ep, (const U *)sorted, off, grid, ring, ring_slot);
+    kern<<<nt, 256, smem, s>>>(g, ep, (const U *)sorted, tr, grid, ring, ring_slot);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one launch per axis when every tile along it is at least W wide, else two (low, high)
@@ -1781,7 +1813,7 @@ int Launch<T>::interp_smem(const Geom &g) {
 
 template <typename T, int W, int D>
 cudaError_t WOps<T, W, D>::interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                  const int *perm, const int *off, const void *g0, const void *g1,
+                                  const int *perm, const int2 *tr, const void *g0, const void *g1,
                                   const double *grad_out, T *grad, cudaStream_t s) {
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
@@ -1789,14 +1821,14 @@ cudaError_t WOps<T, W, D>::interp(const Geom &g, const EsPoly<T> &ep, const void
     auto kern = k_interp<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, off,
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, tr,
                                                 (const C *)g0, (const C *)g1, grad_out, grad);
     return cudaGetLastError();
 }
 
 template <typename T, int W, int D>
 cudaError_t WOps<T, W, D>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                     const int *perm, const int *off, const T *h,
+                                     const int *perm, const int2 *tr, const T *h,
                                      const double *grad_out, const double dscale[3], T *grad,
                                      cudaStream_t s) {
     using U = typename PT<T>::U;
@@ -1804,7 +1836,7 @@ cudaError_t WOps<T, W, D>::interp_kd(const Geom &g, const EsPoly<T> &ep, const v
     auto kern = k_interp_kd<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, off, h, grad_out,
+    kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, tr, h, grad_out,
                                                 (T)dscale[0], (T)dscale[1], (T)dscale[2], grad);
     return cudaGetLastError();
 }
@@ -1831,43 +1863,43 @@ cudaError_t WOps<T, W, D>::interp_kd(const Geom &g, const EsPoly<T> &ep, const v
 
 template <typename T>
 cudaError_t Launch<T>::spread_own(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                  const int *off, T *grid, T *ring, int64_t ring_slot,
+                                  const int2 *tr, T *grid, T *ring, int64_t ring_slot,
                                   cudaStream_t s, int *launches) {
     *launches += 1;   // (the column spread's folds: the same count, z first)
     for (int a = 0; a < g.dim; ++a) *launches += g.tq[a] >= g.width ? 1 : 2;
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::spread_own(g, ep, sorted, off, grid,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::spread_own(g, ep, sorted, tr, grid,
                                                                           ring, ring_slot, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::spread_own(g, ep, sorted, off, grid,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::spread_own(g, ep, sorted, tr, grid,
                                                                           ring, ring_slot, s)));
     }
 }
 
 template <typename T>
 cudaError_t Launch<T>::interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                              const int *perm, const int *off, const void *g0, const void *g1,
+                              const int *perm, const int2 *tr, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s) {
     if (g.dim == 2) {
-        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp(g, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp(g, ep, sorted, perm, tr,
                                                                       g0, g1, grad_out, grad, s)));
     } else {
-        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp(g, ep, sorted, perm, off,
+        FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp(g, ep, sorted, perm, tr,
                                                                       g0, g1, grad_out, grad, s)));
     }
 }
 
 template <typename T>
 cudaError_t Launch<T>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
-                                 const int *perm, const int *off, const T *h,
+                                 const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
                                  cudaStream_t s) {
     if (g.dim == 2) {
         FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp_kd(
-                                         g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
+                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s)));
     } else {
         FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp_kd(
-                                         g, ep, sorted, perm, off, h, grad_out, dscale, grad, s)));
+                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s)));
     }
 }
 

@@ -145,6 +145,7 @@ struct fresco_lbfgs_s {
     size_t es = 4;
     cudaStream_t stream = nullptr;
     int *order = nullptr;   // tile_order: solver position i holds caller point order[i]
+    int *tpre = nullptr;    // tile_order: first solver position of every tile's points
     void *xs = nullptr;     // tile_order: the points in solver order
     bool have_order = false;
     void *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
@@ -188,15 +189,61 @@ struct Ops {
     }
 };
 
-// order[i] = caller index of the i-th point in tile order: the caller index that a float record
-// carries, or the double plans' separate permutation
+// Solver positions of the tiles: pre[t] = points of tiles 0 .. t-1 (the tiles' record ranges tr
+// may have gaps between them), one block scanning the counts 1024 tiles at a time.
+__global__ void __launch_bounds__(1024) k_tile_prefix(const int2 *__restrict__ tr, int64_t n_tiles,
+                                                      int *__restrict__ pre) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < n_tiles; base += 1024) {
+        const int64_t t = base + threadIdx.x;
+        const int v = t < n_tiles ? tr[t].y - tr[t].x : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;
+        }
+        __syncthreads();
+        const int incl = x + (wid > 0 ? warp_tot[wid - 1] : 0);
+        if (t < n_tiles) pre[t] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+}
+
+// order[pre[t] + k] = caller index of the k-th record of tile t (the index a float record
+// carries, or the double plans' separate permutation); one warp per tile
 template <typename T>
 __global__ void __launch_bounds__(256) k_order_from_plan(const void *__restrict__ sorted,
-                                                         const int *__restrict__ perm, int64_t n,
-                                                         int *__restrict__ order) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        order[i] = sizeof(T) == 4 ? (int)reinterpret_cast<const uint4 *>(sorted)[i].w : perm[i];
+                                                         const int *__restrict__ perm,
+                                                         const int2 *__restrict__ tr,
+                                                         const int *__restrict__ pre,
+                                                         int64_t n_tiles, int *__restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_tiles;
+         t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int2 r = tr[t];
+        const int o = pre[t] - r.x;
+        for (int i = r.x + lane; i < r.y; i += 32)
+            order[o + i] = sizeof(T) == 4 ? (int)reinterpret_cast<const uint4 *>(sorted)[i].w
+                                          : perm[i];
+    }
 }
 
 // to_solver: y[i] = x[order[i]]; else x[order[i]] = y[i] (points of dim coordinates)
@@ -248,8 +295,10 @@ fresco_status run_impl(fresco_lbfgs_s *s, void *x_caller, int64_t max_iter,
     if (s->opts.tile_order && !s->have_order) {
         // evaluate in caller order once; its tile order becomes the solver's order
         if ((st = evaluate(s, x_caller, s->loss_x, s->gt))) return st;
-        k_order_from_plan<T><<<pb, 256, 0, s->stream>>>(s->plan->d_sorted, s->plan->d_perm, np,
-                                                         s->order);
+        const int64_t nt = s->plan->geom.n_tiles;
+        k_tile_prefix<<<1, 1024, 0, s->stream>>>(s->plan->d_tr, nt, s->tpre);
+        k_order_from_plan<T><<<pb, 256, 0, s->stream>>>(s->plan->d_sorted, s->plan->d_perm,
+                                                         s->plan->d_tr, s->tpre, nt, s->order);
         k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)x_caller, (T *)s->xs, 1);
         k_permute<T><<<pb, 256, 0, s->stream>>>(s->order, np, dim, (T *)s->gt, (T *)s->g, 1);
         s->have_order = true;
@@ -360,7 +409,7 @@ void lbfgs_free(fresco_lbfgs_s *s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     void *bufs[] = {s->g, s->d, s->xt, s->gt, s->scal, s->part, s->loss_x, s->loss_t,
-                    s->order, s->xs};
+                    s->order, s->tpre, s->xs};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (void *b : s->S)
@@ -429,7 +478,8 @@ fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
     s->Y.assign(o.history, nullptr);
     for (int i = 0; ok && i < o.history; ++i) ok = alloc(&s->S[i], vb) && alloc(&s->Y[i], vb);
     if (ok && o.tile_order)
-        ok = alloc((void **)&s->order, sizeof(int) * (size_t)info.n_points) && alloc(&s->xs, vb);
+        ok = alloc((void **)&s->order, sizeof(int) * (size_t)info.n_points) && alloc(&s->xs, vb) &&
+             alloc((void **)&s->tpre, sizeof(int) * (size_t)plan->geom.n_tiles);
     if (!ok) {
         lbfgs_free(s);
         return FRESCO_ERR_OOM;

@@ -1,13 +1,22 @@
 // Single-plan binning and type-1 spreading over tiles without border sub-bins.
 //
-// Binning (K1) in two passes over the caller's points, with no per-point key or rank arrays:
+// Binning (K1). A plan whose tiles can hold their expected points plus a wide margin in a fixed
+// capacity Geom.tcap per tile places every point in one pass over the caller's points:
+//   k_place_direct  computes each point's tile and record and takes its slot from the tile's
+//                   cursor, pos = atomicAdd(&tcur[t], 1), at record t * tcap + pos;
+// the tile's points are then records [t tcap, t tcap + tcur[t]). A point whose tile is full sets
+// the overflow word tcur[n_tiles]; the compact form below then runs (its kernels do nothing
+// unless the overflow word is set), so any input is binned correctly and uniform inputs pay for
+// one pass only. The compact form, two passes with no per-point key or rank arrays:
 //   k_count  counts the points of every bin (global atomics whose result is unused);
 //   (exclusive scan of the counts into off[], and a copy of off[] into the cursor array cur[])
 //   k_place  recomputes each point's bin and record and takes its sorted position from the
 //            bin's cursor, pos = atomicAdd(&cur[bin], 1).
-// A tile owns Geom.sub consecutive bins, bin = tile * sub + (caller index mod sub): the points of
-// a tile stay contiguous (off[t sub] .. off[(t + 1) sub]), and each cursor takes 1/sub of the
-// tile's atomics, which keeps the returning atomics from queueing on few addresses.
+// In the compact form a tile owns Geom.sub consecutive bins, bin = tile * sub + (caller index mod
+// sub): the points of a tile stay contiguous (off[t sub] .. off[(t + 1) sub]), and each cursor
+// takes 1/sub of the tile's atomics, which keeps the returning atomics from queueing on few
+// addresses. k_tile_ranges writes the record range of every tile, tr[t] = (first, end), from
+// whichever form ran; the spread and interpolation kernels read only tr.
 // The order of the points inside a tile depends on the order the atomics run in. Nothing
 // downstream depends on it: the fixed-point spread sums integers (order independent), the
 // interpolation writes each point's gradient through its caller index.
@@ -87,9 +96,12 @@ __device__ __forceinline__ bool warp_has_runs(int bin, bool in) {
     return __any_sync(0xffffffffu, in && (threadIdx.x & 31) > 0 && prev == bin);
 }
 
+// guard (k_count, k_place): when not null, the kernel does nothing unless *guard != 0
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_count(Geom g, const T *__restrict__ pts,
-                                               int *__restrict__ cnt, int *__restrict__ err) {
+                                               int *__restrict__ cnt, int *__restrict__ err,
+                                               const int *__restrict__ guard) {
+    if (guard && !*guard) return;
     constexpr int IL = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
     bool ok = true;
@@ -129,7 +141,9 @@ template <typename T, int D>
 __global__ void __launch_bounds__(256) k_place(Geom g, const T *__restrict__ pts,
                                                int *__restrict__ cur,
                                                typename PT<T>::U *__restrict__ sorted,
-                                               int *__restrict__ perm) {
+                                               int *__restrict__ perm,
+                                               const int *__restrict__ guard) {
+    if (guard && !*guard) return;
     using U = typename PT<T>::U;
     constexpr int IL = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
@@ -173,6 +187,87 @@ __global__ void __launch_bounds__(256) k_place(Geom g, const T *__restrict__ pts
         for (int k = 0; k < IL; ++k) {
             const int64_t j = j0 + (int64_t)k * blockDim.x;
             if (j < g.n_points) store_record<T, D>(sorted, perm, pos[k], u[k], (int)j);
+        }
+    }
+}
+
+// One pass of the direct form: points j0 .. j0 + g.n_points - 1 of the caller's array (pts points
+// at point j0), each to its tile's next slot. tcur[n_tiles] is the overflow word.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_place_direct(Geom g, const T *__restrict__ pts,
+                                                      int64_t j0, int *__restrict__ tcur,
+                                                      typename PT<T>::U *__restrict__ sorted,
+                                                      int *__restrict__ perm,
+                                                      int *__restrict__ err) {
+    using U = typename PT<T>::U;
+    constexpr int IL = kDirectPointsPerThread;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * IL;
+    const int cap = g.tcap;
+    bool ok = true, over = false;
+    // the loop runs warp-uniformly (whole warps take part in the warp-level matching below)
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x * IL + (threadIdx.x & ~31u);
+         w0 < g.n_points; w0 += stride) {
+        const int64_t jl = w0 + (threadIdx.x & 31);
+        T r[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = jl + (int64_t)k * blockDim.x;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                r[k][a] = (a < D && j < g.n_points) ? pts[j * D + a] : T(0);
+        }
+        int pos[IL], tile[IL];
+        U u[IL][3];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = jl + (int64_t)k * blockDim.x;
+            int rel[3] = {0, 0, 0};
+            T frac[3] = {T(0), T(0), T(0)};
+            const int t = tile_cell<T, D>(g, r[k], rel, frac, ok);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) u[k][a] = a < D ? pack_coord<T>(rel[a], frac[a]) : U(0);
+            const bool in = j < g.n_points;
+            tile[k] = in ? t : -1;
+            if (warp_has_runs(tile[k], in)) {
+                // one cursor atomic per tile and warp; lanes take consecutive slots in lane order
+                const unsigned grp = __match_any_sync(0xffffffffu, tile[k]);
+                const int lane = threadIdx.x & 31, leader = __ffs(grp) - 1;
+                int base = 0;
+                if (in && lane == leader) base = atomicAdd(&tcur[t], __popc(grp));
+                base = __shfl_sync(grp, base, leader);
+                pos[k] = base + __popc(grp & ((1u << lane) - 1u));
+            } else {
+                pos[k] = in ? atomicAdd(&tcur[t], 1) : 0;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IL; ++k) {
+            const int64_t j = jl + (int64_t)k * blockDim.x;
+            if (j >= g.n_points) continue;
+            if (pos[k] < cap)
+                store_record<T, D>(sorted, perm, (int64_t)tile[k] * cap + pos[k], u[k],
+                                   (int)(j0 + j));
+            else
+                over = true;
+        }
+    }
+    if (!ok) atomicOr(err, 1);
+    if (over) atomicOr(&tcur[g.n_tiles], 1);
+}
+
+// Record range of every tile: the direct form's (t tcap, t tcap + tcur[t]) unless its overflow
+// word is set (or the plan has no direct form, tcur null), else the compact form's offsets.
+static __global__ void __launch_bounds__(256) k_tile_ranges(Geom g, const int *__restrict__ tcur,
+                                                            const int *__restrict__ off,
+                                                            int2 *__restrict__ tr) {
+    const bool direct = tcur && !tcur[g.n_tiles];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.n_tiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (direct) {
+            const int b = (int)(t * g.tcap);
+            tr[t] = make_int2(b, b + tcur[t]);
+        } else {
+            tr[t] = make_int2(off[t * g.sub], off[(t + 1) * g.sub]);
         }
     }
 }
@@ -451,7 +546,7 @@ __device__ __forceinline__ int residue_lists(const typename PT<T>::U *__restrict
 template <typename T, int W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
-    const int *__restrict__ off, T *__restrict__ grid, T *__restrict__ ring,
+    const int2 *__restrict__ tr, T *__restrict__ grid, T *__restrict__ ring,
     int64_t ring_slot) {
     using U = typename PT<T>::U;
     constexpr int HL = W / 2;
@@ -467,7 +562,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     tile_extent(g, t, W, s, w, tc);
     const int Ex = w[0] + W, Ey = w[1] + W, Ez = D == 3 ? w[2] + W : 1;
     const int Exy = Ex * Ey, cells = Exy * Ez;
-    const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+    const int p0 = tr[t].x, p1 = tr[t].y;
     const int P = p1 - p0;
     bool fixed = false;
     int sc = 0;
@@ -603,7 +698,7 @@ __device__ __forceinline__ void spread_point_col(const EsPoly<T> &ep, const int 
 template <typename T, int W>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
-    const int *__restrict__ off, T *__restrict__ grid, T *__restrict__ ring,
+    const int2 *__restrict__ tr, T *__restrict__ grid, T *__restrict__ ring,
     int64_t ring_slot) {
     using U = typename PT<T>::U;
     constexpr int D = 3, HL = W / 2, HR = W - HL;
@@ -636,7 +731,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
     __syncthreads();
     if ((int)threadIdx.x < nz) {
         const int64_t t = tile_id(tz0 + threadIdx.x);
-        atomicMax(&s_pmax, off[(t + 1) * g.sub] - off[t * g.sub]);
+        atomicMax(&s_pmax, tr[t].y - tr[t].x);
     }
     {   // zero the buffer, 16 bytes per store
         const int words = NP * Sxy * (int)(sizeof(T) / 4);
@@ -660,7 +755,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
         const int zk = tile_start(tz, g.tq[2], g.tr[2]);
         const int wz = tile_start(tz + 1, g.tq[2], g.tr[2]) - zk;
         const int r0 = (zk - HL - zbase) % NP;     // buffer plane of the region's first plane
-        const int p0 = off[t * g.sub], p1 = off[(t + 1) * g.sub];
+        const int p0 = tr[t].x, p1 = tr[t].y;
         if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
         __syncthreads();
         if (fixed && p1 - p0 <= cap) {

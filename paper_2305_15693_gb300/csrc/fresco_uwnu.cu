@@ -776,7 +776,7 @@ fresco_status nu_eval(fresco_nuwnu_s *p, const T *pts, double *loss, T *grad) {
     const double dscale[3] = {-2.0 / p->h[0], -2.0 / p->h[1], -2.0 / p->h[2]};
     const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(
         sizeof(T) == 4 ? (const void *)&p->ps.p32 : (const void *)&p->ps.p64);
-    UN_CUDA(Launch<T>::interp_kd(p->ps.g, ep, p->ps.sorted, p->ps.perm, p->ps.off,
+    UN_CUDA(Launch<T>::interp_kd(p->ps.g, ep, p->ps.sorted, p->ps.perm, p->ps.tr,
                                  (const T *)p->ps.grid, nullptr, dscale, grad, s));
     p->launches += 3;
     return un_status(cudaGetLastError());

@@ -313,3 +313,39 @@ def test_clustered_points_overflow_the_tile_lists(dim, precision):
     W = 0.5 + g.random(mask.shape[0])
     err = compare(pts, mask, S0, W, precision=precision)
     _assert_within(err, precision)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_one_crowded_tile_falls_back_to_compact_binning(dim, precision):
+    """Uniform points plus a tight clump: one tile receives more points than the direct binning
+    form's fixed capacity per tile (the uniform density's mean plus eight standard deviations), so
+    the evaluation bins again in the compact form; both the device and the host-buffer entry point
+    must match the oracle."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    g = inputs.rng(123 + dim)
+    dt = np.float64 if precision == "f64" else np.float32
+    n_bg, n_cl = (20000, 4000) if dim == 2 else (15000, 6000)
+    pts = np.vstack([g.random((n_bg, dim)), 0.61 + 0.002 * g.random((n_cl, dim))]).astype(dt)
+    mask = inputs.ball_mask(20 if dim == 2 else 6, dim)
+    S0 = g.random(mask.shape[0])
+    W = 0.5 + g.random(mask.shape[0])
+    err = compare(pts, mask, S0, W, precision=precision)
+    _assert_within(err, precision)
+    with fresco.Plan(1.0, mask, S0, W, pts.shape[0], precision=precision) as plan:
+        loss_d, grad_d = plan.loss_grad(torch.from_numpy(pts).cuda())
+        grad_h = np.empty_like(pts)
+        loss_h = plan.loss_grad_host(pts, grad_h)
+        assert plan.status() == 0
+        loss_d, grad_d = float(loss_d.item()), grad_d.cpu().numpy()
+    if precision == "f32" and dim == 2:
+        # fixed-point spreading: the same sums whatever order the points are binned in
+        assert loss_h == loss_d
+        np.testing.assert_array_equal(grad_h, grad_d)
+    else:
+        # the crowded tile spreads with float atomics (FP64 plans; in 3D a z-column segment with
+        # more than 16384 / 3 points a tile), whose sums depend on the order: equal to rounding
+        tol = 1e-12 if precision == "f64" else 1e-5
+        assert abs(loss_h - loss_d) <= tol * abs(loss_d)
+        assert np.linalg.norm(grad_h - grad_d) <= tol * np.linalg.norm(grad_d)
