@@ -255,7 +255,7 @@ fresco_status choose_tiling(Params &P, const int tile_req[3], bool own_tiles = f
         tg.dim = dim;
         tg.width = w;
         tg.list_cap = P.list_cap;
-        tg.zseg = own_tiles && dim == 3 ? kZSegment : 0;
+        tg.zseg = own_tiles && dim == 3 && P.tmax[2] + w <= kColMaxPlanes ? kZSegment : 0;
         for (int a = 0; a < 3; ++a) tg.tmax[a] = a < dim ? P.tmax[a] : 1;
         // the interpolation form this plan uses (direct or kernel derivative)
         const bool kd = P.grad_mode == FRESCO_GRAD_KDERIV;
@@ -649,7 +649,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
     g.list_cap = P.list_cap;
     g.sub = kTileCursors;   // own-points spread: no border strips; sub-cursors per tile
-    g.zseg = dim == 3 ? std::min(kZSegment, P.nb[2]) : 0;
+    g.zseg = dim == 3 && P.tmax[2] + P.width <= kColMaxPlanes ? std::min(kZSegment, P.nb[2]) : 0;
     for (int a = 0; a < 3; ++a) g.strips[a] = 0;
     g.n_bins = g.n_tiles * g.sub;
     if (g.n_bins >= 2147483647LL) return FRESCO_ERR_UNSUPPORTED;
@@ -1041,7 +1041,7 @@ fresco_status fresco::point_side_build(PointSide &ps, int dim, const int nf[3], 
     g.n_tiles = (int64_t)P.nb[0] * P.nb[1] * P.nb[2];
     g.list_cap = P.list_cap;
     g.sub = kTileCursors;
-    g.zseg = dim == 3 ? std::min(kZSegment, P.nb[2]) : 0;
+    g.zseg = dim == 3 && P.tmax[2] + width <= kColMaxPlanes ? std::min(kZSegment, P.nb[2]) : 0;
     g.n_bins = g.n_tiles * g.sub;
     g.n_points = n_points;
     g.width = width;

@@ -16,6 +16,7 @@ constexpr int kMinWidth = 2;
 constexpr int kMaxTileEdge = 255; // tile-relative cell must fit the 8-bit field of a packed coordinate
 constexpr int kTileCursors = 4;   // placement cursors per tile of a single plan (Geom.sub)
 constexpr int kZSegment = 6;      // 3D single plans: tiles per z-column segment (Geom.zseg)
+constexpr int kColMaxPlanes = 64; // column spread: tiles with tmax_z + w above this spread one by one
 constexpr int kDirectPointsPerThread = 8;   // points in flight per thread of k_place_direct
 // fresco_loss_grad_host copies the points in up to kHostChunks pieces of at least
 // kHostChunkBytes, binning each piece while the next one is in flight
@@ -50,6 +51,39 @@ struct Geom {
     double beta;        // ES kernel shape
     double s_hi[3];     // n_f / L split as s_hi + s_lo (s_hi exact in the working precision)
     double s_lo[3];
+};
+
+// Division of non-negative ints by a divisor d (1 <= d < 2^31) fixed for a loop, as a multiply-
+// high, an add and a shift (the round-up method of Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l for 0 <= n < 2^31 (umulhi(n, m) < n, so the sum fits 32 bits).
+struct FastDiv {
+    unsigned m;
+    int l;
+    __host__ __device__ explicit FastDiv(int d) {
+#ifdef __CUDA_ARCH__
+        l = d > 1 ? 32 - __clz(d - 1) : 0;
+        if (d <= (1 << 20)) {
+            // 2^32 (2^l - d) / d in FP64: the product is exact and the quotient, below 2^32, is
+            // rounded by at most 2^-22, less than its distance 1/d to the next integer unless it
+            // is one; so the floor is exact (and costs less than a 64-bit integer division)
+            m = (unsigned)floor((double)((1u << l) - (unsigned)d) * 4294967296.0 / (double)d) + 1u;
+            return;
+        }
+#else
+        l = 0;
+        while ((1LL << l) < d) ++l;
+#endif
+        m = (unsigned)((((unsigned long long)((1ULL << l) - (unsigned long long)d)) << 32) /
+                       (unsigned long long)d + 1ULL);
+    }
+    __host__ __device__ int div(int n) const {
+#ifdef __CUDA_ARCH__
+        return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l);
+#else
+        return (int)((unsigned)((((unsigned long long)(unsigned)n * m) >> 32) + (unsigned)n) >> l);
+#endif
+    }
 };
 
 __host__ __device__ inline int tile_start(int b, int q, int r) { return b * q + (b < r ? b : r); }

@@ -1215,8 +1215,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // FP32 tiles of at most g.list_cap points run in the level-ordered bank-residue schedule of the
 // spread (window loads of a warp hit distinct banks but where a run of 32 entries spans two
 // levels); others one point per thread in sorted order. The tile and its halo are staged with
-// asynchronous copies, row by row (warps take rows, lanes cells), while the block builds the
-// point list from the sorted records.
+// asynchronous copies while the block builds the point list from the sorted records.
 template <typename T, int W, int D>
 __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &ep,
                                                const typename PT<T>::U *__restrict__ sorted,
@@ -1244,30 +1243,32 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
     const int rxy = rw[0] * rw[1];
     T *sh = reinterpret_cast<T *>(sm_raw);
     if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
-    {   // stage the tile and its halo; the staged region is narrower than the grid, so it wraps
-        // at most once per axis
-        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        const int rows = rw[1] * rw[2];
-        int y = threadIdx.x >> 5, z = 0;
-        if (D == 3) {
-            z = y / rw[1];
-            y -= z * rw[1];
-        }
-        for (int row = threadIdx.x >> 5; row < rows; row += nw) {
-            int gy = s[1] - HL + y, gz = D == 3 ? s[2] - HL + z : 0;
-            gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
-            if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
-            const T *src = h + ((int64_t)gz * g.nf[1] + gy) * g.nf[0];
-            T *dst = sh + row * rw[0];
-            for (int x = lane; x < rw[0]; x += 32) {
-                int gx = s[0] - HL + x;
-                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
-                cp_async_elem(dst + x, src + gx);
+    {   // stage the tile and its halo, one cell per thread and step: the cell's row and plane by
+        // multiply-high division. The staged region is narrower than the grid, so it wraps at most
+        // once per axis; a region that does not wrap (most tiles) needs no per-cell wrap tests.
+        const int cells = rxy * rw[2];
+        const FastDiv fx(rw[0]), fy(rw[1]);
+        const int gx0 = s[0] - HL, gy0 = s[1] - HL, gz0 = D == 3 ? s[2] - HL : 0;
+        const bool inside = gx0 >= 0 && gx0 + rw[0] <= g.nf[0] && gy0 >= 0 &&
+                            gy0 + rw[1] <= g.nf[1] &&
+                            (D < 3 || (gz0 >= 0 && gz0 + rw[2] <= g.nf[2]));
+        const int64_t nx = g.nf[0], nxy = (int64_t)g.nf[0] * g.nf[1];
+        if (inside) {
+            const T *src = h + gz0 * nxy + (int64_t)gy0 * nx + gx0;
+            for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+                const int row = fx.div(i), x = i - row * rw[0];
+                const int z = D == 3 ? fy.div(row) : 0, y = row - z * rw[1];
+                cp_async_elem(sh + i, src + z * nxy + (int64_t)y * nx + x);
             }
-            y += nw;
-            while (y >= rw[1]) {   // next row of this warp (nw rows on)
-                y -= rw[1];
-                ++z;
+        } else {
+            for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+                const int row = fx.div(i), x = i - row * rw[0];
+                const int z = D == 3 ? fy.div(row) : 0, y = row - z * rw[1];
+                int gx = gx0 + x, gy = gy0 + y, gz = gz0 + z;
+                gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
+                gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
+                if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
+                cp_async_elem(sh + i, h + gz * nxy + (int64_t)gy * nx + gx);
             }
         }
     }

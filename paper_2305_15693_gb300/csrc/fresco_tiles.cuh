@@ -436,7 +436,7 @@ __device__ __forceinline__ int window_of(const typename PT<T>::U (&u)[3], int Ex
 
 // Levels the schedule tabulates; a tile with a residue of more points (clustered input) lists its
 // points in arrival order instead (correct, with bank conflicts).
-constexpr int kResidueLevels = 256;
+constexpr int kResidueLevels = 128;
 
 // Shared state of the schedule. cnt must be zero (and visible to the block) before the call.
 struct ResidueShared {
@@ -609,27 +609,46 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     }
     __syncthreads();
     const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
-    const int lane = threadIdx.x & 31;
     T *myring = ring + t * ring_slot;
-    // one warp per row of the region: the cells inside the tile go to the grid, the others to the
-    // ring, whose cells of one row are contiguous
-    for (int row = threadIdx.x >> 5; row < Ey * Ez; row += blockDim.x >> 5) {
-        const int ez = D == 3 ? row / Ey : 0, ey = row - ez * Ey;
-        const bool through =
-            (D < 3 || (ez >= HL && ez < HL + w[2])) && (ey >= HL && ey < HL + w[1]);
-        const int64_t gbase =
-            ((int64_t)(D == 3 ? s[2] + ez - HL : 0) * g.nf[1] + (s[1] + ey - HL)) * g.nf[0] +
-            s[0] - HL;
-        T *rrow = myring + ring_index<W, D>(0, ey, ez, w[0], w[1], w[2]);
-        for (int ex = lane; ex < Ex; ex += 32) {
-            const int i = row * Ex + ex;
+    if constexpr (D == 2) {
+        // one warp per row of the region (rows of at least W + 2 cells, most several warps wide):
+        // the cells inside the tile go to the grid, the others to the ring, whose cells of one
+        // row are contiguous
+        const int lane = threadIdx.x & 31;
+        for (int ey = threadIdx.x >> 5; ey < Ey; ey += blockDim.x >> 5) {
+            const bool through = ey >= HL && ey < HL + w[1];
+            const int64_t gbase = (int64_t)(s[1] + ey - HL) * g.nf[0] + s[0] - HL;
+            T *rrow = myring + ring_index<W, D>(0, ey, 0, w[0], w[1], w[2]);
+            for (int ex = lane; ex < Ex; ex += 32) {
+                const int i = ey * Ex + ex;
+                T v;
+                if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i] * finv : ftile[i];
+                else v = ftile[i];
+                if (!through) rrow[ex] = v;
+                else if (ex < HL) rrow[ex] = v;
+                else if (ex >= HL + w[0]) rrow[ex - w[0]] = v;
+                else grid[gbase + ex] = v;
+            }
+        }
+    } else {
+        // 3D rows are short (a warp's lanes would mostly idle per row): one cell per thread and
+        // step, its row and plane by multiply-high division
+        const FastDiv fex(Ex), fey(Ey);
+        const int64_t gorg =
+            ((int64_t)(s[2] - HL) * g.nf[1] + (s[1] - HL)) * g.nf[0] + s[0] - HL;
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            const int row = fex.div(i), ex = i - row * Ex;
+            const int ez = fey.div(row), ey = row - ez * Ey;
             T v;
             if constexpr (sizeof(T) == 4) v = fixed ? (float)itile[i] * finv : ftile[i];
             else v = ftile[i];
-            if (!through) rrow[ex] = v;
-            else if (ex < HL) rrow[ex] = v;
-            else if (ex >= HL + w[0]) rrow[ex - w[0]] = v;
-            else grid[gbase + ex] = v;
+            const bool through = ez >= HL && ez < HL + w[2] && ey >= HL && ey < HL + w[1];
+            if (through && ex >= HL && ex < HL + w[0]) {
+                grid[gorg + ((int64_t)ez * g.nf[1] + ey) * g.nf[0] + ex] = v;
+            } else {
+                const int r = ring_index<W, D>(0, ey, ez, w[0], w[1], w[2]);
+                myring[r + (through && ex >= HL + w[0] ? ex - w[0] : ex)] = v;
+            }
         }
     }
 }
@@ -646,6 +665,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
 // is a multiple of 32 words, so a window's bank residue does not depend on its plane and the
 // residue schedule stays conflict free across the wrap of the buffer. All tiles of a segment use
 // one fixed-point scale, set by the three most crowded consecutive tiles that can reach a plane.
+// Where one plane of a column's buffer goes: its slot in the circular buffer, whether it lies in
+// its owner tile along z, its owner's ring plane (offset into the ring buffer) and the grid cell
+// of its extended region's first row and column.
+struct ColPlane {
+    int slot;
+    int zin;
+    int64_t roff;
+    int64_t goff;
+};
+
 __host__ __device__ inline int col_plane_stride(const Geom &g) {
     return ((g.tmax[0] + g.width) * (g.tmax[1] + g.width) + 31) & ~31;
 }
@@ -704,6 +733,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
     constexpr int D = 3, HL = W / 2, HR = W - HL;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     __shared__ ResidueShared s_rl;
+    __shared__ ColPlane s_pl[kColMaxPlanes];
     __shared__ int s_pmax;
     T *ftile = reinterpret_cast<T *>(sm_raw);
     int *itile = reinterpret_cast<int *>(sm_raw);
@@ -748,7 +778,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
     }
     const float fscale = __int_as_float((127 + sc) << 23);   // 2^sc
     const float finv = __int_as_float((127 - sc) << 23);     // 2^-sc
-    const int lane = threadIdx.x & 31;
     for (int k = 0; k < nz; ++k) {
         const int tz = tz0 + k;
         const int64_t t = tile_id(tz);
@@ -756,6 +785,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
         const int wz = tile_start(tz + 1, g.tq[2], g.tr[2]) - zk;
         const int r0 = (zk - HL - zbase) % NP;     // buffer plane of the region's first plane
         const int p0 = tr[t].x, p1 = tr[t].y;
+        if ((int)threadIdx.x < (k + 1 < nz ? wz : wz + W)) {
+            // destinations of the plane this thread describes (written out after this tile)
+            const int pz = zk - HL + (int)threadIdx.x;
+            int owner, ez, wo;
+            if (pz < zfirst) {
+                owner = tz0;
+                ez = pz - (zfirst - HL);
+                wo = tile_start(tz0 + 1, g.tq[2], g.tr[2]) - zfirst;
+            } else if (pz >= zend) {
+                owner = tz0 + nz - 1;
+                ez = pz - (zlast - HL);
+                wo = zend - zlast;
+            } else {
+                owner = pz < zk ? tz - 1 : tz;
+                const int zo = owner == tz ? zk : tile_start(owner, g.tq[2], g.tr[2]);
+                ez = pz - zo + HL;
+                wo = (owner == tz ? zk + wz : zk) - zo;
+            }
+            ColPlane &pl = s_pl[threadIdx.x];
+            pl.zin = ez >= HL && ez < HL + wo;
+            pl.slot = (r0 + (int)threadIdx.x) % NP;
+            pl.roff = tile_id(owner) * ring_slot + ring_index<W, D>(0, 0, ez, wx, wy, wo);
+            const int64_t gz = pz < 0 ? pz + g.nf[2] : (pz >= g.nf[2] ? pz - g.nf[2] : pz);
+            pl.goff = (gz * g.nf[1] + sy - HL) * g.nf[0] + sx - HL;
+        }
         if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
         __syncthreads();
         if (fixed && p1 - p0 <= cap) {
@@ -787,54 +841,38 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
         }
         __syncthreads();
         // planes no later point of the segment reaches: [zk - HL, zk + wz - HL), or to the end.
-        // A plane's destinations (its owner tile, ring plane and grid plane) are worked out once
-        // per plane; warps then take its rows and lanes its cells.
+        // Every plane's destinations (its owner tile's ring plane, or its grid plane, and its
+        // buffer slot) are worked out once (s_pl, filled before the spread loop's barrier), then
+        // the threads take the cells of all these planes one per step.
         const int pz0 = zk - HL;
-        const int pz1 = k + 1 < nz ? zk + wz - HL : zk + wz + HR;
-        int slot = (pz0 - zbase) % NP;
-        for (int pz = pz0; pz < pz1; ++pz, slot = slot + 1 == NP ? 0 : slot + 1) {
-            // the tile whose ring or cells take this plane, and the plane's place in its region
-            int owner, ez, wo;
-            if (pz < zfirst) {
-                owner = tz0;
-                ez = pz - (zfirst - HL);
-                wo = tile_start(tz0 + 1, g.tq[2], g.tr[2]) - zfirst;
-            } else if (pz >= zend) {
-                owner = tz0 + nz - 1;
-                ez = pz - (zlast - HL);
-                wo = zend - zlast;
+        const int npl = k + 1 < nz ? wz : wz + W;
+        const int pcells = Ex * Ey;
+        const FastDiv fpc(pcells), fex(Ex);
+        for (int i = threadIdx.x; i < npl * pcells; i += blockDim.x) {
+            const int q = fpc.div(i), rem = i - q * pcells;
+            const int ey = fex.div(rem), ex = rem - ey * Ex;
+            const ColPlane &pl = s_pl[q];
+            const int c = pl.slot * Sxy + rem;
+            T v;
+            if constexpr (sizeof(T) == 4) {
+                v = fixed ? (float)itile[c] * finv : ftile[c];
+                itile[c] = 0;
             } else {
-                owner = pz < zk ? tz - 1 : tz;
-                const int zo = owner == tz ? zk : tile_start(owner, g.tq[2], g.tr[2]);
-                ez = pz - zo + HL;
-                wo = (owner == tz ? zk + wz : zk) - zo;
+                v = ftile[c];
+                ftile[c] = T(0);
             }
-            const bool zin = ez >= HL && ez < HL + wo;
-            T *rplane = ring + tile_id(owner) * ring_slot + ring_index<W, D>(0, 0, ez, wx, wy, wo);
-            const int64_t gz = pz < 0 ? pz + g.nf[2] : (pz >= g.nf[2] ? pz - g.nf[2] : pz);
-            const int64_t gplane = (gz * g.nf[1] + sy - HL) * g.nf[0] + sx - HL;
-            for (int ey = threadIdx.x >> 5; ey < Ey; ey += blockDim.x >> 5) {
-                const bool through = zin && ey >= HL && ey < HL + wy;
-                // rows outside the tile are stored whole, rows through it only their W halo cells
-                T *rrow = !zin || ey < HL ? rplane + ey * Ex
-                          : (ey < HL + wy ? rplane + HL * Ex + (ey - HL) * W
-                                          : rplane + HL * Ex + wy * W + (ey - HL - wy) * Ex);
-                T *grow = grid + gplane + (int64_t)ey * g.nf[0];
-                const int base = slot * Sxy + ey * Ex;
-                for (int ex = lane; ex < Ex; ex += 32) {
-                    T v;
-                    if constexpr (sizeof(T) == 4) {
-                        v = fixed ? (float)itile[base + ex] * finv : ftile[base + ex];
-                        itile[base + ex] = 0;
-                    } else {
-                        v = ftile[base + ex];
-                        ftile[base + ex] = T(0);
-                    }
-                    if (!through) rrow[ex] = v;
-                    else if (ex < HL) rrow[ex] = v;
-                    else if (ex >= HL + wx) rrow[ex - wx] = v;
-                    else grow[ex] = v;
-                }
+            // rows outside the tile (or planes outside it in z) are stored whole in the ring, rows
+            // through it only their W halo cells; the cells inside go to the grid
+            const bool yin = pl.zin && ey >= HL && ey < HL + wy;
+            const bool xin = ex >= HL && ex < HL + wx;
+            if (yin && xin) {
+                grid[pl.goff + (int64_t)ey * g.nf[0] + ex] = v;
+            } else {
+                const int r = !pl.zin || ey < HL
+                                  ? ey * Ex + ex
+                                  : (ey < HL + wy ? HL * Ex + (ey - HL) * W + (ex < HL ? ex : ex - wx)
+                                                  : HL * Ex + wy * W + (ey - HL - wy) * Ex + ex);
+                ring[pl.roff + r] = v;
             }
         }
         __syncthreads();
@@ -890,11 +928,27 @@ __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
     const int64_t t_hi = t + (int64_t)(hi_t - tc[A]) * stride_t[A];
     const T *src_ring = ring + t * ring_slot;
     const int count = ext[0] * ext[1] * ext[2];
+    // cell i of the moved block: the extent along A is a constant, the others take a
+    // multiply-high division where they are needed
+    const FastDiv f0(A == 0 ? 1 : ext[0]), f1(A != 1 && D == 3 ? ext[1] : 1);
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         int e[3];
-        e[0] = i % ext[0];
-        e[1] = (i / ext[0]) % ext[1];
-        e[2] = i / (ext[0] * ext[1]);
+        if constexpr (A == 0) {
+            const int q = i / NA;
+            e[0] = i - q * NA;
+            e[2] = D == 3 ? f1.div(q) : 0;
+            e[1] = q - e[2] * ext[1];
+        } else if constexpr (A == 1) {
+            const int q = f0.div(i);
+            e[0] = i - q * ext[0];
+            e[2] = q / NA;
+            e[1] = q - e[2] * NA;
+        } else {
+            const int q = f0.div(i);
+            e[0] = i - q * ext[0];
+            e[2] = f1.div(q);
+            e[1] = q - e[2] * ext[1];
+        }
         // e along folded axes counts from the tile's first cell
 #pragma unroll
         for (int b = 0; b < 3; ++b)
