@@ -657,6 +657,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
     g.width = P.width;
     g.beta = P.beta;
     g.tcap = direct_tile_capacity(g);
+    set_tile_divisors(g);
 
     MaskGeom &m = p->mgeom;
     m.dim = dim;
@@ -1046,6 +1047,7 @@ fresco_status fresco::point_side_build(PointSide &ps, int dim, const int nf[3], 
     g.n_points = n_points;
     g.width = width;
     g.beta = beta;
+    set_tile_divisors(g);
     ps.precision = precision;
     const int64_t cells = (int64_t)g.nf[0] * g.nf[1] * g.nf[2];
     const int pw = es == 4 ? 4 : (dim == 3 ? 4 : 2);
@@ -1496,6 +1498,7 @@ fresco_status batch_build(fresco_batch_s *b, const std::vector<Params> &P,
         g.n_points = n_points[i];
         g.width = p.width;
         g.beta = p.beta;
+        set_tile_divisors(g);
         I.m.dim = dim;
         I.m.kx = K.kx;
         I.m.n_rep = (int64_t)F[i].s0.size();

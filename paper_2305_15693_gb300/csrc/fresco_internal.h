@@ -5,6 +5,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "fresco.h"
@@ -27,6 +28,30 @@ constexpr int64_t kHostChunkBytes = 32ll << 20;
 // Axis 0 is x, the contiguous axis of every grid. With q = nf / nb and r = nf % nb, tile b on an
 // axis covers fine cells [start(b), start(b+1)), start(b) = b q + min(b, r): the first r tiles
 // are q + 1 cells wide, the others q.
+// Division of non-negative ints by a divisor d (1 <= d < 2^31) fixed for a loop, as a multiply-
+// high, an add and a shift (the round-up method of Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l for 0 <= n < 2^31 (umulhi(n, m) < n, so the sum fits 32 bits).
+// The magic numbers of a plan's tile extents are computed on the host (Geom.fdw, Geom.fdp).
+struct FastDiv {
+    unsigned m;
+    int l;
+    FastDiv() = default;
+    __host__ explicit FastDiv(int d) {
+        l = 0;
+        while ((1LL << l) < d) ++l;
+        m = (unsigned)((((unsigned long long)((1ULL << l) - (unsigned long long)d)) << 32) /
+                       (unsigned long long)d + 1ULL);
+    }
+    __host__ __device__ int div(int n) const {
+#ifdef __CUDA_ARCH__
+        return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l);
+#else
+        return (int)((unsigned)((((unsigned long long)(unsigned)n * m) >> 32) + (unsigned)n) >> l);
+#endif
+    }
+};
+
 struct Geom {
     int dim;
     int nf[3];          // fine grid size per axis (1 for unused axes)
@@ -51,40 +76,29 @@ struct Geom {
     double beta;        // ES kernel shape
     double s_hi[3];     // n_f / L split as s_hi + s_lo (s_hi exact in the working precision)
     double s_lo[3];
+    FastDiv fdw[3][4];  // per axis, division by tq, tq + 1, tq + width, tq + 1 + width
+    FastDiv fdp[2][2];  // division by (x tile width + width) (y tile width + width), the x and
+                        // y widths tq or tq + 1
 };
 
-// Division of non-negative ints by a divisor d (1 <= d < 2^31) fixed for a loop, as a multiply-
-// high, an add and a shift (the round-up method of Granlund and Montgomery, "Division by invariant
-// integers using multiplication", 1994): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
-// n / d = (umulhi(n, m) + n) >> l for 0 <= n < 2^31 (umulhi(n, m) < n, so the sum fits 32 bits).
-struct FastDiv {
-    unsigned m;
-    int l;
-    __host__ __device__ explicit FastDiv(int d) {
-#ifdef __CUDA_ARCH__
-        l = d > 1 ? 32 - __clz(d - 1) : 0;
-        if (d <= (1 << 20)) {
-            // 2^32 (2^l - d) / d in FP64: the product is exact and the quotient, below 2^32, is
-            // rounded by at most 2^-22, less than its distance 1/d to the next integer unless it
-            // is one; so the floor is exact (and costs less than a 64-bit integer division)
-            m = (unsigned)floor((double)((1u << l) - (unsigned)d) * 4294967296.0 / (double)d) + 1u;
-            return;
+// Fills g.fdw and g.fdp from g.tq and g.width (host).
+inline void set_tile_divisors(Geom &g) {
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 4; ++k) {
+            const int d = std::max(1, g.tq[a] + (k & 1) + (k >= 2 ? g.width : 0));
+            g.fdw[a][k] = FastDiv(d);
         }
-#else
-        l = 0;
-        while ((1LL << l) < d) ++l;
-#endif
-        m = (unsigned)((((unsigned long long)((1ULL << l) - (unsigned long long)d)) << 32) /
-                       (unsigned long long)d + 1ULL);
-    }
-    __host__ __device__ int div(int n) const {
-#ifdef __CUDA_ARCH__
-        return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l);
-#else
-        return (int)((unsigned)((((unsigned long long)(unsigned)n * m) >> 32) + (unsigned)n) >> l);
-#endif
-    }
-};
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            g.fdp[i][j] = FastDiv(std::max(1, (g.tq[0] + i + g.width) * (g.tq[1] + j + g.width)));
+}
+
+// The divisor of a tile extent along axis A: the tile width w (tq or tq + 1), plus the kernel
+// width if PLUS.
+template <int A, bool PLUS>
+__host__ __device__ __forceinline__ FastDiv tile_div(const Geom &g, int w) {
+    return w == g.tq[A] ? g.fdw[A][PLUS ? 2 : 0] : g.fdw[A][PLUS ? 3 : 1];
+}
 
 __host__ __device__ inline int tile_start(int b, int q, int r) { return b * q + (b < r ? b : r); }
 __host__ __device__ inline int tile_of_cell(int c, int q, int r, float inv) {

@@ -1247,7 +1247,7 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
         // multiply-high division. The staged region is narrower than the grid, so it wraps at most
         // once per axis; a region that does not wrap (most tiles) needs no per-cell wrap tests.
         const int cells = rxy * rw[2];
-        const FastDiv fx(rw[0]), fy(rw[1]);
+        const FastDiv fx = tile_div<0, true>(g, rw[0] - W), fy = tile_div<1, true>(g, rw[1] - W);
         const int gx0 = s[0] - HL, gy0 = s[1] - HL, gz0 = D == 3 ? s[2] - HL : 0;
         const bool inside = gx0 >= 0 && gx0 + rw[0] <= g.nf[0] && gy0 >= 0 &&
                             gy0 + rw[1] <= g.nf[1] &&

@@ -633,7 +633,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_spread_own(
     } else {
         // 3D rows are short (a warp's lanes would mostly idle per row): one cell per thread and
         // step, its row and plane by multiply-high division
-        const FastDiv fex(Ex), fey(Ey);
+        const FastDiv fex = tile_div<0, true>(g, w[0]), fey = tile_div<1, true>(g, w[1]);
         const int64_t gorg =
             ((int64_t)(s[2] - HL) * g.nf[1] + (s[1] - HL)) * g.nf[0] + s[0] - HL;
         for (int i = threadIdx.x; i < cells; i += blockDim.x) {
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
         const int pz0 = zk - HL;
         const int npl = k + 1 < nz ? wz : wz + W;
         const int pcells = Ex * Ey;
-        const FastDiv fpc(pcells), fex(Ex);
+        const FastDiv fpc = g.fdp[wx - g.tq[0]][wy - g.tq[1]], fex = tile_div<0, true>(g, wx);
         for (int i = threadIdx.x; i < npl * pcells; i += blockDim.x) {
             const int q = fpc.div(i), rem = i - q * pcells;
             const int ey = fex.div(rem), ex = rem - ey * Ex;
@@ -930,7 +930,8 @@ __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
     const int count = ext[0] * ext[1] * ext[2];
     // cell i of the moved block: the extent along A is a constant, the others take a
     // multiply-high division where they are needed
-    const FastDiv f0(A == 0 ? 1 : ext[0]), f1(A != 1 && D == 3 ? ext[1] : 1);
+    const FastDiv f0 = (FM & 1) ? tile_div<0, false>(g, w[0]) : tile_div<0, true>(g, w[0]);
+    const FastDiv f1 = (FM & 2) ? tile_div<1, false>(g, w[1]) : tile_div<1, true>(g, w[1]);
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         int e[3];
         if constexpr (A == 0) {
