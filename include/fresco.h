@@ -175,7 +175,9 @@ fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, doubl
                                     void *h_grad);
 
 /* Synchronise the plan's stream and return the first device-detected error, clearing it
- * (FRESCO_ERR_NONFINITE for a NaN/inf coordinate), or a pending CUDA error. */
+ * (FRESCO_ERR_NONFINITE for a NaN/inf coordinate; FRESCO_ERR_TIMEOUT if an interpolation tile's
+ * TMA load did not complete within its bounded wait, the gradient then being undefined), or a
+ * pending CUDA error. */
 fresco_status fresco_status_check(fresco_plan_t p);
 
 /* Per-stage timing with CUDA events on the plan's stream. enable != 0 records events around

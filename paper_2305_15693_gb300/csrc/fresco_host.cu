@@ -244,13 +244,15 @@ fresco_status choose_tiling(Params &P, const int tile_req[3], bool own_tiles = f
             P.nb[a] = choose_tiles(P.nf[a], target[a], minw);
             P.tmax[a] = (P.nf[a] + P.nb[a] - 1) / P.nb[a];
         }
-        // spread list: the expected points reaching a tile plus five standard deviations
-        // (Poisson), at least 1024; a tile beyond it takes the slower float-atomic path
+        // point lists: the expected points of a tile (with its halo for ensembles) plus five
+        // standard deviations (Poisson) and 64; a tile beyond it takes the slower unlisted path
+        // (single plans list a tile's own points; ensembles every point that reaches the tile)
         double hits = density;
-        for (int a = 0; a < dim; ++a) hits *= (double)(P.tmax[a] + w);
+        for (int a = 0; a < dim; ++a) hits *= (double)(P.tmax[a] + (own_tiles ? 0 : w));
+        const double lmin = own_tiles ? 256.0 : 1024.0, lstep = own_tiles ? 32.0 : 256.0;
         P.list_cap = (int)std::min<double>(
             16384.0,
-            std::max(1024.0, std::ceil((hits + 5.0 * std::sqrt(hits) + 64.0) / 256.0) * 256.0));
+            std::max(lmin, std::ceil((hits + 5.0 * std::sqrt(hits) + 64.0) / lstep) * lstep));
         Geom tg{};
         tg.dim = dim;
         tg.width = w;
@@ -607,6 +609,57 @@ fresco_status make_ffts(fresco_plan_s *p) {
     return FRESCO_OK;
 }
 
+// Blocks of a 256-thread tile kernel one SM holds at a given dynamic shared memory (each block
+// also takes up to 4 KB of static shared state and 1 KB the hardware reserves; 228 KB per SM).
+int tile_blocks_per_sm(size_t dyn) { return (int)((228 * 1024) / (dyn + 5 * 1024)); }
+
+// TMA staging of the kernel-derivative interpolation (FP32 plans): the real field h, [nf2][nf1]
+// [nf0] floats, as a tensor whose boxes cover a tile's region from the 16-byte boundary at or
+// below its first column (rows up to 3 elements wider than the region). Sets g.tma and g.tbox
+// and encodes p->tmap; leaves g.tma = 0 (the copy path) where the box or the tensor does not meet
+// the TMA rules (box extents <= 256, rows a multiple of 16 bytes) or where the wider staged box
+// would cost the interpolation kernel resident blocks.
+void setup_interp_tma(fresco_plan_s *p, const void *field) {
+    Geom &g = p->geom;
+    g.tma = 0;
+    if (p->precision != FRESCO_F32 || !p->mgeom.kderiv || (g.nf[0] * 4) % 16 != 0) return;
+    const int w = g.width;
+    Geom t = g;
+    t.tbox[0] = (g.tmax[0] + w + 3 + 3) & ~3;
+    t.tbox[1] = g.tmax[1] + w;
+    t.tbox[2] = g.dim == 3 ? g.tmax[2] + w : 1;
+    for (int a = 0; a < g.dim; ++a)
+        if (t.tbox[a] > 256) return;
+    const size_t before = (size_t)Launch<float>::interp_kd_smem(g);
+    t.tma = 1;
+    const size_t after = (size_t)Launch<float>::interp_kd_smem(t);
+    if (after > kSmemOptin || tile_blocks_per_sm(after) < std::min(tile_blocks_per_sm(before), 3))
+        return;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nf[0], (cuuint64_t)g.nf[1], (cuuint64_t)g.nf[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nf[0] * 4, (cuuint64_t)g.nf[0] * g.nf[1] * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)t.tbox[0], (cuuint32_t)t.tbox[1],
+                               (cuuint32_t)t.tbox[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(
+        &p->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)g.dim, const_cast<void *>(field),
+        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+    g = t;
+}
+
 // Records per tile of the direct binning form: the expected points of the widest tile (uniform
 // density) plus eight Poisson standard deviations and 32, so that uniform and near-uniform inputs
 // never overflow a tile. 0 (compact form only) where the slots would not be indexable in 32 bits
@@ -763,6 +816,7 @@ fresco_status build_plan(fresco_plan_s *p, const Params &P, const Folded &F) {
         FR_CUDA(cudaMemcpy(p->d_ip[a], ip.data(), sizeof(T) * (size_t)n_nu, cudaMemcpyHostToDevice));
     }
     if ((st = make_ffts<T>(p))) return st;
+    setup_interp_tma(p, p->d_r[0]);
     FR_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
     return FRESCO_OK;
 }
@@ -922,7 +976,8 @@ fresco_status backward_impl(fresco_plan_s *p, const double *grad_out, T *grad) {
         }
         StageScope sc(p->prof, p->stream, ST_INTERP);
         FR_CUDA(Launch<T>::interp_kd(g, poly_of<T>(p), p->d_sorted, p->d_perm, p->d_tr,
-                                     (const T *)p->d_r[0], grad_out, p->dscale, grad, s));
+                                     (const T *)p->d_r[0], grad_out, p->dscale, grad, s,
+                                     g.tma ? &p->tmap : nullptr, p->d_err));
         p->launches += 1;
         return FRESCO_OK;
     }
@@ -1314,7 +1369,8 @@ fresco_status fresco_status_check(fresco_plan_t p) {
         int zero = 0;
         FR_CUDA(cudaMemcpy(p->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice));
         if (err & 1) return FRESCO_ERR_NONFINITE;
-        return FRESCO_ERR_BOUNDS;
+        if (err & 4) return FRESCO_ERR_TIMEOUT;
+        return FRESCO_ERR_BOUNDS;   // (bit 2: a point beyond the box; bit 8: a misaligned TMA box)
     }
     return cuda_status(cudaGetLastError());
 }

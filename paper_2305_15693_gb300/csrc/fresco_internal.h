@@ -1,6 +1,7 @@
 // Internal declarations shared by the host code and the kernel translation units of libfresco.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -71,6 +72,9 @@ struct Geom {
     int64_t n_bins;     // n_tiles * sub: the sort key space
     int tcap;           // single plans: records per tile of the direct binning form (0: the plan
                         // bins in the compact form only)
+    int tma;            // single FP32 kernel-derivative plans: 1 if interpolation tiles are staged
+                        // by TMA box loads of tbox elements (x, y, z)
+    int tbox[3];
     int64_t n_points;
     int width;          // ES kernel width w
     double beta;        // ES kernel shape
@@ -246,11 +250,14 @@ struct Launch {
     static cudaError_t interp(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                               const int *perm, const int2 *tr, const void *g0, const void *g1,
                               const double *grad_out, T *grad, cudaStream_t s);
-    // kernel-derivative mode: h is the real field, dscale[a] = -2 n_f[a] / L[a]
+    // kernel-derivative mode: h is the real field, dscale[a] = -2 n_f[a] / L[a]; a plan with
+    // g.tma stages its tiles by TMA box loads through map (the field h as a tensor), and latches
+    // a timed-out load in *err (bit 4)
     static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                                  const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const CUtensorMap *map = nullptr,
+                                 int *err = nullptr);
     static int interp_kd_smem(const Geom &g);
     // real transforms of even length 2M along x as complex transforms of length M: split the
     // forward result into the half spectrum (columns 0..kx, transposed), and merge a transposed
@@ -386,6 +393,7 @@ struct fresco_plan_s {
     int *d_off = nullptr;            // [n_bins + 1] exclusive prefix sum of the counts
     int *d_tcur = nullptr;           // [n_tiles + 1] direct-form cursors, then the overflow word
     int2 *d_tr = nullptr;            // [n_tiles] record range of every tile
+    CUtensorMap tmap{};              // geom.tma: the interpolated real field as a TMA tensor
     int *d_block_sums = nullptr;     // scan scratch
     void *d_grid = nullptr;          // real fine grid (spread output)
     void *d_tw = nullptr;            // exp(-2 pi i k / nf0), k = 0..nf0/4 (real-row split/merge)

@@ -19,6 +19,7 @@
 //               re = d/dr_z (pipeline 1, 3D only).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -518,7 +519,7 @@ __device__ __forceinline__ void spread_tile(const Geom &g, const EsPoly<T> &ep,
     constexpr int NNB = (D == 3) ? 27 : 9;     // neighbouring tiles, this one included
     constexpr int S = (D == 3) ? 27 : 9;       // sub-bins per tile
     constexpr int MAXR = NNB * S;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
+    extern __shared__ __align__(128) unsigned char sm_raw[];
     __shared__ int nb_org[NNB][3], nb_tile[NNB];
     __shared__ int r_p0[MAXR], r_start[MAXR + 1], r_q[MAXR];
     __shared__ int s_nr, s_hits, s_edge;
@@ -939,7 +940,7 @@ __device__ __forceinline__ void interp_tile(const Geom &g, const EsPoly<T> &ep,
                                             T *__restrict__ grad, const int64_t t) {
     using U = typename PT<T>::U;
     using C = typename PT<T>::C;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
+    extern __shared__ __align__(128) unsigned char sm_raw[];
 
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
@@ -1193,10 +1194,14 @@ __device__ __forceinline__ void interp_window_kd(const EsPoly<T> &ep, const int 
 }
 
 // bytes of the staged real field of a kernel-derivative interpolation tile (rounded up to 16)
+// (a plan that stages by TMA boxes: the box of g.tbox elements, whose rows are up to 3 elements
+// wider than the region)
 __host__ __device__ inline size_t interp_kd_tile_bytes(const Geom &g, size_t esize) {
     const int w = g.width;
-    size_t cells = (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) * (g.dim == 3 ? (g.tmax[2] + w) : 1);
-    return (cells * esize + 15) & ~(size_t)15;
+    size_t cells = g.tma ? (size_t)g.tbox[0] * g.tbox[1] * g.tbox[2]
+                         : (size_t)(g.tmax[0] + w) * (g.tmax[1] + w) *
+                               (g.dim == 3 ? (g.tmax[2] + w) : 1);
+    return (cells * esize + 127) & ~(size_t)127;
 }
 
 // One element from global to shared memory without passing through registers (cp.async, 4 or 8
@@ -1212,6 +1217,68 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Tensor-memory-accelerator (TMA) tile loads completing on an mbarrier in shared memory.
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    // make the initialised barrier visible to the asynchronous proxy that completes it
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Polls phase `parity` of the barrier at most `tries` times (each poll may suspend the thread for
+// a while); true once the phase has completed.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int tries) {
+    for (int i = 0; i < tries; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// A box of the tensor map at element coordinates (x, y[, z]) (x a multiple of 4 floats: the box
+// starts on a 16-byte boundary) into shared memory at dst (128-byte aligned).
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z,
+                                            unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+// Polls of a TMA tile load before the kernel gives up and latches FRESCO_ERR_TIMEOUT (bit 4 of
+// the device error word): far beyond any real load (microseconds), tens of milliseconds.
+constexpr int kTmaWaitTries = 1 << 16;
+
+// How a kernel-derivative interpolation tile is staged in shared memory: with px == 0 the region
+// is packed tightly (row pitch rw[0], plane rw[0] rw[1]); else rows have pitch px and planes pp
+// elements, the region starting at column x0 % 4 of its row, and `map` (if not null) describes
+// the field for TMA box loads of g.tbox elements at 16-byte aligned x. err: the plan's device
+// error word (TMA timeouts).
+struct InterpStage {
+    int px, pp;
+    const CUtensorMap *map;
+    int *err;
+};
+
 // FP32 tiles of at most g.list_cap points run in the level-ordered bank-residue schedule of the
 // spread (window loads of a warp hit distinct banks but where a run of 32 entries spans two
 // levels); others one point per thread in sorted order. The tile and its halo are staged with
@@ -1222,10 +1289,15 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
                                                const int *__restrict__ perm, const int p0,
                                                const int p1, const T *__restrict__ h, T dsx,
                                                T dsy, T dsz, T *__restrict__ grad,
-                                               const int64_t t) {
+                                               const int64_t t, const InterpStage st) {
     using U = typename PT<T>::U;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
+    extern __shared__ __align__(128) unsigned char sm_dyn[];
     __shared__ ResidueShared s_rl;
+    __shared__ unsigned long long s_bar;
+    // the dynamic buffer starts after the static shared state, 16-byte aligned; a TMA box needs a
+    // 128-byte aligned destination, so the staged region starts at the next 128-byte boundary
+    // (the launch requests 128 bytes more)
+    unsigned char *sm_raw = sm_dyn + ((128u - (smem_addr(sm_dyn) & 127u)) & 127u);
     const int tc[3] = {(int)(t % g.nb[0]), (int)((t / g.nb[0]) % g.nb[1]),
                        (int)(t / ((int64_t)g.nb[0] * g.nb[1]))};
     constexpr int HL = W / 2;
@@ -1240,25 +1312,45 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
             rw[a] = 1;
         }
     }
-    const int rxy = rw[0] * rw[1];
+    const int px = st.px ? st.px : rw[0], pp = st.px ? st.pp : rw[0] * rw[1];
     T *sh = reinterpret_cast<T *>(sm_raw);
     if (threadIdx.x < 32) s_rl.cnt[threadIdx.x] = 0;
-    {   // stage the tile and its halo, one cell per thread and step: the cell's row and plane by
-        // multiply-high division. The staged region is narrower than the grid, so it wraps at most
-        // once per axis; a region that does not wrap (most tiles) needs no per-cell wrap tests.
-        const int cells = rxy * rw[2];
+    bool tma = false;
+    {   // stage the tile and its halo. The staged region is narrower than the grid, so it wraps
+        // at most once per axis. A region that does not wrap takes one TMA box load when the plan
+        // has a tensor map (the box starts at the 16-byte boundary at or below the region's first
+        // column), else one cell per thread and step without wrap tests; a wrapping region one
+        // cell per thread and step with them (the cell's row and plane by multiply-high division).
         const FastDiv fx = tile_div<0, true>(g, rw[0] - W), fy = tile_div<1, true>(g, rw[1] - W);
         const int gx0 = s[0] - HL, gy0 = s[1] - HL, gz0 = D == 3 ? s[2] - HL : 0;
         const bool inside = gx0 >= 0 && gx0 + rw[0] <= g.nf[0] && gy0 >= 0 &&
                             gy0 + rw[1] <= g.nf[1] &&
                             (D < 3 || (gz0 >= 0 && gz0 + rw[2] <= g.nf[2]));
         const int64_t nx = g.nf[0], nxy = (int64_t)g.nf[0] * g.nf[1];
-        if (inside) {
+        const int cells = rw[0] * rw[1] * rw[2];
+        tma = sizeof(T) == 4 && st.map != nullptr && inside;
+        if (tma && ((smem_addr(sm_raw) & 127u) != 0 || ((gx0 & ~3) & 3) != 0)) {
+            // (never taken: the destination is aligned above and the box's x is a multiple of
+            // four) latch it and stage by copies instead of starting a misaligned TMA load
+            if (threadIdx.x == 0 && st.err) atomicOr(st.err, 8);
+            tma = false;
+        }
+        if (tma) {
+            const int xa = gx0 & ~3;
+            sh += gx0 - xa;
+            if (threadIdx.x == 0) {
+                mbar_init(&s_bar, 1);
+                mbar_expect_tx(&s_bar, (unsigned)((size_t)g.tbox[0] * g.tbox[1] * g.tbox[2] *
+                                                  sizeof(T)));
+                if (D == 3) tma_load_3d(sm_raw, st.map, xa, gy0, gz0, &s_bar);
+                else tma_load_2d(sm_raw, st.map, xa, gy0, &s_bar);
+            }
+        } else if (inside) {
             const T *src = h + gz0 * nxy + (int64_t)gy0 * nx + gx0;
             for (int i = threadIdx.x; i < cells; i += blockDim.x) {
                 const int row = fx.div(i), x = i - row * rw[0];
                 const int z = D == 3 ? fy.div(row) : 0, y = row - z * rw[1];
-                cp_async_elem(sh + i, src + z * nxy + (int64_t)y * nx + x);
+                cp_async_elem(sh + z * pp + y * px + x, src + z * nxy + (int64_t)y * nx + x);
             }
         } else {
             for (int i = threadIdx.x; i < cells; i += blockDim.x) {
@@ -1268,44 +1360,59 @@ __device__ __forceinline__ void interp_tile_kd(const Geom &g, const EsPoly<T> &e
                 gx += gx < 0 ? g.nf[0] : (gx >= g.nf[0] ? -g.nf[0] : 0);
                 gy += gy < 0 ? g.nf[1] : (gy >= g.nf[1] ? -g.nf[1] : 0);
                 if (D == 3) gz += gz < 0 ? g.nf[2] : (gz >= g.nf[2] ? -g.nf[2] : 0);
-                cp_async_elem(sh + i, h + gz * nxy + (int64_t)gy * nx + gx);
+                cp_async_elem(sh + z * pp + y * px + x, h + gz * nxy + (int64_t)gy * nx + gx);
             }
         }
     }
     __syncthreads();
+    // the staged field is in place once the TMA load's barrier phase or this thread's copies have
+    // completed (then the block barrier makes every thread's copies visible)
+    auto staged = [&]() -> bool {
+        if (tma) {
+            if (mbar_wait(&s_bar, 0, kTmaWaitTries)) return true;
+            if (threadIdx.x == 0 && st.err) atomicOr(st.err, 4);
+            mbar_wait(&s_bar, 0, kTmaWaitTries);   // let a late load land before the block exits
+            return false;
+        }
+        cp_async_wait_all();
+        return true;
+    };
     if (sizeof(T) == 4 && p1 - p0 <= g.list_cap) {
         // level-ordered entries: packed window start, D kernel offsets, caller index
         const int cap = g.list_cap;
         int *l_i0 = reinterpret_cast<int *>(sm_raw + interp_kd_tile_bytes(g, sizeof(T)));
+        const int rxy = pp, rx = px;
         float *l_x1 = reinterpret_cast<float *>(l_i0 + cap);
         int *l_j = l_i0 + (1 + D) * cap;
         const int n = residue_lists<T, W, D>(
-            sorted, p0, p1, rw[0], rxy, s_rl,
+            sorted, p0, p1, rx, rxy, s_rl,
             [&](int slot, const int (&i0)[3], const T (&x1)[3], unsigned j) {
                 l_i0[slot] = i0[0] | (i0[1] << 10) | (i0[2] << 20);
 #pragma unroll
                 for (int a = 0; a < D; ++a) l_x1[a * cap + slot] = (float)x1[a];
                 l_j[slot] = (int)j;
             });
-        cp_async_wait_all();
+        const bool ok = staged();
         __syncthreads();
+        if (!ok) return;
         for (int q = threadIdx.x; q < n; q += blockDim.x) {
             const int pk = l_i0[q];
             const int i0[3] = {pk & 1023, (pk >> 10) & 1023, pk >> 20};
             T x1[3] = {T(0), T(0), T(0)};
 #pragma unroll
             for (int a = 0; a < D; ++a) x1[a] = (T)l_x1[a * cap + q];
-            interp_window_kd<T, W, D>(ep, i0, x1, (int64_t)l_j[q], sh, rw[0], rxy, dsx, dsy,
+            interp_window_kd<T, W, D>(ep, i0, x1, (int64_t)l_j[q], sh, rx, rxy, dsx, dsy,
                                       dsz, grad);
         }
         return;
     }
-    cp_async_wait_all();
+    const bool ok = staged();
     __syncthreads();
+    if (!ok) return;
     for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         U u[3];
         const int64_t j = load_record<T, D>(sorted, perm, p, u);
-        interp_point_kd<T, W, D>(ep, u, j, sh, rw[0], rxy, dsx, dsy, dsz, grad);
+        interp_point_kd<T, W, D>(ep, u, j, sh, px, pp, dsx, dsy, dsz, grad);
     }
 }
 
@@ -1315,11 +1422,14 @@ template <typename T, int W, int D>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (D == 3 ? 2 : 3) : 2) k_interp_kd(
     Geom g, EsPoly<T> ep, const typename PT<T>::U *__restrict__ sorted,
     const int *__restrict__ perm, const int2 *__restrict__ tr, const T *__restrict__ h,
-    const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad) {
+    const double *__restrict__ grad_out, T dsx, T dsy, T dsz, T *__restrict__ grad,
+    const __grid_constant__ CUtensorMap map, int *__restrict__ err) {
     const T sc = grad_out ? (T)(*grad_out) : T(1);
     const int2 r = tr[blockIdx.x];
+    InterpStage st{0, 0, nullptr, err};
+    if (g.tma) st = InterpStage{g.tbox[0], g.tbox[0] * g.tbox[1], &map, err};
     interp_tile_kd<T, W, D>(g, ep, sorted, perm, r.x, r.y, h, sc * dsx, sc * dsy, sc * dsz, grad,
-                            blockIdx.x);
+                            blockIdx.x, st);
 }
 
 // Batched kernel-derivative interpolation: a persistent grid walks the tiles of every instance;
@@ -1341,7 +1451,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_interp_kd_b(
                                 (T)(-2.0 * (g.s_hi[0] + g.s_lo[0]) * sc),
                                 (T)(-2.0 * (g.s_hi[1] + g.s_lo[1]) * sc),
                                 (T)(-2.0 * (g.s_hi[2] + g.s_lo[2]) * sc), grad,
-                                t - tile_first[i]);
+                                t - tile_first[i], InterpStage{0, 0, nullptr, nullptr});
         __syncthreads();
     }
 }
@@ -1581,7 +1691,7 @@ struct WOps {
     static cudaError_t interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                                  const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const CUtensorMap *map, int *err);
 };
 
 // the same for the (2D) ensemble kernels
@@ -1765,9 +1875,9 @@ int Launch<T>::spread_smem(const Geom &g) {
 
 template <typename T>
 int Launch<T>::interp_kd_smem(const Geom &g) {
-    // the staged field, then (FP32) the residue-grouped entries: packed window start, D kernel
-    // offsets and the caller index
-    return (int)(interp_kd_tile_bytes(g, sizeof(T)) +
+    // up to 128 bytes to the first 128-byte boundary, the staged field, then (FP32) the level-
+    // ordered entries: packed window start, D kernel offsets and the caller index
+    return (int)(128 + interp_kd_tile_bytes(g, sizeof(T)) +
                  (sizeof(T) == 4 ? (size_t)(2 + g.dim) * 4 * (size_t)g.list_cap : 0));
 }
 
@@ -1831,14 +1941,18 @@ template <typename T, int W, int D>
 cudaError_t WOps<T, W, D>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                                      const int *perm, const int2 *tr, const T *h,
                                      const double *grad_out, const double dscale[3], T *grad,
-                                     cudaStream_t s) {
+                                     cudaStream_t s, const CUtensorMap *map, int *err) {
     using U = typename PT<T>::U;
+    if (g.tma && !map) return cudaErrorInvalidValue;   // a TMA plan stages through its map
     const int smem = Launch<T>::interp_kd_smem(g);
     auto kern = k_interp_kd<T, W, D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    CUtensorMap m{};
+    if (map) m = *map;
     kern<<<(unsigned)g.n_tiles, 256, smem, s>>>(g, ep, (const U *)sorted, perm, tr, h, grad_out,
-                                                (T)dscale[0], (T)dscale[1], (T)dscale[2], grad);
+                                                (T)dscale[0], (T)dscale[1], (T)dscale[2], grad,
+                                                m, err);
     return cudaGetLastError();
 }
 
@@ -1894,13 +2008,15 @@ template <typename T>
 cudaError_t Launch<T>::interp_kd(const Geom &g, const EsPoly<T> &ep, const void *sorted,
                                  const int *perm, const int2 *tr, const T *h,
                                  const double *grad_out, const double dscale[3], T *grad,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const CUtensorMap *map, int *err) {
     if (g.dim == 2) {
         FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 2>::interp_kd(
-                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s)));
+                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s,
+                                         map, err)));
     } else {
         FRESCO_WIDTH_SWITCH(g.width, return (WOps<T, WW, 3>::interp_kd(
-                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s)));
+                                         g, ep, sorted, perm, tr, h, grad_out, dscale, grad, s,
+                                         map, err)));
     }
 }
 
