@@ -52,7 +52,7 @@ class ClockSampler:
 
     def start(self):
         cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "50"]
         if self.device_id:
             cmd += ["-i", self.device_id]
         try:
@@ -63,6 +63,11 @@ class ClockSampler:
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # the timed region starts once the sampler is running (its first row has arrived), so
+        # that even a region of a few tenths of a second is sampled every 50 ms
+        t0 = time.perf_counter()
+        while not self.rows and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -799,7 +804,7 @@ def run_nuwnu(args, fw, rank, world, local_rank, dist_on):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
