@@ -897,8 +897,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_spread_col(
 // pass moves the low band of a tile only if it starts a segment (tz % zseg == 0) and the high
 // band only if it ends one.
 template <typename T, int W, int D, int A, int SIDES, int FM>
-__global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
-                                                   int64_t ring_slot, T *__restrict__ grid) {
+__global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *ring, int64_t ring_slot,
+                                                   T *__restrict__ grid) {
     constexpr int HL = W / 2;
     const int64_t t = blockIdx.x;
     int s[3], w[3], tc[3];
@@ -932,57 +932,78 @@ __global__ void __launch_bounds__(256) k_halo_fold(Geom g, T *__restrict__ ring,
     // multiply-high division where they are needed
     const FastDiv f0 = (FM & 1) ? tile_div<0, false>(g, w[0]) : tile_div<0, true>(g, w[0]);
     const FastDiv f1 = (FM & 2) ? tile_div<1, false>(g, w[1]) : tile_div<1, true>(g, w[1]);
-    for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        int e[3];
-        if constexpr (A == 0) {
-            const int q = i / NA;
-            e[0] = i - q * NA;
-            e[2] = D == 3 ? f1.div(q) : 0;
-            e[1] = q - e[2] * ext[1];
-        } else if constexpr (A == 1) {
-            const int q = f0.div(i);
-            e[0] = i - q * ext[0];
-            e[2] = q / NA;
-            e[1] = q - e[2] * NA;
-        } else {
-            const int q = f0.div(i);
-            e[0] = i - q * ext[0];
-            e[2] = f1.div(q);
-            e[1] = q - e[2] * ext[1];
-        }
-        // e along folded axes counts from the tile's first cell
+    // IL cells per thread and step: their source loads, then their destinations' loads, then the
+    // stores, so that each thread keeps several memory accesses in flight (a cell read here is
+    // never written in the same pass, and no cell is written twice)
+    constexpr int IL = 4;
+    for (int i0 = threadIdx.x; i0 < count; i0 += IL * blockDim.x) {
+        T v[IL];
+        T *dst[IL];
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            if ((FM >> b) & 1) e[b] += HL;
-        if (SIDES == 2) e[A] += HL;   // high band only
-        const bool low = e[A] < HL;
-        if (low ? !do_low : !do_high) continue;
-        if (!low) e[A] += w[A];      // high band: HL + w .. w + W - 1
-        const T v = src_ring[ring_index<W, D>(e[0], e[1], e[2], w[0], w[1], w[2])];
-        // the same cell in the neighbour's extended region
-        int f[3] = {e[0], e[1], e[2]}, fw[3] = {w[0], w[1], w[2]};
-        int64_t u;
-        if (low) {
-            f[A] = e[A] + lo_w;
-            fw[A] = lo_w;
-            u = t_lo;
-        } else {
-            f[A] = e[A] - w[A];
-            fw[A] = hi_w;
-            u = t_hi;
-        }
-        bool inside = true;
+        for (int k = 0; k < IL; ++k) {
+            dst[k] = nullptr;
+            v[k] = T(0);
+            const int i = i0 + k * blockDim.x;
+            if (i >= count) continue;
+            int e[3];
+            if constexpr (A == 0) {
+                const int q = i / NA;
+                e[0] = i - q * NA;
+                e[2] = D == 3 ? f1.div(q) : 0;
+                e[1] = q - e[2] * ext[1];
+            } else if constexpr (A == 1) {
+                const int q = f0.div(i);
+                e[0] = i - q * ext[0];
+                e[2] = q / NA;
+                e[1] = q - e[2] * NA;
+            } else {
+                const int q = f0.div(i);
+                e[0] = i - q * ext[0];
+                e[2] = f1.div(q);
+                e[1] = q - e[2] * ext[1];
+            }
+            // e along folded axes counts from the tile's first cell
 #pragma unroll
-        for (int b = 0; b < D; ++b)
-            if (b != A && !((FM >> b) & 1)) inside = inside && f[b] >= HL && f[b] < HL + fw[b];
-        if (inside) {
-            int gc[3] = {0, 0, 0};
+            for (int b = 0; b < 3; ++b)
+                if ((FM >> b) & 1) e[b] += HL;
+            if (SIDES == 2) e[A] += HL;   // high band only
+            const bool low = e[A] < HL;
+            if (low ? !do_low : !do_high) continue;
+            if (!low) e[A] += w[A];      // high band: HL + w .. w + W - 1
+            v[k] = src_ring[ring_index<W, D>(e[0], e[1], e[2], w[0], w[1], w[2])];
+            // the same cell in the neighbour's extended region
+            int f[3] = {e[0], e[1], e[2]}, fw[3] = {w[0], w[1], w[2]};
+            int64_t u;
+            if (low) {
+                f[A] = e[A] + lo_w;
+                fw[A] = lo_w;
+                u = t_lo;
+            } else {
+                f[A] = e[A] - w[A];
+                fw[A] = hi_w;
+                u = t_hi;
+            }
+            bool inside = true;
 #pragma unroll
-            for (int b = 0; b < D; ++b) gc[b] = (b == A ? (low ? lo_s : hi_s) : s[b]) + f[b] - HL;
-            grid[((int64_t)gc[2] * g.nf[1] + gc[1]) * g.nf[0] + gc[0]] += v;
-        } else {
-            ring[u * ring_slot + ring_index<W, D>(f[0], f[1], f[2], fw[0], fw[1], fw[2])] += v;
+            for (int b = 0; b < D; ++b)
+                if (b != A && !((FM >> b) & 1)) inside = inside && f[b] >= HL && f[b] < HL + fw[b];
+            if (inside) {
+                int gc[3] = {0, 0, 0};
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+                    gc[b] = (b == A ? (low ? lo_s : hi_s) : s[b]) + f[b] - HL;
+                dst[k] = grid + ((int64_t)gc[2] * g.nf[1] + gc[1]) * g.nf[0] + gc[0];
+            } else {
+                dst[k] = ring + u * ring_slot +
+                         ring_index<W, D>(f[0], f[1], f[2], fw[0], fw[1], fw[2]);
+            }
         }
+        T d[IL];
+#pragma unroll
+        for (int k = 0; k < IL; ++k) d[k] = dst[k] ? *dst[k] : T(0);
+#pragma unroll
+        for (int k = 0; k < IL; ++k)
+            if (dst[k]) *dst[k] = d[k] + v[k];
     }
 }
 
