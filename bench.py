@@ -908,6 +908,11 @@ def main():
     t_step = max_over_ranks(ms / args.steps / 1e3, dist_on, "cuda")
     value = replica_throughput(N, world, t_step)
 
+    # e2e through the host-buffer entry point (before the oracle leg, whose host threads and
+    # allocations would share the host with the copies)
+    dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 2)
+    dt_e2e = max_over_ranks(dt_e2e, dist_on, "cuda")
+
     # the oracle on the host cores (a bounded sample of mask rows), and the GPU's rho at the same
     # rows for the accuracy report
     cpu, rho_err = None, None
@@ -946,9 +951,6 @@ def main():
                 "stages_ms": {k: round(v[0] / max(v[1], 1), 3) for k, v in st.items()}}
             del x
 
-    # e2e through the host-buffer entry point
-    dt_e2e, h2d, d2h = time_e2e(plan, pts_np, args.e2e_steps, 1)
-    dt_e2e = max_over_ranks(dt_e2e, dist_on, "cuda")
     plan.close()
 
     # ---- per-stage roofline ------------------------------------------------------------------
