@@ -25,7 +25,7 @@
 // the points of tile t into the tile's extended region (the tile plus W/2 cells below and
 // W - W/2 above on each axis, where a window of a point of the tile can reach) in shared memory,
 // with no bounds checks. It writes the tile's own cells to the grid and the rest of the region
-// (its ring) to a per-tile ring buffer; k_halo_add then adds to every cell near a tile border the
+// (its ring) to a per-tile ring buffer; k_halo_fold then adds to every cell near a tile border the
 // ring values that the neighbouring tiles' points put there, in a fixed order.
 //
 // Ring layout of one tile (extents E_a = w_a + W, HL = W/2): the extended region is walked plane
