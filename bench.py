@@ -668,6 +668,61 @@ def run_accuracy(args, wl):
 
 
 NUWNU_METRIC = "points/s per NUwNU loss+grad eval (free boundaries, real wavevectors)"
+UWNU_METRIC = "weights/s per UwNU loss+grad eval (grid weights, constraints at real frequencies)"
+
+
+def constraint_side_bytes(dim: int, n_k: int, fine: int, esize: int, dq: bool) -> dict:
+    """Algorithmic bytes of the constraint-side kernels of the UwNU / NUwNU plans, per launch:
+    interp reads the fine grid once and each constraint's cell, position, target, weight
+    (and deconvolution factor) and caller index, and writes its strength and S; spread reads
+    each constraint's cell, position and strength and writes the fine grid once."""
+    per_k_in = dim * 4 + dim * esize
+    return {"interp": fine * 2 * esize + n_k * (per_k_in + 2 * esize + (esize if dq else 0) + 4
+                                               + 3 * esize),
+            "spread": n_k * (per_k_in + 2 * esize) + fine * 2 * esize}
+
+
+def constraint_side_roofline(stages: dict, dim: int, n_k: int, fine: int, esize: int, dq: bool,
+                             calls: int, workload: str) -> dict:
+    """HBM roofline of the slower of the two constraint-side kernels (stage times from the
+    plan's event timers, per evaluation; the interp stage also holds the partial-sum kernel).
+    traffic: the ncu DRAM bytes of that kernel on this workload from profiles/traffic.json,
+    when they were taken on the current sources of the weights-on-a-grid plans."""
+    byt = constraint_side_bytes(dim, n_k, fine, esize, dq)
+    peaks = load_peaks() if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    ms = {k: stages[k][0] / max(calls, 1) for k in ("interp", "spread")}
+    dom = max(ms, key=ms.get)
+    achieved = byt[dom] / (ms[dom] / 1e3) / 1e9
+    traffic = None
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            entry = json.load(f).get(workload, {}).get(dom)
+        try:
+            current = _kernel_source_hash("uwnu")
+        except OSError:
+            current = None
+        if entry and current and entry.get("source_hash") == current:
+            traffic = entry.get("bytes_per_launch")
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+            "algorithmic_bytes": byt[dom], "ms_per_launch": ms[dom],
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs, burst)"}
+
+
+def profile_stages(plan, steps: int, run) -> dict:
+    """Per-stage device time of `steps` further evaluations, from the plan's event timers."""
+    import torch
+    plan.profile(True)
+    plan.profile_read()
+    for _ in range(steps):
+        run()
+    torch.cuda.synchronize()
+    st = plan.profile_read()
+    plan.profile(False)
+    return st
 
 
 def run_reference_free(args, fw, rank):
@@ -754,6 +809,11 @@ def run_nuwnu(args, fw, rank, world, local_rank, dist_on):
         s.synchronize()
     dt_e2e = max_over_ranks((time.perf_counter() - t0) / max(args.e2e_steps, 1), dist_on, "cuda")
     info = plan.info
+    stages = profile_stages(plan, args.steps, lambda: plan.loss_grad(pts))
+    esize = 4 if fw.dtype == "f32" else 8
+    fine = int(np.prod(info["n_fine"][:fw.dim]))
+    roof = constraint_side_roofline(stages, fw.dim, k.shape[0], fine, esize, True, args.steps,
+                                    fw.name)
     # accuracy on a subsample the oracle finishes in seconds: 4096 points, all wavevectors
     acc = None
     cpu = None
@@ -791,10 +851,154 @@ def run_nuwnu(args, fw, rank, world, local_rank, dist_on):
                        "n_grid": info["n_grid"][:fw.dim], "n_fine": info["n_fine"][:fw.dim],
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy_vs_oracle": acc,
+            "stages_ms": {k_: round(v[0] / max(v[1], 1), 4) for k_, v in stages.items()},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": world * fw.n_points / dt_e2e, "unit": "points/s",
                     "h2d_bytes_per_step": int(pts_np.nbytes),
                     "d2h_bytes_per_step": int(pts_np.nbytes + 8), "ms_per_step": 1e3 * dt_e2e},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_reference_field(args, fw, rank):
+    """The oracle as the reference arm of a UwNU workload: each step is the loss and gradient of
+    all weights at a bounded sample of the constraints (direct sums), extrapolated to all."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    c = fw.weights().astype(np.float64).reshape(-1)
+    nu = fw.frequencies()
+    S0, W = fw.targets(nu)
+    pos = oracle.grid_points(fw.shape)
+    n_s = min(fw.n_k, 8 * oracle_sample_rows(oracle.threads()))
+    times = []
+    for step in range(args.warmup + args.steps):
+        sl = slice((step * n_s) % fw.n_k, (step * n_s) % fw.n_k + n_s)
+        t0 = time.perf_counter()
+        oracle.weight_loss_grad_k(pos, c, 2.0 * np.pi * nu[sl], S0[sl], W[sl])
+        if step >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    rate = 2.0 * fw.n_weights * n_s / t
+    t_eval = 2.0 * fw.n_weights * fw.n_k / rate
+    value = fw.n_weights / t_eval
+    line = {
+        "impl": "reference", "metric": UWNU_METRIC, "value": value, "unit": "weights/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+        "ms_per_eval_extrapolated": 1e3 * t_eval, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": fw.name, "n_weights": fw.n_weights, "n_modes": fw.n_k,
+                   "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "weights/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": "per step: loss and gradient of all %d weights at %d of the "
+                                   "%d constraints by direct sums; evaluation extrapolated as "
+                                   "2 M^d N_K pair terms" % (fw.n_weights, n_s, fw.n_k)},
+        "e2e": {"value": value, "unit": "weights/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_uwnu(args, fw, rank, world, local_rank, dist_on):
+    """Real weights on a uniform grid with constraints at real frequencies (fresco_uwnu_*)."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    c_np = fw.weights()
+    nu = fw.frequencies()
+    S0, W = fw.targets(nu)
+    c = torch.from_numpy(c_np).cuda()
+    plan = fresco.Uwnu(fw.shape, nu, S0, W, fw.dtype, tol=fw.tol, upsample=fw.upsample)
+    s = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        loss, grad = plan.loss_grad(c)
+    torch.cuda.synchronize()
+    l0 = plan.launch_count()
+    clocks = ClockSampler(_device_selector(local_rank))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist_on:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(args.steps):
+        loss, grad = plan.loss_grad(c)
+    e1.record(s)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_step = max_over_ranks(e0.elapsed_time(e1) / args.steps / 1e3, dist_on, "cuda")
+    launches = plan.launch_count() - l0
+    # e2e: pinned host weights in, loss and gradient out, every step
+    h_c = torch.from_numpy(c_np).pin_memory()
+    h_grad = torch.empty(c_np.shape, dtype=h_c.dtype).pin_memory()
+    h_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        c.copy_(h_c, non_blocking=True)
+        loss, grad = plan.loss_grad(c)
+        h_grad.copy_(grad, non_blocking=True)
+        h_loss.copy_(loss, non_blocking=True)
+        s.synchronize()
+    dt_e2e = max_over_ranks((time.perf_counter() - t0) / max(args.e2e_steps, 1), dist_on, "cuda")
+    info = plan.info
+    stages = profile_stages(plan, args.steps, lambda: plan.loss_grad(c))
+    esize = 4 if fw.dtype == "f32" else 8
+    fine = int(np.prod(info["n_fine"][:fw.dim]))
+    roof = constraint_side_roofline(stages, fw.dim, fw.n_k, fine, esize, False, args.steps,
+                                    fw.name)
+    # accuracy and the oracle's rate on a sample the oracle finishes in seconds: every weight
+    # at 512 of the constraints (a plan of its own on the GPU)
+    acc = None
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        n_s = 512
+        sub = slice(0, n_s)
+        with fresco.Uwnu(fw.shape, nu[sub], S0[sub], W[sub], fw.dtype, tol=fw.tol,
+                         upsample=fw.upsample) as p2:
+            l_g, g_g = p2.loss_grad(c)
+            S_g = p2.S().double().cpu().numpy()
+            l_g, g_g = l_g.item(), g_g.double().cpu().numpy().reshape(-1)
+        c_used = c.double().cpu().numpy().reshape(-1)
+        t0 = time.perf_counter()
+        l_o, g_o, S_o, _ = oracle.weight_loss_grad_k(oracle.grid_points(fw.shape), c_used,
+                                                      2.0 * np.pi * nu[sub], S0[sub], W[sub])
+        t_or = time.perf_counter() - t0
+        acc = {"constraints": n_s, "S_rel_l2": float(np.linalg.norm(S_g - S_o) /
+                                                     np.linalg.norm(S_o)),
+               "loss_rel": abs(l_g - l_o) / abs(l_o),
+               "grad_rel_l2": float(np.linalg.norm(g_g - g_o) / np.linalg.norm(g_o))}
+        rate = 2.0 * fw.n_weights * n_s / t_or      # pair terms / s (rho and gradient)
+        cpu = {"value": fw.n_weights / (2.0 * fw.n_weights * fw.n_k / rate), "unit": "weights/s",
+               "cores": oracle.threads(), "kind": "oracle",
+               "sample": "loss and gradient of all %d weights at the first %d constraints "
+                         "(%.1f s); full evaluation extrapolated as 2 M^d N_K pair terms"
+                         % (fw.n_weights, n_s, t_or)}
+    plan.close()
+    if rank == 0:
+        line = {
+            "metric": UWNU_METRIC, "value": world * fw.n_weights / t_step, "unit": "weights/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": fw.dtype, "data": "synthetic",
+            "config": {"workload": fw.name, "n_weights": fw.n_weights, "dim": fw.dim,
+                       "n_modes": fw.n_k, "nu_max": fw.nu_max, "tol": fw.tol,
+                       "upsample": fw.upsample, "width": info["width"],
+                       "n_fine": info["n_fine"][:fw.dim],
+                       "l2": "fine grid (%.0f MB) below L2; inputs re-read from HBM each step"
+                             % (fine * 2 * esize / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy_vs_oracle": acc,
+            "stages_ms": {k_: round(v[0] / max(v[1], 1), 4) for k_, v in stages.items()},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * fw.n_weights / dt_e2e, "unit": "weights/s",
+                    "h2d_bytes_per_step": int(c_np.nbytes),
+                    "d2h_bytes_per_step": int(c_np.nbytes + 8), "ms_per_step": 1e3 * dt_e2e},
             "clocks": clk,
             "gpu_launches": launches,
         }
@@ -833,13 +1037,17 @@ def main():
     from paper_2305_15693_gb300 import inputs
     ens = None
     fw = None
+    fld = None
     try:
         ens = inputs.ensemble_workload(args.workload)
     except KeyError:
         try:
             fw = inputs.free_workload(args.workload)
         except KeyError:
-            wl = inputs.workload(args.workload)
+            try:
+                fld = inputs.field_workload(args.workload)
+            except KeyError:
+                wl = inputs.workload(args.workload)
             if args.upsample:
                 wl.upsample = args.upsample
             if args.grad_mode:
@@ -850,13 +1058,15 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.accuracy:
-        if fw is not None or ens is not None:
+        if fw is not None or ens is not None or fld is not None:
             raise SystemExit("--accuracy takes a periodic single-problem workload")
         run_accuracy(args, wl)
         return
 
     if args.impl == "reference":
-        if ens is not None:
+        if fld is not None:
+            run_reference_field(args, fld, rank)
+        elif ens is not None:
             run_reference_ensemble(args, ens, rank)
         elif fw is not None:
             run_reference_free(args, fw, rank)
@@ -876,6 +1086,12 @@ def main():
     from paper_2305_15693_gb300 import fresco
     fresco.load()
 
+    if fld is not None:
+        run_uwnu(args, fld, rank, world, local_rank, dist_on)
+        if dist_on:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
     if fw is not None:
         run_nuwnu(args, fw, rank, world, local_rank, dist_on)
         if dist_on:
@@ -1052,20 +1268,35 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def traffic_sources() -> list:
+# Library sources that neither build nor size the single-plan kernels of the traffic entries
+# (sort, spread, mask, interp): the solvers, the allocation-free entry point, the pair term, the
+# shared-memory probe and the weights-on-a-grid / type-3 plans.
+OTHER_PLAN_SOURCES = ("fresco_batch_lbfgs.cu", "fresco_lbfgs.cu", "fresco_noalloc.cu",
+                      "fresco_pair.cu", "fresco_probe.cu", "fresco_uwnu.cu")
+
+
+# The sources of the weights-on-a-grid / type-3 plans' constraint-side kernels (interp, spread).
+UWNU_SOURCES = ("fresco_internal.h", "fresco_kernels.cuh", "fresco_uwnu.cu")
+
+
+def traffic_sources(family: str = "single") -> list:
     """The sources that build (and size the launches of) the kernels the traffic entries
-    describe: every CUDA source and header of the library."""
+    describe: for the single plans every CUDA source and header of the library but
+    OTHER_PLAN_SOURCES; for "uwnu" the constraint-side kernels' UWNU_SOURCES."""
+    if family == "uwnu":
+        return sorted(UWNU_SOURCES)
     import glob
     csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
     return sorted(os.path.basename(f) for f in glob.glob(os.path.join(csrc, "*"))
-                  if f.endswith((".cu", ".cuh", ".h")))
+                  if f.endswith((".cu", ".cuh", ".h"))
+                  and os.path.basename(f) not in OTHER_PLAN_SOURCES)
 
 
-def _kernel_source_hash() -> str:
+def _kernel_source_hash(family: str = "single") -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2305_15693_gb300", "csrc")
-    for name in traffic_sources():
+    for name in traffic_sources(family):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())

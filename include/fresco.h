@@ -403,8 +403,8 @@ fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, c
                               void *stream);
 /* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
  * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. The loss
- * is summed in a fixed order and repeats bitwise; the gradient's type-1 spread adds with floating-
- * point atomics, so repeated calls agree only to rounding (not bitwise). */
+ * is summed in a fixed order and the type-1 spread adds in fixed point (integers scaled per tile
+ * by a power of two below the tile's largest possible cell sum), so repeated calls agree bitwise. */
 fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad);
 fresco_status fresco_uwu_destroy(fresco_uwu_t u);
 
@@ -428,15 +428,18 @@ fresco_status fresco_uwu_destroy(fresco_uwu_t u);
  * the smallest even 2-3-5-7-smooth size >= max(sigma M_a, 2 w). FRESCO_ERR_ARG for invalid
  * arguments, FRESCO_ERR_UNSUPPORTED when the fine grid exceeds 4e9 cells or w > 16. The plan owns
  * copies of the constraints, its fine grid and its cuFFT plan; it computes asynchronously on
- * `stream`. */
+ * `stream`. At plan time the host orders the constraints by the tile of the fine grid that holds
+ * them (32 x 32 cells in 2D, 16 x 8 x 8 in 3D, at most half of each axis) and lists for every
+ * tile the constraints whose kernel support meets it: the interpolation runs in that order, and
+ * the spread runs one block per tile, accumulating in shared memory and storing each cell once. */
 typedef struct fresco_uwnu_s *fresco_uwnu_t;
 fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid, int64_t n_k,
                                const double *nu, const double *S0, const double *W,
                                const fresco_opts *opts, void *stream);
 /* d_c: device [M_{d-1}]..[M_0] of the plan's precision (x fastest, not all zero); d_loss: device
  * double; d_grad: device, same layout as d_c, or NULL. Asynchronous on the plan's stream. The loss
- * is summed in a fixed order and repeats bitwise; the gradient's type-1 spread adds with floating-
- * point atomics, so repeated calls agree only to rounding (not bitwise). */
+ * is summed in a fixed order and the type-1 spread adds in fixed point (integers scaled per tile
+ * by a power of two below the tile's largest possible cell sum), so repeated calls agree bitwise. */
 fresco_status fresco_uwnu_loss_grad(fresco_uwnu_t u, const void *d_c, double *d_loss,
                                     void *d_grad);
 /* After fresco_uwnu_loss_grad: S at the constraints into d_S (device [n_k], plan precision, in
@@ -445,6 +448,18 @@ fresco_status fresco_uwnu_get_S(fresco_uwnu_t u, void *d_S);
 /* Kernel width, shape parameter beta and fine grid (n_fine[3], 1 beyond dim); any may be NULL. */
 fresco_status fresco_uwnu_get_info(fresco_uwnu_t u, int *width, double *beta, int *n_fine);
 fresco_status fresco_uwnu_destroy(fresco_uwnu_t u);
+/* Per-stage timing with CUDA events on the plan's stream, as fresco_profile: enable != 0 records
+ * events around each stage of every later evaluation; _read synchronises, returns accumulated
+ * milliseconds and call counts per stage and resets them. ms and counts have room for
+ * FRESCO_UWNU_N_STAGES entries (counts may be NULL). Stages, in order: 0 the points onto their
+ * grid (point plans only), 1 the weights onto the fine grid and the inverse FFT, 2 the
+ * interpolation at the constraints (S, loss, strengths), 3 the strengths onto the fine grid,
+ * 4 the forward FFT and the gradient on the grid, 5 the gradient at the points (point plans). */
+#define FRESCO_UWNU_N_STAGES 6
+fresco_status fresco_uwnu_profile(fresco_uwnu_t u, int enable);
+fresco_status fresco_uwnu_profile_read(fresco_uwnu_t u, double *ms, int64_t *counts);
+/* Number of libfresco kernels launched through this plan so far (cuFFT's own not included). */
+int64_t fresco_uwnu_launch_count(fresco_uwnu_t u);
 
 /* ---- Points at free positions, constraints at real wavevectors (NUwNU, Methods "Analytical
  * gradients": type-3 transforms of the positions; the main text's quasicrystal targets have
@@ -472,8 +487,8 @@ fresco_status fresco_nuwnu_plan(fresco_nuwnu_t *out, int dim, const double *box,
  * origin on some axis is latched in the device error word (FRESCO_ERR_BOUNDS from
  * fresco_nuwnu_status_check), a NaN or infinite coordinate as
  * FRESCO_ERR_NONFINITE; the results are then undefined. Asynchronous on the plan's stream. The
- * loss repeats bitwise; the type-1 spread of the gradient adds with floating-point atomics, so
- * repeated gradients agree to rounding. */
+ * loss repeats bitwise; the constraint-side spread adds in fixed point, and the points' spread and
+ * gradient are those of the single plans. */
 fresco_status fresco_nuwnu_loss_grad(fresco_nuwnu_t p, const void *d_points, double *d_loss,
                                      void *d_grad);
 /* After fresco_nuwnu_loss_grad: S at the constraints into d_S (device [n_k], plan precision, in
@@ -486,6 +501,9 @@ fresco_status fresco_nuwnu_status_check(fresco_nuwnu_t p);
 fresco_status fresco_nuwnu_get_info(fresco_nuwnu_t p, int *width, int *n_grid, int *n_fine,
                                     int64_t *launches);
 fresco_status fresco_nuwnu_destroy(fresco_nuwnu_t p);
+/* Per-stage timing of the plan's evaluations, stages as fresco_uwnu_profile. */
+fresco_status fresco_nuwnu_profile(fresco_nuwnu_t p, int enable);
+fresco_status fresco_nuwnu_profile_read(fresco_nuwnu_t p, double *ms, int64_t *counts);
 
 /* Free everything the plan owns. Synchronises its stream first. NULL is accepted. */
 fresco_status fresco_destroy(fresco_plan_t p);

@@ -1022,6 +1022,13 @@ fresco_status check_point_ptr(fresco_plan_s *p, const void *ptr) {
 // ---- profiling event pool --------------------------------------------------------------------
 // ---- point sets spread for other transforms (type-3 plans) -------------------------------------
 
+void fresco::es_poly_table(int w, double beta, EsPoly<float> &out) {
+    es_poly<float>(w, beta, out);
+}
+void fresco::es_poly_table(int w, double beta, EsPoly<double> &out) {
+    es_poly<double>(w, beta, out);
+}
+
 void fresco::kernel_ft_at(int w, double beta, const double *theta, int64_t n, double *out) {
     const int nq = 200;
     std::vector<double> x, wq;

@@ -329,6 +329,9 @@ fresco_status point_side_spread(PointSide &ps, const T *pts, cudaStream_t s, int
 // Psi(theta) = integral psi(u) cos(theta u) du of the kernel of width w (u in cells), at n real
 // frequencies theta (radians per cell).
 void kernel_ft_at(int w, double beta, const double *theta, int64_t n, double *out);
+// The piecewise polynomials of the kernel of width w and shape beta that es_weights evaluates.
+void es_poly_table(int w, double beta, EsPoly<float> &out);
+void es_poly_table(int w, double beta, EsPoly<double> &out);
 
 #ifdef __CUDACC__
 // Knuth's two-sum: s + e == a + b exactly (round to nearest, no overflow)

@@ -13,10 +13,18 @@
 //   type 2: U[k] = c_mt / Psi(mt) at k = mt mod n_f, U <- inverse FFT(U), rho~_q = sum_l U[l]
 //           psi(n_f x_q - l) over the w^d cells of the kernel's support;
 //   type 1: U[l] = sum_q C_q psi(n_f x_q - l), U <- forward FFT(U), G(mt) = U[mt mod n_f] / Psi(mt).
-// Psi is the kernel's Fourier transform at integer frequencies (fresco_kernel_ft). The
-// constraints are few next to the pixels, so both NUFFT passes run one thread per constraint
-// straight on the fine grid in global memory (float atomics for the spread) and evaluate the
-// exponential-of-semicircle kernel directly.
+// Psi is the kernel's Fourier transform at integer frequencies (fresco_kernel_ft).
+//
+// The constraints' positions are fixed for the plan's life, so the plan orders them once, on the
+// host, by the tile of the fine grid that holds their cell, and lists for every tile the
+// constraints whose kernel support meets it. The type-2 interpolation then runs over the
+// constraints in that order (in 2D a block stages its tile's window of U in shared memory), and
+// the type-1 spread runs one block per tile: the block adds its list's contributions into the
+// tile in shared memory, in fixed point, and stores every cell of the tile once, so U needs
+// neither global atomics nor zeroing and the result repeats bitwise. Within a tile (or a list)
+// the host deals the constraints over the shared-memory banks their first cells fall in, so the
+// lanes of a warp meet distinct banks. Both evaluate the kernel with the plan's piecewise
+// polynomials (es_weights).
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -42,6 +50,7 @@ namespace {
 
 constexpr double kPiU = 3.141592653589793238462643383279502884;
 constexpr int kUBlocks = 1024;
+constexpr int kUWinBlocks = 16384;
 
 // The plan's rules for the fine grid and the kernel (the same error estimate of the
 // exponential-of-semicircle kernel as fresco_plan): w = ceil(ln(1/eps) / (pi sqrt(1 - 1/sigma))),
@@ -65,22 +74,6 @@ template <typename T>
 using CxT = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
 
 __device__ __forceinline__ int wrap_index(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
-// psi(x1 + k), k = 0..W-1, psi(u) = exp(beta (sqrt(1 - (2u/W)^2) - 1)) for |u| < W/2, and the
-// first cell of the support relative to the point's cell
-template <typename T, int W>
-__device__ __forceinline__ int kernel_row(T frac, T beta, T (&wt)[W]) {
-    T x1;
-    const int c0 = support_start<T, W>(frac, x1);
-    const T s = T(2) / T(W);
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        const T z = (x1 + T(k)) * s;
-        const T q = T(1) - z * z;
-        wt[k] = q > T(0) ? exp(beta * (sqrt(q) - T(1))) : T(0);
-    }
-    return c0;
-}
 
 __device__ __forceinline__ double ublock_sum(double v) {
     __shared__ double ws[32];
@@ -156,35 +149,63 @@ __global__ void __launch_bounds__(256) k_un_fill(UGrid g, int64_t cells, const T
     }
 }
 
-// type 2, step 3, and the loss: rho~_q by interpolation, S_q, the loss and F partials, and the
-// type-1 strengths C_q = 4 W (S - S0) rho~ / rho0
+// Tiles of the fine grid for the type-1 spread: T[a] cells per axis, at most half the axis (so
+// a kernel support, at most half the axis too, meets a tile at one periodic shift only), and
+// nt[a] tiles per axis (the last one may be shorter). Tile t = (tz nt[1] + ty) nt[0] + tx.
+struct UTiles {
+    int T[3];
+    int nt[3];
+};
+constexpr int kUTileCells = 1024;   // T[0] T[1] T[2] at most
+
+// the weight of support cell k of one axis out of the unrolled row (k known only at run time)
+template <typename T, int W>
+__device__ __forceinline__ T pick_weight(const T (&w)[W], int k) {
+    T r = w[0];
+#pragma unroll
+    for (int i = 1; i < W; ++i)
+        if (i == k) r = w[i];
+    return r;
+}
+
+// type 2, step 3, and the loss, over the constraints in tile order (slot q; perm[q] is the
+// caller's index): rho~_q by interpolation, S_q, the loss and F partials, and the type-1
+// strengths C_q = 4 W (S - S0) rho~ / rho0, which stay in tile order for the spread.
 // dq (optional, point plans with constraints at real wavevectors): a per-constraint factor that
 // multiplies the interpolated sum before S is formed (the deconvolution of the points' own
 // spreading kernel); then C_q = 4 W (S - S0) dq rho_q / norm. norm = scal[0] (rho0, or N).
 template <typename T, int W, int D>
-__global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
+__global__ void __launch_bounds__(256) k_un_interp(UGrid g, EsPoly<T> ep, int64_t n_k,
                                                    const int *__restrict__ tcell,
-                                                   const T *__restrict__ tfrac, T beta,
+                                                   const T *__restrict__ tfrac,
                                                    const CxT<T> *__restrict__ U,
                                                    const T *__restrict__ s0,
                                                    const T *__restrict__ wq,
                                                    const double *__restrict__ scal,
                                                    const T *__restrict__ dq,
+                                                   const int *__restrict__ perm,
                                                    CxT<T> *__restrict__ coef, T *__restrict__ S_out,
                                                    double *__restrict__ part) {
-    const double rho0 = scal[0];
-    const T inv_rho0 = (T)(1.0 / rho0);
-    double lsum = 0.0, fsum = 0.0;
+    const T inv_rho0 = (T)(1.0 / scal[0]);
+    DotAcc<T> lacc, facc;   // the loss and F partial sums (no FP64 pipe in the FP32 loop)
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_k;
          q += (int64_t)gridDim.x * blockDim.x) {
         T wt[D][W];
         int st[3] = {0, 0, 0};
 #pragma unroll
-        for (int a = 0; a < D; ++a) st[a] = tcell[q * D + a] + kernel_row<T, W>(tfrac[q * D + a], beta, wt[a]);
+        for (int a = 0; a < D; ++a) {
+            T x1;
+            st[a] = tcell[q * D + a] + support_start<T, W>(tfrac[q * D + a], x1);
+            es_weights<T, W>(ep, x1, wt[a]);
+        }
         T re = T(0), im = T(0);
-        if constexpr (D == 2) {
+        const int n2 = D == 3 ? W : 1;
+        for (int k2 = 0; k2 < n2; ++k2) {
+            const int64_t pl = D == 3 ? (int64_t)wrap_index(st[2] + k2, g.nf[2]) * g.nf[1] : 0;
+            T pr = T(0), pm = T(0);
+#pragma unroll
             for (int k1 = 0; k1 < W; ++k1) {
-                const int64_t row = (int64_t)wrap_index(st[1] + k1, g.nf[1]) * g.nf[0];
+                const int64_t row = (pl + wrap_index(st[1] + k1, g.nf[1])) * g.nf[0];
                 T rr = T(0), ri = T(0);
 #pragma unroll
                 for (int k0 = 0; k0 < W; ++k0) {
@@ -192,28 +213,12 @@ __global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
                     rr = fma(wt[0][k0], v.x, rr);
                     ri = fma(wt[0][k0], v.y, ri);
                 }
-                re = fma(wt[1][k1], rr, re);
-                im = fma(wt[1][k1], ri, im);
+                pr = fma(wt[1][k1], rr, pr);
+                pm = fma(wt[1][k1], ri, pm);
             }
-        } else {
-            for (int k2 = 0; k2 < W; ++k2) {
-                const int64_t pl = (int64_t)wrap_index(st[2] + k2, g.nf[2]) * g.nf[1];
-                T pr = T(0), pm = T(0);
-                for (int k1 = 0; k1 < W; ++k1) {
-                    const int64_t row = (pl + wrap_index(st[1] + k1, g.nf[1])) * g.nf[0];
-                    T rr = T(0), ri = T(0);
-#pragma unroll
-                    for (int k0 = 0; k0 < W; ++k0) {
-                        const CxT<T> v = U[row + wrap_index(st[0] + k0, g.nf[0])];
-                        rr = fma(wt[0][k0], v.x, rr);
-                        ri = fma(wt[0][k0], v.y, ri);
-                    }
-                    pr = fma(wt[1][k1], rr, pr);
-                    pm = fma(wt[1][k1], ri, pm);
-                }
-                re = fma(wt[2][k2], pr, re);
-                im = fma(wt[2][k2], pm, im);
-            }
+            const T w2 = D == 3 ? pick_weight<T, W>(wt[D - 1], k2) : T(1);
+            re = fma(w2, pr, re);
+            im = fma(w2, pm, im);
         }
         T dk = T(1);
         if (dq) {
@@ -222,52 +227,228 @@ __global__ void __launch_bounds__(256) k_un_interp(UGrid g, int64_t n_k,
             im *= dk;
         }
         const T S = (re * re + im * im) * inv_rho0;
-        const double d = (double)S - (double)s0[q];
-        const double w = (double)wq[q];
-        lsum = fma(w * d, d, lsum);
-        fsum = fma(w * (double)S, d, fsum);
-        const T h = (T)(4.0 * w * d / rho0) * dk;
+        const T d = S - s0[q];
+        const T wd = wq[q] * d;
+        lacc.add(wd, d);
+        facc.add(wq[q] * S, d);
+        const T h = T(4) * wd * inv_rho0 * dk;
         coef[q] = CxT<T>{h * re, h * im};
-        S_out[q] = S;
+        S_out[perm[q]] = S;
     }
-    const double bl = ublock_sum(lsum);
-    const double bf = ublock_sum(fsum);
+    const double bl = ublock_sum(lacc.value());
+    const double bf = ublock_sum(facc.value());
     if (threadIdx.x == 0) {
         part[blockIdx.x] = bl;
         part[gridDim.x + blockIdx.x] = bf;
     }
 }
 
-// type 1, step 1: U[l] += C_q psi(n_f x_q - l) over the support of every constraint
-template <typename T, int W, int D>
-__global__ void __launch_bounds__(256) k_un_spread(UGrid g, int64_t n_k,
-                                                   const int *__restrict__ tcell,
-                                                   const T *__restrict__ tfrac, T beta,
-                                                   const CxT<T> *__restrict__ coef,
-                                                   CxT<T> *__restrict__ U) {
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_k;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        T wt[D][W];
-        int st[3] = {0, 0, 0};
+constexpr int kUWinEdge = 48;   // the 2D window edge: tile edge (at most 32) + w (at most 16)
+
+// Blocks per multiprocessor the window interpolation asks for: FP32 at widths 4 to 7 fits in 32
+// registers a thread without spilling, so eight blocks (all 64 warps) stay resident.
+template <typename T, int W>
+constexpr int kWinMinBlocks = sizeof(T) == 4 && W >= 4 && W <= 7 ? 8 : 1;
+
+// The same in 2D from shared memory: a block takes the constraints of one home tile at a time
+// (slots hoff[t] .. hoff[t + 1]), stages the window of U their supports cover (the tile and
+// floor(w / 2) cells before it, w - floor(w / 2) after, wrapped) as real and imaginary planes,
+// and sums each support there.
+template <typename T, int W>
+__global__ void __launch_bounds__(256, kWinMinBlocks<T, W>)
+    k_un_interp_win(UGrid g, UTiles tl, EsPoly<T> ep, int64_t n_tiles,
+                    const int64_t *__restrict__ hoff, const int *__restrict__ tcell,
+                    const T *__restrict__ tfrac, const CxT<T> *__restrict__ U,
+                    const T *__restrict__ s0, const T *__restrict__ wq,
+                    const double *__restrict__ scal, const T *__restrict__ dq,
+                    const int *__restrict__ perm, CxT<T> *__restrict__ coef,
+                    T *__restrict__ S_out, double *__restrict__ part) {
+    constexpr int kWin = kUWinEdge * kUWinEdge;
+    __shared__ T sw[2 * kWin];   // real parts, then imaginary parts at + kWin
+    const T inv_rho0 = (T)(1.0 / scal[0]);
+    DotAcc<T> lacc, facc;   // the loss and F partial sums (no FP64 pipe in the FP32 loop)
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t q0 = hoff[t], q1 = hoff[t + 1];
+        if (q0 == q1) continue;
+        const int tx = (int)(t % tl.nt[0]), ty = (int)(t / tl.nt[0]);
+        const int ws0 = tx * tl.T[0] - W / 2, ws1 = ty * tl.T[1] - W / 2;
+        const int wl0 = min(tl.T[0], g.nf[0] - tx * tl.T[0]) + W;
+        const int wl1 = min(tl.T[1], g.nf[1] - ty * tl.T[1]) + W;
+        __syncthreads();   // the previous tile's sums are done with the window
+        for (int i = threadIdx.x; i < wl0 * wl1; i += blockDim.x) {
+            const int y = i / wl0, x = i - y * wl0;
+            const CxT<T> v = U[(int64_t)wrap_index(ws1 + y, g.nf[1]) * g.nf[0] +
+                               wrap_index(ws0 + x, g.nf[0])];
+            sw[i] = v.x;
+            sw[kWin + i] = v.y;
+        }
+        __syncthreads();
+        for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+            T wx[W], wy[W], x1;
+            const int x0 = tcell[q * 2] + support_start<T, W>(tfrac[q * 2], x1) - ws0;
+            es_weights<T, W>(ep, x1, wx);
+            const int y0 = tcell[q * 2 + 1] + support_start<T, W>(tfrac[q * 2 + 1], x1) - ws1;
+            es_weights<T, W>(ep, x1, wy);
+            const T *row = sw + y0 * wl0 + x0;
+            T re = T(0), im = T(0);
 #pragma unroll
-        for (int a = 0; a < D; ++a) st[a] = tcell[q * D + a] + kernel_row<T, W>(tfrac[q * D + a], beta, wt[a]);
-        const CxT<T> cq = coef[q];
-        const int n2 = D == 3 ? W : 1;
-        for (int k2 = 0; k2 < n2; ++k2) {
-            const int64_t pl = D == 3 ? (int64_t)wrap_index(st[2] + k2, g.nf[2]) * g.nf[1] : 0;
-            const T w2 = D == 3 ? wt[D - 1][k2] : T(1);
             for (int k1 = 0; k1 < W; ++k1) {
-                const int64_t row = (pl + wrap_index(st[1] + k1, g.nf[1])) * g.nf[0];
-                const T w12 = w2 * wt[1][k1];
+                T rr = T(0), ri = T(0);
 #pragma unroll
                 for (int k0 = 0; k0 < W; ++k0) {
-                    const T w = w12 * wt[0][k0];
-                    T *cell = reinterpret_cast<T *>(U + row + wrap_index(st[0] + k0, g.nf[0]));
-                    atomicAdd(cell, w * cq.x);
-                    atomicAdd(cell + 1, w * cq.y);
+                    rr = fma(wx[k0], row[k0], rr);
+                    ri = fma(wx[k0], row[kWin + k0], ri);
+                }
+                re = fma(wy[k1], rr, re);
+                im = fma(wy[k1], ri, im);
+                row += wl0;
+            }
+            T dk = T(1);
+            if (dq) {
+                dk = dq[q];
+                re *= dk;
+                im *= dk;
+            }
+            const T S = (re * re + im * im) * inv_rho0;
+            const T d = S - s0[q];
+            const T wd = wq[q] * d;
+            lacc.add(wd, d);
+            facc.add(wq[q] * S, d);
+            const T h = T(4) * wd * inv_rho0 * dk;
+            coef[q] = CxT<T>{h * re, h * im};
+            S_out[perm[q]] = S;
+        }
+    }
+    const double bl = ublock_sum(lacc.value());
+    const double bf = ublock_sum(facc.value());
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = bl;
+        part[gridDim.x + blockIdx.x] = bf;
+    }
+}
+
+// Fixed-point cells of the spread: 32-bit integers for FP32 plans, 64-bit for FP64. A tile's
+// strengths are scaled by 2^s, s the largest exponent that keeps its largest possible cell sum,
+// (the most supports that cover one of its cells) x (its largest strength component), below
+// 2^kBits; every term is rounded to an integer and the integer adds need no rounding order, so
+// the spread repeats bitwise. The quantum is 2^-kBits of that bound (about 2^-24 of the largest
+// strength for a few dozen covering supports in FP32), finer than the rounding of a float sum
+// of as many terms.
+template <typename T>
+struct SpreadFixed;
+template <>
+struct SpreadFixed<float> {
+    using I = int;
+    static constexpr int kBits = 30;
+    static __device__ __forceinline__ I to_fixed(float v) { return __float2int_rn(v); }
+    static __device__ __forceinline__ void add(I *p, I v) { atomicAdd(p, v); }
+    static __device__ __forceinline__ float from_fixed(I v, int s) { return ldexpf((float)v, -s); }
+};
+template <>
+struct SpreadFixed<double> {
+    using I = long long;
+    static constexpr int kBits = 62;
+    static __device__ __forceinline__ I to_fixed(double v) { return __double2ll_rn(v); }
+    static __device__ __forceinline__ void add(I *p, I v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    }
+    static __device__ __forceinline__ double from_fixed(I v, int s) { return ldexp((double)v, -s); }
+};
+
+// type 1, step 1: one block per tile of U. The block adds C_q psi(n_f x_q - l) of every
+// constraint on the tile's list (slots ent[toff[t] .. toff[t + 1]), in bank order) into the
+// tile's cells in shared memory, clipped to the tile, in fixed point (SpreadFixed; kcov[t]: the
+// most supports that cover one cell of the tile), then stores all of the tile's cells. Every
+// cell of U belongs to one tile, so U is written in full, zeros included.
+template <typename T, int W, int D>
+__global__ void __launch_bounds__(256) k_un_spread(UGrid g, UTiles tl, EsPoly<T> ep,
+                                                   int64_t n_tiles,
+                                                   const int64_t *__restrict__ toff,
+                                                   const int *__restrict__ ent,
+                                                   const int *__restrict__ kcov,
+                                                   const int *__restrict__ tcell,
+                                                   const T *__restrict__ tfrac,
+                                                   const CxT<T> *__restrict__ coef,
+                                                   CxT<T> *__restrict__ U) {
+    using F = SpreadFixed<T>;
+    using I = typename F::I;
+    __shared__ I sh[2 * kUTileCells];   // real parts, then imaginary parts at + kUTileCells
+    __shared__ T s_max[8];
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int tx = (int)(t % tl.nt[0]);
+        const int ty = (int)((t / tl.nt[0]) % tl.nt[1]);
+        const int tz = (int)(t / ((int64_t)tl.nt[0] * tl.nt[1]));
+        const int o[3] = {tx * tl.T[0], ty * tl.T[1], tz * tl.T[2]};
+        const int len[3] = {min(tl.T[0], g.nf[0] - o[0]), min(tl.T[1], g.nf[1] - o[1]),
+                            min(tl.T[2], g.nf[2] - o[2])};
+        const int cells = len[0] * len[1] * len[2];
+        const int64_t e0 = toff[t], e1 = toff[t + 1];
+        // the tile's largest strength component, and its scale
+        T m = T(0);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const CxT<T> c = coef[ent[e]];
+            m = fmax(m, fmax(fabs(c.x), fabs(c.y)));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            sh[i] = 0;
+            sh[kUTileCells + i] = 0;
+        }
+        __syncthreads();
+        m = s_max[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, s_max[w]);
+        int sc = 0;
+        if (m > T(0)) {
+            int ex;
+            frexp((double)kcov[t] * (double)m, &ex);   // kcov m < 2^ex
+            sc = F::kBits - ex;
+        }
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int64_t q = ent[e];
+            T wt[D][W];
+            int lo[3] = {0, 0, 0}, k0[3] = {0, 0, 0}, k1[3] = {1, 1, 1};
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                T x1;
+                // first support cell relative to the tile, at the one shift that meets it
+                int d = tcell[q * D + a] + support_start<T, W>(tfrac[q * D + a], x1) - o[a];
+                if (d >= len[a]) d -= g.nf[a];
+                else if (d + W <= 0) d += g.nf[a];
+                lo[a] = d;
+                k0[a] = max(0, -d);
+                k1[a] = min(W, len[a] - d);
+                es_weights<T, W>(ep, x1, wt[a]);
+            }
+            const CxT<T> c = coef[q];
+            const T csr = ldexp(c.x, sc), csi = ldexp(c.y, sc);
+            for (int k2 = k0[2]; k2 < k1[2]; ++k2) {
+                const T w2 = D == 3 ? pick_weight<T, W>(wt[D - 1], k2) : T(1);
+                for (int k1y = k0[1]; k1y < k1[1]; ++k1y) {
+                    const T wy = w2 * pick_weight<T, W>(wt[1], k1y);
+                    const T cr = wy * csr, ci = wy * csi;
+                    const int row = ((lo[2] + k2) * len[1] + lo[1] + k1y) * len[0] + lo[0];
+#pragma unroll
+                    for (int k = 0; k < W; ++k)
+                        if (k >= k0[0] && k < k1[0]) {
+                            F::add(sh + row + k, F::to_fixed(wt[0][k] * cr));
+                            F::add(sh + kUTileCells + row + k, F::to_fixed(wt[0][k] * ci));
+                        }
                 }
             }
         }
+        __syncthreads();
+        const int64_t sx = g.nf[0], sxy = (int64_t)g.nf[0] * g.nf[1];
+        for (int i = threadIdx.x; i < cells; i += blockDim.x) {
+            const int x = i % len[0];
+            const int r = i / len[0];
+            const int y = r % len[1];
+            const int z = r / len[1];
+            U[(int64_t)(o[2] + z) * sxy + (int64_t)(o[1] + y) * sx + o[0] + x] =
+                CxT<T>{F::from_fixed(sh[i], sc), F::from_fixed(sh[kUTileCells + i], sc)};
+        }
+        __syncthreads();
     }
 }
 
@@ -287,47 +468,6 @@ __global__ void __launch_bounds__(256) k_un_grad(UGrid g, int64_t cells, const T
         const T ip = pixel_site<T>(g, m, ip0, ip1, ip2, f);
         grad[m] = U[f].x * ip - coef * c[m];
     }
-}
-
-template <typename T, int W>
-cudaError_t launch_un_interp(const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
-                             T beta, const void *U, const T *s0, const T *wq, const double *scal,
-                             const T *dq, void *coef, T *S, double *part, int nb, cudaStream_t s) {
-    if (g.dim == 2)
-        k_un_interp<T, W, 2><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta, (const CxT<T> *)U,
-                                                s0, wq, scal, dq, (CxT<T> *)coef, S, part);
-    else
-        k_un_interp<T, W, 3><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta, (const CxT<T> *)U,
-                                                s0, wq, scal, dq, (CxT<T> *)coef, S, part);
-    return cudaGetLastError();
-}
-
-template <typename T, int W>
-cudaError_t launch_un_spread(const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
-                             T beta, const void *coef, void *U, int nb, cudaStream_t s) {
-    if (g.dim == 2)
-        k_un_spread<T, W, 2><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta,
-                                                (const CxT<T> *)coef, (CxT<T> *)U);
-    else
-        k_un_spread<T, W, 3><<<nb, 256, 0, s>>>(g, n_k, tcell, tfrac, beta,
-                                                (const CxT<T> *)coef, (CxT<T> *)U);
-    return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t un_interp(int width, const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
-                      T beta, const void *U, const T *s0, const T *wq, const double *scal,
-                      const T *dq, void *coef, T *S, double *part, int nb, cudaStream_t s) {
-    FRESCO_WIDTH_SWITCH(width, return (launch_un_interp<T, WW>(g, n_k, tcell, tfrac, beta, U, s0,
-                                                               wq, scal, dq, coef, S, part, nb,
-                                                               s)));
-}
-
-template <typename T>
-cudaError_t un_spread(int width, const UGrid &g, int64_t n_k, const int *tcell, const T *tfrac,
-                      T beta, const void *coef, void *U, int nb, cudaStream_t s) {
-    FRESCO_WIDTH_SWITCH(width, return (launch_un_spread<T, WW>(g, n_k, tcell, tfrac, beta, coef,
-                                                               U, nb, s)));
 }
 
 fresco_status un_status(cudaError_t e) {
@@ -350,23 +490,98 @@ fresco_status un_status(cudaError_t e) {
 
 struct fresco_uwnu_s {
     UGrid g{};
+    UTiles tl{};
     int precision = FRESCO_F32, width = 0;
     double beta = 0.0;
-    int64_t cells = 0, fine = 0, n_k = 0;
+    int64_t cells = 0, fine = 0, n_k = 0, n_tiles = 0, n_ent = 0;
     int nb = 1;   // blocks of the per-constraint kernels
     cudaStream_t stream = nullptr;
     std::vector<void *> allocs;
+    EsPoly<float> p32{};
+    EsPoly<double> p64{};
     void *ip[3] = {nullptr, nullptr, nullptr};   // 1 / Psi_a(nu), nu = 0..M_a/2
-    int *tcell = nullptr;                        // [n_k][dim] fine cell of each target
-    void *tfrac = nullptr;                       // [n_k][dim] position inside it, [0, 1)
-    void *s0 = nullptr, *wq = nullptr, *S = nullptr, *coef = nullptr, *U = nullptr;
-    double *part = nullptr, *scal = nullptr;     // scal: rho0, loss, F sum
+    // the constraints in tile order (slot q): caller's index, fine cell and position inside it
+    int *perm = nullptr;                         // [n_k]
+    int *tcell = nullptr;                        // [n_k][dim]
+    void *tfrac = nullptr;                       // [n_k][dim], [0, 1)
+    void *s0 = nullptr, *wq = nullptr, *dq = nullptr;   // [n_k] in tile order (dq: point plans)
+    void *S = nullptr;                           // [n_k] in the caller's order
+    void *coef = nullptr, *U = nullptr;          // strengths in tile order; the fine grid
+    int64_t *hoff = nullptr;                     // [n_tiles + 1] slots of each home tile
+    int64_t *toff = nullptr;                     // [n_tiles + 1] list offsets of the tiles
+    int *ent = nullptr;                          // [n_ent] constraint slots, tile by tile
+    int *kcov = nullptr;                         // [n_tiles] most supports covering one cell
+    double *part = nullptr, *scal = nullptr;     // scal: rho0 (or N), loss, F sum
     cufftHandle fft = 0;
     bool have_fft = false;
     bool evaluated = false;
+    int64_t launches = 0;
+    fresco::StageProfile prof;
 };
 
+// Stages of the per-stage timing (fresco_uwnu_profile, fresco_nuwnu_profile)
+enum {
+    UST_POINT_SPREAD = 0,   // point plans: bounds check, binning and spreading of the points
+    UST_TYPE2 = 1,          // rho0, the weights (or the points' grid) onto U, inverse FFT
+    UST_INTERP = 2,         // interpolation at the constraints, S, loss, strengths
+    UST_SPREAD = 3,         // the strengths onto the tiles of U
+    UST_TYPE1 = 4,          // forward FFT and the weight gradient (or the points' field)
+    UST_POINT_INTERP = 5,   // point plans: kernel-derivative interpolation at the points
+    UST_COUNT = 6
+};
+static_assert((int)UST_COUNT <= (int)fresco::ST_COUNT, "the stage timers hold every stage");
+
 namespace {
+
+template <typename T, int W>
+cudaError_t launch_un_interp(const fresco_uwnu_s *u, const EsPoly<T> &ep, cudaStream_t s) {
+    const auto *U = (const CxT<T> *)u->U;
+    if (u->g.dim == 2)
+        k_un_interp_win<T, W><<<u->nb, 256, 0, s>>>(
+            u->g, u->tl, ep, u->n_tiles, u->hoff, u->tcell, (const T *)u->tfrac, U,
+            (const T *)u->s0, (const T *)u->wq, u->scal, (const T *)u->dq, u->perm,
+            (CxT<T> *)u->coef, (T *)u->S, u->part);
+    else
+        k_un_interp<T, W, 3><<<u->nb, 256, 0, s>>>(
+            u->g, ep, u->n_k, u->tcell, (const T *)u->tfrac, U, (const T *)u->s0,
+            (const T *)u->wq, u->scal, (const T *)u->dq, u->perm, (CxT<T> *)u->coef, (T *)u->S,
+            u->part);
+    return cudaGetLastError();
+}
+
+template <typename T, int W>
+cudaError_t launch_un_spread(const fresco_uwnu_s *u, const EsPoly<T> &ep, cudaStream_t s) {
+    const unsigned nb = (unsigned)std::min<int64_t>(u->n_tiles, 152 * 64);
+    if (u->g.dim == 2)
+        k_un_spread<T, W, 2><<<nb, 256, 0, s>>>(u->g, u->tl, ep, u->n_tiles, u->toff, u->ent,
+                                                u->kcov, u->tcell, (const T *)u->tfrac,
+                                                (const CxT<T> *)u->coef, (CxT<T> *)u->U);
+    else
+        k_un_spread<T, W, 3><<<nb, 256, 0, s>>>(u->g, u->tl, ep, u->n_tiles, u->toff, u->ent,
+                                                u->kcov, u->tcell, (const T *)u->tfrac,
+                                                (const CxT<T> *)u->coef, (CxT<T> *)u->U);
+    return cudaGetLastError();
+}
+
+template <typename T>
+const EsPoly<T> &un_poly(const fresco_uwnu_s *u) {
+    return *reinterpret_cast<const EsPoly<T> *>(sizeof(T) == 4 ? (const void *)&u->p32
+                                                                : (const void *)&u->p64);
+}
+
+// rho~ at the constraints with S, the loss partials and the strengths (one launch)
+template <typename T>
+cudaError_t un_interp(const fresco_uwnu_s *u, cudaStream_t s) {
+    const EsPoly<T> &ep = un_poly<T>(u);
+    FRESCO_WIDTH_SWITCH(u->width, return (launch_un_interp<T, WW>(u, ep, s)));
+}
+
+// the strengths onto every tile of U (one launch)
+template <typename T>
+cudaError_t un_spread(const fresco_uwnu_s *u, cudaStream_t s) {
+    const EsPoly<T> &ep = un_poly<T>(u);
+    FRESCO_WIDTH_SWITCH(u->width, return (launch_un_spread<T, WW>(u, ep, s)));
+}
 
 bool un_alloc(fresco_uwnu_s *u, void **p, size_t bytes) {
     if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
@@ -382,25 +597,235 @@ void un_free(fresco_uwnu_s *u) {
     if (!u) return;
     if (u->stream) cudaStreamSynchronize(u->stream);
     else cudaDeviceSynchronize();
+    u->prof.release();
     if (u->have_fft) cufftDestroy(u->fft);
     for (void *p : u->allocs) cudaFree(p);
     delete u;
 }
 
+// The spread's tiles: up to 32 x 32 cells in 2D and 16 x 8 x 8 in 3D, at most half of each
+// axis (the fine grid is even and at least 2w per axis).
+UTiles un_tiles(const UGrid &g) {
+    static const int t2[3] = {32, 32, 1}, t3[3] = {16, 8, 8};
+    UTiles tl{};
+    for (int a = 0; a < 3; ++a) {
+        tl.T[a] = a < g.dim ? std::min(g.dim == 2 ? t2[a] : t3[a], g.nf[a] / 2) : 1;
+        tl.nt[a] = (g.nf[a] + tl.T[a] - 1) / tl.T[a];
+    }
+    return tl;
+}
+
+// Builds the constraint side of a plan: the deconvolution tables, the kernel polynomials, the
+// constraints' fine cells and positions (from FP64), their tile order and the tiles' lists, and
+// the FFT plan. dq (point plans; may be null): a factor per constraint in the caller's order.
 template <typename T>
-fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, const double *W) {
+fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, const double *W,
+                       const double *dq) {
     using C2 = CxT<T>;
     const UGrid &g = u->g;
     const int dim = g.dim;
     const int64_t nk = u->n_k;
-    bool ok = un_alloc(u, (void **)&u->tcell, sizeof(int) * (size_t)(nk * dim)) &&
+    const int w = u->width;
+    u->tl = un_tiles(g);
+    const UTiles &tl = u->tl;
+    u->n_tiles = (int64_t)tl.nt[0] * tl.nt[1] * tl.nt[2];
+    if (dim == 2)   // the window interpolation: a block per home tile (up to kUWinBlocks)
+        u->nb = (int)std::max<int64_t>(1, std::min<int64_t>(u->n_tiles, kUWinBlocks));
+    fresco::es_poly_table(w, u->beta, u->p32);
+    fresco::es_poly_table(w, u->beta, u->p64);
+
+    // fine cell and fraction of every target x = -nu / M (modulo 1), in the caller's order
+    std::vector<int> cell((size_t)(nk * dim));
+    std::vector<double> frac((size_t)(nk * dim));
+    for (int64_t q = 0; q < nk; ++q)
+        for (int a = 0; a < dim; ++a) {
+            const double x = -nu[q * dim + a] / (double)g.M[a];
+            const double t = (x - std::floor(x)) * (double)g.nf[a];
+            const double c = std::floor(t);
+            int64_t ci = (int64_t)c % g.nf[a];
+            if (ci < 0) ci += g.nf[a];
+            cell[(size_t)(q * dim + a)] = (int)ci;
+            frac[(size_t)(q * dim + a)] = t - c;
+        }
+    // first support cell (relative to the constraint's cell) as the kernels round it: in T
+    auto support_first = [&](double f) {
+        const T ft = (T)f;
+        return (int)std::ceil((double)(ft - (T)0.5 * (T)w));
+    };
+    // Reorders ids[0, n) by dealing them round-robin over the residues key(id) mod 32, so that
+    // consecutive ids (the lanes of a warp) have distinct residues wherever the range allows.
+    std::vector<int> by_key;
+    std::vector<int> keys;
+    auto deal_by_residue = [&](int *ids, int64_t n, auto &&key) {
+        if (n < 2) return;
+        int bucket[33] = {0};
+        keys.resize((size_t)n);
+        for (int64_t j = 0; j < n; ++j) {
+            keys[(size_t)j] = (int)(((key(ids[j]) % 32) + 32) % 32);
+            ++bucket[keys[(size_t)j] + 1];
+        }
+        for (int b = 0; b < 32; ++b) bucket[b + 1] += bucket[b];
+        int next[32];
+        for (int b = 0; b < 32; ++b) next[b] = bucket[b];
+        by_key.resize((size_t)n);
+        for (int64_t j = 0; j < n; ++j) by_key[(size_t)next[keys[(size_t)j]]++] = ids[j];
+        int64_t e = 0;
+        for (int r = 0; e < n; ++r)
+            for (int b = 0; b < 32; ++b)
+                if (bucket[b] + r < bucket[b + 1]) ids[e++] = by_key[(size_t)(bucket[b] + r)];
+    };
+    auto tile_box = [&](int64_t t, int o[3], int len[3]) {
+        const int tc[3] = {(int)(t % tl.nt[0]), (int)((t / tl.nt[0]) % tl.nt[1]),
+                           (int)(t / ((int64_t)tl.nt[0] * tl.nt[1]))};
+        for (int a = 0; a < 3; ++a) {
+            o[a] = tc[a] * tl.T[a];
+            len[a] = std::min(tl.T[a], g.nf[a] - o[a]);
+        }
+    };
+    // tile order: a stable counting sort by the tile that holds the constraint's cell (its home
+    // tile), then, in 2D, each home tile's constraints dealt over the shared-memory banks of
+    // their first window cell in the interpolation (window rows of len_0 + w cells starting at
+    // the tile's origin - floor(w / 2))
+    std::vector<int64_t> cnt((size_t)u->n_tiles + 1, 0);
+    std::vector<int64_t> home((size_t)nk);
+    for (int64_t q = 0; q < nk; ++q) {
+        int64_t t = 0;
+        for (int a = dim - 1; a >= 0; --a)
+            t = t * tl.nt[a] + cell[(size_t)(q * dim + a)] / tl.T[a];
+        home[(size_t)q] = t;
+        ++cnt[(size_t)t + 1];
+    }
+    for (int64_t t = 0; t < u->n_tiles; ++t) cnt[(size_t)t + 1] += cnt[(size_t)t];
+    std::vector<int64_t> hoff(cnt);
+    std::vector<int> perm((size_t)nk);
+    for (int64_t q = 0; q < nk; ++q) perm[(size_t)cnt[(size_t)home[(size_t)q]]++] = (int)q;
+    if (dim == 2)
+        for (int64_t t = 0; t < u->n_tiles; ++t) {
+            int o[3], len[3];
+            tile_box(t, o, len);
+            const int wl0 = len[0] + w;
+            deal_by_residue(&perm[(size_t)hoff[(size_t)t]], hoff[(size_t)t + 1] - hoff[(size_t)t],
+                            [&](int q) {
+                                const int x0 = cell[(size_t)q * 2] - o[0] + w / 2 +
+                                               support_first(frac[(size_t)q * 2]);
+                                const int y0 = cell[(size_t)q * 2 + 1] - o[1] + w / 2 +
+                                               support_first(frac[(size_t)q * 2 + 1]);
+                                return (int64_t)y0 * wl0 + x0;
+                            });
+        }
+    std::vector<int> scell((size_t)(nk * dim));
+    std::vector<T> sfrac((size_t)(nk * dim)), s0((size_t)nk), wq((size_t)nk), sdq;
+    if (dq) sdq.resize((size_t)nk);
+    for (int64_t i = 0; i < nk; ++i) {
+        const int64_t q = perm[(size_t)i];
+        for (int a = 0; a < dim; ++a) {
+            scell[(size_t)(i * dim + a)] = cell[(size_t)(q * dim + a)];
+            sfrac[(size_t)(i * dim + a)] = (T)frac[(size_t)(q * dim + a)];
+        }
+        s0[(size_t)i] = (T)S0[q];
+        wq[(size_t)i] = (T)W[q];
+        if (dq) sdq[(size_t)i] = (T)dq[q];
+    }
+    // the tiles' lists. With the position f in [0, 1] (after rounding to T), the support's first
+    // cell is cell + ceil(f - w/2), so the support lies in [cell - floor(w/2), cell + w -
+    // floor(w/2)]; every tile that range meets (per axis, wrapped) lists the constraint, and the
+    // kernel clips the exact support to the tile.
+    // calls fn(tile) for every tile that lists constraint slot i
+    auto for_tiles = [&](int64_t i, auto &&fn) {
+        int ta[3][8], na[3];
+        for (int a = 0; a < 3; ++a) {
+            na[a] = 0;
+            if (a >= dim) {
+                ta[a][na[a]++] = 0;
+                continue;
+            }
+            const int c = scell[(size_t)(i * dim + a)];
+            for (int k = -(w / 2); k <= w - w / 2; ++k) {
+                int x = c + k;
+                x = x < 0 ? x + g.nf[a] : (x >= g.nf[a] ? x - g.nf[a] : x);
+                const int t = x / tl.T[a];
+                bool seen = false;
+                for (int j = 0; j < na[a]; ++j) seen |= ta[a][j] == t;
+                if (!seen && na[a] < 8) ta[a][na[a]++] = t;
+            }
+        }
+        for (int z = 0; z < na[2]; ++z)
+            for (int y = 0; y < na[1]; ++y)
+                for (int x = 0; x < na[0]; ++x)
+                    fn(((int64_t)ta[2][z] * tl.nt[1] + ta[1][y]) * tl.nt[0] + ta[0][x]);
+    };
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int64_t i = 0; i < nk; ++i) for_tiles(i, [&](int64_t t) { ++cnt[(size_t)t + 1]; });
+    for (int64_t t = 0; t < u->n_tiles; ++t) cnt[(size_t)t + 1] += cnt[(size_t)t];
+    u->n_ent = cnt[(size_t)u->n_tiles];
+    if (u->n_ent >= (int64_t)1 << 31) return FRESCO_ERR_UNSUPPORTED;
+    std::vector<int64_t> toff(cnt);
+    std::vector<int> ent((size_t)std::max<int64_t>(u->n_ent, 1));
+    for (int64_t i = 0; i < nk; ++i)
+        for_tiles(i, [&](int64_t t) { ent[(size_t)cnt[(size_t)t]++] = (int)i; });
+    // Bank order inside each list. The spread's threads step through their supports in lockstep
+    // (row by row, the x offsets unrolled), so a thread's shared-memory bank at every step is its
+    // first cell's local address plus an offset common to the warp, modulo 32: each list is
+    // dealt over those residues.
+    for (int64_t t = 0; t < u->n_tiles; ++t) {
+        int o[3], len[3];
+        tile_box(t, o, len);
+        deal_by_residue(&ent[(size_t)toff[(size_t)t]], toff[(size_t)t + 1] - toff[(size_t)t],
+                        [&](int i) {
+                            int st[3] = {0, 0, 0};
+                            for (int a = 0; a < dim; ++a) {
+                                int d = scell[(size_t)i * dim + a] +
+                                        support_first((double)sfrac[(size_t)i * dim + a]) - o[a];
+                                if (d >= len[a]) d -= g.nf[a];
+                                else if (d + w <= 0) d += g.nf[a];
+                                st[a] = a == 0 ? d : std::max(d, 0);
+                            }
+                            return ((int64_t)st[2] * len[1] + st[1]) * len[0] + st[0];
+                        });
+    }
+    // the most supports that cover one cell of each tile (the spread's fixed-point headroom)
+    std::vector<int> kcov((size_t)u->n_tiles, 0);
+    {
+        std::vector<int> cov;
+        for (int64_t t = 0; t < u->n_tiles; ++t) {
+            if (toff[(size_t)t + 1] == toff[(size_t)t]) continue;
+            int o[3], len[3];
+            tile_box(t, o, len);
+            cov.assign((size_t)len[0] * len[1] * len[2], 0);
+            for (int64_t e = toff[(size_t)t]; e < toff[(size_t)t + 1]; ++e) {
+                const int64_t i = ent[(size_t)e];
+                int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+                for (int a = 0; a < dim; ++a) {
+                    int d = scell[(size_t)i * dim + a] +
+                            support_first((double)sfrac[(size_t)i * dim + a]) - o[a];
+                    if (d >= len[a]) d -= g.nf[a];
+                    else if (d + w <= 0) d += g.nf[a];
+                    lo[a] = std::max(d, 0);
+                    hi[a] = std::min(d + w, len[a]);
+                }
+                for (int z = lo[2]; z < hi[2]; ++z)
+                    for (int y = lo[1]; y < hi[1]; ++y)
+                        for (int x = lo[0]; x < hi[0]; ++x)
+                            ++cov[((size_t)z * len[1] + y) * len[0] + x];
+            }
+            kcov[(size_t)t] = *std::max_element(cov.begin(), cov.end());
+        }
+    }
+
+    bool ok = un_alloc(u, (void **)&u->perm, sizeof(int) * (size_t)nk) &&
+              un_alloc(u, (void **)&u->tcell, sizeof(int) * (size_t)(nk * dim)) &&
               un_alloc(u, &u->tfrac, sizeof(T) * (size_t)(nk * dim)) &&
               un_alloc(u, &u->s0, sizeof(T) * (size_t)nk) &&
               un_alloc(u, &u->wq, sizeof(T) * (size_t)nk) &&
+              (!dq || un_alloc(u, &u->dq, sizeof(T) * (size_t)nk)) &&
               un_alloc(u, &u->S, sizeof(T) * (size_t)nk) &&
               un_alloc(u, &u->coef, sizeof(C2) * (size_t)nk) &&
               un_alloc(u, &u->U, sizeof(C2) * (size_t)u->fine) &&
-              un_alloc(u, (void **)&u->part, sizeof(double) * 2 * kUBlocks) &&
+              un_alloc(u, (void **)&u->hoff, sizeof(int64_t) * hoff.size()) &&
+              un_alloc(u, (void **)&u->toff, sizeof(int64_t) * toff.size()) &&
+              un_alloc(u, (void **)&u->ent, sizeof(int) * ent.size()) &&
+              un_alloc(u, (void **)&u->kcov, sizeof(int) * kcov.size()) &&
+              un_alloc(u, (void **)&u->part, sizeof(double) * 2 * std::max(kUBlocks, u->nb)) &&
               un_alloc(u, (void **)&u->scal, sizeof(double) * 4);
     for (int a = 0; a < 3 && ok; ++a)
         ok = un_alloc(u, &u->ip[a], sizeof(T) * (size_t)(g.M[a] / 2 + 1));
@@ -409,35 +834,23 @@ fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, con
         const int64_t n_nu = g.M[a] / 2 + 1;
         std::vector<double> psi((size_t)n_nu, 1.0);
         if (a < dim) {
-            const fresco_status st = fresco_kernel_ft(u->width, u->beta, g.nf[a], n_nu, psi.data());
+            const fresco_status st = fresco_kernel_ft(w, u->beta, g.nf[a], n_nu, psi.data());
             if (st) return st;
         }
         std::vector<T> ipt((size_t)n_nu);
         for (int64_t i = 0; i < n_nu; ++i) ipt[(size_t)i] = (T)(1.0 / psi[(size_t)i]);
         UN_CUDA(cudaMemcpy(u->ip[a], ipt.data(), sizeof(T) * ipt.size(), cudaMemcpyHostToDevice));
     }
-    {   // targets x = -nu / M (modulo 1) on the fine grid: cell and fraction, from FP64
-        std::vector<int> cell((size_t)(nk * dim));
-        std::vector<T> frac((size_t)(nk * dim)), s0((size_t)nk), w((size_t)nk);
-        for (int64_t q = 0; q < nk; ++q) {
-            for (int a = 0; a < dim; ++a) {
-                const double x = -nu[q * dim + a] / (double)g.M[a];
-                const double t = (x - std::floor(x)) * (double)g.nf[a];
-                double c = std::floor(t);
-                double f = t - c;
-                int64_t ci = (int64_t)c % g.nf[a];
-                if (ci < 0) ci += g.nf[a];
-                cell[(size_t)(q * dim + a)] = (int)ci;
-                frac[(size_t)(q * dim + a)] = (T)f;
-            }
-            s0[(size_t)q] = (T)S0[q];
-            w[(size_t)q] = (T)W[q];
-        }
-        UN_CUDA(cudaMemcpy(u->tcell, cell.data(), sizeof(int) * cell.size(), cudaMemcpyHostToDevice));
-        UN_CUDA(cudaMemcpy(u->tfrac, frac.data(), sizeof(T) * frac.size(), cudaMemcpyHostToDevice));
-        UN_CUDA(cudaMemcpy(u->s0, s0.data(), sizeof(T) * s0.size(), cudaMemcpyHostToDevice));
-        UN_CUDA(cudaMemcpy(u->wq, w.data(), sizeof(T) * w.size(), cudaMemcpyHostToDevice));
-    }
+    UN_CUDA(cudaMemcpy(u->perm, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->tcell, scell.data(), sizeof(int) * scell.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->tfrac, sfrac.data(), sizeof(T) * sfrac.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->s0, s0.data(), sizeof(T) * s0.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->wq, wq.data(), sizeof(T) * wq.size(), cudaMemcpyHostToDevice));
+    if (dq) UN_CUDA(cudaMemcpy(u->dq, sdq.data(), sizeof(T) * sdq.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->hoff, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->toff, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->ent, ent.data(), sizeof(int) * ent.size(), cudaMemcpyHostToDevice));
+    UN_CUDA(cudaMemcpy(u->kcov, kcov.data(), sizeof(int) * kcov.size(), cudaMemcpyHostToDevice));
     const cufftType type = sizeof(T) == 4 ? CUFFT_C2C : CUFFT_Z2Z;
     if (dim == 2) UN_CUFFT(cufftPlan2d(&u->fft, g.nf[1], g.nf[0], type));
     else UN_CUFFT(cufftPlan3d(&u->fft, g.nf[2], g.nf[1], g.nf[0], type));
@@ -463,30 +876,36 @@ fresco_status un_eval(fresco_uwnu_s *u, const T *c, double *loss, T *grad) {
     cudaStream_t s = u->stream;
     const unsigned pb = (unsigned)std::min<int64_t>((u->cells + 255) / 256, 152 * 16);
     const T *ip0 = (const T *)u->ip[0], *ip1 = (const T *)u->ip[1], *ip2 = (const T *)u->ip[2];
-    const T beta = (T)u->beta;
-    // rho0 = sum c^2
-    k_un_sumsq<T><<<kUBlocks, 256, 0, s>>>(c, u->cells, u->part);
-    k_un_sum<<<1, 256, 0, s>>>(u->part, kUBlocks, 1, u->scal);
-    // type 2: rho~ at the constraints, with S, the loss and the type-1 strengths
-    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
-    k_un_fill<T><<<pb, 256, 0, s>>>(g, u->cells, c, ip0, ip1, ip2, (C2 *)u->U);
-    fresco_status st = un_fft<T>(u, CUFFT_INVERSE);
-    if (st) return st;
-    UN_CUDA(un_interp<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, beta, u->U,
-                         (const T *)u->s0, (const T *)u->wq, u->scal, (const T *)nullptr, u->coef,
-                         (T *)u->S, u->part, u->nb, s));
-    k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 2, u->scal + 1);
-    UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    {   // rho0 = sum c^2; type 2: the weights over Psi onto U, inverse FFT
+        fresco::StageScope sc(u->prof, s, UST_TYPE2);
+        k_un_sumsq<T><<<kUBlocks, 256, 0, s>>>(c, u->cells, u->part);
+        k_un_sum<<<1, 256, 0, s>>>(u->part, kUBlocks, 1, u->scal);
+        UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
+        k_un_fill<T><<<pb, 256, 0, s>>>(g, u->cells, c, ip0, ip1, ip2, (C2 *)u->U);
+        const fresco_status st = un_fft<T>(u, CUFFT_INVERSE);
+        if (st) return st;
+    }
+    {   // rho~ at the constraints, with S, the loss and the type-1 strengths
+        fresco::StageScope sc(u->prof, s, UST_INTERP);
+        UN_CUDA(un_interp<T>(u, s));
+        k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 2, u->scal + 1);
+        UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+    u->launches += 5;
     u->evaluated = true;
     if (!grad) return un_status(cudaGetLastError());
-    // type 1: the strengths back onto the pixels, then the weight gradient
-    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
-    UN_CUDA(un_spread<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, beta, u->coef, u->U,
-                         u->nb, s));
-    st = un_fft<T>(u, CUFFT_FORWARD);
-    if (st) return st;
-    k_un_grad<T><<<pb, 256, 0, s>>>(g, u->cells, c, ip0, ip1, ip2, (const C2 *)u->U, u->scal,
-                                    grad);
+    {   // type 1: the strengths onto U
+        fresco::StageScope sc(u->prof, s, UST_SPREAD);
+        UN_CUDA(un_spread<T>(u, s));
+    }
+    {   // forward FFT, then the weight gradient
+        fresco::StageScope sc(u->prof, s, UST_TYPE1);
+        const fresco_status st = un_fft<T>(u, CUFFT_FORWARD);
+        if (st) return st;
+        k_un_grad<T><<<pb, 256, 0, s>>>(g, u->cells, c, ip0, ip1, ip2, (const C2 *)u->U, u->scal,
+                                        grad);
+    }
+    u->launches += 2;
     return un_status(cudaGetLastError());
 }
 
@@ -543,8 +962,8 @@ fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid,
     u->n_k = n_k;
     u->nb = (int)std::max<int64_t>(1, std::min<int64_t>((n_k + 255) / 256, kUBlocks));
     u->stream = (cudaStream_t)stream;
-    const fresco_status st = o.precision == FRESCO_F64 ? un_build<double>(u, nu, S0, W)
-                                                       : un_build<float>(u, nu, S0, W);
+    const fresco_status st = o.precision == FRESCO_F64 ? un_build<double>(u, nu, S0, W, nullptr)
+                                                       : un_build<float>(u, nu, S0, W, nullptr);
     if (st) {
         un_free(u);
         return st;
@@ -581,6 +1000,27 @@ fresco_status fresco_uwnu_destroy(fresco_uwnu_t u) {
     un_free(u);
     return FRESCO_OK;
 }
+
+fresco_status fresco_uwnu_profile(fresco_uwnu_t u, int enable) {
+    if (!u) return FRESCO_ERR_ARG;
+    u->prof.on = enable != 0;
+    return FRESCO_OK;
+}
+
+fresco_status fresco_uwnu_profile_read(fresco_uwnu_t u, double *ms, int64_t *counts) {
+    if (!u || !ms) return FRESCO_ERR_ARG;
+    UN_CUDA(u->stream ? cudaStreamSynchronize(u->stream) : cudaDeviceSynchronize());
+    double all_ms[fresco::ST_COUNT];
+    int64_t all_counts[fresco::ST_COUNT];
+    u->prof.read(all_ms, all_counts);
+    for (int i = 0; i < UST_COUNT; ++i) {
+        ms[i] = all_ms[i];
+        if (counts) counts[i] = all_counts[i];
+    }
+    return FRESCO_OK;
+}
+
+int64_t fresco_uwnu_launch_count(fresco_uwnu_t u) { return u ? u->launches : 0; }
 
 }  // extern "C"
 
@@ -679,7 +1119,6 @@ struct fresco_nuwnu_s {
     double box[3] = {1, 1, 1};
     double h[3] = {1, 1, 1};
     int64_t n_points = 0, cells = 0;
-    void *dq = nullptr;           // [n_k] 1 / Psi1(theta_q)
     cudaStream_t stream = nullptr;
     int64_t launches = 0;
 };
@@ -692,7 +1131,6 @@ void nu_free(fresco_nuwnu_s *p) {
     else cudaDeviceSynchronize();
     if (p->c) un_free(p->c);
     fresco::point_side_free(p->ps);
-    if (p->dq) cudaFree(p->dq);
     delete p;
 }
 
@@ -705,23 +1143,17 @@ fresco_status nu_build(fresco_nuwnu_s *p, const double *kvec, const double *S0, 
     std::vector<double> nu((size_t)(n_k * dim));
     std::vector<double> theta((size_t)n_k);
     std::vector<double> psi((size_t)n_k);
-    std::vector<T> dq((size_t)n_k, T(1));
+    std::vector<double> dq((size_t)n_k, 1.0);   // 1 / Psi1(theta_q)
     for (int a = 0; a < dim; ++a) {
         for (int64_t q = 0; q < n_k; ++q) {
             theta[(size_t)q] = kvec[q * dim + a] * p->h[a];
             nu[(size_t)(q * dim + a)] = theta[(size_t)q] * (double)u->g.M[a] / (2.0 * kPiU);
         }
         fresco::kernel_ft_at(u->width, u->beta, theta.data(), n_k, psi.data());
-        for (int64_t q = 0; q < n_k; ++q) dq[(size_t)q] = (T)((double)dq[(size_t)q] / psi[(size_t)q]);
+        for (int64_t q = 0; q < n_k; ++q) dq[(size_t)q] /= psi[(size_t)q];
     }
-    fresco_status st = un_build<T>(u, nu.data(), S0, W);
+    fresco_status st = un_build<T>(u, nu.data(), S0, W, dq.data());
     if (st) return st;
-    if (cudaMalloc(&p->dq, sizeof(T) * (size_t)n_k) != cudaSuccess) {
-        cudaGetLastError();
-        p->dq = nullptr;
-        return FRESCO_ERR_OOM;
-    }
-    UN_CUDA(cudaMemcpy(p->dq, dq.data(), sizeof(T) * (size_t)n_k, cudaMemcpyHostToDevice));
     const double norm = (double)p->n_points;   // S = |rho|^2 / N
     UN_CUDA(cudaMemcpy(u->scal, &norm, sizeof(double), cudaMemcpyHostToDevice));
     // point side: the n1 grid over the periodic box n1 h
@@ -746,38 +1178,53 @@ fresco_status nu_eval(fresco_nuwnu_s *p, const T *pts, double *loss, T *grad) {
     cudaStream_t s = p->stream;
     const unsigned pb = (unsigned)std::min<int64_t>((p->cells + 255) / 256, 152 * 16);
     const T *ip0 = (const T *)u->ip[0], *ip1 = (const T *)u->ip[1], *ip2 = (const T *)u->ip[2];
-    // the grid keeps spare cells beyond the box, so half a cell of slack (FP32 coordinates of
-    // points on a face may round just outside it) changes nothing
-    k_nu_bounds<T><<<(unsigned)std::min<int64_t>((p->n_points + 255) / 256, 152 * 8), 256, 0, s>>>(
-        pts, p->n_points, p->dim, 0.5 * (p->box[0] + p->h[0]), 0.5 * (p->box[1] + p->h[1]),
-        0.5 * (p->box[2] + p->h[2]), p->ps.err);
-    fresco_status st = fresco::point_side_spread<T>(p->ps, pts, s, &p->launches);
-    if (st) return st;
-    // type 2 of the spread grid at the wavevectors, S, the loss and the type-1 strengths
-    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
-    k_nu_fill<T><<<pb, 256, 0, s>>>(g, p->cells, (const T *)p->ps.grid, ip0, ip1, ip2, (C2 *)u->U);
-    st = un_fft<T>(u, CUFFT_INVERSE);
-    if (st) return st;
-    UN_CUDA(un_interp<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, (T)u->beta, u->U,
-                         (const T *)u->s0, (const T *)u->wq, u->scal, (const T *)p->dq, u->coef,
-                         (T *)u->S, u->part, u->nb, s));
-    k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 1, u->scal + 1);
-    UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    fresco_status st;
+    {   // the points onto their grid; the grid keeps spare cells beyond the box, so half a cell
+        // of slack (FP32 coordinates of points on a face may round just outside it) changes nothing
+        fresco::StageScope sc(u->prof, s, UST_POINT_SPREAD);
+        k_nu_bounds<T><<<(unsigned)std::min<int64_t>((p->n_points + 255) / 256, 152 * 8), 256, 0,
+                         s>>>(pts, p->n_points, p->dim, 0.5 * (p->box[0] + p->h[0]),
+                              0.5 * (p->box[1] + p->h[1]), 0.5 * (p->box[2] + p->h[2]),
+                              p->ps.err);
+        st = fresco::point_side_spread<T>(p->ps, pts, s, &p->launches);
+        if (st) return st;
+    }
+    {   // type 2 of the spread grid: onto U, inverse FFT
+        fresco::StageScope sc(u->prof, s, UST_TYPE2);
+        UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
+        k_nu_fill<T><<<pb, 256, 0, s>>>(g, p->cells, (const T *)p->ps.grid, ip0, ip1, ip2,
+                                        (C2 *)u->U);
+        st = un_fft<T>(u, CUFFT_INVERSE);
+        if (st) return st;
+    }
+    {   // at the wavevectors: S, the loss and the type-1 strengths
+        fresco::StageScope sc(u->prof, s, UST_INTERP);
+        UN_CUDA(un_interp<T>(u, s));
+        k_un_sum<<<1, 256, 0, s>>>(u->part, u->nb, 1, u->scal + 1);
+        UN_CUDA(cudaMemcpyAsync(loss, u->scal + 1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     p->launches += 4;
     u->evaluated = true;
     if (!grad) return un_status(cudaGetLastError());
-    // type 1 of the strengths onto the grid, then the kernel-derivative interpolation
-    UN_CUDA(cudaMemsetAsync(u->U, 0, sizeof(C2) * (size_t)u->fine, s));
-    UN_CUDA(un_spread<T>(u->width, g, u->n_k, u->tcell, (const T *)u->tfrac, (T)u->beta, u->coef,
-                         u->U, u->nb, s));
-    st = un_fft<T>(u, CUFFT_FORWARD);
-    if (st) return st;
-    k_nu_field<T><<<pb, 256, 0, s>>>(g, p->cells, ip0, ip1, ip2, (const C2 *)u->U, (T *)p->ps.grid);
-    const double dscale[3] = {-2.0 / p->h[0], -2.0 / p->h[1], -2.0 / p->h[2]};
-    const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(
-        sizeof(T) == 4 ? (const void *)&p->ps.p32 : (const void *)&p->ps.p64);
-    UN_CUDA(Launch<T>::interp_kd(p->ps.g, ep, p->ps.sorted, p->ps.perm, p->ps.tr,
-                                 (const T *)p->ps.grid, nullptr, dscale, grad, s));
+    {   // type 1 of the strengths onto U
+        fresco::StageScope sc(u->prof, s, UST_SPREAD);
+        UN_CUDA(un_spread<T>(u, s));
+    }
+    {   // forward FFT, the field on the points' grid
+        fresco::StageScope sc(u->prof, s, UST_TYPE1);
+        st = un_fft<T>(u, CUFFT_FORWARD);
+        if (st) return st;
+        k_nu_field<T><<<pb, 256, 0, s>>>(g, p->cells, ip0, ip1, ip2, (const C2 *)u->U,
+                                         (T *)p->ps.grid);
+    }
+    {   // the kernel-derivative interpolation at the points
+        fresco::StageScope sc(u->prof, s, UST_POINT_INTERP);
+        const double dscale[3] = {-2.0 / p->h[0], -2.0 / p->h[1], -2.0 / p->h[2]};
+        const EsPoly<T> &ep = *reinterpret_cast<const EsPoly<T> *>(
+            sizeof(T) == 4 ? (const void *)&p->ps.p32 : (const void *)&p->ps.p64);
+        UN_CUDA(Launch<T>::interp_kd(p->ps.g, ep, p->ps.sorted, p->ps.perm, p->ps.tr,
+                                     (const T *)p->ps.grid, nullptr, dscale, grad, s));
+    }
     p->launches += 3;
     return un_status(cudaGetLastError());
 }
@@ -919,6 +1366,16 @@ fresco_status fresco_nuwnu_get_info(fresco_nuwnu_t p, int *width, int *n_grid, i
 fresco_status fresco_nuwnu_destroy(fresco_nuwnu_t p) {
     nu_free(p);
     return FRESCO_OK;
+}
+
+fresco_status fresco_nuwnu_profile(fresco_nuwnu_t p, int enable) {
+    if (!p) return FRESCO_ERR_ARG;
+    return fresco_uwnu_profile(p->c, enable);
+}
+
+fresco_status fresco_nuwnu_profile_read(fresco_nuwnu_t p, double *ms, int64_t *counts) {
+    if (!p) return FRESCO_ERR_ARG;
+    return fresco_uwnu_profile_read(p->c, ms, counts);
 }
 
 }  // extern "C"

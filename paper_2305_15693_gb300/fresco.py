@@ -32,6 +32,8 @@ FRESCO_GRAD_DIRECT = 0
 FRESCO_GRAD_KDERIV = 1
 FRESCO_N_STAGES = 7
 STAGES = ("sort", "spread", "fft_fwd", "mask", "loss", "fft_inv", "interp")
+FRESCO_UWNU_N_STAGES = 6
+UWNU_STAGES = ("point_spread", "type2", "interp", "spread", "type1", "point_interp")
 
 # every entry point declared in include/fresco.h
 EXPORTS = (
@@ -50,9 +52,11 @@ EXPORTS = (
     "fresco_batch_profile_read", "fresco_batch_get_info",
     "fresco_uwu_plan", "fresco_uwu_loss_grad", "fresco_uwu_destroy",
     "fresco_uwnu_plan", "fresco_uwnu_loss_grad", "fresco_uwnu_get_S", "fresco_uwnu_get_info",
-    "fresco_uwnu_destroy", "fresco_smem_peak",
+    "fresco_uwnu_destroy", "fresco_uwnu_profile", "fresco_uwnu_profile_read",
+    "fresco_uwnu_launch_count", "fresco_smem_peak",
     "fresco_nuwnu_plan", "fresco_nuwnu_loss_grad", "fresco_nuwnu_get_S",
     "fresco_nuwnu_status_check", "fresco_nuwnu_get_info", "fresco_nuwnu_destroy",
+    "fresco_nuwnu_profile", "fresco_nuwnu_profile_read",
 )
 FRESCO_LOSS_NOALLOC_MAX_ROWS = 65536 * 4096
 
@@ -172,6 +176,9 @@ def load(path: str = LIB_PATH):
             "fresco_uwnu_get_S": (I, [P, P]),
             "fresco_uwnu_get_info": (I, [P, P, P, P]),
             "fresco_uwnu_destroy": (I, [P]),
+            "fresco_uwnu_profile": (I, [P, I]),
+            "fresco_uwnu_profile_read": (I, [P, P, P]),
+            "fresco_uwnu_launch_count": (I64, [P]),
             "fresco_smem_peak": (I, [I, P, P, P]),
             "fresco_nuwnu_plan": (I, [P, I, P, I64, I64, P, P, P, P, P]),
             "fresco_nuwnu_loss_grad": (I, [P, P, P, P]),
@@ -179,6 +186,8 @@ def load(path: str = LIB_PATH):
             "fresco_nuwnu_status_check": (I, [P]),
             "fresco_nuwnu_get_info": (I, [P, P, P, P, P]),
             "fresco_nuwnu_destroy": (I, [P]),
+            "fresco_nuwnu_profile": (I, [P, I]),
+            "fresco_nuwnu_profile_read": (I, [P, P, P]),
         })
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -731,6 +740,33 @@ def fresco_uwnu_destroy(plan):
     _check(load().fresco_uwnu_destroy(plan), "fresco_uwnu_destroy")
 
 
+def _uwnu_profile_read(fn, plan, name):
+    ms = np.zeros(FRESCO_UWNU_N_STAGES)
+    cnt = np.zeros(FRESCO_UWNU_N_STAGES, dtype=np.int64)
+    _check(fn(plan, ms.ctypes.data, cnt.ctypes.data), name)
+    return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(UWNU_STAGES)}
+
+
+def fresco_uwnu_profile(plan, enable: bool):
+    _check(load().fresco_uwnu_profile(plan, 1 if enable else 0), "fresco_uwnu_profile")
+
+
+def fresco_uwnu_profile_read(plan):
+    return _uwnu_profile_read(load().fresco_uwnu_profile_read, plan, "fresco_uwnu_profile_read")
+
+
+def fresco_uwnu_launch_count(plan) -> int:
+    return int(load().fresco_uwnu_launch_count(plan))
+
+
+def fresco_nuwnu_profile(plan, enable: bool):
+    _check(load().fresco_nuwnu_profile(plan, 1 if enable else 0), "fresco_nuwnu_profile")
+
+
+def fresco_nuwnu_profile_read(plan):
+    return _uwnu_profile_read(load().fresco_nuwnu_profile_read, plan, "fresco_nuwnu_profile_read")
+
+
 class Uwnu:
     """Weights on a uniform grid with constraints at real frequencies (fresco_uwnu_* in
     include/fresco.h). Weights and gradients are CUDA tensors of shape grid_shape[::-1] (x the
@@ -764,6 +800,15 @@ class Uwnu:
         out = t.empty(self.n_k, dtype=self.dtype, device="cuda")
         fresco_uwnu_get_S(self.handle, out)
         return out
+
+    def profile(self, enable=True):
+        fresco_uwnu_profile(self.handle, enable)
+
+    def profile_read(self):
+        return fresco_uwnu_profile_read(self.handle)
+
+    def launch_count(self) -> int:
+        return fresco_uwnu_launch_count(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -864,6 +909,12 @@ class Nuwnu:
         out = self._torch.empty(self.n_k, dtype=self.dtype, device="cuda")
         fresco_nuwnu_get_S(self.handle, out)
         return out
+
+    def profile(self, enable=True):
+        fresco_nuwnu_profile(self.handle, enable)
+
+    def profile_read(self):
+        return fresco_nuwnu_profile_read(self.handle)
 
     def status(self) -> int:
         return fresco_nuwnu_status_check(self.handle)

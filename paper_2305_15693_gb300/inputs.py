@@ -311,6 +311,63 @@ def free_workload(name: str) -> FreeWorkload:
 
 
 @dataclass
+class FieldWorkload:
+    """Real weights on a uniform grid with constraints at real frequencies (the UwNU form): a
+    density field of M^d pixels with weights uniform in [0, 1), n_k constraints at frequencies
+    uniform in the ball |nu| <= nu_max (cycles per grid length), targets zero (a stealthy-like
+    band) except a ring of n_peaks Gaussian peaks one cycle wide at radius nu_max / 4 (the
+    six-fold target of the paper's UwNU fields, at real rather than lattice frequencies)."""
+    name: str
+    dim: int
+    M: int                 # pixels per axis
+    n_k: int
+    nu_max: float
+    dtype: str
+    seed: int = 0
+    tol: float = 1e-6
+    upsample: float = 2.0
+    n_peaks: int = 6
+    peak_height: float = 10.0
+
+    @property
+    def shape(self):
+        return (self.M,) * self.dim
+
+    @property
+    def n_weights(self) -> int:
+        return self.M ** self.dim
+
+    def weights(self) -> np.ndarray:
+        """Weights [M]*dim (x the last, contiguous index)."""
+        dt = np.float64 if self.dtype == "f64" else np.float32
+        return rng(self.seed).random(self.shape).astype(dt)
+
+    def frequencies(self) -> np.ndarray:
+        g = rng(self.seed + 1)
+        nu = g.standard_normal((self.n_k, self.dim))
+        nu *= (self.nu_max * g.random(self.n_k) ** (1.0 / self.dim)
+               / np.linalg.norm(nu, axis=1))[:, None]
+        return nu
+
+    def targets(self, nu: np.ndarray):
+        r = 0.25 * self.nu_max
+        ang = 2 * np.pi * np.arange(self.n_peaks) / self.n_peaks
+        c = np.zeros((self.n_peaks, self.dim))
+        c[:, 0], c[:, 1] = r * np.cos(ang), r * np.sin(ang)
+        S0 = np.zeros(nu.shape[0])
+        for p in range(self.n_peaks):
+            S0 += self.peak_height * np.exp(-((nu - c[p]) ** 2).sum(1) / 2.0)
+        return S0, np.ones(nu.shape[0])
+
+
+def field_workload(name: str) -> FieldWorkload:
+    """The named UwNU workloads."""
+    if name == "hexfield2d_m1024_k1e6_f32":
+        return FieldWorkload(name, 2, 1024, 10**6, 460.0, "f32", seed=13)
+    raise KeyError(name)
+
+
+@dataclass
 class Ensemble:
     """Many independent 2D problems: instance i has n_points[i] uniform points in a periodic box
     boxes[i] (a square of that side) and the ball mask of radius K[i] (from chi[i]), with a

@@ -73,6 +73,7 @@ def test_traffic_sources_exist_and_hash_is_stable():
                         "paper_2305_15693_gb300", "csrc")
     names = bench.traffic_sources()
     assert "fresco_kernels.cuh" in names and "fresco_tiles.cuh" in names
+    assert "fresco_host.cu" in names and "fresco_uwnu.cu" not in names
     for name in names:
         assert os.path.isfile(os.path.join(csrc, name)), name
     h = bench._kernel_source_hash()
@@ -105,3 +106,16 @@ def test_smem_roofline_counts_w_to_the_d_operations_per_point():
     assert out["interp"]["frac"] == pytest.approx(49e8 / 4e-3 / 9.8e12, abs=1e-4)
     out3 = bench.smem_rooflines(stages, 1 << 24, 3, 7, {"atomic_add": 1.0, "load": 1.0})
     assert out3["spread"]["ops_per_launch"] == float((1 << 24) * 343)
+
+
+def test_uwnu_traffic_sources_and_constraint_bytes():
+    assert bench.traffic_sources("uwnu") == ["fresco_internal.h", "fresco_kernels.cuh",
+                                             "fresco_uwnu.cu"]
+    h = bench._kernel_source_hash("uwnu")
+    assert len(h) == 16 and h != bench._kernel_source_hash()
+    # 2D FP32, 10 constraints, a 4 x 4 fine grid: interp reads the grid once (128 B) and per
+    # constraint cell + position (16 B), target and weight (8 B), caller index (4 B), writes the
+    # strength and S (12 B); spread reads cell + position + strength (24 B) and writes the grid
+    b = bench.constraint_side_bytes(2, 10, 16, 4, False)
+    assert b == {"interp": 128 + 10 * 40, "spread": 10 * 24 + 128}
+    assert bench.constraint_side_bytes(2, 10, 16, 4, True)["interp"] == 128 + 10 * 44

@@ -114,3 +114,17 @@ def test_point_outside_the_box_is_flagged():
         pts[17, 1] = 0.25
         plan.loss_grad(torch.from_numpy(pts).cuda())
         assert plan.status() == 0                        # the error word was cleared
+
+
+def test_nuwnu_profile_stages():
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    pts, k, S0, W = _problem(2, 500, 300, 91, [1.0, 1.0], 2 * np.pi * 10.5)
+    p = torch.from_numpy(pts).to("cuda", torch.float32)
+    with fresco.Nuwnu([1.0, 1.0], k, S0, W, pts.shape[0], "f32") as plan:
+        plan.profile(True)
+        plan.loss_grad(p)
+        st = plan.profile_read()
+        plan.profile(False)
+    for name in ("point_spread", "type2", "interp", "spread", "type1", "point_interp"):
+        assert st[name][1] == 1 and st[name][0] > 0.0, (name, st)

@@ -116,3 +116,70 @@ def test_uwnu_rejects_bad_arguments():
         fresco.Uwnu((8, 8), nu, [0.0], [-1.0])                    # negative weight
     with pytest.raises(fresco.FrescoError):
         fresco.Uwnu((8, 8), nu, [0.0], [1.0], upsample=4.0)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_uwnu_crowded_tile_and_seam(precision):
+    """Constraints packed into one tile of the fine grid (a tile list longer than a block's
+    threads), at integer and half-integer frequencies (supports that start on tile boundaries),
+    and at frequencies whose support wraps across the grid's periodic seam."""
+    shape = (64, 48)
+    g = inputs.rng(81)
+    crowd = 3.0 + 0.05 * g.random((700, 2))
+    seam = np.array([[0.0, 0.0], [0.5, -0.5], [32.0, 24.0], [-32.0, -24.0], [31.9, 0.1],
+                     [-0.01, 23.99], [-31.99, -23.9]])
+    lattice = g.integers(-40, 40, (100, 2)).astype(np.float64) / 2
+    nu = np.concatenate([crowd, seam, lattice])
+    S0 = 0.5 * g.random(nu.shape[0])
+    W = 0.5 + g.random(nu.shape[0])
+    c = g.standard_normal(shape[0] * shape[1])
+    c_used, (loss, grad, S, info) = _run(shape, c, nu, S0, W, precision)
+    l_o, g_o, S_o, _ = oracle.weight_loss_grad_k(oracle.grid_points(shape), c_used,
+                                                  2.0 * np.pi * nu, S0, W)
+    bar = BAR[precision]
+    assert rel_l2(S, S_o) <= bar["S"]
+    assert abs(loss - l_o) <= bar["loss"] * abs(l_o)
+    assert rel_l2(grad, g_o) <= bar["grad"]
+
+
+def test_uwnu_profile_and_launch_count():
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    shape = (40, 36)
+    c, nu, S0, W = _problem(shape, 50, 5, span=15.0)
+    c_dev = torch.from_numpy(c.reshape(shape[::-1])).to("cuda", torch.float32)
+    with fresco.Uwnu(shape, nu, S0, W, "f32") as u:
+        n0 = u.launch_count()
+        u.profile(True)
+        u.loss_grad(c_dev)
+        u.loss_grad(c_dev)
+        st = u.profile_read()
+        assert u.launch_count() - n0 == 14          # seven kernels per evaluation
+        u.profile(False)
+        u.loss_grad(c_dev, want_grad=False)
+        assert u.launch_count() - n0 == 19          # five without the gradient
+        torch.cuda.synchronize()
+        assert u.profile_read()["interp"][1] == 0   # nothing recorded while off
+    for name in ("type2", "interp", "spread", "type1"):
+        assert st[name][1] == 2 and st[name][0] > 0.0
+    assert st["point_spread"][1] == 0 and st["point_interp"][1] == 0
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_uwnu_repeats_bitwise(precision):
+    """The spread adds in fixed point, so every output of a repeated call is bitwise equal."""
+    import torch
+    from paper_2305_15693_gb300 import fresco
+    shape = (96, 80)
+    c, nu, S0, W = _problem(shape, 3000, 83, span=40.0)
+    dt = torch.float64 if precision == "f64" else torch.float32
+    c_dev = torch.from_numpy(c.reshape(shape[::-1])).to("cuda", dt)
+    with fresco.Uwnu(shape, nu, S0, W, precision) as u:
+        l1, g1 = u.loss_grad(c_dev)
+        S1 = u.S()
+        l1, g1 = l1.clone(), g1.clone()
+        l2, g2 = u.loss_grad(c_dev)
+        S2 = u.S()
+        torch.cuda.synchronize()
+    assert l1.item() == l2.item()
+    assert torch.equal(g1, g2) and torch.equal(S1, S2)
