@@ -563,6 +563,7 @@ fresco_status fresco_batch_lbfgs_create(fresco_batch_lbfgs_t *out, fresco_batch_
 }
 
 fresco_status fresco_batch_lbfgs_start(fresco_batch_lbfgs_t s, const void *d_points) {
+    fresco::clear_pending_error();
     if (!s || !d_points) return FRESCO_ERR_ARG;
     const int n = s->n_inst, dim = s->b->dim;
     std::vector<BLState> h(n);
@@ -589,6 +590,7 @@ fresco_status fresco_batch_lbfgs_start(fresco_batch_lbfgs_t s, const void *d_poi
 }
 
 fresco_status fresco_batch_lbfgs_step(fresco_batch_lbfgs_t s, int64_t n_steps) {
+    fresco::clear_pending_error();
     if (!s || !s->started || n_steps < 0) return FRESCO_ERR_ARG;
     for (int64_t k = 0; k < n_steps; ++k) {
         if (!s->stream || (!s->gexec && s->steps == 0)) {
@@ -630,6 +632,7 @@ fresco_status fresco_batch_lbfgs_step(fresco_batch_lbfgs_t s, int64_t n_steps) {
 
 fresco_status fresco_batch_lbfgs_read(fresco_batch_lbfgs_t s, void *d_points,
                                       fresco_lbfgs_report *reports, int64_t *n_running) {
+    fresco::clear_pending_error();
     if (!s || !s->started) return FRESCO_ERR_ARG;
     cudaError_t e = cudaSuccess;
     if (d_points)

@@ -1299,6 +1299,7 @@ fresco_status fresco_set_stream(fresco_plan_t p, void *stream) {
 }
 
 fresco_status fresco_forward(fresco_plan_t p, const void *d_points, double *d_loss) {
+    fresco::clear_pending_error();
     if (!p || !d_loss) return FRESCO_ERR_ARG;
     fresco_status st = check_point_ptr(p, d_points);
     if (st) return st;
@@ -1307,6 +1308,7 @@ fresco_status fresco_forward(fresco_plan_t p, const void *d_points, double *d_lo
 }
 
 fresco_status fresco_backward(fresco_plan_t p, const double *d_grad_out, void *d_grad) {
+    fresco::clear_pending_error();
     if (!p || !p->forward_done) return FRESCO_ERR_ARG;
     fresco_status st = check_point_ptr(p, d_grad);
     if (st) return st;
@@ -1321,6 +1323,7 @@ fresco_status fresco_loss_grad(fresco_plan_t p, const void *d_points, double *d_
 }
 
 fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S) {
+    fresco::clear_pending_error();
     if (!p || !p->forward_done) return FRESCO_ERR_ARG;
     if (!d_rho && !d_S) return FRESCO_OK;
     if (!p->d_mask_orig) {
@@ -1346,6 +1349,7 @@ fresco_status fresco_get_rho_S(fresco_plan_t p, void *d_rho, void *d_S) {
 
 fresco_status fresco_loss_grad_host(fresco_plan_t p, const void *h_points, double *h_loss,
                                     void *h_grad) {
+    fresco::clear_pending_error();
     if (!p || !h_points || !h_loss) return FRESCO_ERR_ARG;
     const size_t bytes = p->esize * (size_t)p->n_points * p->dim;
     fresco_status st;
@@ -1891,6 +1895,7 @@ fresco_status fresco_batch_plan(fresco_batch_t *out, int dim, int n_inst, const 
 
 fresco_status fresco_batch_loss_grad(fresco_batch_t b, const void *d_points, double *d_losses,
                                      void *d_grad) {
+    fresco::clear_pending_error();
     if (!b || !d_points || !d_losses) return FRESCO_ERR_ARG;
     if (b->precision == FRESCO_F64)
         return batch_eval<double>(b, (const double *)d_points, d_losses, (double *)d_grad);
@@ -1899,6 +1904,7 @@ fresco_status fresco_batch_loss_grad(fresco_batch_t b, const void *d_points, dou
 
 fresco_status fresco_batch_graph_capture(fresco_batch_t b, const void *d_points, double *d_losses,
                                          void *d_grad) {
+    fresco::clear_pending_error();
     if (!b || !d_points || !d_losses || !b->stream) return FRESCO_ERR_ARG;
     // one ordinary evaluation first (sets kernel attributes, warms the cuFFT plans)
     fresco_status st = fresco_batch_loss_grad(b, d_points, d_losses, d_grad);
@@ -1930,6 +1936,7 @@ fresco_status fresco_batch_graph_capture(fresco_batch_t b, const void *d_points,
 }
 
 fresco_status fresco_batch_graph_launch(fresco_batch_t b) {
+    fresco::clear_pending_error();
     if (!b || !b->gexec) return FRESCO_ERR_ARG;
     FR_CUDA(cudaGraphLaunch(b->gexec, b->stream));
     return FRESCO_OK;
@@ -2298,6 +2305,7 @@ fresco_status fresco_uwu_plan(fresco_uwu_t *out, int dim, const int64_t *grid, c
 }
 
 fresco_status fresco_uwu_loss_grad(fresco_uwu_t u, const void *d_c, double *d_loss, void *d_grad) {
+    fresco::clear_pending_error();
     if (!u || !d_c || !d_loss) return FRESCO_ERR_ARG;
     if (u->precision == FRESCO_F64)
         return uwu_eval<double>(u, (const double *)d_c, d_loss, (double *)d_grad);

@@ -329,6 +329,10 @@ fresco_status point_side_spread(PointSide &ps, const T *pts, cudaStream_t s, int
 // Psi(theta) = integral psi(u) cos(theta u) du of the kernel of width w (u in cells), at n real
 // frequencies theta (radians per cell).
 void kernel_ft_at(int w, double beta, const double *theta, int64_t n, double *out);
+// Entry points that launch work call this first: it clears a pending (non-sticky) launch error of
+// earlier, unrelated work on the calling thread, so that the error they report after their own
+// launches is theirs.
+inline void clear_pending_error() { (void)cudaGetLastError(); }
 // The piecewise polynomials of the kernel of width w and shape beta that es_weights evaluates.
 void es_poly_table(int w, double beta, EsPoly<float> &out);
 void es_poly_table(int w, double beta, EsPoly<double> &out);

@@ -491,6 +491,7 @@ fresco_status fresco_lbfgs_create(fresco_lbfgs_t *out, fresco_plan_t plan,
 
 fresco_status fresco_lbfgs_run(fresco_lbfgs_t s, void *d_points, int64_t max_iter,
                                fresco_lbfgs_report *report) {
+    fresco::clear_pending_error();
     if (!s || !d_points || max_iter < 0) return FRESCO_ERR_ARG;
     s->stream = s->plan->stream;
     if (s->es == 8) return run_impl<double>(s, d_points, max_iter, report);

@@ -298,6 +298,7 @@ fresco_status fresco_pair_plan(fresco_pair_t *out, int dim, const double *box, i
 
 fresco_status fresco_pair_energy_grad(fresco_pair_t p, const void *d_points, double *d_energy,
                                       void *d_grad, int accumulate) {
+    fresco::clear_pending_error();
     if (!p || !d_points || !d_energy || !d_grad) return FRESCO_ERR_ARG;
     if (p->precision == FRESCO_F64) return pair_eval<double>(p, d_points, d_energy, d_grad, accumulate);
     return pair_eval<float>(p, d_points, d_energy, d_grad, accumulate);

@@ -974,6 +974,7 @@ fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid,
 
 fresco_status fresco_uwnu_loss_grad(fresco_uwnu_t u, const void *d_c, double *d_loss,
                                     void *d_grad) {
+    fresco::clear_pending_error();
     if (!u || !d_c || !d_loss) return FRESCO_ERR_ARG;
     if (u->precision == FRESCO_F64)
         return un_eval<double>(u, (const double *)d_c, d_loss, (double *)d_grad);
@@ -981,6 +982,7 @@ fresco_status fresco_uwnu_loss_grad(fresco_uwnu_t u, const void *d_c, double *d_
 }
 
 fresco_status fresco_uwnu_get_S(fresco_uwnu_t u, void *d_S) {
+    fresco::clear_pending_error();
     if (!u || !d_S || !u->evaluated) return FRESCO_ERR_ARG;
     const size_t es = u->precision == FRESCO_F64 ? 8 : 4;
     return un_status(cudaMemcpyAsync(d_S, u->S, es * (size_t)u->n_k, cudaMemcpyDeviceToDevice,
@@ -1327,7 +1329,7 @@ fresco_status fresco_nuwnu_plan(fresco_nuwnu_t *out, int dim, const double *box,
 fresco_status fresco_nuwnu_loss_grad(fresco_nuwnu_t p, const void *d_points, double *d_loss,
                                      void *d_grad) {
     if (!p || !d_points || !d_loss) return FRESCO_ERR_ARG;
-    cudaGetLastError();
+    fresco::clear_pending_error();
     if (p->precision == FRESCO_F64)
         return nu_eval<double>(p, (const double *)d_points, d_loss, (double *)d_grad);
     return nu_eval<float>(p, (const float *)d_points, d_loss, (float *)d_grad);
