@@ -238,3 +238,24 @@ def test_uwnu_unsupported_sizes(fr):
         with pytest.raises(fr.FrescoError) as e:
             fr.fresco_uwnu_plan(grid, nu, [0.0], [1.0], fr.make_opts(**kw))
         assert e.value.status == fr.FRESCO_ERR_UNSUPPORTED
+
+
+def test_uwnu_profile_entry_points_reject_null_handles(fr):
+    """The stage-timer and launch-count entry points of the weights-on-a-grid and type-3 plans
+    answer a null handle without touching the device."""
+    import ctypes
+    lib = fr.load()
+    ms = (ctypes.c_double * fr.FRESCO_UWNU_N_STAGES)()
+    assert lib.fresco_uwnu_profile(None, 1) == fr.FRESCO_ERR_ARG
+    assert lib.fresco_uwnu_profile_read(None, ms, None) == fr.FRESCO_ERR_ARG
+    assert lib.fresco_nuwnu_profile(None, 1) == fr.FRESCO_ERR_ARG
+    assert lib.fresco_nuwnu_profile_read(None, ms, None) == fr.FRESCO_ERR_ARG
+    assert lib.fresco_uwnu_launch_count(None) == 0
+    assert len(fr.UWNU_STAGES) == fr.FRESCO_UWNU_N_STAGES
+
+
+def test_stage_counts_match_the_header(fr):
+    src = open(os.path.join(ROOT, "include", "fresco.h")).read()
+    assert int(re.search(r"#define FRESCO_UWNU_N_STAGES (\d+)", src).group(1)) == \
+        fr.FRESCO_UWNU_N_STAGES
+    assert int(re.search(r"#define FRESCO_N_STAGES (\d+)", src).group(1)) == fr.FRESCO_N_STAGES
