@@ -1272,11 +1272,11 @@ def main():
 # (sort, spread, mask, interp): the solvers, the allocation-free entry point, the pair term, the
 # shared-memory probe and the weights-on-a-grid / type-3 plans.
 OTHER_PLAN_SOURCES = ("fresco_batch_lbfgs.cu", "fresco_lbfgs.cu", "fresco_noalloc.cu",
-                      "fresco_pair.cu", "fresco_probe.cu", "fresco_uwnu.cu")
+                      "fresco_pair.cu", "fresco_probe.cu", "fresco_uwnu.cu", "fresco_uwnu_tiles.h")
 
 
 # The sources of the weights-on-a-grid / type-3 plans' constraint-side kernels (interp, spread).
-UWNU_SOURCES = ("fresco_internal.h", "fresco_kernels.cuh", "fresco_uwnu.cu")
+UWNU_SOURCES = ("fresco_internal.h", "fresco_kernels.cuh", "fresco_uwnu.cu", "fresco_uwnu_tiles.h")
 
 
 def traffic_sources(family: str = "single") -> list:

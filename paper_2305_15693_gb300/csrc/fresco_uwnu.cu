@@ -36,6 +36,7 @@
 
 #include "fresco.h"
 #include "fresco_kernels.cuh"
+#include "fresco_uwnu_tiles.h"
 
 using namespace fresco;
 
@@ -149,14 +150,7 @@ __global__ void __launch_bounds__(256) k_un_fill(UGrid g, int64_t cells, const T
     }
 }
 
-// Tiles of the fine grid for the type-1 spread: T[a] cells per axis, at most half the axis (so
-// a kernel support, at most half the axis too, meets a tile at one periodic shift only), and
-// nt[a] tiles per axis (the last one may be shorter). Tile t = (tz nt[1] + ty) nt[0] + tx.
-struct UTiles {
-    int T[3];
-    int nt[3];
-};
-constexpr int kUTileCells = 1024;   // T[0] T[1] T[2] at most
+constexpr int kUTileCells = 1024;   // T[0] T[1] T[2] at most (UTiles, fresco_uwnu_tiles.h)
 
 // the weight of support cell k of one axis out of the unrolled row (k known only at run time)
 template <typename T, int W>
@@ -603,18 +597,6 @@ void un_free(fresco_uwnu_s *u) {
     delete u;
 }
 
-// The spread's tiles: up to 32 x 32 cells in 2D and 16 x 8 x 8 in 3D, at most half of each
-// axis (the fine grid is even and at least 2w per axis).
-UTiles un_tiles(const UGrid &g) {
-    static const int t2[3] = {32, 32, 1}, t3[3] = {16, 8, 8};
-    UTiles tl{};
-    for (int a = 0; a < 3; ++a) {
-        tl.T[a] = a < g.dim ? std::min(g.dim == 2 ? t2[a] : t3[a], g.nf[a] / 2) : 1;
-        tl.nt[a] = (g.nf[a] + tl.T[a] - 1) / tl.T[a];
-    }
-    return tl;
-}
-
 // Builds the constraint side of a plan: the deconvolution tables, the kernel polynomials, the
 // constraints' fine cells and positions (from FP64), their tile order and the tiles' lists, and
 // the FFT plan. dq (point plans; may be null): a factor per constraint in the caller's order.
@@ -626,7 +608,7 @@ fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, con
     const int dim = g.dim;
     const int64_t nk = u->n_k;
     const int w = u->width;
-    u->tl = un_tiles(g);
+    u->tl = utiles_for(dim, g.nf);
     const UTiles &tl = u->tl;
     u->n_tiles = (int64_t)tl.nt[0] * tl.nt[1] * tl.nt[2];
     if (dim == 2)   // the window interpolation: a block per home tile (up to kUWinBlocks)
@@ -647,72 +629,14 @@ fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, con
             cell[(size_t)(q * dim + a)] = (int)ci;
             frac[(size_t)(q * dim + a)] = t - c;
         }
-    // first support cell (relative to the constraint's cell) as the kernels round it: in T
-    auto support_first = [&](double f) {
-        const T ft = (T)f;
-        return (int)std::ceil((double)(ft - (T)0.5 * (T)w));
-    };
-    // Reorders ids[0, n) by dealing them round-robin over the residues key(id) mod 32, so that
-    // consecutive ids (the lanes of a warp) have distinct residues wherever the range allows.
-    std::vector<int> by_key;
-    std::vector<int> keys;
-    auto deal_by_residue = [&](int *ids, int64_t n, auto &&key) {
-        if (n < 2) return;
-        int bucket[33] = {0};
-        keys.resize((size_t)n);
-        for (int64_t j = 0; j < n; ++j) {
-            keys[(size_t)j] = (int)(((key(ids[j]) % 32) + 32) % 32);
-            ++bucket[keys[(size_t)j] + 1];
-        }
-        for (int b = 0; b < 32; ++b) bucket[b + 1] += bucket[b];
-        int next[32];
-        for (int b = 0; b < 32; ++b) next[b] = bucket[b];
-        by_key.resize((size_t)n);
-        for (int64_t j = 0; j < n; ++j) by_key[(size_t)next[keys[(size_t)j]]++] = ids[j];
-        int64_t e = 0;
-        for (int r = 0; e < n; ++r)
-            for (int b = 0; b < 32; ++b)
-                if (bucket[b] + r < bucket[b + 1]) ids[e++] = by_key[(size_t)(bucket[b] + r)];
-    };
-    auto tile_box = [&](int64_t t, int o[3], int len[3]) {
-        const int tc[3] = {(int)(t % tl.nt[0]), (int)((t / tl.nt[0]) % tl.nt[1]),
-                           (int)(t / ((int64_t)tl.nt[0] * tl.nt[1]))};
-        for (int a = 0; a < 3; ++a) {
-            o[a] = tc[a] * tl.T[a];
-            len[a] = std::min(tl.T[a], g.nf[a] - o[a]);
-        }
-    };
-    // tile order: a stable counting sort by the tile that holds the constraint's cell (its home
-    // tile), then, in 2D, each home tile's constraints dealt over the shared-memory banks of
-    // their first window cell in the interpolation (window rows of len_0 + w cells starting at
-    // the tile's origin - floor(w / 2))
-    std::vector<int64_t> cnt((size_t)u->n_tiles + 1, 0);
-    std::vector<int64_t> home((size_t)nk);
-    for (int64_t q = 0; q < nk; ++q) {
-        int64_t t = 0;
-        for (int a = dim - 1; a >= 0; --a)
-            t = t * tl.nt[a] + cell[(size_t)(q * dim + a)] / tl.T[a];
-        home[(size_t)q] = t;
-        ++cnt[(size_t)t + 1];
-    }
-    for (int64_t t = 0; t < u->n_tiles; ++t) cnt[(size_t)t + 1] += cnt[(size_t)t];
-    std::vector<int64_t> hoff(cnt);
-    std::vector<int> perm((size_t)nk);
-    for (int64_t q = 0; q < nk; ++q) perm[(size_t)cnt[(size_t)home[(size_t)q]]++] = (int)q;
-    if (dim == 2)
-        for (int64_t t = 0; t < u->n_tiles; ++t) {
-            int o[3], len[3];
-            tile_box(t, o, len);
-            const int wl0 = len[0] + w;
-            deal_by_residue(&perm[(size_t)hoff[(size_t)t]], hoff[(size_t)t + 1] - hoff[(size_t)t],
-                            [&](int q) {
-                                const int x0 = cell[(size_t)q * 2] - o[0] + w / 2 +
-                                               support_first(frac[(size_t)q * 2]);
-                                const int y0 = cell[(size_t)q * 2 + 1] - o[1] + w / 2 +
-                                               support_first(frac[(size_t)q * 2 + 1]);
-                                return (int64_t)y0 * wl0 + x0;
-                            });
-        }
+    // tile order, the tiles' lists and their cover counts (fresco_uwnu_tiles.h)
+    UTilePlan tp;
+    if (!build_utile_plan<T>(dim, g.nf, w, tl, cell.data(), frac.data(), nk, tp))
+        return FRESCO_ERR_UNSUPPORTED;
+    u->n_ent = tp.n_ent;
+    const std::vector<int> &perm = tp.perm;
+    const std::vector<int64_t> &hoff = tp.hoff, &toff = tp.toff;
+    const std::vector<int> &ent = tp.ent, &kcov = tp.kcov;
     std::vector<int> scell((size_t)(nk * dim));
     std::vector<T> sfrac((size_t)(nk * dim)), s0((size_t)nk), wq((size_t)nk), sdq;
     if (dq) sdq.resize((size_t)nk);
@@ -725,91 +649,6 @@ fresco_status un_build(fresco_uwnu_s *u, const double *nu, const double *S0, con
         s0[(size_t)i] = (T)S0[q];
         wq[(size_t)i] = (T)W[q];
         if (dq) sdq[(size_t)i] = (T)dq[q];
-    }
-    // the tiles' lists. With the position f in [0, 1] (after rounding to T), the support's first
-    // cell is cell + ceil(f - w/2), so the support lies in [cell - floor(w/2), cell + w -
-    // floor(w/2)]; every tile that range meets (per axis, wrapped) lists the constraint, and the
-    // kernel clips the exact support to the tile.
-    // calls fn(tile) for every tile that lists constraint slot i
-    auto for_tiles = [&](int64_t i, auto &&fn) {
-        int ta[3][8], na[3];
-        for (int a = 0; a < 3; ++a) {
-            na[a] = 0;
-            if (a >= dim) {
-                ta[a][na[a]++] = 0;
-                continue;
-            }
-            const int c = scell[(size_t)(i * dim + a)];
-            for (int k = -(w / 2); k <= w - w / 2; ++k) {
-                int x = c + k;
-                x = x < 0 ? x + g.nf[a] : (x >= g.nf[a] ? x - g.nf[a] : x);
-                const int t = x / tl.T[a];
-                bool seen = false;
-                for (int j = 0; j < na[a]; ++j) seen |= ta[a][j] == t;
-                if (!seen && na[a] < 8) ta[a][na[a]++] = t;
-            }
-        }
-        for (int z = 0; z < na[2]; ++z)
-            for (int y = 0; y < na[1]; ++y)
-                for (int x = 0; x < na[0]; ++x)
-                    fn(((int64_t)ta[2][z] * tl.nt[1] + ta[1][y]) * tl.nt[0] + ta[0][x]);
-    };
-    std::fill(cnt.begin(), cnt.end(), 0);
-    for (int64_t i = 0; i < nk; ++i) for_tiles(i, [&](int64_t t) { ++cnt[(size_t)t + 1]; });
-    for (int64_t t = 0; t < u->n_tiles; ++t) cnt[(size_t)t + 1] += cnt[(size_t)t];
-    u->n_ent = cnt[(size_t)u->n_tiles];
-    if (u->n_ent >= (int64_t)1 << 31) return FRESCO_ERR_UNSUPPORTED;
-    std::vector<int64_t> toff(cnt);
-    std::vector<int> ent((size_t)std::max<int64_t>(u->n_ent, 1));
-    for (int64_t i = 0; i < nk; ++i)
-        for_tiles(i, [&](int64_t t) { ent[(size_t)cnt[(size_t)t]++] = (int)i; });
-    // Bank order inside each list. The spread's threads step through their supports in lockstep
-    // (row by row, the x offsets unrolled), so a thread's shared-memory bank at every step is its
-    // first cell's local address plus an offset common to the warp, modulo 32: each list is
-    // dealt over those residues.
-    for (int64_t t = 0; t < u->n_tiles; ++t) {
-        int o[3], len[3];
-        tile_box(t, o, len);
-        deal_by_residue(&ent[(size_t)toff[(size_t)t]], toff[(size_t)t + 1] - toff[(size_t)t],
-                        [&](int i) {
-                            int st[3] = {0, 0, 0};
-                            for (int a = 0; a < dim; ++a) {
-                                int d = scell[(size_t)i * dim + a] +
-                                        support_first((double)sfrac[(size_t)i * dim + a]) - o[a];
-                                if (d >= len[a]) d -= g.nf[a];
-                                else if (d + w <= 0) d += g.nf[a];
-                                st[a] = a == 0 ? d : std::max(d, 0);
-                            }
-                            return ((int64_t)st[2] * len[1] + st[1]) * len[0] + st[0];
-                        });
-    }
-    // the most supports that cover one cell of each tile (the spread's fixed-point headroom)
-    std::vector<int> kcov((size_t)u->n_tiles, 0);
-    {
-        std::vector<int> cov;
-        for (int64_t t = 0; t < u->n_tiles; ++t) {
-            if (toff[(size_t)t + 1] == toff[(size_t)t]) continue;
-            int o[3], len[3];
-            tile_box(t, o, len);
-            cov.assign((size_t)len[0] * len[1] * len[2], 0);
-            for (int64_t e = toff[(size_t)t]; e < toff[(size_t)t + 1]; ++e) {
-                const int64_t i = ent[(size_t)e];
-                int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
-                for (int a = 0; a < dim; ++a) {
-                    int d = scell[(size_t)i * dim + a] +
-                            support_first((double)sfrac[(size_t)i * dim + a]) - o[a];
-                    if (d >= len[a]) d -= g.nf[a];
-                    else if (d + w <= 0) d += g.nf[a];
-                    lo[a] = std::max(d, 0);
-                    hi[a] = std::min(d + w, len[a]);
-                }
-                for (int z = lo[2]; z < hi[2]; ++z)
-                    for (int y = lo[1]; y < hi[1]; ++y)
-                        for (int x = lo[0]; x < hi[0]; ++x)
-                            ++cov[((size_t)z * len[1] + y) * len[0] + x];
-            }
-            kcov[(size_t)t] = *std::max_element(cov.begin(), cov.end());
-        }
     }
 
     bool ok = un_alloc(u, (void **)&u->perm, sizeof(int) * (size_t)nk) &&

@@ -110,7 +110,7 @@ def test_smem_roofline_counts_w_to_the_d_operations_per_point():
 
 def test_uwnu_traffic_sources_and_constraint_bytes():
     assert bench.traffic_sources("uwnu") == ["fresco_internal.h", "fresco_kernels.cuh",
-                                             "fresco_uwnu.cu"]
+                                             "fresco_uwnu.cu", "fresco_uwnu_tiles.h"]
     h = bench._kernel_source_hash("uwnu")
     assert len(h) == 16 and h != bench._kernel_source_hash()
     # 2D FP32, 10 constraints, a 4 x 4 fine grid: interp reads the grid once (128 B) and per
