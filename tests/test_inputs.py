@@ -70,3 +70,29 @@ def test_peaked_target_is_centrosymmetric():
     for r, v in zip(m, s0):
         assert lut[tuple(-r)] == pytest.approx(v, rel=1e-12, abs=1e-300)
     assert s0.max() > 50
+
+
+def test_variant_workloads_follow_their_recipes():
+    """The NUwNU and UwNU bench workloads: seeded, sized and shaped as stated."""
+    fw = inputs.free_workload("quasicrystal2d_n1e6_k1e6_f32")
+    k = fw.wavevectors()
+    assert k.shape == (10**6, 2) and np.abs(np.linalg.norm(k, axis=1)).max() <= fw.kmax * (1 + 1e-12)
+    S0, W = fw.targets(k[:1000])
+    assert (W == 1).all() and (S0 >= 0).all() and S0.max() <= fw.n_points / fw.n_peaks * 1.01
+    np.testing.assert_array_equal(k[:5], fw.wavevectors()[:5])
+    fld = inputs.field_workload("hexfield2d_m1024_k1e6_f32")
+    c = fld.weights()
+    assert c.shape == (1024, 1024) and c.dtype == np.float32 and 0 <= c.min() and c.max() < 1
+    nu = fld.frequencies()
+    assert nu.shape == (10**6, 2) and np.linalg.norm(nu, axis=1).max() <= fld.nu_max * (1 + 1e-12)
+    # six peaks of height 10 on the ring |nu| = nu_max / 4, 60 degrees apart
+    r = 0.25 * fld.nu_max
+    ang = np.arange(6) * np.pi / 3
+    centres = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)
+    S0, W = fld.targets(centres)
+    assert (W == 1).all() and np.allclose(S0, 10.0, rtol=1e-6)
+    S0_far, _ = fld.targets(np.array([[0.0, 0.0], [fld.nu_max, 0.0]]))
+    assert S0_far.max() < 1e-100
+    np.testing.assert_array_equal(nu[:5], fld.frequencies()[:5])
+    with pytest.raises(KeyError):
+        inputs.field_workload("nope")
