@@ -431,7 +431,9 @@ fresco_status fresco_uwu_destroy(fresco_uwu_t u);
  * `stream`. At plan time the host orders the constraints by the tile of the fine grid that holds
  * them (32 x 32 cells in 2D, 16 x 8 x 8 in 3D, at most half of each axis) and lists for every
  * tile the constraints whose kernel support meets it: the interpolation runs in that order, and
- * the spread runs one block per tile, accumulating in shared memory and storing each cell once. */
+ * the spread runs one block per tile, accumulating in shared memory and storing each cell once.
+ * That host work grows as n_k w^d (the tiles' cover counts): about 0.5 s per 10^6 constraints at
+ * w = 7 in 2D. The tile lists hold fewer than 2^31 entries (FRESCO_ERR_UNSUPPORTED beyond). */
 typedef struct fresco_uwnu_s *fresco_uwnu_t;
 fresco_status fresco_uwnu_plan(fresco_uwnu_t *out, int dim, const int64_t *grid, int64_t n_k,
                                const double *nu, const double *S0, const double *W,
